@@ -1,0 +1,117 @@
+"""Exact, enumerative statement of the global Curveball Markov chain for tiny
+graphs (test helper; pure Python, no Philox, no keys).
+
+A state is a frozenset of edges (a, b) with a < b.  A single trade of u and v
+(Def. "Simple Undirected Trade", Section 3.2) keeps the common neighbours and
+the edge {u, v}, and gives u a uniformly random |A_{u-v}|-subset of the disjoint
+set D (Section 4: "draw |A_u n D| nodes from D for u uniformly at random").  A
+global trade (Def. "Undirected Global Trade", Section 3.3) draws a uniform
+permutation pi and applies the floor(n/2) trades {pi(2i-1), pi(2i)} in order.
+"""
+from fractions import Fraction
+from itertools import combinations, permutations
+from math import comb
+
+
+def adjacency(state, n):
+    adj = [set() for _ in range(n)]
+    for a, b in state:
+        adj[a].add(b)
+        adj[b].add(a)
+    return adj
+
+
+def trade_outcomes(state, n, u, v):
+    """{next_state: probability} of one uniform trade of u and v."""
+    adj = adjacency(state, n)
+    auv = adj[u] - adj[v] - {v}
+    avu = adj[v] - adj[u] - {u}
+    d = sorted(auv | avu)
+    a = len(auv)
+    rest = {e for e in state if u not in e and v not in e}
+    keep = {(min(u, x), max(u, x)) for x in adj[u] - auv} | {(min(v, x), max(v, x)) for x in adj[v] - avu}
+    out = {}
+    p = Fraction(1, comb(len(d), a))
+    for su in combinations(d, a):
+        su = set(su)
+        new = set(rest) | keep
+        new |= {(min(u, x), max(u, x)) for x in su}
+        new |= {(min(v, x), max(v, x)) for x in d if x not in su}
+        key = frozenset(new)
+        out[key] = out.get(key, 0) + p
+    return out
+
+
+def global_trade_outcomes(state, n, order):
+    """Distribution after the trades (order[2t], order[2t+1]), t = 0.. in sequence."""
+    dist = {state: Fraction(1)}
+    for t in range(n // 2):
+        u, v = order[2 * t], order[2 * t + 1]
+        nd = {}
+        for s, p in dist.items():
+            for s2, q in trade_outcomes(s, n, u, v).items():
+                nd[s2] = nd.get(s2, 0) + p * q
+        dist = nd
+    return dist
+
+
+def global_trade_row(state, n):
+    """Exact transition probabilities of one global trade from `state`."""
+    row = {}
+    perms = list(permutations(range(n)))
+    w = Fraction(1, len(perms))
+    for order in perms:
+        for s2, q in global_trade_outcomes(state, n, order).items():
+            row[s2] = row.get(s2, 0) + w * q
+    return row
+
+
+def single_trades_row(state, n, k):
+    """k successive single trades, each on a uniformly random unordered pair."""
+    pairs = list(combinations(range(n), 2))
+    dist = {state: Fraction(1)}
+    for _ in range(k):
+        nd = {}
+        for s, p in dist.items():
+            for (u, v) in pairs:
+                for s2, q in trade_outcomes(s, n, u, v).items():
+                    nd[s2] = nd.get(s2, 0) + p * q / len(pairs)
+        dist = nd
+    return dist
+
+
+def omega(degrees):
+    """All simple graphs on len(degrees) labelled nodes with this degree sequence."""
+    n = len(degrees)
+    cand = list(combinations(range(n), 2))
+    out = []
+
+    def rec(i, rem, chosen):
+        if i == len(cand):
+            if all(r == 0 for r in rem):
+                out.append(frozenset(chosen))
+            return
+        a, b = cand[i]
+        # prune: remaining capacity of a must be satisfiable by later pairs
+        if rem[a] > 0 and rem[b] > 0:
+            rem[a] -= 1; rem[b] -= 1
+            chosen.append((a, b))
+            rec(i + 1, rem, chosen)
+            chosen.pop()
+            rem[a] += 1; rem[b] += 1
+        # skip the pair only if a can still reach its degree with later pairs
+        later_a = sum(1 for (x, y) in cand[i + 1:] if a in (x, y))
+        if rem[a] <= later_a:
+            rec(i + 1, rem, chosen)
+
+    rec(0, list(degrees), [])
+    return out
+
+
+def to_csr(state, n):
+    import numpy as np
+    adj = adjacency(state, n)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(adj[x]) for x in range(n)])
+    col = np.array([y for x in range(n) for y in sorted(adj[x])], dtype=np.int32)
+    return rp, col
