@@ -1,0 +1,166 @@
+/*
+ * cb.h -- C ABI of the GB300 global Curveball library (libcb.so).
+ *
+ * The library randomises a simple undirected graph with the undirected global
+ * Curveball chain of Carstens, Hamann, Meyer, Penschuck, Tran and Wagner,
+ * "Parallel and I/O-efficient Randomisation of Massive Networks using Global
+ * Curveball Trades":
+ *   - Def. "Simple Undirected Trade" (Section 3.2, Fig. 2): nodes u and v keep
+ *     their common neighbours; their disjoint neighbours D are shuffled and
+ *     dealt back so that both degrees are kept;
+ *   - Def. "Undirected Global Trade" (Section 3.3): a random permutation pi
+ *     pairs the nodes into floor(n/2) trades applied in index order (one
+ *     "super step");
+ *   - Section 4: the algorithm draws each trade's shuffle itself.
+ * The result of every super step is bit-identical to applying the trades one
+ * after another in index order; how the permutation and shuffles are drawn
+ * from (seed, super-step index) is fixed below (see cb_global_trades).
+ *
+ * Conventions for every entry point:
+ *   - Sizes are 64-bit; node ids are int32 in [0, n); n <= 2^31 - 1; the
+ *     number of undirected edges m must be < 2^32 and every node's degree
+ *     < n.
+ *   - mem_kind says where a caller buffer lives: CB_HOST (pageable or pinned
+ *     host memory) or CB_DEVICE (device memory of the current CUDA device,
+ *     e.g. a torch tensor's data_ptr()).
+ *   - Return codes: CB_OK (0) or a negative CB_E* code.  Nothing aborts or
+ *     traps; after an error cb_last_error() describes it.  An error latched
+ *     by a device check (CB_ECHECK) makes later calls on the handle fail.
+ *   - One host thread at a time per handle.  Work is issued on the handle's
+ *     stream; calls that return data to the caller synchronise that stream.
+ */
+#ifndef CB_H
+#define CB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CB_OK 0
+#define CB_EINVAL (-1)   /* bad argument or graph not simple / not symmetric */
+#define CB_ENOMEM (-2)   /* device or host allocation failed */
+#define CB_ECUDA (-3)    /* a CUDA runtime call failed */
+#define CB_ECHECK (-5)   /* a device-side invariant check failed */
+#define CB_ESIZE (-6)    /* caller buffer too small (size reported) */
+#define CB_ERANGE (-7)   /* super-step counter would exceed 2^32 - 2 */
+
+#define CB_HOST 0
+#define CB_DEVICE 1
+
+typedef struct cb_graph* cb_handle;
+
+/*
+ * Create a randomisation state from a CSR adjacency.
+ *   n          number of nodes.
+ *   row_ptr    n+1 int64 offsets, row_ptr[0] = 0, non-decreasing.
+ *   col        row_ptr[n] int32 neighbour ids; every undirected edge {a,b}
+ *              appears as b in row a and as a in row b; no self loops, no
+ *              repeated neighbour (Section 2: simple graphs).  Rows need not
+ *              be sorted.
+ *   seed       64-bit seed of every random draw.
+ *   first_step index of the first super step (0 normally; k to continue a
+ *              chain exported after k super steps).
+ *   mem_kind   where row_ptr and col live (CB_HOST / CB_DEVICE).
+ *   cuda_stream a cudaStream_t to issue all work on, or NULL for a stream
+ *              owned by the handle.
+ *   out        receives the handle.
+ * The inputs are copied; the caller keeps ownership of its buffers.  Returns
+ * CB_EINVAL if the graph is not simple and symmetric.
+ */
+int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t seed,
+              uint64_t first_step, int mem_kind, void* cuda_stream, cb_handle* out);
+
+/*
+ * Run `supersteps` global trades (Def. "Undirected Global Trade").
+ * Super step g (g counts from first_step):
+ *   - permutation: node x gets key philox64(seed; x, 0, g, 0), nodes are
+ *     sorted by (key, x); trade t is (order[2t], order[2t+1]); for odd n the
+ *     node at the last position is not traded;
+ *   - shuffle of trade t: each disjoint neighbour is keyed by its edge to u or
+ *     v, identified by the positions lo < hi of the edge's endpoints at the
+ *     start of super step g: Philox4x32-10(seed; lo, hi, g, 1) = r0..r3, key
+ *     r0<<32|r1 if position lo belongs to trade t, else r2<<32|r3; D is
+ *     ordered by (key, lo, hi) and u receives the first |A_{u-v}| elements.
+ * philox64(...) = r0<<32 | r1 of Philox4x32-10 (Salmon et al., SC'11) with
+ * key words (low, high) 32 bits of the seed.  Asynchronous on the handle's
+ * stream except for a short host wait per super step while rare trade
+ * dependencies are resolved.  Returns CB_ERANGE if the step counter would pass
+ * 2^32 - 2.
+ */
+int cb_global_trades(cb_handle h, uint32_t supersteps);
+
+/*
+ * Export the current graph as its canonical edge list: m pairs [a, b] with
+ * a < b in lexicographic order (Section 2 "ordered edges"), written as 2m
+ * int32 values a0, b0, a1, b1, ... into `edges` (mem_kind says where).
+ * edges == NULL: only *m_out is set.  capacity_pairs < m: CB_ESIZE and *m_out
+ * is set.  Synchronises the handle's stream.
+ */
+int cb_export_edges(cb_handle h, int32_t* edges, int64_t capacity_pairs, int64_t* m_out,
+                    int mem_kind);
+
+/* Release every device buffer of the handle; NULL is ignored. */
+void cb_destroy(cb_handle h);
+
+/* Index of the next super step to run (first_step + super steps done). */
+int cb_step(cb_handle h, uint64_t* g);
+
+/* Wait for all work on the handle's stream; returns a latched device error. */
+int cb_sync(cb_handle h);
+
+/* Description of the last error on this handle ("" if none; NULL handle: global). */
+const char* cb_last_error(cb_handle h);
+
+/* Number of nodes and undirected edges. */
+int cb_info(cb_handle h, int64_t* n, int64_t* m);
+
+/*
+ * The permutation pi of super step g (Def. "Undirected Global Trade"):
+ * order_out[p] = node at position p (n int32, mem_kind says where).  Does not
+ * change the state.  Synchronises the handle's stream.
+ */
+int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
+
+/*
+ * Counters of the last cb_global_trades call, for tests and tuning:
+ * out[0] = dependency-resolution passes of the last super step,
+ * out[1] = trades deferred to a later pass (summed over its passes),
+ * out[2] = trades handled by the warp path, out[3] = by the block path,
+ * out[4] = trades whose workspace did not fit in shared memory,
+ * out[5] = kernel launches issued by the call.
+ * `count` = capacity of out; returns the number of counters written.
+ */
+int cb_stats(cb_handle h, int64_t* out, int count);
+
+/*
+ * Device time in milliseconds of the phases of the last cb_global_trades
+ * call, summed over its super steps, measured with CUDA events on the
+ * handle's stream while the "timing" option is on (zeros otherwise):
+ * ms[0] = permutation of the next step and its row offsets, ms[1] = the
+ * threshold phase (every trade's |A_{u-v}|-th smallest key, including the
+ * passes that resolve dependent trades), ms[2] = the rebuild phase (new rows
+ * for the next step), ms[3] = whole super steps.  Returns the number of
+ * values written (<= count).
+ */
+int cb_timings(cb_handle h, double* ms, int count);
+
+/*
+ * Tuning / test knobs (key, value); returns CB_EINVAL for an unknown key.
+ *   "warp_max"  largest trade size (deg u + deg v) on the warp path [256];
+ *               values are clamped to 32..256.
+ *   "smem_max"  largest trade size kept in shared memory on the block path;
+ *               larger trades use a global-memory workspace [4096]; 64..12288.
+ *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];
+ *               larger buckets take the global-memory fallback; 2..4096.
+ *   "timing"    1: record CUDA events around the phases of each super step
+ *               (adds one stream synchronisation per super step) [0].
+ */
+int cb_set_option(cb_handle h, const char* key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CB_H */

@@ -1,0 +1,122 @@
+// Internal state and helpers of libcb (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "cb.h"
+
+namespace cb {
+
+// Device-side error codes latched in Graph::err (first one wins).
+enum DevErr : int32_t {
+  kErrNone = 0,
+  kErrRowLength = 1,     // a rebuilt row does not match the degree
+  kErrRowSide = 2,       // entry written to the wrong row of a trade
+  kErrValidate = 3,      // input graph not simple / symmetric / in range
+  kErrBucket = 4,        // permutation bucket bookkeeping failed
+};
+
+constexpr int kWarpCapMax = 256;    // largest trade (deg u + deg v) on the warp path
+constexpr int kBlockThreads = 256;  // CTA size of the block path
+constexpr int kWarpsPerCta = 8;     // warps per CTA on the warp path
+
+struct Graph {
+  int64_t n = 0, nnz = 0, m = 0, T = 0, ntasks = 0;
+  uint64_t seed = 0, g = 0;
+  int64_t maxdeg = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, num_sms = 0;
+
+  // constant per graph
+  int32_t* deg_id = nullptr;      // degree by node id
+  int64_t* rp_id = nullptr;       // id-space row offsets (n+1)
+  // per super step (ping-pong index `cur`)
+  int cur = 0;
+  int32_t* order[2] = {nullptr, nullptr};  // node at each position
+  int64_t* rp[2] = {nullptr, nullptr};     // position-space row offsets (n+1)
+  int32_t* col[2] = {nullptr, nullptr};    // position-space rows, ascending
+  int32_t* pos_next = nullptr;             // position of each node id in step g+1
+  int32_t* M = nullptr;                    // step-g position -> step-(g+1) position
+  int32_t* deg_next = nullptr;             // degree by step-(g+1) position
+  uint8_t* stash = nullptr;                // per entry: bit0 own flip, bit1 in far trade's D
+  uint64_t* thr_key = nullptr;             // per trade: threshold key
+  uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)
+  uint32_t* done = nullptr;                // per trade: stamp g+1 once the threshold is published
+  int32_t* list_warp = nullptr;            // trades on the warp path
+  int32_t* list_block = nullptr;           // trades on the block path
+  int32_t* list_def[2] = {nullptr, nullptr};
+  int32_t* counters = nullptr;             // [0] warp list len, [1] block list len, [2..3] deferred
+  int32_t* err = nullptr;                  // latched device error
+  // workspaces
+  void* ws_global = nullptr;               // global workspace for trades too big for smem
+  size_t ws_slice = 0;                     // bytes per CTA slice
+  int ws_ctas = 0;                         // number of slices
+  void* sort_ws = nullptr;                 // permutation sort scratch
+  size_t sort_ws_bytes = 0;
+  void* scan_ws = nullptr;
+  size_t scan_ws_bytes = 0;
+  int32_t* host_counters = nullptr;        // pinned mirror of counters
+
+  // knobs
+  int warp_max = kWarpCapMax;
+  int smem_max = 4096;
+  int bucket_cap = 2048;
+
+  // stats of the last cb_global_trades
+  int64_t stats[8] = {0};
+  int64_t launches = 0;                    // kernel launches issued by this handle
+  bool timing = false;                     // record CUDA events around the phases
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double phase_ms[4] = {0, 0, 0, 0};       // permutation+prep, thresholds, rebuild, whole step
+  int latched = CB_OK;
+  std::string last_error;
+};
+
+inline int64_t next_pow2_host(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Records an error on the graph (or globally) and returns the code.
+int fail(Graph* g, int code, const std::string& msg);
+int cuda_fail(Graph* g, cudaError_t e, const char* what);
+
+#define CB_CUDA(g, call)                                        \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::cb::cuda_fail((g), e_, #call); \
+  } while (0)
+
+// ---- kernels / host launchers implemented in the .cu files ----
+// scan.cu
+size_t scan_ws_bytes(int64_t n);
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total
+cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, void* ws, cudaStream_t s,
+                               int64_t* launches = nullptr);
+
+// permute.cu
+size_t perm_ws_bytes(int64_t n);
+// order_out[p] = node at position p in super step g; pos_out[x] = position of x (may be null)
+int compute_permutation(Graph* h, uint64_t g, int32_t* order_out, int32_t* pos_out);
+// M, deg_next and rp[1-cur] for the step after the current one
+int prepare_next(Graph* h);
+
+// rows.cu
+// dst row q <- src row rowmap[q] with values mapped through valmap (identity if null), ascending
+int permute_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* src_col,
+                 const int32_t* rowmap, const int32_t* valmap, const int64_t* dst_rp, int32_t* dst_col);
+int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n);
+int check_row_offsets(Graph* h, const int64_t* rp, int64_t n);
+int invert_permutation(Graph* h, const int32_t* order, int32_t* pos);
+int export_pairs(Graph* h, const int64_t* rp, const int32_t* col, int32_t* pairs);
+
+// trade.cu
+int super_step(Graph* h);
+
+}  // namespace cb
+
+struct cb_graph : cb::Graph {};

@@ -1,0 +1,225 @@
+// The permutation pi of a super step (Def. "Undirected Global Trade"): node x
+// gets the key philox64(seed; x, 0, g, 0) and the nodes are ordered by
+// (key, x).  Sorting is MSD-bucketed: a histogram of the top B key bits, a
+// scatter of (key, x) into buckets, then one CTA sorts each bucket (about 512
+// entries, keys are uniform) in shared memory.  A bucket above the shared
+// memory cap is ranked by a slow global-memory fallback.
+#include "cb_internal.cuh"
+#include "philox.cuh"
+#include "team.cuh"
+
+namespace cb {
+namespace {
+
+constexpr int kPermThreads = 256;
+
+int bucket_bits(int64_t n) {
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= n) ++lg;
+  return lg > 9 ? lg - 9 : 0;
+}
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, int B) {
+  return B == 0 ? 0u : static_cast<uint32_t>(key >> (64 - B));
+}
+
+__global__ void k_perm_hist(int64_t n, uint64_t seed, uint32_t g, int B, int32_t* __restrict__ hist) {
+  extern __shared__ int32_t sh[];
+  const int nb = 1 << B;
+  const bool local = nb <= 4096;
+  if (local) {
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+  }
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t b = bucket_of(node_key(seed, static_cast<uint32_t>(x), g), B);
+    if (local) atomicAdd(&sh[b], 1); else atomicAdd(&hist[b], 1);
+  }
+  if (local) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+      if (sh[i]) atomicAdd(&hist[i], sh[i]);
+  }
+}
+
+__global__ void k_perm_scatter(int64_t n, uint64_t seed, uint32_t g, int B,
+                               const int64_t* __restrict__ boff, int32_t* __restrict__ cursor,
+                               uint64_t* __restrict__ bkey, int32_t* __restrict__ bid) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t k = node_key(seed, static_cast<uint32_t>(x), g);
+    const uint32_t b = bucket_of(k, B);
+    const int64_t slot = boff[b] + atomicAdd(&cursor[b], 1);
+    bkey[slot] = k;
+    bid[slot] = static_cast<int32_t>(x);
+  }
+}
+
+__device__ __forceinline__ bool pair_less(uint64_t ka, int32_t ia, uint64_t kb, int32_t ib) {
+  return ka < kb || (ka == kb && ia < ib);
+}
+
+// One CTA per bucket: bitonic sort of (key, id) pairs in shared memory.
+__global__ void __launch_bounds__(kPermThreads) k_bucket_sort(
+    int nb, const int64_t* __restrict__ boff, const uint64_t* __restrict__ bkey,
+    const int32_t* __restrict__ bid, int cap, int32_t* __restrict__ order,
+    int32_t* __restrict__ pos, int32_t* __restrict__ overflow, int cap_pow2) {
+  extern __shared__ uint64_t shk[];
+  int32_t* shi = reinterpret_cast<int32_t*>(shk + cap_pow2);   // padding up to cap_pow2 fits
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t o = boff[b];
+    const int64_t bs = boff[b + 1] - o;
+    const int s = static_cast<int>(bs < int64_t(cap) + 1 ? bs : int64_t(cap) + 1);
+    if (s > cap) {
+      if (threadIdx.x == 0) overflow[1 + atomicAdd(&overflow[0], 1)] = b;
+      continue;
+    }
+    if (s == 0) continue;
+    int P = 1;
+    while (P < s) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      shk[i] = i < s ? bkey[o + i] : ~0ull;
+      shi[i] = i < s ? bid[o + i] : 0x7fffffff;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const int l = i ^ j;
+          if (l > i) {
+            const uint64_t ka = shk[i], kb = shk[l];
+            const int32_t ia = shi[i], ib = shi[l];
+            const bool up = (i & k) == 0;
+            if (pair_less(kb, ib, ka, ia) == up) {
+              shk[i] = kb; shk[l] = ka; shi[i] = ib; shi[l] = ia;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < s; i += blockDim.x) {
+      order[o + i] = shi[i];
+      if (pos) pos[shi[i]] = static_cast<int32_t>(o + i);
+    }
+    __syncthreads();
+  }
+}
+
+// Fallback for buckets above the shared-memory cap: rank by counting.
+__global__ void k_bucket_overflow(const int32_t* __restrict__ overflow, const int64_t* __restrict__ boff,
+                                  const uint64_t* __restrict__ bkey, const int32_t* __restrict__ bid,
+                                  int32_t* __restrict__ order, int32_t* __restrict__ pos) {
+  const int cnt = overflow[0];
+  for (int q = blockIdx.x; q < cnt; q += gridDim.x) {
+    const int b = overflow[1 + q];
+    const int64_t o = boff[b], s = boff[b + 1] - o;
+    for (int64_t i = threadIdx.x; i < s; i += blockDim.x) {
+      const uint64_t ki = bkey[o + i];
+      const int32_t ii = bid[o + i];
+      int64_t r = 0;
+      for (int64_t j = 0; j < s; ++j) r += pair_less(bkey[o + j], bid[o + j], ki, ii) ? 1 : 0;
+      order[o + r] = ii;
+      if (pos) pos[ii] = static_cast<int32_t>(o + r);
+    }
+  }
+}
+
+__global__ void k_prep_next(int64_t n, const int32_t* __restrict__ order_cur, const int32_t* __restrict__ order_next,
+                            const int32_t* __restrict__ pos_next, const int32_t* __restrict__ deg_id,
+                            int32_t* __restrict__ M, int32_t* __restrict__ deg_next) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
+    M[p] = pos_next[order_cur[p]];
+    deg_next[p] = deg_id[order_next[p]];
+  }
+}
+
+struct PermWs {
+  int32_t* hist;      // nb
+  int32_t* cursor;    // nb
+  int64_t* boff;      // nb + 1
+  int32_t* overflow;  // nb + 1
+  uint64_t* bkey;     // n
+  int32_t* bid;       // n
+  void* scan;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+PermWs carve(void* base, int64_t n) {
+  const int64_t nb = int64_t(1) << bucket_bits(n);
+  char* p = static_cast<char*>(base);
+  PermWs w;
+  w.hist = reinterpret_cast<int32_t*>(p); p += align_up(sizeof(int32_t) * nb);
+  w.cursor = reinterpret_cast<int32_t*>(p); p += align_up(sizeof(int32_t) * nb);
+  w.boff = reinterpret_cast<int64_t*>(p); p += align_up(sizeof(int64_t) * (nb + 1));
+  w.overflow = reinterpret_cast<int32_t*>(p); p += align_up(sizeof(int32_t) * (nb + 1));
+  w.bkey = reinterpret_cast<uint64_t*>(p); p += align_up(sizeof(uint64_t) * n);
+  w.bid = reinterpret_cast<int32_t*>(p); p += align_up(sizeof(int32_t) * n);
+  w.scan = p;
+  return w;
+}
+
+unsigned grid_for(int64_t work, int threads, int num_sms) {
+  const int64_t want = (work + threads - 1) / threads;
+  const int64_t cap = int64_t(num_sms) * 16;
+  return static_cast<unsigned>(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+}  // namespace
+
+size_t perm_ws_bytes(int64_t n) {
+  const int64_t nb = int64_t(1) << bucket_bits(n);
+  return align_up(sizeof(int32_t) * nb) * 2 + align_up(sizeof(int64_t) * (nb + 1)) +
+         align_up(sizeof(int32_t) * (nb + 1)) + align_up(sizeof(uint64_t) * n) +
+         align_up(sizeof(int32_t) * n) + scan_ws_bytes(nb + 1) + 256;
+}
+
+int compute_permutation(Graph* h, uint64_t g, int32_t* order_out, int32_t* pos_out) {
+  const int64_t n = h->n;
+  if (n == 0) return CB_OK;
+  const int B = bucket_bits(n);
+  const int nb = 1 << B;
+  PermWs w = carve(h->sort_ws, n);
+  cudaStream_t s = h->stream;
+  CB_CUDA(h, cudaMemsetAsync(w.hist, 0, sizeof(int32_t) * nb, s));
+  CB_CUDA(h, cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * nb, s));
+  CB_CUDA(h, cudaMemsetAsync(w.overflow, 0, sizeof(int32_t), s));
+  const unsigned grid = grid_for(n, kPermThreads, h->num_sms);
+  const size_t hsm = nb <= 4096 ? sizeof(int32_t) * nb : 0;
+  k_perm_hist<<<grid, kPermThreads, hsm, s>>>(n, h->seed, static_cast<uint32_t>(g), B, w.hist);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  CB_CUDA(h, exclusive_scan_i32(w.hist, w.boff, nb, w.scan, s, &h->launches));
+  k_perm_scatter<<<grid, kPermThreads, 0, s>>>(n, h->seed, static_cast<uint32_t>(g), B, w.boff, w.cursor,
+                                               w.bkey, w.bid);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  const int cap = h->bucket_cap;
+  int cap_pow2 = 1;
+  while (cap_pow2 < cap) cap_pow2 <<= 1;
+  const size_t ssm = static_cast<size_t>(cap_pow2) * (sizeof(uint64_t) + sizeof(int32_t));
+  const unsigned sgrid = static_cast<unsigned>(nb < h->num_sms * 8 ? nb : h->num_sms * 8);
+  k_bucket_sort<<<sgrid, kPermThreads, ssm, s>>>(nb, w.boff, w.bkey, w.bid, cap, order_out, pos_out, w.overflow,
+                                                cap_pow2);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  k_bucket_overflow<<<64, kPermThreads, 0, s>>>(w.overflow, w.boff, w.bkey, w.bid, order_out, pos_out);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  return CB_OK;
+}
+
+int prepare_next(Graph* h) {
+  const int nxt = 1 - h->cur;
+  int rc = compute_permutation(h, h->g + 1, h->order[nxt], h->pos_next);
+  if (rc) return rc;
+  const unsigned grid = grid_for(h->n, kPermThreads, h->num_sms);
+  k_prep_next<<<grid, kPermThreads, 0, h->stream>>>(h->n, h->order[h->cur], h->order[nxt], h->pos_next,
+                                                    h->deg_id, h->M, h->deg_next);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  CB_CUDA(h, exclusive_scan_i32(h->deg_next, h->rp[nxt], h->n, h->scan_ws, h->stream, &h->launches));
+  return CB_OK;
+}
+
+}  // namespace cb

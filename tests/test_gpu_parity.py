@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact agreement is required: the super step is integer work with a fixed
+random stream (Def. "Undirected Global Trade", Section 3.3; Def. "Simple
+Undirected Trade", Section 3.2).  Small cases run the oracle live; the
+n=2^20 workload compares against stored per-step hashes written by
+tests/golden/make_goldens.py from the oracle.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1804_08487_gb300 import synth
+from paper_1804_08487_gb300.cb import CB_EINVAL, CB_ESIZE, CbError, Curveball
+from tests import exact
+from tests.helpers import (canonical_from_csr, check_simple_canonical, csr_from_edges, degrees,
+                           edge_hash)
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _csr(edges, n):
+    return exact.to_csr(frozenset((min(a, b), max(a, b)) for a, b in edges), n)
+
+
+def _run_pair(row_ptr, col, seed, steps, first_step=0, options=None, check_stats=None):
+    c = Curveball(row_ptr, col, seed, first_step)
+    for k, v in (options or {}).items():
+        c.set_option(k, v)
+    o = Oracle(row_ptr, col, seed, first_step)
+    n = len(row_ptr) - 1
+    assert np.array_equal(c.edges(), o.edges())
+    for step in range(steps):
+        c.global_trades(1)
+        o.superstep(1)
+        got, want = c.edges(), o.edges()
+        assert got.shape == want.shape
+        assert np.array_equal(got, want), f"mismatch after super step {first_step + step + 1}"
+        if len(got):
+            check_simple_canonical(got, n)
+        if check_stats:
+            check_stats(c.stats())
+    assert c.step == first_step + steps
+    return c
+
+
+def test_import_export_roundtrip():
+    g = synth.powerlaw_graph(3001, 3, 80, 2.0, 17)
+    c = Curveball(g.row_ptr, g.col, 5)
+    assert np.array_equal(c.edges(), canonical_from_csr(g.row_ptr, g.col))
+
+
+def test_unsorted_rows_accepted():
+    g = synth.powerlaw_graph(500, 3, 40, 2.0, 3)
+    col = g.col.copy()
+    rng = np.random.default_rng(0)
+    for x in range(500):
+        rng.shuffle(col[g.row_ptr[x]:g.row_ptr[x + 1]])
+    c = Curveball(g.row_ptr, col, 5)
+    assert np.array_equal(c.edges(), canonical_from_csr(g.row_ptr, g.col))
+
+
+@pytest.mark.parametrize("n,seed", [(4096, 42), (1001, 7), (1, 3), (2, 4)])
+def test_permutation_matches_oracle(n, seed):
+    g = synth.powerlaw_graph(n, 1 if n < 4 else 3, max(2, min(n, 50)), 2.0, seed) if n > 2 else None
+    if g is None:
+        rp, col = _csr([(0, 1)] if n == 2 else [], n)
+    else:
+        rp, col = g.row_ptr, g.col
+    c = Curveball(rp, col, seed)
+    o = Oracle(rp, col, seed)
+    for step in (0, 1, 2, 1000, 2**31):
+        assert np.array_equal(c.permutation(step), o.permutation(step).astype(np.int32))
+
+
+def test_plain_n4096_every_super_step():
+    """The n=4096 PLD([10,100),2) workload: 10 super steps, seed 42, bit-exact
+    after every super step, and equal to the stored oracle hashes."""
+    w = synth.PLAIN["n4096"]
+    g = w.graph()
+    with open(os.path.join(GOLDEN, "plain_n4096.json")) as f:
+        gold = json.load(f)
+    c = _run_pair(g.row_ptr, g.col, w.chain_seed, w.supersteps)
+    assert edge_hash(c.edges()) == gold["edge_sha256_after_step"][str(w.supersteps)]
+
+
+CASES = [
+    # n, a, b, gamma, seed, options
+    (64, 3, 20, 2.0, 5, {}),
+    (65, 2, 30, 2.0, 6, {}),
+    (300, 4, 100, 2.0, 7, {}),
+    (301, 4, 100, 2.5, 8, {}),
+    (2000, 10, 300, 2.0, 9, {}),
+    (2001, 10, 300, 2.0, 10, {"warp_max": 32}),       # most trades on the block path
+    (1500, 20, 400, 2.0, 11, {"smem_max": 64}),       # global-memory workspace
+    (777, 5, 200, 2.0, 12, {"bucket_cap": 2}),        # permutation sort fallback
+    (3000, 4, 1500, 2.0, 13, {}),                     # heavy tail: block-path hubs
+]
+
+
+@pytest.mark.parametrize("n,a,b,gamma,seed,opts", CASES)
+def test_random_graphs_every_super_step(n, a, b, gamma, seed, opts):
+    g = synth.powerlaw_graph(n, a, b, gamma, seed)
+    _run_pair(g.row_ptr, g.col, seed * 31 + 1, 4, options=opts)
+
+
+@pytest.mark.parametrize("n,a,b,seed", [(16, 5, 12, 1), (17, 6, 14, 2), (40, 10, 30, 3), (120, 20, 80, 4),
+                                        (400, 60, 300, 5)])
+def test_dense_graphs_resolve_dependencies(n, a, b, seed):
+    """Dense graphs have many trades that depend on an earlier one (blocks of
+    two or more edges); the result must still equal index-order processing."""
+    g = synth.powerlaw_graph(n, a, b, 2.0, seed)
+    seen = []
+    _run_pair(g.row_ptr, g.col, seed, 6, check_stats=lambda s: seen.append(s["passes"]))
+    _run_pair(g.row_ptr, g.col, seed + 100, 3, options={"warp_max": 32})
+
+
+def test_dependency_passes_happen():
+    g = synth.powerlaw_graph(400, 60, 300, 2.0, 5)
+    c = Curveball(g.row_ptr, g.col, 9)
+    c.set_option("warp_max", 32)
+    passes = []
+    for _ in range(5):
+        c.global_trades(1)
+        passes.append(c.stats()["passes"])
+    assert max(passes) > 1
+
+
+@pytest.mark.parametrize("name", ["single_edge", "empty", "isolated", "star", "complete", "two_stars",
+                                  "matching", "path_odd"])
+def test_edge_cases(name):
+    if name == "single_edge":
+        n, edges = 2, [(0, 1)]
+    elif name == "empty":
+        n, edges = 10, []
+    elif name == "isolated":
+        n, edges = 1, []
+    elif name == "star":
+        n, edges = 300, [(0, i) for i in range(1, 300)]
+    elif name == "complete":
+        n, edges = 9, [(i, j) for i in range(9) for j in range(i + 1, 9)]
+    elif name == "two_stars":
+        n, edges = 401, [(0, i) for i in range(2, 201)] + [(1, i) for i in range(201, 401)]
+    elif name == "matching":
+        n, edges = 4, [(0, 1), (2, 3)]
+    else:
+        n, edges = 11, [(i, i + 1) for i in range(10)]
+    rp, col = _csr(edges, n)
+    _run_pair(rp, col, 77, 5)
+
+
+def test_huge_star_uses_global_workspace():
+    n = 20000                      # max degree 19999: rows and trades above every shared-memory cap
+    edges = [(0, i) for i in range(1, n)] + [(i, i + 1) for i in range(1, n - 1, 2)]
+    rp, col = _csr(edges, n)
+    _run_pair(rp, col, 3, 2, check_stats=lambda s: None)
+
+
+def test_resume_from_export_and_determinism():
+    w = synth.PLAIN["n4096"]
+    g = w.graph()
+    a = Curveball(g.row_ptr, g.col, 42)
+    a.global_trades(10)
+    b = Curveball(g.row_ptr, g.col, 42)
+    b.global_trades(5)
+    rp, col = csr_from_edges(b.edges(), g.n)
+    c = Curveball(rp, col, 42, first_step=5)
+    c.global_trades(5)
+    assert np.array_equal(a.edges(), c.edges())
+    d = Curveball(g.row_ptr, g.col, 42)
+    d.global_trades(3)
+    d.global_trades(7)
+    assert np.array_equal(a.edges(), d.edges())
+
+
+def test_invariants_hold_over_many_steps():
+    g = synth.powerlaw_graph(5000, 5, 500, 2.0, 21)
+    deg0 = np.diff(g.row_ptr)
+    c = Curveball(g.row_ptr, g.col, 1234)
+    for _ in range(10):
+        c.global_trades(3)
+        e = c.edges()
+        check_simple_canonical(e, 5000)
+        assert (degrees(e, 5000) == deg0).all()
+
+
+def test_rejects_invalid_graphs():
+    rp, col = _csr([(0, 1), (1, 2)], 3)
+    bad_sym = col.copy()
+    bad_sym[0] = 2                     # row 0 lists 2, row 2 does not list 0
+    with pytest.raises(CbError) as e:
+        Curveball(rp, bad_sym, 1)
+    assert e.value.code == CB_EINVAL
+    loop_rp = np.array([0, 1, 1], dtype=np.int64)
+    with pytest.raises(CbError):
+        Curveball(loop_rp, np.array([0], dtype=np.int32), 1)  # self loop
+    dup_rp = np.array([0, 2, 4], dtype=np.int64)
+    with pytest.raises(CbError):
+        Curveball(dup_rp, np.array([1, 1, 0, 0], dtype=np.int32), 1)  # multi-edge
+    with pytest.raises(CbError):
+        Curveball(np.array([0, 1, 2], dtype=np.int64), np.array([5, 0], dtype=np.int32), 1)  # out of range
+
+
+def test_export_capacity_checked():
+    import ctypes
+    from paper_1804_08487_gb300 import cb as cbmod
+    rp, col = _csr([(0, 1), (1, 2)], 3)
+    c = Curveball(rp, col, 1)
+    m = ctypes.c_int64(0)
+    buf = np.zeros(2, dtype=np.int32)
+    rc = cbmod.load().cb_export_edges(c.h, buf.ctypes.data, 1, ctypes.byref(m), cbmod.CB_HOST)
+    assert rc == CB_ESIZE and m.value == 2
+
+
+def test_device_buffers_via_torch():
+    torch = pytest.importorskip("torch")
+    g = synth.powerlaw_graph(2000, 5, 100, 2.0, 8)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    stream = torch.cuda.Stream()
+    c = Curveball(rp, col, 99, stream=stream)
+    c.global_trades(3)
+    out = torch.zeros(2 * g.m, dtype=torch.int32, device="cuda")
+    c.edges(out)
+    o = Oracle(g.row_ptr, g.col, 99)
+    o.superstep(3)
+    assert np.array_equal(out.cpu().numpy().reshape(-1, 2), o.edges())
+
+
+def test_plain_n2p20_matches_stored_oracle_hashes():
+    """n=2^20 PLD([10,1000),2), seed 7, 20 super steps: every step equals the
+    oracle (stored hashes), and the generator reproduces the stored graph."""
+    path = os.path.join(GOLDEN, "plain_n2p20.json")
+    if not os.path.exists(path):
+        pytest.skip("golden file not generated")
+    with open(path) as f:
+        gold = json.load(f)
+    w = synth.PLAIN["n2^20"]
+    g = w.graph()
+    import hashlib
+    gh = hashlib.sha256(g.row_ptr.astype("<i8").tobytes() + g.col.astype("<i4").tobytes()).hexdigest()
+    assert gh == gold["graph_sha256"]
+    c = Curveball(g.row_ptr, g.col, w.chain_seed)
+    for step in range(1, w.supersteps + 1):
+        c.global_trades(1)
+        if str(step) in gold["edge_sha256_after_step"]:
+            assert edge_hash(c.edges()) == gold["edge_sha256_after_step"][str(step)], step
