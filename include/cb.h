@@ -147,11 +147,14 @@ int cb_stats(cb_handle h, int64_t* out, int count);
 int cb_timings(cb_handle h, double* ms, int count);
 
 /*
- * Tuning / test knobs (key, value); returns CB_EINVAL for an unknown key.
- *   "warp_max"  largest trade size (deg u + deg v) on the warp path [256];
- *               values are clamped to 32..256.
- *   "smem_max"  largest trade size kept in shared memory on the block path;
- *               larger trades use a global-memory workspace [4096]; 64..12288.
+ * Tuning / test knobs (key, value); returns CB_EINVAL for an unknown key or a
+ * value out of range.  Trade size = deg u + deg v.
+ *   "warp_max"  trades up to this size run on one warp [128]; 0..128.
+ *   "block_max" trades up to this size run on a 256-thread CTA [2048];
+ *               0..2048 (values below warp_max act as warp_max).
+ *   "smem_max"  larger trades run on a 1024-thread CTA and keep up to this
+ *               many entries in shared memory, more in a global-memory
+ *               workspace [8192]; 64..8192.
  *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];
  *               larger buckets take the global-memory fallback; 2..4096.
  *   "timing"    1: record CUDA events around the phases of each super step

@@ -46,8 +46,9 @@ void release(Graph* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
-                  h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->done, h->list_warp,
-                  h->list_block, h->list_def[0], h->list_def[1], h->counters, h->err, h->ws_global,
+                  h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
+                  h->list[0], h->list[1], h->list[2], h->list_def[0][0], h->list_def[0][1], h->list_def[0][2],
+                  h->list_def[1][0], h->list_def[1][1], h->list_def[1][2], h->counters, h->err, h->ws_global,
                   h->sort_ws, h->scan_ws};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -153,7 +154,7 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
   cudaStream_t s = h->stream;
   int rc;
   if (dalloc(&h->rp_id, n + 1) || dalloc(&h->deg_id, n) || dalloc(&h->col[0], nnz) || dalloc(&h->col[1], nnz) ||
-      dalloc(&h->err, 8) || dalloc(&h->counters, 8) || cudaMallocHost(&h->host_counters, 8 * sizeof(int32_t)))
+      dalloc(&h->err, 8) || dalloc(&h->counters, 16) || cudaMallocHost(&h->host_counters, 16 * sizeof(int32_t)))
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
   CB_CUDA(h, cudaMemsetAsync(h->err, 0, 8 * sizeof(int32_t), s));
   CB_CUDA(h, cudaMemcpyAsync(h->rp_id, row_ptr, sizeof(int64_t) * (n + 1), kind, s));
@@ -178,8 +179,11 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
   if (dalloc(&h->order[0], n) || dalloc(&h->order[1], n) || dalloc(&h->rp[0], n + 1) || dalloc(&h->rp[1], n + 1) ||
       dalloc(&h->pos_next, n) || dalloc(&h->M, n) || dalloc(&h->deg_next, n) || dalloc(&h->stash, nnz) ||
       dalloc(&h->thr_key, h->ntasks) || dalloc(&h->thr_tb, h->ntasks) || dalloc(&h->done, h->ntasks) ||
-      dalloc(&h->list_warp, h->ntasks) || dalloc(&h->list_block, h->ntasks) ||
-      dalloc(&h->list_def[0], h->ntasks) || dalloc(&h->list_def[1], h->ntasks) ||
+      dalloc(&h->thr_top, h->ntasks) || dalloc(&h->list[0], h->ntasks) || dalloc(&h->list[1], h->ntasks) ||
+      dalloc(&h->list[2], h->ntasks) || dalloc(&h->list_def[0][0], h->ntasks) ||
+      dalloc(&h->list_def[0][1], h->ntasks) || dalloc(&h->list_def[0][2], h->ntasks) ||
+      dalloc(&h->list_def[1][0], h->ntasks) || dalloc(&h->list_def[1][1], h->ntasks) ||
+      dalloc(&h->list_def[1][2], h->ntasks) ||
       cudaMalloc(&h->sort_ws, h->sort_ws_bytes) || cudaMalloc(&h->scan_ws, h->scan_ws_bytes))
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
@@ -299,11 +303,17 @@ int cb_timings(cb_handle h, double* ms, int count) {
 int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!h || !key) return fail(h, CB_EINVAL, "bad argument");
   if (!std::strcmp(key, "warp_max")) {
-    h->warp_max = static_cast<int>(std::min<int64_t>(std::max<int64_t>(value, 32), kWarpCapMax));
+    if (value < 0 || value > kWarpCapMax) return fail(h, CB_EINVAL, "warp_max out of range [0, 128]");
+    h->warp_max = static_cast<int>(value);
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "block_max")) {
+    if (value < 0 || value > kBlockMaxCap) return fail(h, CB_EINVAL, "block_max out of range [0, 2048]");
+    h->block_max = static_cast<int>(value);
     return CB_OK;
   }
   if (!std::strcmp(key, "smem_max")) {
-    if (value < 64 || value > 12288) return fail(h, CB_EINVAL, "smem_max out of range [64, 12288]");
+    if (value < 64 || value > kSmemMaxCap) return fail(h, CB_EINVAL, "smem_max out of range [64, 8192]");
     h->smem_max = static_cast<int>(value);
     return size_trade_workspace(h);
   }

@@ -18,7 +18,9 @@ enum DevErr : int32_t {
   kErrBucket = 4,        // permutation bucket bookkeeping failed
 };
 
-constexpr int kWarpCapMax = 256;    // largest trade (deg u + deg v) on the warp path
+constexpr int kWarpCapMax = 128;    // largest trade (deg u + deg v) on the warp path
+constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
+constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
 constexpr int kWarpsPerCta = 8;     // warps per CTA on the warp path
 
@@ -43,12 +45,12 @@ struct Graph {
   int32_t* deg_next = nullptr;             // degree by step-(g+1) position
   uint8_t* stash = nullptr;                // per entry: bit0 own flip, bit1 in far trade's D
   uint64_t* thr_key = nullptr;             // per trade: threshold key
+  uint8_t* thr_top = nullptr;              // per trade: top 6 bits of the threshold key
   uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)
   uint32_t* done = nullptr;                // per trade: stamp g+1 once the threshold is published
-  int32_t* list_warp = nullptr;            // trades on the warp path
-  int32_t* list_block = nullptr;           // trades on the block path
-  int32_t* list_def[2] = {nullptr, nullptr};
-  int32_t* counters = nullptr;             // [0] warp list len, [1] block list len, [2..3] deferred
+  int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (warp, 256, 1024 threads)
+  int32_t* list_def[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // deferred, ping-pong
+  int32_t* counters = nullptr;             // list lengths, deferred counts, global-slice count (12)
   int32_t* err = nullptr;                  // latched device error
   // workspaces
   void* ws_global = nullptr;               // global workspace for trades too big for smem
@@ -62,7 +64,8 @@ struct Graph {
 
   // knobs
   int warp_max = kWarpCapMax;
-  int smem_max = 4096;
+  int block_max = kBlockMaxCap;
+  int smem_max = kSmemMaxCap;
   int bucket_cap = 2048;
 
   // stats of the last cb_global_trades
