@@ -127,7 +127,7 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
  * Counters of the last cb_global_trades call, for tests and tuning:
  * out[0] = dependency-resolution passes of the last super step,
  * out[1] = trades deferred to a later pass (summed over its passes),
- * out[2] = trades handled by the warp path, out[3] = by the block path,
+ * out[2] = trades on the tile path, out[3] = on the 256- and 1024-thread paths,
  * out[4] = trades whose workspace did not fit in shared memory,
  * out[5] = kernel launches issued by the call.
  * `count` = capacity of out; returns the number of counters written.
@@ -149,9 +149,10 @@ int cb_timings(cb_handle h, double* ms, int count);
 /*
  * Tuning / test knobs (key, value); returns CB_EINVAL for an unknown key or a
  * value out of range.  Trade size = deg u + deg v.
- *   "warp_max"  trades up to this size run on one warp [128]; 0..128.
+ *   "tile_max"  trades up to this size run on the flat tile path (one
+ *               thread per entry, many trades per CTA) [128]; 0..128.
  *   "block_max" trades up to this size run on a 256-thread CTA [2048];
- *               0..2048 (values below warp_max act as warp_max).
+ *               0..2048 (values below tile_max act as tile_max).
  *   "smem_max"  larger trades run on a 1024-thread CTA and keep up to this
  *               many entries in shared memory, more in a global-memory
  *               workspace [8192]; 64..8192.

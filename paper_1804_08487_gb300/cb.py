@@ -170,7 +170,7 @@ def cb_permutation(h, g: int):
 def cb_stats(h):
     out = (C.c_int64 * 8)()
     k = _check(load().cb_stats(h, out, 8), h)
-    names = ["passes", "deferred", "warp_trades", "block_trades", "global_ws_trades", "launches"]
+    names = ["passes", "deferred", "tile_trades", "block_trades", "global_ws_trades", "launches"]
     return {names[i]: out[i] for i in range(k)}
 
 

@@ -18,11 +18,10 @@ enum DevErr : int32_t {
   kErrBucket = 4,        // permutation bucket bookkeeping failed
 };
 
-constexpr int kWarpCapMax = 128;    // largest trade (deg u + deg v) on the warp path
+constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
 constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
-constexpr int kWarpsPerCta = 8;     // warps per CTA on the warp path
 
 struct Graph {
   int64_t n = 0, nnz = 0, m = 0, T = 0, ntasks = 0;
@@ -48,9 +47,12 @@ struct Graph {
   uint8_t* thr_top = nullptr;              // per trade: top 6 bits of the threshold key
   uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)
   uint32_t* done = nullptr;                // per trade: stamp g+1 once the threshold is published
-  int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (warp, 256, 1024 threads)
-  int32_t* list_def[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // deferred, ping-pong
-  int32_t* counters = nullptr;             // list lengths, deferred counts, global-slice count (12)
+  int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (tile, 256, 1024 threads), index order
+  int64_t* tile_off = nullptr;             // per tile-class trade: prefix of its weight max(L, 4)
+  int32_t* cls_flag = nullptr;             // 4 x ntasks scratch: class flags and tile weights
+  int64_t* cls_scan = nullptr;             // 4 x (ntasks+1) scratch: their exclusive scans
+  int32_t* list_def[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // deferred trades (256 / 1024 path), ping-pong
+  int64_t* counters = nullptr;             // list lengths, tile weight, deferred counts, global slices (16)
   int32_t* err = nullptr;                  // latched device error
   // workspaces
   void* ws_global = nullptr;               // global workspace for trades too big for smem
@@ -60,10 +62,10 @@ struct Graph {
   size_t sort_ws_bytes = 0;
   void* scan_ws = nullptr;
   size_t scan_ws_bytes = 0;
-  int32_t* host_counters = nullptr;        // pinned mirror of counters
+  int64_t* host_counters = nullptr;        // pinned mirror of counters
 
   // knobs
-  int warp_max = kWarpCapMax;
+  int tile_max = kTileMaxCap;
   int block_max = kBlockMaxCap;
   int smem_max = kSmemMaxCap;
   int bucket_cap = 2048;

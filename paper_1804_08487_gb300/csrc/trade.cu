@@ -27,9 +27,12 @@
 //     threshold (six-bit prefix first, the full key only on a prefix tie), and
 //     positions are mapped to step g+1.
 //
-// Trades of at most `warp_max` entries run on one warp, up to `block_max` on a
-// 256-thread CTA, larger ones on a 1024-thread CTA with up to `smem_max`
-// entries in shared memory (a global-memory slice above that).
+// Trades of at most `tile_max` entries run on the flat tile path: a CTA takes
+// a run of consecutive small trades (about 1024 entries) with one thread per
+// entry and loops over each trade's own entries in shared memory.  Trades up
+// to `block_max` entries run one per 256-thread CTA, larger ones one per
+// 1024-thread CTA with up to `smem_max` entries in shared memory (a
+// global-memory slice above that).
 #include <algorithm>
 
 #include "cb_internal.cuh"
@@ -50,7 +53,10 @@ constexpr uint8_t kUV = 8;      // the edge {u_t, v_t}
 // row, bit1 in v's row, bit2 the u-row entry flips, bit3 the v-row entry flips
 constexpr int kMedThreads = 256;
 constexpr int kBigThreads = 1024;
-constexpr int kWarpCapA = kWarpCapMax;   // entries per warp-path trade (static shared memory)
+constexpr int kTileThreads = 256;
+constexpr int kTileCap = 1024;                       // weight units per tile (weight = max(L, 4))
+constexpr int kTileTrades = kTileCap / 4;            // so at most 256 trades per tile
+constexpr int kTileSlots = kTileCap + kTileMaxCap;   // a trade may start just before the cap
 
 struct StepCtx {
   int64_t n, T;
@@ -68,8 +74,8 @@ struct StepCtx {
   const int64_t* rp_next;
   int32_t* col_next;
   int32_t* def_out;
-  int32_t* def_count;
-  int32_t* gws_count;
+  unsigned long long* def_count;
+  unsigned long long* gws_count;
 };
 
 struct SelOut {
@@ -253,25 +259,33 @@ __device__ void radix_digit(Team& tm, const WsA& w, int L, int shift, uint32_t p
 }
 
 // k-th smallest (1-based) (key, lo, hi) over D: two radix digits on the stored
-// 16-bit key prefixes, then the full keys of the remaining candidates.
+// 16-bit key prefixes, then the full keys of the few remaining candidates.
 template <class Team>
 __device__ void select_kth(Team& tm, const StepCtx& c, const WsA& w, int L, int64_t t, int k, SelOut* out) {
   const int64_t t2 = 2 * t;
   radix_digit(tm, w, L, 8, 0, k, out);
   const uint32_t b1 = static_cast<uint32_t>(out->bin);
   int kk = k - out->below;
-  const int cnt1 = out->cnt;
+  int cnt = out->cnt;
   tm.sync();
   uint32_t prefix = b1 << 8;
   bool full16 = false;
-  if (cnt1 > 1) {
+  if (cnt > 1) {
     radix_digit(tm, w, L, 0, b1, kk, out);
     prefix |= static_cast<uint32_t>(out->bin);
     kk -= out->below;
+    cnt = out->cnt;
     tm.sync();
     full16 = true;
   }
-  // candidates share the prefix; rank them by the full (key, lo, hi)
+  constexpr int kCand = 32;   // candidates ranked in shared memory (the histogram's space)
+  uint64_t* ck = reinterpret_cast<uint64_t*>(w.hist);
+  uint64_t* ctb = ck + kCand;
+  int* ncand = reinterpret_cast<int*>(ctb + kCand);
+  if (cnt > 1 && cnt <= kCand) {
+    if (tm.rank == 0) *ncand = 0;
+    tm.sync();
+  }
   for (int i = tm.rank; i < L; i += Team::N) {
     const uint8_t m = w.meta[i];
     if (!(m & kInD)) continue;
@@ -279,22 +293,42 @@ __device__ void select_kth(Team& tm, const StepCtx& c, const WsA& w, int L, int6
     if (full16 ? (tp != prefix) : ((tp >> 8) != b1)) continue;
     const uint32_t lo = lo_of(t2, m, w.y[i]), hi = hi_of(t2, m, w.y[i]);
     const uint64_t ki = own_key(c, t, lo, hi), tbi = tie_break(lo, hi);
-    int r = 0;
-    for (int j = 0; j < L; ++j) {
-      const uint8_t mj = w.meta[j];
-      if (j == i || !(mj & kInD)) continue;
-      const uint32_t tj = w.top[j];
-      if (full16 ? (tj != prefix) : ((tj >> 8) != b1)) continue;
-      const uint32_t loj = lo_of(t2, mj, w.y[j]), hij = hi_of(t2, mj, w.y[j]);
-      const uint64_t kj = own_key(c, t, loj, hij);
-      r += (kj < ki || (kj == ki && tie_break(loj, hij) < tbi));
-    }
-    if (r == kk - 1) {
+    if (cnt == 1) {            // the only element with this prefix
       out->key = ki;
       out->tb = tbi;
+    } else if (cnt <= kCand) {
+      const int q = atomicAdd(ncand, 1);
+      ck[q] = ki;
+      ctb[q] = tbi;
+    } else {                   // many equal prefixes: rank against every other candidate
+      int r = 0;
+      for (int j = 0; j < L; ++j) {
+        const uint8_t mj = w.meta[j];
+        if (j == i || !(mj & kInD)) continue;
+        const uint32_t tj = w.top[j];
+        if (full16 ? (tj != prefix) : ((tj >> 8) != b1)) continue;
+        const uint32_t loj = lo_of(t2, mj, w.y[j]), hij = hi_of(t2, mj, w.y[j]);
+        const uint64_t kj = own_key(c, t, loj, hij);
+        r += (kj < ki || (kj == ki && tie_break(loj, hij) < tbi));
+      }
+      if (r == kk - 1) {
+        out->key = ki;
+        out->tb = tbi;
+      }
     }
   }
   tm.sync();
+  if (cnt > 1 && cnt <= kCand) {
+    for (int q = tm.rank; q < cnt; q += Team::N) {
+      int r = 0;
+      for (int j = 0; j < cnt; ++j) r += (ck[j] < ck[q] || (ck[j] == ck[q] && ctb[j] < ctb[q]));
+      if (r == kk - 1) {
+        out->key = ck[q];
+        out->tb = ctb[q];
+      }
+    }
+    tm.sync();
+  }
 }
 
 // Phase A for trade t.
@@ -371,7 +405,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     w.meta[i] = m;
   }
   if (tm.any(defer)) {
-    if (tm.rank == 0) c.def_out[atomicAdd(c.def_count, 1)] = static_cast<int32_t>(t);
+    if (tm.rank == 0) c.def_out[atomicAdd(c.def_count, 1ull)] = static_cast<int32_t>(t);
     tm.sync();
     return;
   }
@@ -505,46 +539,383 @@ __device__ void phase_b(Team& tm, const StepCtx& c, int64_t t) {
   if (tm.rank == 0 && base0 != du) latch(c.err, kErrRowSide);
 }
 
-// ---------------------------------------------------------------- kernels
+// ---------------------------------------------------------- classification
 
-__global__ void k_classify(StepCtx c, int64_t ntasks, int warp_max, int block_max, int32_t* __restrict__ lw,
-                           int32_t* __restrict__ lm, int32_t* __restrict__ lb, int32_t* __restrict__ counters) {
+// Class of each trade (tile / 256 / 1024 threads) and its tile weight.
+__global__ void k_class_flags(StepCtx c, int64_t ntasks, int tile_max, int block_max, int32_t* __restrict__ f) {
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
     const TradeRows tr = trade_rows(c, t);
     const int L = tr.du + tr.dv;
-    if (L <= warp_max) lw[atomicAdd(&counters[0], 1)] = static_cast<int32_t>(t);
-    else if (L <= block_max) lm[atomicAdd(&counters[1], 1)] = static_cast<int32_t>(t);
-    else lb[atomicAdd(&counters[2], 1)] = static_cast<int32_t>(t);
+    const int cls = L <= tile_max ? 0 : (L <= block_max ? 1 : 2);
+    f[t] = cls == 0;
+    f[ntasks + t] = cls == 1;
+    f[2 * ntasks + t] = cls == 2;
+    f[3 * ntasks + t] = cls == 0 ? max(L, kTileCap / kTileTrades) : 0;
   }
 }
 
-struct WarpWsA {
-  unsigned long long hash[2 * kWarpCapA];
-  uint32_t hist[256];
-  int32_t y[kWarpCapA];
-  uint16_t top[kWarpCapA];
-  uint8_t meta[kWarpCapA];
-  uint8_t far[kWarpCapA];
-  SelOut sel;
+// Stable compaction of each class into index order, plus tile offsets.
+__global__ void k_class_scatter(int64_t ntasks, const int32_t* __restrict__ f, const int64_t* __restrict__ sc,
+                                int32_t* __restrict__ l0, int32_t* __restrict__ l1, int32_t* __restrict__ l2,
+                                int64_t* __restrict__ tile_off) {
+  const int64_t n1 = ntasks + 1;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
+    if (f[t]) {
+      const int64_t k = sc[t];
+      l0[k] = static_cast<int32_t>(t);
+      tile_off[k] = sc[3 * n1 + t];
+    } else if (f[ntasks + t]) {
+      l1[sc[n1 + t]] = static_cast<int32_t>(t);
+    } else {
+      l2[sc[2 * n1 + t]] = static_cast<int32_t>(t);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- tile path
+
+struct TileShared {
+  uint64_t key[kTileSlots];     // full own key of each element of D
+  int32_t y[kTileSlots];        // entries; in phase B the mapped output position
+  uint8_t meta[kTileSlots];
+  uint8_t far[kTileSlots];
+  uint8_t owner[kTileSlots];    // local trade index, 255 = padding slot
+  int64_t b0[kTileTrades];
+  int32_t t[kTileTrades];
+  int32_t acnt[kTileTrades];    // |A_{u-v}| (phase A) / u's entries placed (phase B)
+  int32_t flags[kTileTrades];   // bit0 deferred, bit1 has a dependent later trade
+  int16_t du[kTileTrades], dv[kTileTrades], lofs[kTileTrades];
+  int64_t ou[kTileTrades], ov[kTileTrades];
+  int32_t scan[kTileThreads / 32 + 2];
+  int64_t first, base;
+  int32_t ntr, nslots;
 };
 
-__global__ void __launch_bounds__(256) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ list,
-                                                      const int32_t* __restrict__ count) {
-  __shared__ WarpWsA ws[kWarpsPerCta];
-  WarpTeam tm;
-  const int wid = threadIdx.x >> 5;
-  const int64_t len = *count;
-  for (int64_t q = blockIdx.x * int64_t(kWarpsPerCta) + wid; q < len; q += int64_t(gridDim.x) * kWarpsPerCta) {
-    const int64_t t = list[q];
+__device__ __forceinline__ int tile_owner(const TileShared& sh, int e) {
+  int lo = 0, hi = sh.ntr;   // last local trade with lofs <= e
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (sh.lofs[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Set up tile `tile`: its trades and entries (y) in shared memory.  Returns
+// false when the tile is empty.
+__device__ bool tile_setup(const StepCtx& c, TileShared& sh, const int32_t* list, const int64_t* tile_off,
+                           int64_t ntrades, int64_t total_w, int64_t tile, bool load_stash) {
+  if (threadIdx.x == 0) {
+    const int64_t lo = tile * kTileCap, hi = lo + kTileCap;
+    const int64_t a = lower_bound(tile_off, static_cast<int>(ntrades), lo);
+    const int64_t b = lower_bound(tile_off, static_cast<int>(ntrades), hi);
+    sh.first = a;
+    sh.ntr = static_cast<int32_t>(b - a);
+    sh.base = a < ntrades ? tile_off[a] : 0;
+    sh.nslots = static_cast<int32_t>((b < ntrades ? tile_off[b] : total_w) - sh.base);
+  }
+  __syncthreads();
+  if (sh.ntr == 0) return false;
+  for (int j = threadIdx.x; j < sh.ntr; j += blockDim.x) {
+    const int64_t k = sh.first + j;
+    const int32_t t = list[k];
     const TradeRows tr = trade_rows(c, t);
-    WsA w{ws[wid].y, ws[wid].top, ws[wid].meta, ws[wid].far, ws[wid].hash, ws[wid].hist, hash_lg(tr.du + tr.dv)};
-    phase_a(tm, c, t, w, &ws[wid].sel);
+    sh.t[j] = t;
+    sh.b0[j] = tr.b0;
+    sh.du[j] = static_cast<int16_t>(tr.du);
+    sh.dv[j] = static_cast<int16_t>(tr.dv);
+    sh.lofs[j] = static_cast<int16_t>(tile_off[k] - sh.base);
+    sh.acnt[j] = 0;
+    sh.flags[j] = 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < sh.nslots; e += blockDim.x) {
+    const int k = tile_owner(sh, e);
+    const int i = e - sh.lofs[k];
+    if (i < sh.du[k] + sh.dv[k]) {
+      sh.owner[e] = static_cast<uint8_t>(k);
+      sh.y[e] = __ldcg(c.col + sh.b0[k] + i);
+      if (load_stash) sh.meta[e] = c.stash[sh.b0[k] + i];
+    } else {
+      sh.owner[e] = 255;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const int32_t* __restrict__ list,
+                                                               const int64_t* __restrict__ tile_off,
+                                                               const int64_t* __restrict__ counts) {
+  __shared__ TileShared sh;
+  const int64_t ntrades = counts[0], total_w = counts[3];
+  const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (!tile_setup(c, sh, list, tile_off, ntrades, total_w, tile, false)) continue;
+    const int E = sh.nslots;
+    // block analysis, dependencies, keys
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = sh.owner[e];
+      if (k == 255) continue;
+      const int64_t t = sh.t[k], t2 = 2 * t;
+      const int lo0 = sh.lofs[k], du = sh.du[k], L = du + sh.dv[k];
+      const int r = (e - lo0) >= du;
+      const int32_t yy = sh.y[e];
+      const int64_t s = yy >> 1;
+      const bool single = (t2 + 1 >= c.n);
+      sh.far[e] = 0;
+      if (s == t) {
+        sh.meta[e] = static_cast<uint8_t>(r | kUV);
+        continue;
+      }
+      int bits = 0;   // presence of (row, column) in the block with trade s
+      for (int j = lo0; j < lo0 + L; ++j) {
+        const int32_t yj = sh.y[j];
+        if ((yj >> 1) == s) bits |= 1 << (2 * ((j - lo0) >= du) + (yj & 1));
+      }
+      const int u0 = bits & 1, u1 = (bits >> 1) & 1, v0 = (bits >> 2) & 1, v1 = (bits >> 3) & 1;
+      const int cu = u0 + u1, cv = v0 + v1;
+      uint8_t m = static_cast<uint8_t>(r | (u0 << 4) | (u1 << 5) | (v0 << 6) | (v1 << 7));
+      if (!single && s > t && s < c.T && cu + cv >= 2 && (u0 + v0 == 1 || u1 + v1 == 1))
+        atomicOr(&sh.flags[k], 2);
+      int col_now = yy & 1;
+      int other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
+      if (!single && s < t && (cu + cv >= 2) && (cu == 1 || cv == 1)) {
+        if (ld_acquire(c.done + s) != c.stamp) {
+          atomicOr(&sh.flags[k], 1);
+          continue;
+        }
+        int m1[2][2] = {{0, 0}, {0, 0}};
+        const int bb[2][2] = {{u0, u1}, {v0, v1}};
+        const int cnt_row[2] = {cu, cv};
+#pragma unroll
+        for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+          for (int gam = 0; gam < 2; ++gam) {
+            if (!bb[rho][gam]) continue;
+            int g2 = gam;
+            if (cnt_row[rho] == 1) {
+              const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(2 * s + gam);
+              g2 = far_keeps_low(c, s, min(x, y), max(x, y)) ? 0 : 1;
+            }
+            m1[rho][g2] = 1;
+            if (rho == r && gam == (yy & 1)) col_now = g2;
+          }
+        other = m1[1 - r][col_now];
+      }
+      const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
+      const uint32_t lo = min(x, y), hi = max(x, y);
+      const EdgeKeys ek = edge_keys(c.seed, lo, hi, c.g);
+      const bool lo_mine = (lo >> 1) == static_cast<uint32_t>(t);
+      sh.key[e] = lo_mine ? ek.lo_side : ek.hi_side;
+      sh.far[e] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
+      if (!other && !single) {
+        m |= kInD;
+        if (r == 0) atomicAdd(&sh.acnt[k], 1);
+      }
+      sh.meta[e] = m;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x)
+      if (sh.flags[k] & 1) c.def_out[atomicAdd(c.def_count, 1ull)] = sh.t[k];
+    // rank each element of D within its trade by (key, lo, hi); u keeps ranks < a
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = sh.owner[e];
+      if (k == 255 || (sh.flags[k] & 1)) continue;
+      const uint8_t m = sh.meta[e];
+      if (!(m & kInD)) continue;
+      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
+      const int lo0 = sh.lofs[k], L = sh.du[k] + sh.dv[k];
+      const uint64_t ki = sh.key[e];
+      int rank = 0;
+      for (int j = lo0; j < lo0 + L; ++j) {
+        if (!(sh.meta[j] & kInD)) continue;
+        const uint64_t kj = sh.key[j];
+        if (kj < ki) {
+          ++rank;
+        } else if (kj == ki && j != e) {
+          rank += tie_break(lo_of(t2, sh.meta[j], sh.y[j]), hi_of(t2, sh.meta[j], sh.y[j])) <
+                  tie_break(lo_of(t2, m, sh.y[e]), hi_of(t2, m, sh.y[e]));
+        }
+      }
+      const int a = sh.acnt[k];
+      const int r = m & kR;
+      if ((rank < a ? 0 : 1) != r) sh.meta[e] = m | kFlip;
+      if (rank == a - 1) {   // the threshold element publishes its trade's threshold
+        const int32_t t = sh.t[k];
+        c.thr_key[t] = ki;
+        c.thr_tb[t] = tie_break(lo_of(t2, m, sh.y[e]), hi_of(t2, m, sh.y[e]));
+        c.thr_top[t] = static_cast<uint8_t>(ki >> 58);
+        if (sh.flags[k] & 2) {
+          __threadfence();
+          st_release(c.done + t, c.stamp);
+        }
+      }
+    }
+    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
+      const int32_t t = sh.t[k];
+      if ((sh.flags[k] & 1) || sh.acnt[k] != 0 || 2 * int64_t(t) + 1 >= c.n) continue;
+      c.thr_key[t] = 0;   // a = 0: u keeps nothing
+      c.thr_tb[t] = 0;
+      c.thr_top[t] = 0;
+      if (sh.flags[k] & 2) {
+        __threadfence();
+        st_release(c.done + t, c.stamp);
+      }
+    }
+    __syncthreads();
+    // will the far trade consider this edge?  Write the stash byte.
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = sh.owner[e];
+      if (k == 255 || (sh.flags[k] & 1)) continue;
+      const uint8_t m = sh.meta[e];
+      const int f = (m & kFlip) ? 1 : 0;
+      int in_far = 0;
+      const int64_t t = sh.t[k];
+      if (!(m & kUV)) {
+        const int r = m & kR;
+        const int32_t yy = sh.y[e];
+        const int64_t s = yy >> 1;
+        const int u0 = (m >> 4) & 1, u1 = (m >> 5) & 1, v0 = (m >> 6) & 1, v1 = (m >> 7) & 1;
+        const int cr = r ? (v0 + v1) : (u0 + u1);
+        if (2 * t + 1 >= c.n || s < t) {
+          in_far = (cr == 1);
+        } else if (s < c.T) {
+          if (u0 + u1 + v0 + v1 == 1) {
+            in_far = 1;
+          } else {   // block after t's own decisions
+            const int lo0 = sh.lofs[k], du = sh.du[k], L = du + sh.dv[k];
+            const int myrow = r ^ f;
+            int same = 0;
+            for (int j = lo0; j < lo0 + L; ++j) {
+              if ((sh.y[j] >> 1) != s) continue;
+              const int rj = (j - lo0) >= du, fj = (sh.meta[j] & kFlip) ? 1 : 0;
+              same += ((rj ^ fj) == myrow);
+            }
+            in_far = (same == 1);
+          }
+        }
+      }
+      const int i = e - sh.lofs[k];
+      c.stash[sh.b0[k] + i] = static_cast<uint8_t>(f | (in_far << 1) | (in_far ? (sh.far[e] << 2) : 0));
+    }
+    __syncthreads();
   }
 }
+
+// Exclusive prefix sum over sh.nslots values v(e) held in `val` (uint8), in
+// place into `out` (int32); 256 threads, each over a contiguous chunk.
+__device__ void tile_scan(TileShared& sh, const uint8_t* val, int32_t* out, int E) {
+  const int per = (E + kTileThreads - 1) / kTileThreads;
+  const int b = threadIdx.x * per;
+  int local = 0;
+  for (int j = 0; j < per; ++j)
+    if (b + j < E) local += val[b + j];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh.scan[w] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int tv = threadIdx.x < kTileThreads / 32 ? sh.scan[threadIdx.x] : 0;
+    int sv = tv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, sv, o);
+      if (threadIdx.x >= o) sv += y;
+    }
+    if (threadIdx.x < kTileThreads / 32) sh.scan[threadIdx.x] = sv - tv;
+  }
+  __syncthreads();
+  int run = x - local + sh.scan[w];
+  for (int j = 0; j < per; ++j)
+    if (b + j < E) {
+      out[b + j] = run;
+      run += val[b + j];
+    }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const int32_t* __restrict__ list,
+                                                               const int64_t* __restrict__ tile_off,
+                                                               const int64_t* __restrict__ counts) {
+  __shared__ TileShared sh;
+  const int64_t ntrades = counts[0], total_w = counts[3];
+  const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (!tile_setup(c, sh, list, tile_off, ntrades, total_w, tile, true)) continue;
+    const int E = sh.nslots;
+    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
+      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
+      const int32_t pu = c.M[t2];
+      sh.ou[k] = c.rp_next[pu];
+      bool bad = c.rp_next[pu + 1] - sh.ou[k] != sh.du[k];
+      sh.ov[k] = 0;
+      if (sh.dv[k] > 0) {
+        const int32_t pv = c.M[t2 + 1];
+        sh.ov[k] = c.rp_next[pv];
+        bad |= c.rp_next[pv + 1] - sh.ov[k] != sh.dv[k];
+      }
+      if (bad) latch(c.err, kErrRowLength);
+    }
+    // side and far end of every entry; far[] marks entries going to u's new row
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = sh.owner[e];
+      sh.far[e] = 0;
+      if (k == 255) continue;
+      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
+      const int r = (e - sh.lofs[k]) >= sh.du[k];
+      const int32_t yy = sh.y[e];
+      const uint8_t st = sh.meta[e];
+      const int r2 = r ^ (st & 1);
+      int32_t y2 = yy;
+      if (st & 2) {
+        const int64_t s = yy >> 1;
+        const uint32_t ft = st >> 2, tt = c.thr_top[s];
+        bool low;
+        if (ft != tt) {
+          low = ft < tt;
+        } else {
+          const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
+          low = far_keeps_low(c, s, min(x, y), max(x, y));
+        }
+        y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
+      }
+      sh.y[e] = c.M[y2];
+      sh.far[e] = static_cast<uint8_t>(r2 == 0);
+      sh.meta[e] = static_cast<uint8_t>(r2);
+    }
+    __syncthreads();
+    int32_t* pre = reinterpret_cast<int32_t*>(sh.key);   // keys are not used in phase B
+    tile_scan(sh, sh.far, pre, E);
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = sh.owner[e];
+      if (k == 255) continue;
+      const int lo0 = sh.lofs[k];
+      const int before0 = pre[e] - pre[lo0];
+      if (sh.meta[e] == 0) {
+        c.col_next[sh.ou[k] + before0] = sh.y[e];
+      } else {
+        c.col_next[sh.ov[k] + (e - lo0 - before0)] = sh.y[e];
+      }
+      const int L = sh.du[k] + sh.dv[k];
+      if (e == lo0 + L - 1) {   // last entry of the trade: u's row must be exactly full
+        const int n0 = before0 + (sh.meta[e] == 0);
+        if (n0 != sh.du[k]) latch(c.err, kErrRowSide);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- team paths
 
 template <int NT>
 __global__ void __launch_bounds__(NT) k_phase_a_block(StepCtx c, const int32_t* __restrict__ list,
-                                                      const int32_t* __restrict__ count, int smem_max, char* gws,
+                                                      const int64_t* __restrict__ count, int smem_max, char* gws,
                                                       size_t slice) {
   extern __shared__ __align__(16) char sbuf[];
   __shared__ int64_t red[NT / 32 + 2];
@@ -558,24 +929,15 @@ __global__ void __launch_bounds__(NT) k_phase_a_block(StepCtx c, const int32_t* 
     char* base = sbuf;
     if (L > smem_max) {
       base = gws + slice * blockIdx.x;
-      if (threadIdx.x == 0) atomicAdd(c.gws_count, 1);
+      if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
     }
     phase_a(tm, c, t, carve_a(base, L), &sel);
   }
 }
 
-__global__ void __launch_bounds__(256) k_phase_b_warp(StepCtx c, const int32_t* __restrict__ list,
-                                                      const int32_t* __restrict__ count) {
-  WarpTeam tm;
-  const int wid = threadIdx.x >> 5;
-  const int64_t len = *count;
-  for (int64_t q = blockIdx.x * int64_t(kWarpsPerCta) + wid; q < len; q += int64_t(gridDim.x) * kWarpsPerCta)
-    phase_b(tm, c, list[q]);
-}
-
 template <int NT>
 __global__ void __launch_bounds__(NT) k_phase_b_block(StepCtx c, const int32_t* __restrict__ list,
-                                                      const int32_t* __restrict__ count) {
+                                                      const int64_t* __restrict__ count) {
   __shared__ int64_t red[NT / 32 + 2];
   BlockTeam<NT> tm(red);
   const int64_t len = *count;
@@ -614,23 +976,37 @@ int super_step(Graph* h) {
   c.M = h->M;
   c.rp_next = h->rp[nxt];
   c.col_next = h->col[nxt];
-  int32_t* cnt = h->counters;   // [0..2] class lists, [3..8] deferred (ping-pong x class), [9] global slices
-  c.gws_count = cnt + 9;
-  CB_CUDA(h, cudaMemsetAsync(cnt, 0, 12 * sizeof(int32_t), s));
+  // counters: [0..2] class list lengths, [3] tile weight total, [4+2p+q] deferred
+  // list q (0: 256-thread, 1: 1024-thread) of ping-pong side p, [8] global slices
+  int64_t* cnt = h->counters;
+  unsigned long long* ucnt = reinterpret_cast<unsigned long long*>(cnt);
+  c.gws_count = ucnt + 8;
+  CB_CUDA(h, cudaMemsetAsync(cnt, 0, 16 * sizeof(int64_t), s));
   const int64_t ntasks = h->ntasks;
   if (ntasks == 0) {
     h->cur = nxt;
     h->g += 1;
     return CB_OK;
   }
-  const int warp_max = std::min(h->warp_max, kWarpCapA);
-  const int block_max = std::max(h->block_max, warp_max);
-  {
-    const int64_t want = (ntasks + 255) / 256;
-    const unsigned grid = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(want, h->num_sms * 8)));
-    k_classify<<<grid, 256, 0, s>>>(c, ntasks, warp_max, block_max, h->list[0], h->list[1], h->list[2], cnt);
+  const int tile_max = std::min(h->tile_max, kTileMaxCap);
+  const int block_max = std::max(h->block_max, tile_max);
+  auto grid_n = [&](int64_t work) {
+    return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, h->num_sms * 8)));
+  };
+  {  // classes in index order (stable compaction) and tile offsets
+    k_class_flags<<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, tile_max, block_max, h->cls_flag);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
+    const int64_t n1 = ntasks + 1;
+    for (int q = 0; q < 4; ++q)
+      CB_CUDA(h, exclusive_scan_i32(h->cls_flag + q * ntasks, h->cls_scan + q * n1, ntasks, h->scan_ws, s,
+                                    &h->launches));
+    k_class_scatter<<<grid_n(ntasks), 256, 0, s>>>(ntasks, h->cls_flag, h->cls_scan, h->list[0], h->list[1],
+                                                    h->list[2], h->tile_off);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    for (int q = 0; q < 4; ++q)
+      CB_CUDA(h, cudaMemcpyAsync(cnt + q, h->cls_scan + q * n1 + ntasks, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   }
   const size_t med_smem = ws_a_bytes(std::max(block_max, 1));
   const size_t big_smem = ws_a_bytes(std::max(h->smem_max, 1));
@@ -638,59 +1014,61 @@ int super_step(Graph* h) {
                                   static_cast<int>(med_smem)));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(big_smem)));
-  const unsigned wgrid = static_cast<unsigned>(h->num_sms * 6);
+  const unsigned tgrid = static_cast<unsigned>(h->num_sms * 8);
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
   char* gws = static_cast<char*>(h->ws_global);
-
-  // phase A: one launch per class over its list, then passes over deferred trades
-  auto launch_a = [&](const int32_t* const* lists, const int32_t* counts, int out) -> int {
-    for (int k = 0; k < 3; ++k) {
-      c.def_out = h->list_def[out][k];
-      c.def_count = cnt + 3 + 3 * out + k;
-      if (k == 0) {
-        k_phase_a_warp<<<wgrid, 256, 0, s>>>(c, lists[0], counts + 0);
-      } else if (k == 1) {
-        k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem, s>>>(c, lists[1], counts + 1, block_max, gws,
-                                                                         h->ws_slice);
-      } else {
-        k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, lists[2], counts + 2, h->smem_max, gws,
-                                                                         h->ws_slice);
-      }
-      CB_CUDA(h, cudaGetLastError());
-      ++h->launches;
-    }
+  auto launch_med = [&](const int32_t* list, const int64_t* count, int out) -> int {
+    c.def_out = h->list_def[out][0];
+    c.def_count = ucnt + 4 + 2 * out;
+    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem, s>>>(c, list, count, block_max, gws, h->ws_slice);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
     return CB_OK;
   };
-  const int32_t* first[3] = {h->list[0], h->list[1], h->list[2]};
-  if ((rc = launch_a(first, cnt, 0))) return rc;
+  auto launch_big = [&](const int32_t* list, const int64_t* count, int out) -> int {
+    c.def_out = h->list_def[out][1];
+    c.def_count = ucnt + 5 + 2 * out;
+    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, list, count, h->smem_max, gws, h->ws_slice);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    return CB_OK;
+  };
+  // phase A, first pass: tile path (deferred trades go to the 256-thread list), then the team paths
+  c.def_out = h->list_def[0][0];
+  c.def_count = ucnt + 4;
+  k_phase_a_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  if ((rc = launch_med(h->list[1], cnt + 1, 0))) return rc;
+  if ((rc = launch_big(h->list[2], cnt + 2, 0))) return rc;
   int64_t passes = 1, deferred_total = 0;
   int in = 0;
   for (;;) {
-    CB_CUDA(h, cudaMemcpyAsync(h->host_counters, cnt, 12 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(h, cudaMemcpyAsync(h->host_counters, cnt, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CB_CUDA(h, cudaStreamSynchronize(s));
-    const int32_t* hc = h->host_counters;
+    const int64_t* hc = h->host_counters;
     if (passes == 1) {
       h->stats[2] = hc[0];
       h->stats[3] = hc[1] + hc[2];
     }
-    const int64_t ndef = int64_t(hc[3 + 3 * in]) + hc[4 + 3 * in] + hc[5 + 3 * in];
+    const int64_t ndef = hc[4 + 2 * in] + hc[5 + 2 * in];
     if (ndef == 0) break;
     deferred_total += ndef;
     if (passes > 100000) return fail(h, CB_ECHECK, "dependency resolution did not converge");
     const int out = 1 - in;
-    CB_CUDA(h, cudaMemsetAsync(cnt + 3 + 3 * out, 0, 3 * sizeof(int32_t), s));
-    const int32_t* lists[3] = {h->list_def[in][0], h->list_def[in][1], h->list_def[in][2]};
-    if ((rc = launch_a(lists, cnt + 3 + 3 * in, out))) return rc;
+    CB_CUDA(h, cudaMemsetAsync(cnt + 4 + 2 * out, 0, 2 * sizeof(int64_t), s));
+    if ((rc = launch_med(h->list_def[in][0], cnt + 4 + 2 * in, out))) return rc;
+    if ((rc = launch_big(h->list_def[in][1], cnt + 5 + 2 * in, out))) return rc;
     in = out;
     ++passes;
   }
   h->stats[0] = passes;
   h->stats[1] = deferred_total;
-  h->stats[4] = h->host_counters[9];
+  h->stats[4] = h->host_counters[8];
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
   // phase B
-  k_phase_b_warp<<<wgrid, 256, 0, s>>>(c, h->list[0], cnt + 0);
+  k_phase_b_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   k_phase_b_block<kMedThreads><<<mgrid, kMedThreads, 0, s>>>(c, h->list[1], cnt + 1);

@@ -95,9 +95,9 @@ CASES = [
     (300, 4, 100, 2.0, 7, {}),
     (301, 4, 100, 2.5, 8, {}),
     (2000, 10, 300, 2.0, 9, {}),
-    (2001, 10, 300, 2.0, 10, {"warp_max": 32}),       # most trades on the 256-thread path
+    (2001, 10, 300, 2.0, 10, {"tile_max": 32}),       # most trades on the 256-thread path
     (1500, 20, 400, 2.0, 11, {"block_max": 0, "smem_max": 64}),   # global-memory workspace
-    (1200, 10, 300, 2.0, 14, {"warp_max": 0, "block_max": 0}),    # everything on the 1024-thread path
+    (1200, 10, 300, 2.0, 14, {"tile_max": 0, "block_max": 0}),    # everything on the 1024-thread path
     (777, 5, 200, 2.0, 12, {"bucket_cap": 2}),        # permutation sort fallback
     (3000, 4, 1500, 2.0, 13, {}),                     # heavy tail: block-path hubs
 ]
@@ -117,14 +117,14 @@ def test_dense_graphs_resolve_dependencies(n, a, b, seed):
     g = synth.powerlaw_graph(n, a, b, 2.0, seed)
     seen = []
     _run_pair(g.row_ptr, g.col, seed, 6, check_stats=lambda s: seen.append(s["passes"]))
-    _run_pair(g.row_ptr, g.col, seed + 100, 3, options={"warp_max": 32})
-    _run_pair(g.row_ptr, g.col, seed + 200, 3, options={"warp_max": 0, "block_max": 0, "smem_max": 64})
+    _run_pair(g.row_ptr, g.col, seed + 100, 3, options={"tile_max": 32})
+    _run_pair(g.row_ptr, g.col, seed + 200, 3, options={"tile_max": 0, "block_max": 0, "smem_max": 64})
 
 
 def test_dependency_passes_happen():
     g = synth.powerlaw_graph(400, 60, 300, 2.0, 5)
     c = Curveball(g.row_ptr, g.col, 9)
-    c.set_option("warp_max", 32)
+    c.set_option("tile_max", 32)
     passes = []
     for _ in range(5):
         c.global_trades(1)
