@@ -307,6 +307,11 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     h->tile_max = static_cast<int>(value);
     return CB_OK;
   }
+  if (!std::strcmp(key, "tile_paths")) {
+    if (value < 0 || value > 3) return fail(h, CB_EINVAL, "tile_paths out of range [0, 3]");
+    h->tile_paths = static_cast<int>(value);
+    return CB_OK;
+  }
   if (!std::strcmp(key, "block_max")) {
     if (value < 0 || value > kBlockMaxCap) return fail(h, CB_EINVAL, "block_max out of range [0, 2048]");
     h->block_max = static_cast<int>(value);

@@ -57,6 +57,7 @@ constexpr int kTileThreads = 256;
 constexpr int kTileCap = 1024;                       // weight units per tile (weight = max(L, 4))
 constexpr int kTileTrades = kTileCap / 4;            // so at most 256 trades per tile
 constexpr int kTileSlots = kTileCap + kTileMaxCap;   // a trade may start just before the cap
+constexpr int kNoOwner = 0xFFFF;
 
 struct StepCtx {
   int64_t n, T;
@@ -579,7 +580,7 @@ struct TileShared {
   int32_t y[kTileSlots];        // entries; in phase B the mapped output position
   uint8_t meta[kTileSlots];
   uint8_t far[kTileSlots];
-  uint8_t owner[kTileSlots];    // local trade index, 255 = padding slot
+  uint16_t owner[kTileSlots];   // local trade index (< 256), kNoOwner = padding slot
   int64_t b0[kTileTrades];
   int32_t t[kTileTrades];
   int32_t acnt[kTileTrades];    // |A_{u-v}| (phase A) / u's entries placed (phase B)
@@ -632,11 +633,11 @@ __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const int32_t* list
     const int k = tile_owner(sh, e);
     const int i = e - sh.lofs[k];
     if (i < sh.du[k] + sh.dv[k]) {
-      sh.owner[e] = static_cast<uint8_t>(k);
+      sh.owner[e] = static_cast<uint16_t>(k);
       sh.y[e] = __ldcg(c.col + sh.b0[k] + i);
       if (load_stash) sh.meta[e] = c.stash[sh.b0[k] + i];
     } else {
-      sh.owner[e] = 255;
+      sh.owner[e] = kNoOwner;
     }
   }
   __syncthreads();
@@ -655,7 +656,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
     // block analysis, dependencies, keys
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
       const int k = sh.owner[e];
-      if (k == 255) continue;
+      if (k == kNoOwner) continue;
       const int64_t t = sh.t[k], t2 = 2 * t;
       const int lo0 = sh.lofs[k], du = sh.du[k], L = du + sh.dv[k];
       const int r = (e - lo0) >= du;
@@ -720,7 +721,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
     // rank each element of D within its trade by (key, lo, hi); u keeps ranks < a
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
       const int k = sh.owner[e];
-      if (k == 255 || (sh.flags[k] & 1)) continue;
+      if (k == kNoOwner || (sh.flags[k] & 1)) continue;
       const uint8_t m = sh.meta[e];
       if (!(m & kInD)) continue;
       const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
@@ -766,7 +767,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
     // will the far trade consider this edge?  Write the stash byte.
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
       const int k = sh.owner[e];
-      if (k == 255 || (sh.flags[k] & 1)) continue;
+      if (k == kNoOwner || (sh.flags[k] & 1)) continue;
       const uint8_t m = sh.meta[e];
       const int f = (m & kFlip) ? 1 : 0;
       int in_far = 0;
@@ -865,7 +866,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
       const int k = sh.owner[e];
       sh.far[e] = 0;
-      if (k == 255) continue;
+      if (k == kNoOwner) continue;
       const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
       const int r = (e - sh.lofs[k]) >= sh.du[k];
       const int32_t yy = sh.y[e];
@@ -893,7 +894,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
     tile_scan(sh, sh.far, pre, E);
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
       const int k = sh.owner[e];
-      if (k == 255) continue;
+      if (k == kNoOwner) continue;
       const int lo0 = sh.lofs[k];
       const int before0 = pre[e] - pre[lo0];
       if (sh.meta[e] == 0) {
@@ -1037,9 +1038,13 @@ int super_step(Graph* h) {
   // phase A, first pass: tile path (deferred trades go to the 256-thread list), then the team paths
   c.def_out = h->list_def[0][0];
   c.def_count = ucnt + 4;
-  k_phase_a_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
+  if (h->tile_paths & 1) {
+    k_phase_a_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+  } else if ((rc = launch_med(h->list[0], cnt + 0, 0))) {
+    return rc;
+  }
   if ((rc = launch_med(h->list[1], cnt + 1, 0))) return rc;
   if ((rc = launch_big(h->list[2], cnt + 2, 0))) return rc;
   int64_t passes = 1, deferred_total = 0;
@@ -1068,7 +1073,11 @@ int super_step(Graph* h) {
   h->stats[4] = h->host_counters[8];
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
   // phase B
-  k_phase_b_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
+  if (h->tile_paths & 2) {
+    k_phase_b_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
+  } else {
+    k_phase_b_block<kMedThreads><<<mgrid, kMedThreads, 0, s>>>(c, h->list[0], cnt + 0);
+  }
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   k_phase_b_block<kMedThreads><<<mgrid, kMedThreads, 0, s>>>(c, h->list[1], cnt + 1);

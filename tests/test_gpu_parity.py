@@ -99,6 +99,8 @@ CASES = [
     (1500, 20, 400, 2.0, 11, {"block_max": 0, "smem_max": 64}),   # global-memory workspace
     (1200, 10, 300, 2.0, 14, {"tile_max": 0, "block_max": 0}),    # everything on the 1024-thread path
     (777, 5, 200, 2.0, 12, {"bucket_cap": 2}),        # permutation sort fallback
+    (2500, 3, 60, 2.0, 15, {"tile_paths": 1}),        # tile thresholds, 256-thread rebuild
+    (2500, 3, 60, 2.0, 16, {"tile_paths": 2}),        # 256-thread thresholds, tile rebuild
     (3000, 4, 1500, 2.0, 13, {}),                     # heavy tail: block-path hubs
 ]
 
@@ -133,7 +135,7 @@ def test_dependency_passes_happen():
 
 
 @pytest.mark.parametrize("name", ["single_edge", "empty", "isolated", "star", "complete", "two_stars",
-                                  "matching", "path_odd"])
+                                  "matching", "path_odd", "cycle_big", "matching_big", "star_matching"])
 def test_edge_cases(name):
     if name == "single_edge":
         n, edges = 2, [(0, 1)]
@@ -149,6 +151,12 @@ def test_edge_cases(name):
         n, edges = 401, [(0, i) for i in range(2, 201)] + [(1, i) for i in range(201, 401)]
     elif name == "matching":
         n, edges = 4, [(0, 1), (2, 3)]
+    elif name == "cycle_big":       # every trade has 4 entries: tiles hold their maximum of trades
+        n, edges = 5001, [(i, (i + 1) % 5001) for i in range(5001)]
+    elif name == "matching_big":
+        n, edges = 4000, [(i, i + 1) for i in range(0, 4000, 2)]
+    elif name == "star_matching":
+        n, edges = 600, [(0, i) for i in range(1, 600)] + [(i, i + 1) for i in range(1, 598, 2)]
     else:
         n, edges = 11, [(i, i + 1) for i in range(10)]
     rp, col = _csr(edges, n)
