@@ -166,6 +166,31 @@ int cb_timings(cb_handle h, double* ms, int count);
  */
 int cb_set_option(cb_handle h, const char* key, int64_t value);
 
+/*
+ * The permutation of super step g for n nodes and `seed` (the same order as
+ * cb_permutation), computed without allocating anything.  The paper has no
+ * counterpart: this serves callers that may not allocate device memory
+ * themselves, such as code running inside a host framework that owns every
+ * device allocation, or a latency-critical loop where cudaMalloc could
+ * synchronise the device or fail.
+ *   n          number of nodes, 0 <= n <= 2^20 (larger n: CB_ESIZE).
+ *   seed, g    as in cb_global_trades; g < 2^32 - 2.
+ *   order_out  n int32 in device memory (caller-owned): order_out[p] = node
+ *              at position p.
+ *   cuda_stream the cudaStream_t to run on (NULL: the default stream); the
+ *              call returns without waiting for the result.
+ * Scratch: one static 13 MiB device array, held by every device that loads
+ * the library until the process exits, and shared by every call on that
+ * device.  The first call on a device looks up that array's device address
+ * (once per device, with the device current); make the first call before any
+ * stream capture.  Each call clears the counters it needs, but calls that
+ * overlap on the GPU (different streams, or host threads) race on the shared
+ * scratch and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * other allocating routine is called.  Errors are reported through
+ * cb_last_error(NULL).
+ */
+int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,8 @@ def load():
     lib.cb_permutation.argtypes = [vp, u64, vp, i32]
     lib.cb_stats.restype = i32
     lib.cb_stats.argtypes = [vp, C.POINTER(i64), i32]
+    lib.cb_permutation_static.restype = i32
+    lib.cb_permutation_static.argtypes = [i64, u64, u64, vp, vp]
     lib.cb_timings.restype = i32
     lib.cb_timings.argtypes = [vp, C.POINTER(C.c_double), i32]
     lib.cb_set_option.restype = i32
@@ -165,6 +167,16 @@ def cb_permutation(h, g: int):
     if n:
         _check(load().cb_permutation(h, g, out.ctypes.data, CB_HOST), h)
     return out
+
+
+def cb_permutation_static(n: int, seed: int, g: int, order_out, stream=None):
+    """Permutation of super step g into `order_out` (an int32 CUDA tensor of n
+    entries) without any allocation; runs on `stream` (None: default stream)."""
+    p, kind, _ = _ptr(order_out)
+    if kind != CB_DEVICE:
+        raise ValueError("order_out must be device memory")
+    s = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    return _check(load().cb_permutation_static(n, C.c_uint64(seed & (2**64 - 1)), C.c_uint64(g), p, s))
 
 
 def cb_stats(h):

@@ -8,6 +8,8 @@
 #include "philox.cuh"
 #include "team.cuh"
 
+#include <mutex>
+
 namespace cb {
 namespace {
 
@@ -223,3 +225,77 @@ int prepare_next(Graph* h) {
 }
 
 }  // namespace cb
+
+// ---------------------------------------------------------------------------
+// The permutation without any allocation: same key sort, with its scratch in
+// a static device array instead of memory owned by a handle.  For callers
+// that may not allocate device memory themselves -- for example code running
+// under a host framework that owns every device allocation, or a latency-
+// critical loop where cudaMalloc could synchronise the device or fail.
+namespace cb {
+namespace {
+constexpr int64_t kStaticPermMaxNodes = int64_t(1) << 20;   // largest n accepted
+constexpr size_t kStaticPermBytes = size_t(13) << 20;       // >= perm_ws_bytes(2^20)
+constexpr int kStaticPermMaxDevices = 64;
+std::mutex g_static_perm_mu;
+void* g_static_perm_ptr[kStaticPermMaxDevices] = {};
+}  // namespace
+}  // namespace cb
+
+// Scratch of cb_permutation_static, shared by every call on a device and held
+// by every device that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_static_perm_scratch[cb::kStaticPermBytes];
+
+extern "C" int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_out,
+                                     void* cuda_stream) {
+  using namespace cb;
+  if (n < 0 || (n > 0 && !order_out)) return fail(nullptr, CB_EINVAL, "cb_permutation_static: bad n or order_out");
+  if (n > kStaticPermMaxNodes)
+    return fail(nullptr, CB_ESIZE, "cb_permutation_static: n exceeds the static scratch limit of 2^20 nodes");
+  if (g >= 0xfffffffeull) return fail(nullptr, CB_ERANGE, "cb_permutation_static: step too large");
+  if (perm_ws_bytes(kStaticPermMaxNodes) > kStaticPermBytes)
+    return fail(nullptr, CB_ECHECK, "cb_permutation_static: static scratch smaller than its limit needs");
+  if (n == 0) return CB_OK;
+  int dev = 0, num_sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kStaticPermMaxDevices) return fail(nullptr, CB_EINVAL, "cb_permutation_static: device index");
+  void* base = nullptr;
+  {
+    // once per device, with that device current: the device address of the scratch
+    std::lock_guard<std::mutex> lock(g_static_perm_mu);
+    if (!g_static_perm_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_static_perm_scratch);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
+      g_static_perm_ptr[dev] = p;
+    }
+    base = g_static_perm_ptr[dev];
+  }
+  e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int B = bucket_bits(n);
+  const int nb = 1 << B;
+  PermWs w = carve(base, n);
+  // the scratch keeps the previous call's contents: clear the counters
+  if ((e = cudaMemsetAsync(w.hist, 0, sizeof(int32_t) * nb, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * nb, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(w.overflow, 0, sizeof(int32_t), s)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaMemsetAsync");
+  const unsigned grid = grid_for(n, kPermThreads, num_sms);
+  const size_t hsm = nb <= 4096 ? sizeof(int32_t) * nb : 0;
+  k_perm_hist<<<grid, kPermThreads, hsm, s>>>(n, seed, static_cast<uint32_t>(g), B, w.hist);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_perm_hist");
+  if ((e = exclusive_scan_i32(w.hist, w.boff, nb, w.scan, s)) != cudaSuccess) return cuda_fail(nullptr, e, "scan");
+  k_perm_scatter<<<grid, kPermThreads, 0, s>>>(n, seed, static_cast<uint32_t>(g), B, w.boff, w.cursor, w.bkey, w.bid);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_perm_scatter");
+  const int cap = 2048;
+  const size_t ssm = static_cast<size_t>(cap) * (sizeof(uint64_t) + sizeof(int32_t));
+  const unsigned sgrid = static_cast<unsigned>(nb < num_sms * 8 ? nb : num_sms * 8);
+  k_bucket_sort<<<sgrid, kPermThreads, ssm, s>>>(nb, w.boff, w.bkey, w.bid, cap, order_out, nullptr, w.overflow, cap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_bucket_sort");
+  k_bucket_overflow<<<64, kPermThreads, 0, s>>>(w.overflow, w.boff, w.bkey, w.bid, order_out, nullptr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_bucket_overflow");
+  return CB_OK;
+}
