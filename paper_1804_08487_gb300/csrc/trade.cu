@@ -58,6 +58,8 @@ constexpr int kTileCap = 1024;                       // weight units per tile (w
 constexpr int kTileTrades = kTileCap / 4;            // so at most 256 trades per tile
 constexpr int kTileSlots = kTileCap + kTileMaxCap;   // a trade may start just before the cap
 constexpr int kNoOwner = 0xFFFF;
+constexpr int kTileHashLg = 11;
+constexpr int kTileHash = 1 << kTileHashLg;          // > 1.7 x the slots of a tile
 
 struct StepCtx {
   int64_t n, T;
@@ -575,21 +577,23 @@ __global__ void k_class_scatter(int64_t ntasks, const int32_t* __restrict__ f, c
 
 // ---------------------------------------------------------------- tile path
 
-struct TileShared {
-  uint64_t key[kTileSlots];     // full own key of each element of D
-  int32_t y[kTileSlots];        // entries; in phase B the mapped output position
-  uint8_t meta[kTileSlots];
-  uint8_t far[kTileSlots];
-  uint16_t owner[kTileSlots];   // local trade index (< 256), kNoOwner = padding slot
+struct TileShared {              // per-trade data of the current tile
   int64_t b0[kTileTrades];
+  int64_t ou[kTileTrades], ov[kTileTrades];
   int32_t t[kTileTrades];
-  int32_t acnt[kTileTrades];    // |A_{u-v}| (phase A) / u's entries placed (phase B)
+  int32_t acnt[kTileTrades];    // |A_{u-v}| (phase A)
   int32_t flags[kTileTrades];   // bit0 deferred, bit1 has a dependent later trade
   int16_t du[kTileTrades], dv[kTileTrades], lofs[kTileTrades];
-  int64_t ou[kTileTrades], ov[kTileTrades];
   int32_t scan[kTileThreads / 32 + 2];
   int64_t first, base;
   int32_t ntr, nslots;
+};
+
+// Per-entry arrays of a tile (phase-specific layouts provide them).
+struct TileEntries {
+  int32_t* y;
+  uint16_t* owner;
+  uint8_t* stash;    // loaded only when non-null
 };
 
 __device__ __forceinline__ int tile_owner(const TileShared& sh, int e) {
@@ -603,8 +607,8 @@ __device__ __forceinline__ int tile_owner(const TileShared& sh, int e) {
 
 // Set up tile `tile`: its trades and entries (y) in shared memory.  Returns
 // false when the tile is empty.
-__device__ bool tile_setup(const StepCtx& c, TileShared& sh, const int32_t* list, const int64_t* tile_off,
-                           int64_t ntrades, int64_t total_w, int64_t tile, bool load_stash) {
+__device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& te, const int32_t* list,
+                           const int64_t* tile_off, int64_t ntrades, int64_t total_w, int64_t tile) {
   if (threadIdx.x == 0) {
     const int64_t lo = tile * kTileCap, hi = lo + kTileCap;
     const int64_t a = lower_bound(tile_off, static_cast<int>(ntrades), lo);
@@ -633,46 +637,111 @@ __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const int32_t* list
     const int k = tile_owner(sh, e);
     const int i = e - sh.lofs[k];
     if (i < sh.du[k] + sh.dv[k]) {
-      sh.owner[e] = static_cast<uint16_t>(k);
-      sh.y[e] = __ldcg(c.col + sh.b0[k] + i);
-      if (load_stash) sh.meta[e] = c.stash[sh.b0[k] + i];
+      te.owner[e] = static_cast<uint16_t>(k);
+      te.y[e] = __ldcg(c.col + sh.b0[k] + i);
+      if (te.stash) te.stash[e] = c.stash[sh.b0[k] + i];
     } else {
-      sh.owner[e] = kNoOwner;
+      te.owner[e] = kNoOwner;
     }
   }
   __syncthreads();
   return true;
 }
 
+// Phase A for a tile of small trades, one thread per entry.  The 2x2 block
+// matrices come from a hash keyed by (local trade, far trade), the
+// |A_{u-v}|-th smallest key of every trade from a radix select with 4-bit
+// digits that all trades of the tile run together.
+struct TileA {
+  uint64_t key[kTileSlots];               // full own key
+  unsigned long long hash[kTileHash];     // (key+1) << 16 | flags
+  union {
+    uint32_t hist[kTileTrades * 8];       // 16 bins per trade, two 16-bit counters per word
+    uint64_t thr_tb[kTileTrades];         // after the selection: threshold tie-break
+  };
+  uint64_t prefix[kTileTrades];           // radix-select prefix, then the threshold key
+  int32_t y[kTileSlots];
+  uint16_t owner[kTileSlots];
+  uint8_t meta[kTileSlots];
+  uint8_t far[kTileSlots];
+  int32_t kk[kTileTrades];                // rank still sought (1-based)
+  int8_t shift[kTileTrades];
+  int32_t more;                           // some trade still selecting
+};
+
+__device__ __forceinline__ uint64_t tile_hkey(int k, int64_t s) {
+  return ((static_cast<uint64_t>(k) << 31) | static_cast<uint64_t>(s)) + 1;
+}
+__device__ __forceinline__ uint32_t tile_hslot(uint64_t hk) {
+  const uint32_t x = static_cast<uint32_t>(hk) * 0x9E3779B1u ^ static_cast<uint32_t>(hk >> 32) * 0x85EBCA6Bu;
+  return x >> (32 - kTileHashLg);
+}
+__device__ void tile_hinsert(unsigned long long* h, uint64_t hk, uint32_t bit) {
+  uint32_t s = tile_hslot(hk);
+  const unsigned long long want = static_cast<unsigned long long>(hk) << 16;
+  for (;;) {
+    unsigned long long cur = h[s];
+    if (cur == 0ull) {
+      const unsigned long long prev = atomicCAS(&h[s], 0ull, want | bit);
+      if (prev == 0ull) return;
+      cur = prev;
+    }
+    if ((cur >> 16) == hk) {
+      atomicOr(reinterpret_cast<unsigned int*>(&h[s]), bit);
+      return;
+    }
+    s = (s + 1) & (kTileHash - 1);
+  }
+}
+__device__ __forceinline__ int tile_hfind(const unsigned long long* h, uint64_t hk) {
+  uint32_t s = tile_hslot(hk);
+  for (;;) {
+    const unsigned long long cur = h[s];
+    if (cur == 0ull) return -1;
+    if ((cur >> 16) == hk) return static_cast<int>(s);
+    s = (s + 1) & (kTileHash - 1);
+  }
+}
+
 __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const int32_t* __restrict__ list,
                                                                const int64_t* __restrict__ tile_off,
                                                                const int64_t* __restrict__ counts) {
   __shared__ TileShared sh;
+  extern __shared__ __align__(16) char dsm[];
+  TileA& ta = *reinterpret_cast<TileA*>(dsm);
   const int64_t ntrades = counts[0], total_w = counts[3];
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (!tile_setup(c, sh, list, tile_off, ntrades, total_w, tile, false)) continue;
+    for (int i = threadIdx.x; i < kTileHash; i += blockDim.x) ta.hash[i] = 0ull;
+    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, nullptr}, list, tile_off, ntrades, total_w, tile)) continue;
     const int E = sh.nslots;
+    // entries into the hash: presence bit (row, column) per (trade, far trade)
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = ta.owner[e];
+      if (k == kNoOwner) continue;
+      const int32_t yy = ta.y[e];
+      const int64_t s = yy >> 1;
+      if (s == sh.t[k]) continue;
+      const int r = (e - sh.lofs[k]) >= sh.du[k];
+      tile_hinsert(ta.hash, tile_hkey(k, s), 1u << (2 * r + (yy & 1)));
+    }
+    __syncthreads();
     // block analysis, dependencies, keys
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = sh.owner[e];
+      const int k = ta.owner[e];
       if (k == kNoOwner) continue;
       const int64_t t = sh.t[k], t2 = 2 * t;
-      const int lo0 = sh.lofs[k], du = sh.du[k], L = du + sh.dv[k];
-      const int r = (e - lo0) >= du;
-      const int32_t yy = sh.y[e];
+      const int r = (e - sh.lofs[k]) >= sh.du[k];
+      const int32_t yy = ta.y[e];
       const int64_t s = yy >> 1;
       const bool single = (t2 + 1 >= c.n);
-      sh.far[e] = 0;
+      ta.far[e] = 0;
       if (s == t) {
-        sh.meta[e] = static_cast<uint8_t>(r | kUV);
+        ta.meta[e] = static_cast<uint8_t>(r | kUV);
         continue;
       }
-      int bits = 0;   // presence of (row, column) in the block with trade s
-      for (int j = lo0; j < lo0 + L; ++j) {
-        const int32_t yj = sh.y[j];
-        if ((yj >> 1) == s) bits |= 1 << (2 * ((j - lo0) >= du) + (yj & 1));
-      }
+      const int slot = tile_hfind(ta.hash, tile_hkey(k, s));
+      const uint32_t bits = static_cast<uint32_t>(ta.hash[slot]);
       const int u0 = bits & 1, u1 = (bits >> 1) & 1, v0 = (bits >> 2) & 1, v1 = (bits >> 3) & 1;
       const int cu = u0 + u1, cv = v0 + v1;
       uint8_t m = static_cast<uint8_t>(r | (u0 << 4) | (u1 << 5) | (v0 << 6) | (v1 << 7));
@@ -707,74 +776,123 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
       const uint32_t lo = min(x, y), hi = max(x, y);
       const EdgeKeys ek = edge_keys(c.seed, lo, hi, c.g);
       const bool lo_mine = (lo >> 1) == static_cast<uint32_t>(t);
-      sh.key[e] = lo_mine ? ek.lo_side : ek.hi_side;
-      sh.far[e] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
+      ta.key[e] = lo_mine ? ek.lo_side : ek.hi_side;
+      ta.far[e] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
       if (!other && !single) {
         m |= kInD;
         if (r == 0) atomicAdd(&sh.acnt[k], 1);
       }
-      sh.meta[e] = m;
+      ta.meta[e] = m;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x)
-      if (sh.flags[k] & 1) c.def_out[atomicAdd(c.def_count, 1ull)] = sh.t[k];
-    // rank each element of D within its trade by (key, lo, hi); u keeps ranks < a
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = sh.owner[e];
-      if (k == kNoOwner || (sh.flags[k] & 1)) continue;
-      const uint8_t m = sh.meta[e];
-      if (!(m & kInD)) continue;
-      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
-      const int lo0 = sh.lofs[k], L = sh.du[k] + sh.dv[k];
-      const uint64_t ki = sh.key[e];
-      int rank = 0;
-      for (int j = lo0; j < lo0 + L; ++j) {
-        if (!(sh.meta[j] & kInD)) continue;
-        const uint64_t kj = sh.key[j];
-        if (kj < ki) {
-          ++rank;
-        } else if (kj == ki && j != e) {
-          rank += tie_break(lo_of(t2, sh.meta[j], sh.y[j]), hi_of(t2, sh.meta[j], sh.y[j])) <
-                  tie_break(lo_of(t2, m, sh.y[e]), hi_of(t2, m, sh.y[e]));
-        }
-      }
-      const int a = sh.acnt[k];
-      const int r = m & kR;
-      if ((rank < a ? 0 : 1) != r) sh.meta[e] = m | kFlip;
-      if (rank == a - 1) {   // the threshold element publishes its trade's threshold
-        const int32_t t = sh.t[k];
-        c.thr_key[t] = ki;
-        c.thr_tb[t] = tie_break(lo_of(t2, m, sh.y[e]), hi_of(t2, m, sh.y[e]));
-        c.thr_top[t] = static_cast<uint8_t>(ki >> 58);
-        if (sh.flags[k] & 2) {
-          __threadfence();
-          st_release(c.done + t, c.stamp);
-        }
-      }
-    }
+    // deferred trades leave; the others start selecting their a-th smallest key
     for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
       const int32_t t = sh.t[k];
-      if ((sh.flags[k] & 1) || sh.acnt[k] != 0 || 2 * int64_t(t) + 1 >= c.n) continue;
-      c.thr_key[t] = 0;   // a = 0: u keeps nothing
-      c.thr_tb[t] = 0;
-      c.thr_top[t] = 0;
-      if (sh.flags[k] & 2) {
-        __threadfence();
-        st_release(c.done + t, c.stamp);
+      if (sh.flags[k] & 1) c.def_out[atomicAdd(c.def_count, 1ull)] = t;
+      const bool skip = (sh.flags[k] & 1) || sh.acnt[k] == 0 || 2 * int64_t(t) + 1 >= c.n;
+      ta.kk[k] = skip ? 0 : sh.acnt[k];
+      ta.shift[k] = skip ? -1 : 60;
+      ta.prefix[k] = 0;
+    }
+    __syncthreads();
+    for (int round = 0; round < 16; ++round) {
+      for (int i = threadIdx.x; i < kTileTrades * 8; i += blockDim.x) ta.hist[i] = 0;
+      if (threadIdx.x == 0) ta.more = 0;
+      __syncthreads();
+      for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int k = ta.owner[e];
+        if (k == kNoOwner || !(ta.meta[e] & kInD)) continue;
+        const int sft = ta.shift[k];
+        if (sft < 0) continue;
+        const uint64_t key = ta.key[e];
+        if (sft < 60 && (key >> (sft + 4)) != (ta.prefix[k] >> (sft + 4))) continue;
+        const uint32_t d = static_cast<uint32_t>(key >> sft) & 15u;
+        atomicAdd(&ta.hist[k * 8 + (d >> 1)], (d & 1) ? 0x10000u : 1u);
+      }
+      __syncthreads();
+      for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
+        const int sft = ta.shift[k];
+        if (sft < 0) continue;
+        int below = 0, kk = ta.kk[k];
+        for (int b = 0; b < 16; ++b) {
+          const uint32_t w = ta.hist[k * 8 + (b >> 1)];
+          const int cb = static_cast<int>((b & 1) ? (w >> 16) : (w & 0xffffu));
+          if (below < kk && kk <= below + cb) {
+            ta.kk[k] = kk - below;
+            ta.prefix[k] |= static_cast<uint64_t>(b) << sft;
+            if (cb == 1 || sft == 0) {
+              ta.shift[k] = static_cast<int8_t>(-2 - sft);   // resolved; -2 - shift keeps the last shift
+            } else {
+              ta.shift[k] = static_cast<int8_t>(sft - 4);
+              ta.more = 1;
+            }
+            break;
+          }
+          below += cb;
+        }
+      }
+      __syncthreads();
+      if (!ta.more) break;
+    }
+    for (int k = threadIdx.x; k < kTileTrades; k += blockDim.x) ta.thr_tb[k] = 0;   // histogram no longer needed
+    __syncthreads();
+    // the threshold element of each trade: the one matching its prefix (ties on
+    // all 64 bits, which need the (lo, hi) order, are ranked explicitly)
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = ta.owner[e];
+      if (k == kNoOwner || !(ta.meta[e] & kInD)) continue;
+      const int code = ta.shift[k];
+      if (code > -2) continue;
+      const int sft = -2 - code;
+      const uint64_t key = ta.key[e];
+      if ((key >> sft) != (ta.prefix[k] >> sft)) continue;
+      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
+      const uint8_t m = ta.meta[e];
+      const uint64_t tb = tie_break(lo_of(t2, m, ta.y[e]), hi_of(t2, m, ta.y[e]));
+      if (sft > 0) {
+        ta.prefix[k] = key;
+        ta.thr_tb[k] = tb;
+      } else {   // every candidate has this exact key
+        const int lo0 = sh.lofs[k], L = sh.du[k] + sh.dv[k];
+        int r = 0;
+        for (int j = lo0; j < lo0 + L; ++j) {
+          if (j == e || !(ta.meta[j] & kInD) || ta.key[j] != key) continue;
+          r += tie_break(lo_of(t2, ta.meta[j], ta.y[j]), hi_of(t2, ta.meta[j], ta.y[j])) < tb;
+        }
+        if (r == ta.kk[k] - 1) ta.thr_tb[k] = tb;
+      }
+    }
+    __syncthreads();
+    // own decisions; flips go into the hash for the far-side test
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      const int k = ta.owner[e];
+      if (k == kNoOwner || (sh.flags[k] & 1)) continue;
+      const uint8_t m = ta.meta[e];
+      if (!(m & kInD)) continue;
+      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
+      const int r = m & kR;
+      const bool has_thr = ta.shift[k] <= -2;
+      const bool low = has_thr && at_or_below(ta.key[e], tie_break(lo_of(t2, m, ta.y[e]), hi_of(t2, m, ta.y[e])),
+                                              ta.prefix[k], ta.thr_tb[k]);
+      if ((low ? 0 : 1) != r) {
+        ta.meta[e] = m | kFlip;
+        const int32_t yy = ta.y[e];
+        const int slot = tile_hfind(ta.hash, tile_hkey(k, yy >> 1));
+        atomicOr(reinterpret_cast<unsigned int*>(&ta.hash[slot]), 16u << (2 * r + (yy & 1)));
       }
     }
     __syncthreads();
     // will the far trade consider this edge?  Write the stash byte.
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = sh.owner[e];
+      const int k = ta.owner[e];
       if (k == kNoOwner || (sh.flags[k] & 1)) continue;
-      const uint8_t m = sh.meta[e];
+      const uint8_t m = ta.meta[e];
       const int f = (m & kFlip) ? 1 : 0;
       int in_far = 0;
       const int64_t t = sh.t[k];
       if (!(m & kUV)) {
         const int r = m & kR;
-        const int32_t yy = sh.y[e];
+        const int32_t yy = ta.y[e];
         const int64_t s = yy >> 1;
         const int u0 = (m >> 4) & 1, u1 = (m >> 5) & 1, v0 = (m >> 6) & 1, v1 = (m >> 7) & 1;
         const int cr = r ? (v0 + v1) : (u0 + u1);
@@ -783,21 +901,35 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
         } else if (s < c.T) {
           if (u0 + u1 + v0 + v1 == 1) {
             in_far = 1;
-          } else {   // block after t's own decisions
-            const int lo0 = sh.lofs[k], du = sh.du[k], L = du + sh.dv[k];
+          } else {   // block after t's own decisions: presence bits 0..3, flips 4..7
+            const uint32_t fl = static_cast<uint32_t>(ta.hash[tile_hfind(ta.hash, tile_hkey(k, s))]);
             const int myrow = r ^ f;
             int same = 0;
-            for (int j = lo0; j < lo0 + L; ++j) {
-              if ((sh.y[j] >> 1) != s) continue;
-              const int rj = (j - lo0) >= du, fj = (sh.meta[j] & kFlip) ? 1 : 0;
-              same += ((rj ^ fj) == myrow);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (!((fl >> q) & 1)) continue;
+              same += (((q >> 1) ^ ((fl >> (4 + q)) & 1)) == myrow);
             }
             in_far = (same == 1);
           }
         }
       }
-      const int i = e - sh.lofs[k];
-      c.stash[sh.b0[k] + i] = static_cast<uint8_t>(f | (in_far << 1) | (in_far ? (sh.far[e] << 2) : 0));
+      c.stash[sh.b0[k] + (e - sh.lofs[k])] =
+          static_cast<uint8_t>(f | (in_far << 1) | (in_far ? (ta.far[e] << 2) : 0));
+    }
+    // publish every completed trade's threshold (fenced when a later trade waits on it)
+    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
+      const int32_t t = sh.t[k];
+      if ((sh.flags[k] & 1) || 2 * int64_t(t) + 1 >= c.n) continue;
+      const bool has_thr = ta.shift[k] <= -2;
+      const uint64_t tk = has_thr ? ta.prefix[k] : 0;
+      c.thr_key[t] = tk;
+      c.thr_tb[t] = has_thr ? ta.thr_tb[k] : 0;
+      c.thr_top[t] = static_cast<uint8_t>(tk >> 58);
+      if (sh.flags[k] & 2) {
+        __threadfence();
+        st_release(c.done + t, c.stamp);
+      }
     }
     __syncthreads();
   }
@@ -840,14 +972,23 @@ __device__ void tile_scan(TileShared& sh, const uint8_t* val, int32_t* out, int 
   __syncthreads();
 }
 
+struct TileB {
+  int32_t pre[kTileSlots];     // prefix count of entries going to u's new row
+  int32_t y[kTileSlots];       // entries, then their step-(g+1) positions
+  uint16_t owner[kTileSlots];
+  uint8_t stash[kTileSlots];   // stash byte, then the new side
+  uint8_t to_u[kTileSlots];
+};
+
 __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const int32_t* __restrict__ list,
                                                                const int64_t* __restrict__ tile_off,
                                                                const int64_t* __restrict__ counts) {
   __shared__ TileShared sh;
+  __shared__ TileB tb;
   const int64_t ntrades = counts[0], total_w = counts[3];
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (!tile_setup(c, sh, list, tile_off, ntrades, total_w, tile, true)) continue;
+    if (!tile_setup(c, sh, TileEntries{tb.y, tb.owner, tb.stash}, list, tile_off, ntrades, total_w, tile)) continue;
     const int E = sh.nslots;
     for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
       const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
@@ -862,15 +1003,15 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
       }
       if (bad) latch(c.err, kErrRowLength);
     }
-    // side and far end of every entry; far[] marks entries going to u's new row
+    // side and far end of every entry
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = sh.owner[e];
-      sh.far[e] = 0;
+      const int k = tb.owner[e];
+      tb.to_u[e] = 0;
       if (k == kNoOwner) continue;
       const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
       const int r = (e - sh.lofs[k]) >= sh.du[k];
-      const int32_t yy = sh.y[e];
-      const uint8_t st = sh.meta[e];
+      const int32_t yy = tb.y[e];
+      const uint8_t st = tb.stash[e];
       const int r2 = r ^ (st & 1);
       int32_t y2 = yy;
       if (st & 2) {
@@ -885,26 +1026,25 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
         }
         y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
       }
-      sh.y[e] = c.M[y2];
-      sh.far[e] = static_cast<uint8_t>(r2 == 0);
-      sh.meta[e] = static_cast<uint8_t>(r2);
+      tb.y[e] = c.M[y2];
+      tb.to_u[e] = static_cast<uint8_t>(r2 == 0);
+      tb.stash[e] = static_cast<uint8_t>(r2);
     }
     __syncthreads();
-    int32_t* pre = reinterpret_cast<int32_t*>(sh.key);   // keys are not used in phase B
-    tile_scan(sh, sh.far, pre, E);
+    tile_scan(sh, tb.to_u, tb.pre, E);
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = sh.owner[e];
+      const int k = tb.owner[e];
       if (k == kNoOwner) continue;
       const int lo0 = sh.lofs[k];
-      const int before0 = pre[e] - pre[lo0];
-      if (sh.meta[e] == 0) {
-        c.col_next[sh.ou[k] + before0] = sh.y[e];
+      const int before0 = tb.pre[e] - tb.pre[lo0];
+      if (tb.stash[e] == 0) {
+        c.col_next[sh.ou[k] + before0] = tb.y[e];
       } else {
-        c.col_next[sh.ov[k] + (e - lo0 - before0)] = sh.y[e];
+        c.col_next[sh.ov[k] + (e - lo0 - before0)] = tb.y[e];
       }
       const int L = sh.du[k] + sh.dv[k];
       if (e == lo0 + L - 1) {   // last entry of the trade: u's row must be exactly full
-        const int n0 = before0 + (sh.meta[e] == 0);
+        const int n0 = before0 + (tb.stash[e] == 0);
         if (n0 != sh.du[k]) latch(c.err, kErrRowSide);
       }
     }
@@ -1016,6 +1156,8 @@ int super_step(Graph* h) {
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(big_smem)));
   const unsigned tgrid = static_cast<unsigned>(h->num_sms * 8);
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(sizeof(TileA))));
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
   char* gws = static_cast<char*>(h->ws_global);
@@ -1039,7 +1181,7 @@ int super_step(Graph* h) {
   c.def_out = h->list_def[0][0];
   c.def_count = ucnt + 4;
   if (h->tile_paths & 1) {
-    k_phase_a_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
+    k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, cnt);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
   } else if ((rc = launch_med(h->list[0], cnt + 0, 0))) {
