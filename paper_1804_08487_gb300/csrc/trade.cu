@@ -666,7 +666,6 @@ struct TileA {
   uint8_t far[kTileSlots];
   int32_t kk[kTileTrades];                // rank still sought (1-based)
   int8_t shift[kTileTrades];
-  int32_t more;                           // some trade still selecting
 };
 
 __device__ __forceinline__ uint64_t tile_hkey(int k, int64_t s) {
@@ -797,7 +796,6 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
     __syncthreads();
     for (int round = 0; round < 16; ++round) {
       for (int i = threadIdx.x; i < kTileTrades * 8; i += blockDim.x) ta.hist[i] = 0;
-      if (threadIdx.x == 0) ta.more = 0;
       __syncthreads();
       for (int e = threadIdx.x; e < E; e += blockDim.x) {
         const int k = ta.owner[e];
@@ -810,10 +808,12 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
         atomicAdd(&ta.hist[k * 8 + (d >> 1)], (d & 1) ? 0x10000u : 1u);
       }
       __syncthreads();
+      bool more = false;
       for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
         const int sft = ta.shift[k];
         if (sft < 0) continue;
-        int below = 0, kk = ta.kk[k];
+        int below = 0;
+        const int kk = ta.kk[k];
         for (int b = 0; b < 16; ++b) {
           const uint32_t w = ta.hist[k * 8 + (b >> 1)];
           const int cb = static_cast<int>((b & 1) ? (w >> 16) : (w & 0xffffu));
@@ -824,15 +824,14 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
               ta.shift[k] = static_cast<int8_t>(-2 - sft);   // resolved; -2 - shift keeps the last shift
             } else {
               ta.shift[k] = static_cast<int8_t>(sft - 4);
-              ta.more = 1;
+              more = true;
             }
             break;
           }
           below += cb;
         }
       }
-      __syncthreads();
-      if (!ta.more) break;
+      if (!__syncthreads_or(more)) break;   // every thread takes the same exit
     }
     for (int k = threadIdx.x; k < kTileTrades; k += blockDim.x) ta.thr_tb[k] = 0;   // histogram no longer needed
     __syncthreads();
