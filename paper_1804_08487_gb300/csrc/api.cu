@@ -47,7 +47,7 @@ void release(Graph* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
-                  h->list[0], h->list[1], h->list[2], h->tile_off, h->cls_flag, h->cls_scan,
+                  h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
                   h->list_def[0][0], h->list_def[0][1], h->list_def[1][0], h->list_def[1][1], h->counters, h->err,
                   h->ws_global, h->sort_ws, h->scan_ws};
   for (void* b : bufs)
@@ -180,7 +180,7 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
       dalloc(&h->pos_next, n) || dalloc(&h->M, n) || dalloc(&h->deg_next, n) || dalloc(&h->stash, nnz) ||
       dalloc(&h->thr_key, h->ntasks) || dalloc(&h->thr_tb, h->ntasks) || dalloc(&h->done, h->ntasks) ||
       dalloc(&h->thr_top, h->ntasks) || dalloc(&h->list[0], h->ntasks) || dalloc(&h->list[1], h->ntasks) ||
-      dalloc(&h->list[2], h->ntasks) || dalloc(&h->tile_off, h->ntasks) || dalloc(&h->cls_flag, 4 * h->ntasks) ||
+      dalloc(&h->list[2], h->ntasks) || dalloc(&h->tile_off, h->ntasks) || dalloc(&h->tile_first, h->ntasks + 2) || dalloc(&h->cls_flag, 4 * h->ntasks) ||
       dalloc(&h->cls_scan, 4 * (h->ntasks + 1)) || dalloc(&h->list_def[0][0], h->ntasks) ||
       dalloc(&h->list_def[0][1], h->ntasks) || dalloc(&h->list_def[1][0], h->ntasks) ||
       dalloc(&h->list_def[1][1], h->ntasks) ||

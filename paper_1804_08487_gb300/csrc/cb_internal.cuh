@@ -49,6 +49,7 @@ struct Graph {
   uint32_t* done = nullptr;                // per trade: stamp g+1 once the threshold is published
   int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (tile, 256, 1024 threads), index order
   int64_t* tile_off = nullptr;             // per tile-class trade: prefix of its weight max(L, 4)
+  int32_t* tile_first = nullptr;           // first tile-class trade of each tile (+ end sentinel)
   int32_t* cls_flag = nullptr;             // 4 x ntasks scratch: class flags and tile weights
   int64_t* cls_scan = nullptr;             // 4 x (ntasks+1) scratch: their exclusive scans
   int32_t* list_def[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // deferred trades (256 / 1024 path), ping-pong

@@ -575,6 +575,21 @@ __global__ void k_class_scatter(int64_t ntasks, const int32_t* __restrict__ f, c
   }
 }
 
+// First tile-class trade of every tile (tile i = weight offsets [i C, (i+1) C)),
+// plus the end sentinel; one thread per tile-class trade.
+__global__ void k_tile_first(const int64_t* __restrict__ tile_off, const int64_t* __restrict__ counts,
+                             int32_t* __restrict__ tile_first) {
+  const int64_t ntr = counts[0], total_w = counts[3];
+  const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < ntr; k += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t cur = tile_off[k] / kTileCap;
+    const int64_t prev = k ? tile_off[k - 1] / kTileCap : -1;
+    for (int64_t i = prev + 1; i <= cur; ++i) tile_first[i] = static_cast<int32_t>(k);
+    if (k == ntr - 1)
+      for (int64_t i = cur + 1; i <= ntiles; ++i) tile_first[i] = static_cast<int32_t>(ntr);
+  }
+}
+
 // ---------------------------------------------------------------- tile path
 
 struct TileShared {              // per-trade data of the current tile
@@ -608,11 +623,11 @@ __device__ __forceinline__ int tile_owner(const TileShared& sh, int e) {
 // Set up tile `tile`: its trades and entries (y) in shared memory.  Returns
 // false when the tile is empty.
 __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& te, const int32_t* list,
-                           const int64_t* tile_off, int64_t ntrades, int64_t total_w, int64_t tile) {
+                           const int64_t* tile_off, const int32_t* tile_first, int64_t ntrades, int64_t total_w,
+                           int64_t tile) {
   if (threadIdx.x == 0) {
-    const int64_t lo = tile * kTileCap, hi = lo + kTileCap;
-    const int64_t a = lower_bound(tile_off, static_cast<int>(ntrades), lo);
-    const int64_t b = lower_bound(tile_off, static_cast<int>(ntrades), hi);
+    const int64_t a = tile_first[tile];
+    const int64_t b = tile_first[tile + 1];
     sh.first = a;
     sh.ntr = static_cast<int32_t>(b - a);
     sh.base = a < ntrades ? tile_off[a] : 0;
@@ -704,6 +719,7 @@ __device__ __forceinline__ int tile_hfind(const unsigned long long* h, uint64_t 
 
 __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const int32_t* __restrict__ list,
                                                                const int64_t* __restrict__ tile_off,
+                                                               const int32_t* __restrict__ tile_first,
                                                                const int64_t* __restrict__ counts) {
   __shared__ TileShared sh;
   extern __shared__ __align__(16) char dsm[];
@@ -712,7 +728,8 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (int i = threadIdx.x; i < kTileHash; i += blockDim.x) ta.hash[i] = 0ull;
-    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, nullptr}, list, tile_off, ntrades, total_w, tile)) continue;
+    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, nullptr}, list, tile_off, tile_first, ntrades, total_w, tile))
+      continue;
     const int E = sh.nslots;
     // entries into the hash: presence bit (row, column) per (trade, far trade)
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
@@ -981,13 +998,15 @@ struct TileB {
 
 __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const int32_t* __restrict__ list,
                                                                const int64_t* __restrict__ tile_off,
+                                                               const int32_t* __restrict__ tile_first,
                                                                const int64_t* __restrict__ counts) {
   __shared__ TileShared sh;
   __shared__ TileB tb;
   const int64_t ntrades = counts[0], total_w = counts[3];
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (!tile_setup(c, sh, TileEntries{tb.y, tb.owner, tb.stash}, list, tile_off, ntrades, total_w, tile)) continue;
+    if (!tile_setup(c, sh, TileEntries{tb.y, tb.owner, tb.stash}, list, tile_off, tile_first, ntrades, total_w, tile))
+      continue;
     const int E = sh.nslots;
     for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
       const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
@@ -1147,6 +1166,9 @@ int super_step(Graph* h) {
     ++h->launches;
     for (int q = 0; q < 4; ++q)
       CB_CUDA(h, cudaMemcpyAsync(cnt + q, h->cls_scan + q * n1 + ntasks, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_tile_first<<<grid_n(ntasks), 256, 0, s>>>(h->tile_off, cnt, h->tile_first);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
   }
   const size_t med_smem = ws_a_bytes(std::max(block_max, 1));
   const size_t big_smem = ws_a_bytes(std::max(h->smem_max, 1));
@@ -1180,7 +1202,7 @@ int super_step(Graph* h) {
   c.def_out = h->list_def[0][0];
   c.def_count = ucnt + 4;
   if (h->tile_paths & 1) {
-    k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, cnt);
+    k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
   } else if ((rc = launch_med(h->list[0], cnt + 0, 0))) {
@@ -1215,7 +1237,7 @@ int super_step(Graph* h) {
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
   // phase B
   if (h->tile_paths & 2) {
-    k_phase_b_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, cnt);
+    k_phase_b_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt);
   } else {
     k_phase_b_block<kMedThreads><<<mgrid, kMedThreads, 0, s>>>(c, h->list[0], cnt + 0);
   }
