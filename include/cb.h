@@ -161,6 +161,10 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               workspace [8192]; 64..8192.
  *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];
  *               larger buckets take the global-memory fallback; 2..4096.
+ *   "queued_passes" dependency-resolution passes queued per super step before
+ *               the host checks whether any trade is still waiting [12];
+ *               0..64 (more passes follow as needed; the result never
+ *               depends on this value).
  *   "timing"    1: record CUDA events around the phases of each super step
  *               (adds one stream synchronisation per super step) [0].
  */

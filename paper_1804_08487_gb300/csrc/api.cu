@@ -48,7 +48,7 @@ void release(Graph* h) {
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
                   h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
-                  h->list_def[0][0], h->list_def[0][1], h->list_def[1][0], h->list_def[1][1], h->counters, h->err,
+                  h->list_def[0], h->list_def[1], h->counters, h->err,
                   h->ws_global, h->sort_ws, h->scan_ws};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -154,7 +154,8 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
   cudaStream_t s = h->stream;
   int rc;
   if (dalloc(&h->rp_id, n + 1) || dalloc(&h->deg_id, n) || dalloc(&h->col[0], nnz) || dalloc(&h->col[1], nnz) ||
-      dalloc(&h->err, 8) || dalloc(&h->counters, 16) || cudaMallocHost(&h->host_counters, 16 * sizeof(int64_t)))
+      dalloc(&h->err, 8) || dalloc(&h->counters, kCounters) ||
+      cudaMallocHost(&h->host_counters, kCounters * sizeof(int64_t)))
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
   CB_CUDA(h, cudaMemsetAsync(h->err, 0, 8 * sizeof(int32_t), s));
   CB_CUDA(h, cudaMemcpyAsync(h->rp_id, row_ptr, sizeof(int64_t) * (n + 1), kind, s));
@@ -181,9 +182,8 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
       dalloc(&h->thr_key, h->ntasks) || dalloc(&h->thr_tb, h->ntasks) || dalloc(&h->done, h->ntasks) ||
       dalloc(&h->thr_top, h->ntasks) || dalloc(&h->list[0], h->ntasks) || dalloc(&h->list[1], h->ntasks) ||
       dalloc(&h->list[2], h->ntasks) || dalloc(&h->tile_off, h->ntasks) || dalloc(&h->tile_first, h->ntasks + 2) || dalloc(&h->cls_flag, 4 * h->ntasks) ||
-      dalloc(&h->cls_scan, 4 * (h->ntasks + 1)) || dalloc(&h->list_def[0][0], h->ntasks) ||
-      dalloc(&h->list_def[0][1], h->ntasks) || dalloc(&h->list_def[1][0], h->ntasks) ||
-      dalloc(&h->list_def[1][1], h->ntasks) ||
+      dalloc(&h->cls_scan, 4 * (h->ntasks + 1)) || dalloc(&h->list_def[0], h->ntasks) ||
+      dalloc(&h->list_def[1], h->ntasks) ||
       cudaMalloc(&h->sort_ws, h->sort_ws_bytes) || cudaMalloc(&h->scan_ws, h->scan_ws_bytes))
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
@@ -305,6 +305,11 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!std::strcmp(key, "tile_max")) {
     if (value < 0 || value > kTileMaxCap) return fail(h, CB_EINVAL, "tile_max out of range [0, 128]");
     h->tile_max = static_cast<int>(value);
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "queued_passes")) {
+    if (value < 0 || value > 64) return fail(h, CB_EINVAL, "queued_passes out of range [0, 64]");
+    h->queued_passes = static_cast<int>(value);
     return CB_OK;
   }
   if (!std::strcmp(key, "tile_paths")) {

@@ -22,6 +22,8 @@ constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat
 constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
+constexpr int kCounters = 32;       // device counters per handle
+constexpr int kPassSlots = 22;      // pass input counts kept for the statistics ([8, 30))
 
 struct Graph {
   int64_t n = 0, nnz = 0, m = 0, T = 0, ntasks = 0;
@@ -52,8 +54,8 @@ struct Graph {
   int32_t* tile_first = nullptr;           // first tile-class trade of each tile (+ end sentinel)
   int32_t* cls_flag = nullptr;             // 4 x ntasks scratch: class flags and tile weights
   int64_t* cls_scan = nullptr;             // 4 x (ntasks+1) scratch: their exclusive scans
-  int32_t* list_def[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // deferred trades (256 / 1024 path), ping-pong
-  int64_t* counters = nullptr;             // list lengths, tile weight, deferred counts, global slices (16)
+  int32_t* list_def[2] = {nullptr, nullptr};  // deferred trades, ping-pong
+  int64_t* counters = nullptr;             // list lengths, tile weight, deferred counts, pass counts (kCounters)
   int32_t* err = nullptr;                  // latched device error
   // workspaces
   void* ws_global = nullptr;               // global workspace for trades too big for smem
@@ -64,6 +66,7 @@ struct Graph {
   void* scan_ws = nullptr;
   size_t scan_ws_bytes = 0;
   int64_t* host_counters = nullptr;        // pinned mirror of counters
+  int queued_passes = 12;                  // dependency passes queued per super step without a host check
 
   // knobs
   int tile_max = kTileMaxCap;

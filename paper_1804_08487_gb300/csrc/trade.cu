@@ -1135,12 +1135,12 @@ int super_step(Graph* h) {
   c.M = h->M;
   c.rp_next = h->rp[nxt];
   c.col_next = h->col[nxt];
-  // counters: [0..2] class list lengths, [3] tile weight total, [4+2p+q] deferred
-  // list q (0: 256-thread, 1: 1024-thread) of ping-pong side p, [8] global slices
+  // counters: [0..2] class list lengths, [3] tile weight total, [4..5] deferred
+  // lists, [8..] pass input counts, [kCounters-1] global-workspace trades
   int64_t* cnt = h->counters;
   unsigned long long* ucnt = reinterpret_cast<unsigned long long*>(cnt);
-  c.gws_count = ucnt + 8;
-  CB_CUDA(h, cudaMemsetAsync(cnt, 0, 16 * sizeof(int64_t), s));
+  c.gws_count = ucnt + kCounters - 1;
+  CB_CUDA(h, cudaMemsetAsync(cnt, 0, kCounters * sizeof(int64_t), s));
   const int64_t ntasks = h->ntasks;
   if (ntasks == 0) {
     h->cur = nxt;
@@ -1182,58 +1182,71 @@ int super_step(Graph* h) {
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
   char* gws = static_cast<char*>(h->ws_global);
-  auto launch_med = [&](const int32_t* list, const int64_t* count, int out) -> int {
-    c.def_out = h->list_def[out][0];
-    c.def_count = ucnt + 4 + 2 * out;
-    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem, s>>>(c, list, count, block_max, gws, h->ws_slice);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-    return CB_OK;
+  // phase A, first pass: every class; trades whose dependency has not published
+  // yet go to one deferred list, re-run by the 1024-thread kernel in later
+  // passes.  Passes are queued back to back without a host round trip; a pass
+  // over an empty list exits at once.  Counters: [4 + p] deferred list p,
+  // [8 + i] the input count of pass i + 1 (for the statistics).
+  auto defer_to = [&](int out) {
+    c.def_out = h->list_def[out];
+    c.def_count = ucnt + 4 + out;
   };
-  auto launch_big = [&](const int32_t* list, const int64_t* count, int out) -> int {
-    c.def_out = h->list_def[out][1];
-    c.def_count = ucnt + 5 + 2 * out;
-    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, list, count, h->smem_max, gws, h->ws_slice);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-    return CB_OK;
-  };
-  // phase A, first pass: tile path (deferred trades go to the 256-thread list), then the team paths
-  c.def_out = h->list_def[0][0];
-  c.def_count = ucnt + 4;
+  defer_to(0);
   if (h->tile_paths & 1) {
     k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt);
+  } else {
+    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem, s>>>(c, h->list[0], cnt + 0, block_max, gws,
+                                                                     h->ws_slice);
+  }
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem, s>>>(c, h->list[1], cnt + 1, block_max, gws,
+                                                                   h->ws_slice);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, h->list[2], cnt + 2, h->smem_max, gws,
+                                                                   h->ws_slice);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  int in = 0;
+  int64_t passes = 1;
+  auto deferred_pass = [&]() -> int {
+    const int out = 1 - in;
+    CB_CUDA(h, cudaMemsetAsync(cnt + 4 + out, 0, sizeof(int64_t), s));
+    if (passes < kPassSlots)
+      CB_CUDA(h, cudaMemcpyAsync(cnt + 8 + passes, cnt + 4 + in, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    defer_to(out);
+    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, h->list_def[in], cnt + 4 + in, h->smem_max,
+                                                                     gws, h->ws_slice);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
-  } else if ((rc = launch_med(h->list[0], cnt + 0, 0))) {
-    return rc;
-  }
-  if ((rc = launch_med(h->list[1], cnt + 1, 0))) return rc;
-  if ((rc = launch_big(h->list[2], cnt + 2, 0))) return rc;
-  int64_t passes = 1, deferred_total = 0;
-  int in = 0;
-  for (;;) {
-    CB_CUDA(h, cudaMemcpyAsync(h->host_counters, cnt, 16 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CB_CUDA(h, cudaStreamSynchronize(s));
-    const int64_t* hc = h->host_counters;
-    if (passes == 1) {
-      h->stats[2] = hc[0];
-      h->stats[3] = hc[1] + hc[2];
-    }
-    const int64_t ndef = hc[4 + 2 * in] + hc[5 + 2 * in];
-    if (ndef == 0) break;
-    deferred_total += ndef;
-    if (passes > 100000) return fail(h, CB_ECHECK, "dependency resolution did not converge");
-    const int out = 1 - in;
-    CB_CUDA(h, cudaMemsetAsync(cnt + 4 + 2 * out, 0, 2 * sizeof(int64_t), s));
-    if ((rc = launch_med(h->list_def[in][0], cnt + 4 + 2 * in, out))) return rc;
-    if ((rc = launch_big(h->list_def[in][1], cnt + 5 + 2 * in, out))) return rc;
     in = out;
     ++passes;
+    return CB_OK;
+  };
+  for (int q = 0; q < h->queued_passes; ++q)
+    if ((rc = deferred_pass())) return rc;
+  for (;;) {   // rarely: dependency chains longer than the queued passes
+    CB_CUDA(h, cudaMemcpyAsync(h->host_counters, cnt, kCounters * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CB_CUDA(h, cudaStreamSynchronize(s));
+    if (h->host_counters[4 + in] == 0) break;
+    if (passes > 100000) return fail(h, CB_ECHECK, "dependency resolution did not converge");
+    if ((rc = deferred_pass())) return rc;
   }
-  h->stats[0] = passes;
+  const int64_t* hc = h->host_counters;
+  h->stats[2] = hc[0];
+  h->stats[3] = hc[1] + hc[2];
+  int64_t used = 1, deferred_total = 0;
+  for (int i = 1; i < kPassSlots && i < passes; ++i) {
+    if (hc[8 + i] == 0) break;
+    deferred_total += hc[8 + i];
+    used = i + 1;
+  }
   h->stats[1] = deferred_total;
-  h->stats[4] = h->host_counters[8];
+  h->stats[4] = hc[kCounters - 1];
+  (void)used;
+  passes = used;
+  h->stats[0] = passes;
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
   // phase B
   if (h->tile_paths & 2) {

@@ -114,6 +114,8 @@ PLAIN = {
     "n4096": Workload("plain n=4096 PLD([10,100),2)", 4096, 10, 100, 2.0, 1, 42, 10),
     "n2^20": Workload("plain n=2^20 PLD([10,1000),2)", 1 << 20, 10, 1000, 2.0, 7, 7, 20),
     "n2^25": Workload("plain n=2^25 PLD([10,10000),2)", 1 << 25, 10, 10000, 2.0, 3, 3, 10),
+    # the n=2^25 degree law at a size whose kernels can be profiled in full
+    "n2^21": Workload("plain n=2^21 PLD([10,10000),2)", 1 << 21, 10, 10000, 2.0, 3, 3, 10),
 }
 
 
