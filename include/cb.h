@@ -85,9 +85,8 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
  *     ordered by (key, lo, hi) and u receives the first |A_{u-v}| elements.
  * philox64(...) = r0<<32 | r1 of Philox4x32-10 (Salmon et al., SC'11) with
  * key words (low, high) 32 bits of the seed.  Asynchronous on the handle's
- * stream except for a short host wait per super step while rare trade
- * dependencies are resolved.  Returns CB_ERANGE if the step counter would pass
- * 2^32 - 2.
+ * stream (with the "timing" option on, it waits once per super step).
+ * Returns CB_ERANGE if the step counter would pass 2^32 - 2.
  */
 int cb_global_trades(cb_handle h, uint32_t supersteps);
 
@@ -124,8 +123,10 @@ int cb_info(cb_handle h, int64_t* n, int64_t* m);
 int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
 
 /*
- * Counters of the last cb_global_trades call, for tests and tuning:
- * out[0] = dependency-resolution passes of the last super step,
+ * Counters of the last cb_global_trades call, for tests and tuning
+ * (synchronises the handle's stream):
+ * out[0] = dependency-resolution passes of the last super step (the final
+ *          in-order pass counts as one),
  * out[1] = trades deferred to a later pass (summed over its passes),
  * out[2] = trades on the tile path, out[3] = on the 256- and 1024-thread paths,
  * out[4] = trades whose workspace did not fit in shared memory,

@@ -177,13 +177,15 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
   }
   h->sort_ws_bytes = perm_ws_bytes(std::max<int64_t>(n, 1));
   h->scan_ws_bytes = scan_ws_bytes(n + 1);
+  int64_t def_cap = 1;   // the in-order resolver bitonic-sorts a deferred list padded to a power of two
+  while (def_cap < h->ntasks) def_cap <<= 1;
   if (dalloc(&h->order[0], n) || dalloc(&h->order[1], n) || dalloc(&h->rp[0], n + 1) || dalloc(&h->rp[1], n + 1) ||
       dalloc(&h->pos_next, n) || dalloc(&h->M, n) || dalloc(&h->deg_next, n) || dalloc(&h->stash, nnz) ||
       dalloc(&h->thr_key, h->ntasks) || dalloc(&h->thr_tb, h->ntasks) || dalloc(&h->done, h->ntasks) ||
       dalloc(&h->thr_top, h->ntasks) || dalloc(&h->list[0], h->ntasks) || dalloc(&h->list[1], h->ntasks) ||
       dalloc(&h->list[2], h->ntasks) || dalloc(&h->tile_off, h->ntasks) || dalloc(&h->tile_first, h->ntasks + 2) || dalloc(&h->cls_flag, 4 * h->ntasks) ||
-      dalloc(&h->cls_scan, 4 * (h->ntasks + 1)) || dalloc(&h->list_def[0], h->ntasks) ||
-      dalloc(&h->list_def[1], h->ntasks) ||
+      dalloc(&h->cls_scan, 4 * (h->ntasks + 1)) || dalloc(&h->list_def[0], def_cap) ||
+      dalloc(&h->list_def[1], def_cap) ||
       cudaMalloc(&h->sort_ws, h->sort_ws_bytes) || cudaMalloc(&h->scan_ws, h->scan_ws_bytes))
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
@@ -288,6 +290,27 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind) {
 
 int cb_stats(cb_handle h, int64_t* out, int count) {
   if (!h || !out || count < 0) return fail(h, CB_EINVAL, "bad argument");
+  // counters of the last super step (reset at the start of each one)
+  CB_CUDA(h, cudaMemcpyAsync(h->host_counters, h->counters, kCounters * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             h->stream));
+  CB_CUDA(h, cudaStreamSynchronize(h->stream));
+  const int64_t* hc = h->host_counters;
+  int64_t passes = 1, deferred = 0;
+  for (int i = 1; i < kPassSlots && i < h->last_passes_queued; ++i) {
+    if (hc[8 + i] == 0) break;
+    deferred += hc[8 + i];
+    passes = i + 1;
+  }
+  const int64_t left = hc[4 + h->last_in];   // run by the resolver
+  if (left) {
+    deferred += left;
+    passes += 1;
+  }
+  h->stats[0] = passes;
+  h->stats[1] = deferred;
+  h->stats[2] = hc[0];
+  h->stats[3] = hc[1] + hc[2];
+  h->stats[4] = hc[kCounters - 1];
   const int k = std::min(count, 6);
   for (int i = 0; i < k; ++i) out[i] = h->stats[i];
   return k;

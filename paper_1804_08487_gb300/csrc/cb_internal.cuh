@@ -16,6 +16,7 @@ enum DevErr : int32_t {
   kErrRowSide = 2,       // entry written to the wrong row of a trade
   kErrValidate = 3,      // input graph not simple / symmetric / in range
   kErrBucket = 4,        // permutation bucket bookkeeping failed
+  kErrResolve = 5,       // a trade could not run in index order
 };
 
 constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
@@ -66,7 +67,9 @@ struct Graph {
   void* scan_ws = nullptr;
   size_t scan_ws_bytes = 0;
   int64_t* host_counters = nullptr;        // pinned mirror of counters
-  int queued_passes = 12;                  // dependency passes queued per super step without a host check
+  int queued_passes = 12;                  // dependency passes queued per super step before the resolver
+  int64_t last_passes_queued = 0;
+  int last_in = 0;                         // deferred list the resolver read in the last super step
 
   // knobs
   int tile_max = kTileMaxCap;

@@ -1103,6 +1103,43 @@ __global__ void __launch_bounds__(NT) k_phase_b_block(StepCtx c, const int32_t* 
   for (int64_t q = blockIdx.x; q < len; q += gridDim.x) phase_b(tm, c, list[q]);
 }
 
+// Trades still deferred after the queued passes: one CTA sorts them and runs
+// them in index order, so every trade they wait on is complete when they run
+// (the earliest deferred trade's predecessors always are).  Normally empty.
+__global__ void __launch_bounds__(kBigThreads) k_resolve(StepCtx c, const int32_t* __restrict__ list,
+                                                         const int64_t* __restrict__ count, int32_t* __restrict__ sorted,
+                                                         int smem_max, char* gws, size_t slice) {
+  extern __shared__ __align__(16) char sbuf[];
+  __shared__ int64_t red[kBigThreads / 32 + 2];
+  __shared__ SelOut sel;
+  BlockTeam<kBigThreads> tm(red);
+  const int64_t len = *count;
+  if (len == 0) return;
+  int64_t P = 1;
+  while (P < len) P <<= 1;
+  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sorted[i] = i < len ? list[i] : 0x7fffffff;
+  __syncthreads();
+  for (int64_t k = 2; k <= P; k <<= 1)
+    for (int64_t j = k >> 1; j > 0; j >>= 1) {
+      for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const int64_t l = i ^ j;
+        if (l > i) {
+          const int32_t x = sorted[i], y = sorted[l];
+          if ((x > y) == ((i & k) == 0)) { sorted[i] = y; sorted[l] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  for (int64_t q = 0; q < len; ++q) {
+    const int64_t t = sorted[q];
+    const TradeRows tr = trade_rows(c, t);
+    const int L = tr.du + tr.dv;
+    char* base = L > smem_max ? gws : sbuf;
+    phase_a(tm, c, t, carve_a(base, L), &sel);
+  }
+  if (threadIdx.x == 0 && *c.def_count != 0) latch(c.err, kErrResolve);
+}
+
 }  // namespace
 
 size_t trade_ws_slice_bytes(int64_t max_trade) {
@@ -1226,27 +1263,17 @@ int super_step(Graph* h) {
   };
   for (int q = 0; q < h->queued_passes; ++q)
     if ((rc = deferred_pass())) return rc;
-  for (;;) {   // rarely: dependency chains longer than the queued passes
-    CB_CUDA(h, cudaMemcpyAsync(h->host_counters, cnt, kCounters * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CB_CUDA(h, cudaStreamSynchronize(s));
-    if (h->host_counters[4 + in] == 0) break;
-    if (passes > 100000) return fail(h, CB_ECHECK, "dependency resolution did not converge");
-    if ((rc = deferred_pass())) return rc;
-  }
-  const int64_t* hc = h->host_counters;
-  h->stats[2] = hc[0];
-  h->stats[3] = hc[1] + hc[2];
-  int64_t used = 1, deferred_total = 0;
-  for (int i = 1; i < kPassSlots && i < passes; ++i) {
-    if (hc[8 + i] == 0) break;
-    deferred_total += hc[8 + i];
-    used = i + 1;
-  }
-  h->stats[1] = deferred_total;
-  h->stats[4] = hc[kCounters - 1];
-  (void)used;
-  passes = used;
-  h->stats[0] = passes;
+  // whatever is still deferred runs in index order on one CTA (no host round trip)
+  c.def_out = h->list_def[1 - in];   // never written: the resolver defers nothing
+  c.def_count = ucnt + kCounters - 2;
+  CB_CUDA(h, cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(big_smem)));
+  k_resolve<<<1, kBigThreads, big_smem, s>>>(c, h->list_def[in], cnt + 4 + in, h->list_def[1 - in], h->smem_max,
+                                             gws, h->ws_slice);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  h->last_passes_queued = passes;
+  h->last_in = in;
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
   // phase B
   if (h->tile_paths & 2) {
