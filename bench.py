@@ -2,7 +2,7 @@
 """Throughput of the global Curveball super step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload n2^25|n2^20|n4096]
+                    [--workload n2^25|n2^20|n2^21|n4096|ensemble]
 
 One "step" is one global super step (Def. "Undirected Global Trade",
 Section 3.3) over the whole graph.  The metric is edge-trades/s = m * steps /
@@ -14,6 +14,12 @@ replica of the graph with its own chain seed: the chain itself does not shard.
 
 --impl reference times the sequential CPU oracle (the reference this project
 is checked against) on a bounded sample of the same workload family.
+
+The line also carries "batched": the ensemble workload (256 independent
+graphs, n log-uniform in [2^10, 2^16], 50 super steps each) run as one batch
+handle (one CUDA-graph launch per super step, autotuned work split) against
+256 sequential plain runs on the same GPU.  --workload ensemble makes that
+the headline of the line.
 """
 import argparse
 import json
@@ -38,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n2^25")
+    ap.add_argument("--batched", type=int, default=1, help="1: add the batched-ensemble comparison to the line")
+    ap.add_argument("--requests", type=int, default=200, help="serving workload: number of requests replayed")
     return ap.parse_args()
 
 
@@ -138,6 +146,299 @@ def config_of(w, g, world):
             "parallelism": "replicas" if world > 1 else "single"}
 
 
+# -------------------------------------------------------------- ensemble
+
+ENSEMBLE_GRAPHS = 256
+ENSEMBLE_STEPS = 50
+ENSEMBLE_NAME = ("ensemble of 256 graphs: n log-uniform in [2^10, 2^16], PLD([4, n/16), gamma in [2, 3]), "
+                 "Havel-Hakimi, seed 1000+i, 50 super steps each")
+
+
+def ensemble_graphs(count=ENSEMBLE_GRAPHS):
+    from paper_1804_08487_gb300 import synth
+    members = [synth.ensemble_member(i) for i in range(count)]
+    graphs = []
+    for w in members:
+        g = w.graph()
+        graphs.append((g.row_ptr, g.col))
+    return graphs, [w.chain_seed for w in members]
+
+
+def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=12, clocks=None):
+    """Batched: one handle, autotuned (its tuning steps are untimed warm-up),
+    CUDA-graph replay, `steps` timed super steps.  Plain: each graph in its
+    own handle, `steps` super steps each, timed one after another (device
+    time summed), with direct launches and with CUDA-graph replay."""
+    import torch
+    from paper_1804_08487_gb300 import cb
+
+    total_m = sum(int(rp[-1]) // 2 for rp, _ in graphs)
+    total_n = sum(len(rp) - 1 for rp, _ in graphs)
+    ens = cb.Ensemble(graphs, seeds, stream=stream)
+    tuned = ens.autotune(tune_steps)
+    ens.set_option("cuda_graph", 1)
+    ens.global_trades(2)
+    ens.sync()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.start()
+    e0.record(stream)
+    ens.global_trades(steps)
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop() if clocks else None
+    batched_ms = e0.elapsed_time(e1)
+    launches = int(ens.stats().get("launches", 0))
+    ens.close()
+
+    def plain(use_graph):
+        total = 0.0
+        for (rp, col), sd in zip(graphs, seeds):
+            c = cb.Curveball(rp, col, sd, stream=stream)
+            c.set_option("cuda_graph", use_graph)
+            c.sync()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.global_trades(steps)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+            c.close()
+        return total
+
+    plain_ms = plain(0)
+    plain_graph_ms = plain(1)
+    et = total_m * steps
+    return {
+        "workload": ENSEMBLE_NAME, "graphs": len(graphs), "n_total": total_n, "m_total": total_m,
+        "steps": steps, "batched_ms": batched_ms, "batched_edge_trades_s": et / (batched_ms / 1e3),
+        "plain_ms": plain_ms, "plain_edge_trades_s": et / (plain_ms / 1e3),
+        "plain_cuda_graph_ms": plain_graph_ms, "plain_cuda_graph_edge_trades_s": et / (plain_graph_ms / 1e3),
+        "speedup_vs_plain": plain_ms / batched_ms, "speedup_vs_plain_cuda_graph": plain_graph_ms / batched_ms,
+        "autotuned": tuned, "batched_launches": launches, "clocks": clk,
+    }
+
+
+def _oracle_member_rate(args):
+    """Oracle edge-trades/s on one graph of the ensemble (a worker process)."""
+    i, steps = args
+    from oracle import Oracle
+    from paper_1804_08487_gb300 import synth
+    w = synth.ensemble_member(i)
+    g = w.graph()
+    o = Oracle(g.row_ptr, g.col, w.chain_seed)
+    t0 = time.perf_counter()
+    o.superstep(steps)
+    return g.m * steps, time.perf_counter() - t0
+
+
+def ensemble_cpu_sample(graphs_sampled=32, steps=5):
+    """The oracle on a bounded sample of the ensemble: the first 32 graphs,
+    5 super steps each, the graphs spread over every host core."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_member_rate, [(i, steps) for i in range(graphs_sampled)], chunksize=1)
+    wall = time.perf_counter() - t0
+    work = sum(r[0] for r in res)
+    return work / wall, cores, (f"oracle on graphs 0..{graphs_sampled - 1} of the ensemble, {steps} super steps "
+                                f"each, {cores} worker processes (wall time incl. graph generation)")
+
+
+def run_ensemble(args):
+    import torch
+    from paper_1804_08487_gb300 import cb
+
+    rank, world, local = dist_env()
+    # the oracle pool starts before this process touches the GPU
+    cpu_v, cpu_cores, cpu_desc = ensemble_cpu_sample() if rank == 0 else (None, None, None)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    graphs, seeds = ensemble_graphs()
+    seeds = [s + 1000003 * rank for s in seeds]   # each replica its own chains
+    stream = torch.cuda.Stream()
+    r = measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, clocks=ClockSampler(local))
+    t_ms = r["batched_ms"]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    # end to end: create from pinned host buffers, the super steps, every
+    # graph's edge list back to pinned host memory
+    rp_all = torch.from_numpy(__import__("numpy").concatenate([g[0] for g in graphs])).pin_memory()
+    col_all = torch.from_numpy(__import__("numpy").concatenate([g[1] for g in graphs])).pin_memory()
+    ns = [len(g[0]) - 1 for g in graphs]
+    out_h = torch.empty(2 * r["m_total"], dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = cb.cb_create_batch(ns, rp_all, col_all, seeds, 0, stream)
+    cb.cb_set_option(h, "cuda_graph", 1)
+    cb.cb_global_trades(h, ENSEMBLE_STEPS)
+    cb.cb_export_edges(h, out_h)
+    cb.cb_sync(h)
+    e2e_s = time.perf_counter() - t0
+    cb.cb_destroy(h)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    K = ENSEMBLE_STEPS
+    b_min = 16 * r["m_total"] + 24 * r["n_total"]
+    gbs = b_min / (t_ms / K / 1e3) / 1e9
+    value = world * r["m_total"] * K / (t_ms / 1e3)
+    line = {
+        "metric": METRIC + " (batched ensemble)", "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": 14, "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": ENSEMBLE_NAME, "graphs": r["graphs"], "n_total": r["n_total"],
+                   "m_total": r["m_total"], "l2": "inputs smaller than L2 are re-read every step (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "whole super step", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"},
+        "batched_vs_plain": r["speedup_vs_plain"],
+        "batched": r,
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_desc},
+        "e2e": {"value": world * r["m_total"] * K / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": (rp_all.numel() * 8 + col_all.numel() * 4) / K,
+                "d2h_bytes_per_step": out_h.numel() * 4 / K},
+        "gpu_launches": r["batched_launches"],
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------- serving
+
+SERVING_REQUESTS = 200
+SERVING_BUDGET = 120 * 10**9
+SERVING_NAME = ("serving: Poisson arrivals (mean 200 req/s), n log-uniform in [2^12, 2^22], PLD([4, n/16], "
+                "gamma in [2, 3]), Havel-Hakimi, 5..50 super steps, seed = request index, 120 GB budget")
+
+
+def _serving_graph(i):
+    from paper_1804_08487_gb300 import synth
+    w = synth.serving_request(i)
+    g = w.graph()
+    return i, g.row_ptr, g.col, w.chain_seed, w.supersteps
+
+
+def serving_requests(count):
+    """Every request's graph, generated on all host cores (spawn pool, before
+    any GPU work of this process)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+        out = pool.map(_serving_graph, range(count), chunksize=1)
+    return sorted(out)
+
+
+def measure_serving(reqs, arrivals, budget=SERVING_BUDGET, max_active=64, depth=2, clocks=None):
+    """Replay the arrivals into the serving loop: a thread submits request i
+    at arrival time i; latency = finished - submitted (the server's clock)."""
+    import threading
+    import numpy as np
+    from paper_1804_08487_gb300 import cb
+
+    srv = cb.Server(budget, max_active=max_active, depth=depth)
+    t0 = time.perf_counter()
+    ids = {}
+
+    def submitter():
+        for (i, rp, col, seed, steps), at in zip(reqs, arrivals):
+            delay = t0 + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids[srv.submit(rp, col, seed, steps)] = i
+
+    if clocks:
+        clocks.start()
+    th = threading.Thread(target=submitter)
+    th.start()
+    results = {}
+    while len(results) < len(reqs):
+        for rid in srv.poll(timeout_ms=200):
+            edges, times = srv.result(rid)
+            results[rid] = (times, edges)
+    th.join()
+    clk = clocks.stop() if clocks else None
+    st = srv.stats()
+    srv.close()
+    lat = np.array([results[r][0][3] - results[r][0][0] for r in sorted(results)])
+    first = min(results[r][0][0] for r in results)
+    last = max(results[r][0][3] for r in results)
+    work = sum(int(rp[-1]) // 2 * steps for _, rp, _, _, steps in reqs)
+    by_index = {ids[r]: results[r][1] for r in results}
+    return {
+        "requests": len(reqs), "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+        "mean_s": float(lat.mean()), "max_s": float(lat.max()), "makespan_s": last - first,
+        "edge_trades": work, "edge_trades_s": work / (last - first),
+        "reserved_peak_bytes": st.get("reserved_peak_bytes"), "steps_issued": st.get("steps_issued"),
+        "failed": st.get("failed"), "clocks": clk,
+    }, by_index
+
+
+def measure_plain_sequential(reqs, results=None):
+    """The same requests one at a time through plain handles (create, super
+    steps, export), wall time; optionally checks each edge list against the
+    served one."""
+    import numpy as np
+    from paper_1804_08487_gb300 import cb
+    total = 0.0
+    same = True
+    for i, rp, col, seed, steps in reqs:
+        t = time.perf_counter()
+        c = cb.Curveball(rp, col, seed)
+        c.global_trades(steps)
+        e = c.edges()
+        c.close()
+        total += time.perf_counter() - t
+        if results is not None:
+            same &= bool(np.array_equal(e, results[i]))
+    work = sum(int(rp[-1]) // 2 * steps for _, rp, _, _, steps in reqs)
+    return {"seconds": total, "edge_trades_s": work / total, "served_equal_alone": same if results else None}
+
+
+def run_serving(args):
+    import torch
+    from paper_1804_08487_gb300 import synth
+
+    rank, world, local = dist_env()
+    count = args.requests
+    reqs = serving_requests(count)
+    arrivals = synth.serving_arrivals(count)
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    served, by_index = measure_serving(reqs, arrivals, clocks=ClockSampler(local))
+    plain = measure_plain_sequential(reqs, by_index)
+    line = {
+        "metric": METRIC + " (serving)", "value": served["edge_trades_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": sum(r[4] for r in reqs), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": SERVING_NAME, "requests": count, "budget_bytes": SERVING_BUDGET,
+                   "max_active": 64, "depth": 2, "parallelism": "single"},
+        "latency": {"p50_s": served["p50_s"], "p99_s": served["p99_s"], "mean_s": served["mean_s"],
+                    "max_s": served["max_s"]},
+        "serving": served, "plain_sequential": plain,
+        "served_vs_plain": served["edge_trades_s"] / plain["edge_trades_s"],
+        "e2e": {"value": served["edge_trades_s"], "unit": UNIT,
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+        "clocks": served["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args):
@@ -209,6 +510,10 @@ def run_ours(args):
         e2e_max = float(tt.item())
     h2d = (g.row_ptr.nbytes + g.col.nbytes) / args.steps
     d2h = (2 * g.m * 4) / args.steps
+    batched = None
+    if args.batched:
+        graphs, seeds = ensemble_graphs()
+        batched = measure_ensemble(graphs, seeds, stream)
 
     if rank != 0:
         if world > 1:
@@ -245,6 +550,8 @@ def run_ours(args):
                               "rebuild": phase_ms["rebuild"], "step": phases["step_ms"] / K},
         "dependency_passes_last_step": stats.get("passes"),
     }
+    if batched is not None:
+        line["batched"] = batched
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -256,6 +563,18 @@ def run_ours(args):
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload == "ensemble":
+        value, cores, sample = ensemble_cpu_sample()
+        line = {
+            "impl": "reference", "metric": METRIC + " (batched ensemble)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": 5, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": ENSEMBLE_NAME, "sample": "graphs 0..31", "parallelism": "host processes"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
         return
     w = workload(args.workload)
     from paper_1804_08487_gb300 import synth
@@ -287,6 +606,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -73,6 +73,45 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
               uint64_t first_step, int mem_kind, void* cuda_stream, cb_handle* out);
 
 /*
+ * Create one state holding `count` independent graphs (an ensemble), each
+ * randomised by its own chain exactly as cb_create would do for it alone:
+ * graph i with its own seed; its node ids, permutation and shuffle keys are
+ * local to it.  A super step (cb_global_trades) advances every graph by one
+ * global trade in the same launches.  Section 3.3's odd-n rule holds per
+ * graph: the node at a graph's last position is not traded.
+ *   count      number of graphs, >= 1.
+ *   n          host array of count node counts (n_i >= 0, sum < 2^31).
+ *   row_ptr    the graphs' CSR offsets one after another: n_0+1 values for
+ *              graph 0 (starting at 0), then n_1+1 for graph 1, ...
+ *   col        the graphs' neighbour ids one after another (row_ptr_i[n_i]
+ *              local ids in [0, n_i) for graph i); each graph simple and
+ *              symmetric as for cb_create.
+ *   seeds      host array of count seeds.
+ *   first_step index of the first super step, shared by every graph.
+ *   mem_kind   where row_ptr and col live; n and seeds are host arrays.
+ *   cuda_stream, out as for cb_create.
+ * Synchronises.  cb_info reports the totals (n counts one padding node per
+ * odd graph); cb_graph_info each graph.
+ */
+int cb_create_batch(int32_t count, const int64_t* n, const int64_t* row_ptr, const int32_t* col,
+                    const uint64_t* seeds, uint64_t first_step, int mem_kind, void* cuda_stream,
+                    cb_handle* out);
+
+/* Number of graphs of the handle (1 for cb_create); negative on error. */
+int cb_graph_count(cb_handle h);
+
+/* Nodes and undirected edges of graph `index` of the handle. */
+int cb_graph_info(cb_handle h, int32_t index, int64_t* n, int64_t* m);
+
+/*
+ * Export graph `index` of the handle as its canonical edge list (local ids,
+ * same format and rules as cb_export_edges).  Exporting several graphs after
+ * the same super step computes the edge lists once.  Synchronises.
+ */
+int cb_export_graph(cb_handle h, int32_t index, int32_t* edges, int64_t capacity_pairs, int64_t* m_out,
+                    int mem_kind);
+
+/*
  * Run `supersteps` global trades (Def. "Undirected Global Trade").
  * Super step g (g counts from first_step):
  *   - permutation: node x gets key philox64(seed; x, 0, g, 0), nodes are
@@ -95,7 +134,8 @@ int cb_global_trades(cb_handle h, uint32_t supersteps);
  * a < b in lexicographic order (Section 2 "ordered edges"), written as 2m
  * int32 values a0, b0, a1, b1, ... into `edges` (mem_kind says where).
  * edges == NULL: only *m_out is set.  capacity_pairs < m: CB_ESIZE and *m_out
- * is set.  Synchronises the handle's stream.
+ * is set.  For a handle of several graphs: every graph's list in turn, local
+ * ids, m = the total.  Synchronises the handle's stream.
  */
 int cb_export_edges(cb_handle h, int32_t* edges, int64_t capacity_pairs, int64_t* m_out,
                     int mem_kind);
@@ -112,19 +152,22 @@ int cb_sync(cb_handle h);
 /* Description of the last error on this handle ("" if none; NULL handle: global). */
 const char* cb_last_error(cb_handle h);
 
-/* Number of nodes and undirected edges. */
+/* Number of nodes and undirected edges (over every graph of the handle). */
 int cb_info(cb_handle h, int64_t* n, int64_t* m);
 
 /*
  * The permutation pi of super step g (Def. "Undirected Global Trade"):
  * order_out[p] = node at position p (n int32, mem_kind says where).  Does not
- * change the state.  Synchronises the handle's stream.
+ * change the state.  For several graphs: each graph's permutation at step g
+ * over its own range of the handle's node ids.  Synchronises the handle's
+ * stream.
  */
 int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
 
 /*
  * Counters of the last cb_global_trades call, for tests and tuning
- * (synchronises the handle's stream):
+ * (synchronises the handle's stream; out[5] counts the kernels inside the
+ * CUDA graphs replayed when "cuda_graph" is on):
  * out[0] = dependency-resolution passes of the last super step (the final
  *          in-order pass counts as one),
  * out[1] = trades deferred to a later pass (summed over its passes),
@@ -149,7 +192,12 @@ int cb_timings(cb_handle h, double* ms, int count);
 
 /*
  * Tuning / test knobs (key, value); returns CB_EINVAL for an unknown key or a
- * value out of range.  Trade size = deg u + deg v.
+ * value out of range.  None changes any result.  Trade size = deg u + deg v.
+ *   "cuda_graph" 1: record one super step (per ping-pong parity) as a CUDA
+ *               graph on the first cb_global_trades call and replay it, one
+ *               graph launch per super step [0].  Not while "timing" is on.
+ *               The handle's stream must support capture (not the legacy
+ *               default stream).  Changing any other option re-records.
  *   "tile_max"  trades up to this size run on the flat tile path (one
  *               thread per entry, many trades per CTA) [128]; 0..128.
  *   "tile_paths" bit 0: threshold phase of tile-path trades on the tile
@@ -195,6 +243,16 @@ int cb_set_option(cb_handle h, const char* key, int64_t value);
  * cb_last_error(NULL).
  */
 int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_out, void* cuda_stream);
+
+/*
+ * Pick the fastest work split for this handle: runs up to max_steps real
+ * super steps (they advance the chain; the result does not depend on the
+ * options), each under one candidate setting of "tile_max", "block_max" and
+ * "queued_passes", timed with CUDA events, and keeps the fastest.  chosen
+ * (may be NULL) receives up to `count` values: tile_max, block_max,
+ * queued_passes, super steps used.  Returns the number of values written.
+ */
+int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count);
 
 #ifdef __cplusplus
 }

@@ -88,7 +88,7 @@ def build_cuda(force: bool = False, verbose_ptxas: bool = False) -> Path:
         for _, err in results:
             print(err)
     objs = [str(o) for o, _ in results]
-    _atomic_build(out, lambda tmp: _run(["nvcc", "-shared"] + NVCC_ARCH + ["-o", tmp] + objs))
+    _atomic_build(out, lambda tmp: _run(["nvcc", "-shared"] + NVCC_ARCH + ["-o", tmp] + objs + ["-lpthread"]))
     return out
 
 

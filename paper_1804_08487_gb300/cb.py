@@ -35,10 +35,12 @@ class CbError(RuntimeError):
 
 
 def declared_functions():
-    """Names of the functions declared in include/cb.h."""
-    text = (Path(INCLUDE) / "cb.h").read_text()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(cb_[a-z_0-9]+)\s*\(", text)))
+    """Names of the functions declared in include/*.h."""
+    names = set()
+    for hdr in sorted(Path(INCLUDE).glob("*.h")):
+        text = re.sub(r"/\*.*?\*/", "", hdr.read_text(), flags=re.S)
+        names |= set(re.findall(r"\b(cb_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def load():
@@ -76,6 +78,32 @@ def load():
     lib.cb_timings.argtypes = [vp, C.POINTER(C.c_double), i32]
     lib.cb_set_option.restype = i32
     lib.cb_set_option.argtypes = [vp, C.c_char_p, i64]
+    lib.cb_create_batch.restype = i32
+    lib.cb_create_batch.argtypes = [i32, vp, vp, vp, vp, u64, i32, vp, C.POINTER(vp)]
+    lib.cb_graph_count.restype = i32
+    lib.cb_graph_count.argtypes = [vp]
+    lib.cb_graph_info.restype = i32
+    lib.cb_graph_info.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
+    lib.cb_export_graph.restype = i32
+    lib.cb_export_graph.argtypes = [vp, i32, vp, i64, C.POINTER(i64), i32]
+    lib.cb_autotune.restype = i32
+    lib.cb_autotune.argtypes = [vp, u32, C.POINTER(i64), i32]
+    lib.cb_device_bytes.restype = i32
+    lib.cb_device_bytes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    lib.cb_estimate_bytes.restype = i64
+    lib.cb_estimate_bytes.argtypes = [i64, i64, i64]
+    lib.cb_server_create.restype = i32
+    lib.cb_server_create.argtypes = [i64, i32, i32, C.POINTER(vp)]
+    lib.cb_server_submit.restype = i32
+    lib.cb_server_submit.argtypes = [vp, i64, vp, vp, u64, u32, C.POINTER(i64)]
+    lib.cb_server_poll.restype = i32
+    lib.cb_server_poll.argtypes = [vp, C.POINTER(i64), i32, i32]
+    lib.cb_server_result.restype = i32
+    lib.cb_server_result.argtypes = [vp, i64, vp, i64, C.POINTER(i64), C.POINTER(C.c_double)]
+    lib.cb_server_stats.restype = i32
+    lib.cb_server_stats.argtypes = [vp, C.POINTER(i64), i32]
+    lib.cb_server_destroy.restype = None
+    lib.cb_server_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -115,6 +143,59 @@ def cb_create(n, row_ptr, col, seed, first_step=0, stream=None):
     _check(lib.cb_create(n, rp, cp, C.c_uint64(seed & (2**64 - 1)), C.c_uint64(first_step), kind_rp, s,
                          C.byref(h)))
     return h
+
+
+def cb_create_batch(ns, row_ptr, col, seeds, first_step=0, stream=None):
+    """Handle for an ensemble: ns[i] nodes per graph, row_ptr = every graph's
+    n_i+1 offsets one after another, col = every graph's entries (local ids)
+    one after another, seeds[i] per graph."""
+    lib = load()
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    if isinstance(row_ptr, np.ndarray):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+    rp, kind_rp, keep_rp = _ptr(row_ptr)
+    cp, kind_c, keep_c = _ptr(col)
+    if cp is not None and kind_rp != kind_c:
+        raise ValueError("row_ptr and col must live in the same memory")
+    h = C.c_void_p()
+    s = None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib.cb_create_batch(len(ns), ns.ctypes.data, rp, cp, seeds.ctypes.data, C.c_uint64(first_step),
+                               kind_rp, s, C.byref(h)))
+    return h
+
+
+def cb_graph_count(h) -> int:
+    return _check(load().cb_graph_count(h), h)
+
+
+def cb_graph_info(h, index: int):
+    n, m = C.c_int64(0), C.c_int64(0)
+    _check(load().cb_graph_info(h, index, C.byref(n), C.byref(m)), h)
+    return n.value, m.value
+
+
+def cb_export_graph(h, index: int, out=None):
+    """Canonical edge list of graph `index` (local ids), as cb_export_edges."""
+    lib = load()
+    m = C.c_int64(0)
+    _check(lib.cb_export_graph(h, index, None, 0, C.byref(m), CB_HOST), h)
+    if out is None:
+        arr = np.zeros((m.value, 2), dtype=np.int32)
+        if m.value:
+            _check(lib.cb_export_graph(h, index, arr.ctypes.data, m.value, C.byref(m), CB_HOST), h)
+        return arr
+    p, kind, _ = _ptr(out)
+    _check(lib.cb_export_graph(h, index, p, out.numel() // 2, C.byref(m), kind), h)
+    return out
+
+
+def cb_autotune(h, max_steps: int):
+    out = (C.c_int64 * 4)()
+    k = _check(load().cb_autotune(h, max_steps, out, 4), h)
+    names = ["tile_max", "block_max", "queued_passes", "steps"]
+    return {names[i]: out[i] for i in range(k)}
 
 
 def cb_global_trades(h, supersteps: int):
@@ -226,6 +307,9 @@ class Curveball:
     def set_option(self, key, value):
         cb_set_option(self.h, key, value)
 
+    def autotune(self, max_steps: int):
+        return cb_autotune(self.h, max_steps)
+
     def sync(self):
         cb_sync(self.h)
 
@@ -233,6 +317,114 @@ class Curveball:
         if getattr(self, "h", None):
             cb_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble(Curveball):
+    """Owning wrapper around a handle of many independent graphs.
+
+    `graphs` is a list of (row_ptr int64[n_i+1], col int32[...]) numpy pairs
+    and `seeds` one seed per graph; they are passed to the library one after
+    another (cb_create_batch)."""
+
+    def __init__(self, graphs, seeds, first_step=0, stream=None):
+        ns = [len(rp) - 1 for rp, _ in graphs]
+        row_ptr = np.concatenate([np.asarray(rp, dtype=np.int64) for rp, _ in graphs])
+        col = np.concatenate([np.asarray(c, dtype=np.int32) for _, c in graphs] + [np.zeros(0, np.int32)])
+        self.h = cb_create_batch(ns, row_ptr, col, seeds, first_step, stream)
+
+    def __len__(self):
+        return cb_graph_count(self.h)
+
+    def info(self, index: int):
+        return cb_graph_info(self.h, index)
+
+    def graph_edges(self, index: int, out=None):
+        return cb_export_graph(self.h, index, out)
+
+
+def cb_device_bytes(h):
+    now, peak = C.c_int64(0), C.c_int64(0)
+    _check(load().cb_device_bytes(h, C.byref(now), C.byref(peak)), h)
+    return now.value, peak.value
+
+
+def cb_estimate_bytes(n: int, nnz: int, max_degree: int) -> int:
+    return _check(load().cb_estimate_bytes(n, nnz, max_degree))
+
+
+def cb_server_create(hbm_budget_bytes: int, max_active: int = 64, depth: int = 2):
+    s = C.c_void_p()
+    _check(load().cb_server_create(int(hbm_budget_bytes), max_active, depth, C.byref(s)))
+    return s
+
+
+def cb_server_submit(s, row_ptr, col, seed: int, supersteps: int) -> int:
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    rid = C.c_int64(0)
+    _check(load().cb_server_submit(s, len(rp) - 1, rp.ctypes.data, cl.ctypes.data if cl.size else None,
+                                   C.c_uint64(seed & (2**64 - 1)), supersteps, C.byref(rid)))
+    return rid.value
+
+
+def cb_server_poll(s, timeout_ms: int = 0, capacity: int = 1024):
+    buf = (C.c_int64 * capacity)()
+    k = _check(load().cb_server_poll(s, buf, capacity, timeout_ms))
+    return [buf[i] for i in range(k)]
+
+
+def cb_server_result(s, rid: int):
+    """(edges int32 (m, 2), times [submitted, admitted, resident, finished]);
+    raises CbError if the request failed.  Releases the request."""
+    lib = load()
+    m = C.c_int64(0)
+    t = (C.c_double * 4)()
+    _check(lib.cb_server_result(s, rid, None, 0, C.byref(m), t))
+    arr = np.zeros((max(m.value, 1), 2), dtype=np.int32)
+    _check(lib.cb_server_result(s, rid, arr.ctypes.data, m.value, C.byref(m), t))
+    return arr[:m.value], [t[i] for i in range(4)]
+
+
+def cb_server_stats(s):
+    out = (C.c_int64 * 8)()
+    k = _check(load().cb_server_stats(s, out, 8))
+    names = ["submitted", "queued", "resident", "finished", "reserved_bytes", "reserved_peak_bytes",
+             "steps_issued", "failed"]
+    return {names[i]: out[i] for i in range(k)}
+
+
+def cb_server_destroy(s):
+    load().cb_server_destroy(s)
+
+
+class Server:
+    """Owning wrapper around the serving loop (include/cb_serve.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, depth: int = 2):
+        self.s = cb_server_create(hbm_budget_bytes, max_active, depth)
+
+    def submit(self, row_ptr, col, seed: int, supersteps: int) -> int:
+        return cb_server_submit(self.s, row_ptr, col, seed, supersteps)
+
+    def poll(self, timeout_ms: int = 0, capacity: int = 1024):
+        return cb_server_poll(self.s, timeout_ms, capacity)
+
+    def result(self, rid: int):
+        return cb_server_result(self.s, rid)
+
+    def stats(self):
+        return cb_server_stats(self.s)
+
+    def close(self):
+        if getattr(self, "s", None):
+            cb_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

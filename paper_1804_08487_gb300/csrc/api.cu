@@ -35,11 +35,25 @@ unsigned grid1d(int64_t work, int num_sms) {
   return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(num_sms) * 16)));
 }
 
+// Device memory of a handle is stream-ordered (the device's memory pool, on
+// the handle's stream): creating and destroying handles never waits for work
+// of other streams, so many handles can come and go while others run.
+cudaError_t dmalloc(Graph* h, void** p, size_t bytes) {
+  const cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
+  if (e == cudaSuccess) {
+    h->dev_bytes += static_cast<int64_t>(bytes);
+    h->dev_bytes_peak = std::max(h->dev_bytes_peak, h->dev_bytes);
+  }
+  return e;
+}
 template <class T>
-cudaError_t dalloc(T** p, int64_t count) {
+cudaError_t dalloc(Graph* h, T** p, int64_t count) {
   *p = nullptr;
   if (count <= 0) count = 1;
-  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * static_cast<size_t>(count));
+  return dmalloc(h, reinterpret_cast<void**>(p), sizeof(T) * static_cast<size_t>(count));
+}
+void dfree(Graph* h, void* p) {
+  if (p) cudaFreeAsync(p, h->stream);
 }
 
 void release(Graph* h) {
@@ -49,10 +63,13 @@ void release(Graph* h) {
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
                   h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
                   h->list_def[0], h->list_def[1], h->counters, h->err,
-                  h->ws_global, h->sort_ws, h->scan_ws};
-  for (void* b : bufs)
-    if (b) cudaFree(b);
-  if (h->host_counters) cudaFreeHost(h->host_counters);
+                  h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs};
+  if (h->stream)
+    for (void* b : bufs) dfree(h, b);
+  for (auto& x : h->step_exec)
+    if (x) cudaGraphExecDestroy(x);
+  delete[] h->hsegs;
+  delete[] h->host_counters;
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -72,7 +89,8 @@ int check_device_error(Graph* h) {
 
 int size_trade_workspace(Graph* h) {
   if (h->ws_global) {
-    cudaFree(h->ws_global);
+    dfree(h, h->ws_global);
+    h->dev_bytes -= static_cast<int64_t>(h->ws_slice * h->ws_ctas);
     h->ws_global = nullptr;
   }
   const int64_t max_trade = 2 * h->maxdeg;
@@ -82,7 +100,7 @@ int size_trade_workspace(Graph* h) {
     h->ws_slice = trade_ws_slice_bytes(std::max<int64_t>(max_trade, 1));
     const size_t budget = size_t(2) << 30;
     h->ws_ctas = static_cast<int>(std::max<size_t>(1, std::min<size_t>(h->num_sms * 2, budget / h->ws_slice)));
-    CB_CUDA(h, cudaMalloc(&h->ws_global, h->ws_slice * h->ws_ctas));
+    CB_CUDA(h, dmalloc(h, &h->ws_global, h->ws_slice * h->ws_ctas));
   }
   return CB_OK;
 }
@@ -103,6 +121,250 @@ int cuda_fail(Graph* g, cudaError_t e, const char* what) {
 
 }  // namespace cb
 
+namespace cb {
+namespace {
+
+// Batch input: graph i's offsets start at rp_in + rpo[i] (n_i + 1 values, the
+// first 0) and its entries, local ids, sit at the same entry offsets in col
+// (padding nodes have no entries).  Builds the combined id-space offsets and
+// adds each graph's first node id to its entries.
+__global__ void k_batch_offsets(int64_t N, const Seg* __restrict__ segs, const int32_t* __restrict__ seg_of,
+                                const int64_t* __restrict__ rp_in, const int64_t* __restrict__ rpo,
+                                const int64_t* __restrict__ eoff, int64_t nnz, int64_t* __restrict__ rp,
+                                int32_t* err) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x <= N; x += int64_t(gridDim.x) * blockDim.x) {
+    if (x == N) {
+      rp[N] = nnz;
+      continue;
+    }
+    const int i = seg_of[x];
+    const int64_t l = x - segs[i].off, n = segs[i].n;
+    const int64_t v = rp_in[rpo[i] + (l < n ? l : n)];
+    if (l == 0 && v != 0) atomicCAS(err, 0, static_cast<int32_t>(kErrValidate));
+    rp[x] = eoff[i] + v;
+  }
+}
+
+__global__ void k_batch_cols(int64_t N, const Seg* __restrict__ segs, const int32_t* __restrict__ seg_of,
+                             const int64_t* __restrict__ rp, int32_t* __restrict__ col, int32_t* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < N; x += nw) {
+    const Seg& S = segs[seg_of[x]];
+    const int32_t off = static_cast<int32_t>(S.off), n = static_cast<int32_t>(S.n);
+    for (int64_t e = rp[x] + lane; e < rp[x + 1]; e += 32) {
+      const int32_t y = col[e];
+      if (y < 0 || y >= n) atomicCAS(err, 0, static_cast<int32_t>(kErrValidate));
+      col[e] = y + off;
+    }
+  }
+}
+
+__global__ void k_fill_seg_of(int64_t N, const Seg* __restrict__ segs, int nseg, int32_t* __restrict__ seg_of) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < N; x += int64_t(gridDim.x) * blockDim.x) {
+    int lo = 0, hi = nseg;   // last segment with off <= x
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (segs[mid].off <= x) lo = mid; else hi = mid;
+    }
+    seg_of[x] = lo;
+  }
+}
+
+Graph* new_graph(void* cuda_stream, int* rc) {
+  *rc = CB_OK;
+  cb_graph* h = new (std::nothrow) cb_graph();
+  if (!h) {
+    *rc = fail(nullptr, CB_ENOMEM, "host allocation failed");
+    return nullptr;
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+      h->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e != cudaSuccess) {
+    *rc = cuda_fail(nullptr, e, "device set-up");
+    delete h;
+    return nullptr;
+  }
+  return h;
+}
+
+void destroy_graph(Graph* h) {
+  release(h);
+  delete static_cast<cb_graph*>(h);
+}
+
+// Common part of handle creation.  On entry: n, nnz, the segment table (host
+// and device, seg_of for batches) and the id-space CSR (rp_id, col[0],
+// unsorted rows) are in place.  Validates, sizes the workspaces and lays the
+// graph out for its first super step.
+int finish_create(Graph* h) {
+  const int64_t n = h->n, nnz = h->nnz;
+  cudaStream_t s = h->stream;
+  int rc;
+  h->m = nnz / 2;
+  h->T = n / 2;
+  h->ntasks = h->T + (n & 1);
+  if ((rc = init_trade_kernels(h))) return rc;
+  if ((rc = check_row_offsets(h, h->rp_id, n))) return rc;
+  {
+    unsigned long long* dmax = reinterpret_cast<unsigned long long*>(h->counters);
+    CB_CUDA(h, cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s));
+    if (n) k_degrees<<<grid1d(n, h->num_sms), 256, 0, s>>>(n, h->rp_id, h->deg_id, dmax);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    unsigned long long hm = 0;
+    CB_CUDA(h, cudaMemcpyAsync(&hm, dmax, sizeof(hm), cudaMemcpyDeviceToHost, s));
+    if ((rc = check_device_error(h))) {
+      h->last_error = "row_ptr is not a valid CSR offset array (degrees in [0, n), ids in range)";
+      return CB_EINVAL;
+    }
+    h->maxdeg = static_cast<int64_t>(hm);
+  }
+  h->sort_ws_bytes = perm_ws_bytes(std::max<int64_t>(n, 1), h->nbuckets);
+  h->scan_ws_bytes = scan_ws_bytes(std::max<int64_t>(n + 1, h->nbuckets + 1));
+  int64_t def_cap = 1;   // the in-order resolver bitonic-sorts a deferred list padded to a power of two
+  while (def_cap < h->ntasks) def_cap <<= 1;
+  if (dalloc(h, &h->order[0], n) || dalloc(h, &h->order[1], n) || dalloc(h, &h->rp[0], n + 1) || dalloc(h, &h->rp[1], n + 1) ||
+      dalloc(h, &h->pos_next, n) || dalloc(h, &h->M, n) || dalloc(h, &h->deg_next, n) || dalloc(h, &h->stash, nnz) ||
+      dalloc(h, &h->thr_key, h->ntasks) || dalloc(h, &h->thr_tb, h->ntasks) || dalloc(h, &h->done, h->ntasks) ||
+      dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->list[0], h->ntasks) || dalloc(h, &h->list[1], h->ntasks) ||
+      dalloc(h, &h->list[2], h->ntasks) || dalloc(h, &h->tile_off, h->ntasks) || dalloc(h, &h->tile_first, h->ntasks + 2) ||
+      dalloc(h, &h->cls_flag, 4 * h->ntasks) || dalloc(h, &h->cls_scan, 4 * (h->ntasks + 1)) ||
+      dalloc(h, &h->list_def[0], def_cap) || dalloc(h, &h->list_def[1], def_cap) ||
+      dmalloc(h, &h->sort_ws, h->sort_ws_bytes) || dmalloc(h, &h->scan_ws, h->scan_ws_bytes))
+    return fail(h, CB_ENOMEM, "device allocation failed");
+  CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
+  if ((rc = size_trade_workspace(h))) return rc;
+  // sort every row (id space) into col[1] and validate: simple and symmetric
+  if ((rc = permute_rows(h, n, h->rp_id, h->col[0], nullptr, nullptr, h->rp_id, h->col[1]))) return rc;
+  if ((rc = validate_sorted_graph(h, h->rp_id, h->col[1], n))) return rc;
+  if ((rc = check_device_error(h))) {
+    h->last_error = "graph is not simple and symmetric";
+    return CB_EINVAL;
+  }
+  // position-space layout of the first super step
+  h->cur = 0;
+  if ((rc = compute_permutation(h, 0, -1, h->order[0], h->pos_next))) return rc;
+  if (n) k_gather_deg<<<grid1d(n, h->num_sms), 256, 0, s>>>(n, h->order[0], h->deg_id, h->deg_next);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  CB_CUDA(h, exclusive_scan_i32(h->deg_next, h->rp[0], n, h->scan_ws, s, &h->launches));
+  if ((rc = permute_rows(h, n, h->rp_id, h->col[1], h->order[0], h->pos_next, h->rp[0], h->col[0]))) return rc;
+  return check_device_error(h);
+}
+
+void drop_step_graphs(Graph* h) {
+  for (auto& x : h->step_exec)
+    if (x) {
+      cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+}
+
+// Records one super step per ping-pong parity into a CUDA graph.  A super
+// step has no host round trip and reads every per-step value (step counters,
+// counts) from device memory, so replaying the two graphs alternately is the
+// same as calling super_step.  Host state is left as it was.
+int capture_step_graphs(Graph* h) {
+  const int cur0 = h->cur;
+  const uint64_t g0 = h->g;
+  const int64_t l0 = h->launches;
+  int rc = CB_OK;
+  for (int p = 0; p < 2 && rc == CB_OK; ++p) {
+    h->cur = p;
+    const int64_t lb = h->launches;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(h, e, "cudaStreamBeginCapture");
+      break;
+    }
+    rc = super_step(h);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(h->stream, &gr);
+    h->step_launches = h->launches - lb;
+    if (rc == CB_OK && e != cudaSuccess) rc = cuda_fail(h, e, "cudaStreamEndCapture");
+    if (rc == CB_OK) {
+      e = cudaGraphInstantiate(&h->step_exec[p], gr, 0);
+      if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    if (gr) cudaGraphDestroy(gr);
+    h->cur = cur0;
+    h->g = g0;
+  }
+  h->launches = l0;
+  if (rc) drop_step_graphs(h);
+  return rc;
+}
+
+// Every graph's canonical pairs (local ids) of the current step in h->pairs.
+int ensure_pairs(Graph* h) {
+  if (h->pairs && h->pairs_step == h->g) return CB_OK;
+  if (!h->pairs && dalloc(h, &h->pairs, 2 * std::max<int64_t>(h->m, 1)))
+    return fail(h, CB_ENOMEM, "device allocation failed");
+  int rc;
+  const int spare = 1 - h->cur;
+  if ((rc = invert_permutation(h, h->order[h->cur], h->pos_next))) return rc;
+  if ((rc = permute_rows(h, h->n, h->rp[h->cur], h->col[h->cur], h->pos_next, h->order[h->cur], h->rp_id,
+                         h->col[spare])))
+    return rc;
+  if ((rc = export_pairs(h, h->rp_id, h->col[spare], h->pairs))) return rc;
+  if ((rc = check_device_error(h))) return rc;
+  h->pairs_step = h->g;
+  return CB_OK;
+}
+
+int copy_pairs(Graph* h, int64_t first, int64_t count, int32_t* edges, int mem_kind) {
+  if (count == 0) return CB_OK;
+  CB_CUDA(h, cudaMemcpyAsync(edges, h->pairs + 2 * first, sizeof(int32_t) * 2 * count,
+                             mem_kind == CB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+  CB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return CB_OK;
+}
+
+int upload_segs(Graph* h) {
+  CB_CUDA(h, cudaMemcpyAsync(h->segs, h->hsegs, sizeof(Seg) * h->nseg, cudaMemcpyHostToDevice, h->stream));
+  return CB_OK;
+}
+
+}  // namespace
+
+int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sms) {
+  // mirrors the allocations of cb_create + finish_create + size_trade_workspace
+  // + a host export's temporary pairs (2m int32)
+  const int64_t ntasks = n / 2 + (n & 1);
+  int64_t def_cap = 1;
+  while (def_cap < ntasks) def_cap <<= 1;
+  const int64_t nb = int64_t(1) << bucket_bits(n);
+  int64_t b = 0;
+  b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * nnz + 32 + 8 * kCounters;             // cb_create
+  b += 2 * 4 * n + 2 * 8 * (n + 1) + 3 * 4 * n + nnz;                                     // per node, stash
+  b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 16 + 32) + 4 * (ntasks + 2) + 32 + 2 * 4 * def_cap;
+  b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
+  const int64_t max_trade = 2 * maxdeg;
+  if (max_trade > kSmemMaxCap || maxdeg > 16384) {
+    const size_t slice = trade_ws_slice_bytes(std::max<int64_t>(max_trade, 1));
+    const size_t ctas = std::max<size_t>(1, std::min<size_t>(num_sms * 2, (size_t(2) << 30) / slice));
+    b += static_cast<int64_t>(slice * ctas);
+  }
+  b += 4 * std::max<int64_t>(nnz, 2);
+  return b + b / 64 + (int64_t(16) << 20);   // pool rounding and per-allocation slack
+}
+
+int prepare_step_graphs(Graph* h) {
+  if (!h->use_graph || h->step_exec[0]) return CB_OK;
+  return capture_step_graphs(h);
+}
+
+}  // namespace cb
+
 using namespace cb;
 
 extern "C" {
@@ -114,23 +376,14 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
   if (n < 0 || n > 0x7fffffffLL || !row_ptr || (mem_kind != CB_HOST && mem_kind != CB_DEVICE))
     return fail(nullptr, CB_EINVAL, "bad n, row_ptr or mem_kind");
   if (first_step >= 0xfffffffeull) return fail(nullptr, CB_ERANGE, "first_step too large");
-  cb_graph* h = new (std::nothrow) cb_graph();
-  if (!h) return fail(nullptr, CB_ENOMEM, "host allocation failed");
-  auto bail = [&](int rc) {
+  int rc;
+  Graph* h = new_graph(cuda_stream, &rc);
+  if (!h) return rc;
+  auto bail = [&](int code) {
     g_error = h->last_error;
-    release(h);
-    delete h;
-    return rc;
+    destroy_graph(h);
+    return code;
   };
-  CB_CUDA(h, cudaGetDevice(&h->device)) ;
-  CB_CUDA(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
-  if (cuda_stream) {
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {
-    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
-      return bail(fail(h, CB_ECUDA, "stream creation failed"));
-    h->own_stream = true;
-  }
   const cudaMemcpyKind kind = mem_kind == CB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   int64_t ends[2] = {0, 0};
   if (mem_kind == CB_HOST) {
@@ -146,67 +399,154 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
     return bail(fail(h, CB_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] even, < 2^33"));
   h->n = n;
   h->nnz = nnz;
-  h->m = nnz / 2;
-  h->T = n / 2;
-  h->ntasks = h->T + (n & 1);
   h->seed = seed;
   h->g = first_step;
+  h->nseg = 1;
+  h->hsegs = new (std::nothrow) Seg[1];
+  if (!h->hsegs) return bail(fail(h, CB_ENOMEM, "host allocation failed"));
+  {
+    Seg& S = h->hsegs[0];
+    S = Seg{};
+    S.seed = seed;
+    S.n = S.span = n;
+    S.m = nnz / 2;
+    S.g = static_cast<uint32_t>(first_step);
+    S.B = bucket_bits(n);
+    h->nbuckets = int64_t(1) << S.B;
+  }
   cudaStream_t s = h->stream;
-  int rc;
-  if (dalloc(&h->rp_id, n + 1) || dalloc(&h->deg_id, n) || dalloc(&h->col[0], nnz) || dalloc(&h->col[1], nnz) ||
-      dalloc(&h->err, 8) || dalloc(&h->counters, kCounters) ||
-      cudaMallocHost(&h->host_counters, kCounters * sizeof(int64_t)))
+  if (dalloc(h, &h->segs, 1) || dalloc(h, &h->rp_id, n + 1) || dalloc(h, &h->deg_id, n) || dalloc(h, &h->col[0], nnz) ||
+      dalloc(h, &h->col[1], nnz) || dalloc(h, &h->err, 8) || dalloc(h, &h->counters, kCounters) ||
+      !(h->host_counters = new (std::nothrow) int64_t[kCounters]))
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
   CB_CUDA(h, cudaMemsetAsync(h->err, 0, 8 * sizeof(int32_t), s));
+  if ((rc = upload_segs(h))) return bail(rc);
   CB_CUDA(h, cudaMemcpyAsync(h->rp_id, row_ptr, sizeof(int64_t) * (n + 1), kind, s));
   if (nnz) CB_CUDA(h, cudaMemcpyAsync(h->col[0], col, sizeof(int32_t) * nnz, kind, s));
-  if ((rc = check_row_offsets(h, h->rp_id, n))) return bail(rc);
-  {
-    unsigned long long* dmax = reinterpret_cast<unsigned long long*>(h->counters);
-    CB_CUDA(h, cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s));
-    if (n) k_degrees<<<grid1d(n, h->num_sms), 256, 0, s>>>(n, h->rp_id, h->deg_id, dmax);
-    CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-    unsigned long long hm = 0;
-    CB_CUDA(h, cudaMemcpyAsync(&hm, dmax, sizeof(hm), cudaMemcpyDeviceToHost, s));
-    if ((rc = check_device_error(h))) {
-      h->last_error = "row_ptr is not a valid CSR offset array (degrees must be in [0, n))";
-      return bail(CB_EINVAL);
-    }
-    h->maxdeg = static_cast<int64_t>(hm);
+  if ((rc = finish_create(h))) return bail(rc);
+  *out = static_cast<cb_graph*>(h);
+  return CB_OK;
+}
+
+int cb_create_batch(int32_t count, const int64_t* n, const int64_t* row_ptr, const int32_t* col,
+                    const uint64_t* seeds, uint64_t first_step, int mem_kind, void* cuda_stream, cb_handle* out) {
+  if (!out) return fail(nullptr, CB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !n || !seeds || !row_ptr || (mem_kind != CB_HOST && mem_kind != CB_DEVICE))
+    return fail(nullptr, CB_EINVAL, "bad count, n, seeds, row_ptr or mem_kind");
+  if (first_step >= 0xfffffffeull) return fail(nullptr, CB_ERANGE, "first_step too large");
+  int64_t N = 0, nrp = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    if (n[i] < 0) return fail(nullptr, CB_EINVAL, "negative graph size");
+    N += n[i] + (n[i] & 1);
+    nrp += n[i] + 1;
   }
-  h->sort_ws_bytes = perm_ws_bytes(std::max<int64_t>(n, 1));
-  h->scan_ws_bytes = scan_ws_bytes(n + 1);
-  int64_t def_cap = 1;   // the in-order resolver bitonic-sorts a deferred list padded to a power of two
-  while (def_cap < h->ntasks) def_cap <<= 1;
-  if (dalloc(&h->order[0], n) || dalloc(&h->order[1], n) || dalloc(&h->rp[0], n + 1) || dalloc(&h->rp[1], n + 1) ||
-      dalloc(&h->pos_next, n) || dalloc(&h->M, n) || dalloc(&h->deg_next, n) || dalloc(&h->stash, nnz) ||
-      dalloc(&h->thr_key, h->ntasks) || dalloc(&h->thr_tb, h->ntasks) || dalloc(&h->done, h->ntasks) ||
-      dalloc(&h->thr_top, h->ntasks) || dalloc(&h->list[0], h->ntasks) || dalloc(&h->list[1], h->ntasks) ||
-      dalloc(&h->list[2], h->ntasks) || dalloc(&h->tile_off, h->ntasks) || dalloc(&h->tile_first, h->ntasks + 2) || dalloc(&h->cls_flag, 4 * h->ntasks) ||
-      dalloc(&h->cls_scan, 4 * (h->ntasks + 1)) || dalloc(&h->list_def[0], def_cap) ||
-      dalloc(&h->list_def[1], def_cap) ||
-      cudaMalloc(&h->sort_ws, h->sort_ws_bytes) || cudaMalloc(&h->scan_ws, h->scan_ws_bytes))
+  if (N > 0x7fffffffLL) return fail(nullptr, CB_EINVAL, "batch exceeds 2^31-1 nodes");
+  int rc;
+  Graph* h = new_graph(cuda_stream, &rc);
+  if (!h) return rc;
+  auto bail = [&](int code) {
+    g_error = h->last_error;
+    destroy_graph(h);
+    return code;
+  };
+  // every graph's offsets on the host: sizes and entry offsets
+  const int64_t* rph = row_ptr;
+  int64_t* rp_copy = nullptr;
+  if (mem_kind == CB_DEVICE) {
+    rp_copy = new (std::nothrow) int64_t[nrp];
+    if (!rp_copy) return bail(fail(h, CB_ENOMEM, "host allocation failed"));
+    if (cudaMemcpy(rp_copy, row_ptr, sizeof(int64_t) * nrp, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      delete[] rp_copy;
+      return bail(fail(h, CB_EINVAL, "row_ptr is not readable device memory"));
+    }
+    rph = rp_copy;
+  }
+  h->nseg = count;
+  h->hsegs = new (std::nothrow) Seg[count];
+  int64_t* rpo = new (std::nothrow) int64_t[2 * static_cast<size_t>(count)];
+  if (!h->hsegs || !rpo) {
+    delete[] rp_copy;
+    delete[] rpo;
+    return bail(fail(h, CB_ENOMEM, "host allocation failed"));
+  }
+  int64_t* eoff = rpo + count;
+  int64_t off = 0, r = 0, e = 0, base = 0, pairs = 0;
+  bool bad = false;
+  for (int32_t i = 0; i < count; ++i) {
+    Seg& S = h->hsegs[i];
+    S = Seg{};
+    S.seed = seeds[i];
+    S.off = off;
+    S.n = n[i];
+    S.span = n[i] + (n[i] & 1);
+    S.bucket_base = base;
+    S.B = bucket_bits(S.span);
+    S.g = static_cast<uint32_t>(first_step);
+    const int64_t z = rph[r + n[i]];
+    bad |= rph[r] != 0 || z < 0 || (z & 1);
+    for (int64_t l = 0; l < n[i] && !bad; ++l)   // offsets must not run backwards (they index col below)
+      bad |= rph[r + l + 1] < rph[r + l];
+    S.m = z / 2;
+    S.pair_off = pairs;
+    rpo[i] = r;
+    eoff[i] = e;
+    off += S.span;
+    r += n[i] + 1;
+    e += z;
+    base += int64_t(1) << S.B;
+    pairs += S.m;
+  }
+  delete[] rp_copy;
+  if (bad || e / 2 >= (int64_t(1) << 32) || (e > 0 && !col)) {
+    delete[] rpo;
+    return bail(fail(h, CB_EINVAL, "each graph's row_ptr must start at 0, not decrease and end even"));
+  }
+  h->n = N;
+  h->nnz = e;
+  h->seed = seeds[0];
+  h->g = first_step;
+  h->nbuckets = base;
+  cudaStream_t s = h->stream;
+  int64_t* d_rp_in = nullptr;
+  int64_t* d_rpo = nullptr;
+  if (dalloc(h, &h->segs, count) || dalloc(h, &h->seg_of, N) || dalloc(h, &h->rp_id, N + 1) || dalloc(h, &h->deg_id, N) ||
+      dalloc(h, &h->col[0], e) || dalloc(h, &h->col[1], e) || dalloc(h, &h->err, 8) || dalloc(h, &h->counters, kCounters) ||
+      !(h->host_counters = new (std::nothrow) int64_t[kCounters]) || dalloc(h, &d_rp_in, nrp) ||
+      dalloc(h, &d_rpo, 2 * static_cast<int64_t>(count))) {
+    delete[] rpo;
+    dfree(h, d_rp_in);
+    dfree(h, d_rpo);
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
-  CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
-  if ((rc = size_trade_workspace(h))) return bail(rc);
-  // sort every row (id space) into col[1] and validate: simple and symmetric
-  if ((rc = permute_rows(h, n, h->rp_id, h->col[0], nullptr, nullptr, h->rp_id, h->col[1]))) return bail(rc);
-  if ((rc = validate_sorted_graph(h, h->rp_id, h->col[1], n))) return bail(rc);
+  }
+  const cudaMemcpyKind kind = mem_kind == CB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t ce = cudaMemsetAsync(h->err, 0, 8 * sizeof(int32_t), s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(h->segs, h->hsegs, sizeof(Seg) * count, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_rpo, rpo, sizeof(int64_t) * 2 * count, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_rp_in, row_ptr, sizeof(int64_t) * nrp, kind, s);
+  if (ce == cudaSuccess && e) ce = cudaMemcpyAsync(h->col[0], col, sizeof(int32_t) * e, kind, s);
+  if (ce == cudaSuccess && N) {
+    k_fill_seg_of<<<grid1d(N, h->num_sms), 256, 0, s>>>(N, h->segs, count, h->seg_of);
+    k_batch_offsets<<<grid1d(N + 1, h->num_sms), 256, 0, s>>>(N, h->segs, h->seg_of, d_rp_in, d_rpo, d_rpo + count,
+                                                              e, h->rp_id, h->err);
+    k_batch_cols<<<grid1d(N * 32, h->num_sms), 256, 0, s>>>(N, h->segs, h->seg_of, h->rp_id, h->col[0], h->err);
+    h->launches += 3;
+    ce = cudaGetLastError();
+  } else if (ce == cudaSuccess) {
+    ce = cudaMemsetAsync(h->rp_id, 0, sizeof(int64_t), s);
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  delete[] rpo;
+  dfree(h, d_rp_in);
+  dfree(h, d_rpo);
+  if (ce != cudaSuccess) return bail(cuda_fail(h, ce, "batch import"));
   if ((rc = check_device_error(h))) {
-    h->last_error = "graph is not simple and symmetric";
+    h->last_error = "a graph's row_ptr or ids are out of range";
     return bail(CB_EINVAL);
   }
-  // position-space layout of the first super step
-  h->cur = 0;
-  if ((rc = compute_permutation(h, h->g, h->order[0], h->pos_next))) return bail(rc);
-  if (n) k_gather_deg<<<grid1d(n, h->num_sms), 256, 0, s>>>(n, h->order[0], h->deg_id, h->deg_next);
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-  CB_CUDA(h, exclusive_scan_i32(h->deg_next, h->rp[0], n, h->scan_ws, s, &h->launches));
-  if ((rc = permute_rows(h, n, h->rp_id, h->col[1], h->order[0], h->pos_next, h->rp[0], h->col[0]))) return bail(rc);
-  if ((rc = check_device_error(h))) return bail(rc);
-  *out = h;
+  if ((rc = finish_create(h))) return bail(rc);
+  *out = static_cast<cb_graph*>(h);
   return CB_OK;
 }
 
@@ -216,12 +556,66 @@ int cb_global_trades(cb_handle h, uint32_t supersteps) {
   if (h->g + supersteps >= 0xfffffffeull) return fail(h, CB_ERANGE, "super-step counter would pass 2^32-2");
   const int64_t launches0 = h->launches;
   for (double& v : h->phase_ms) v = 0;
-  for (uint32_t i = 0; i < supersteps; ++i) {
-    const int rc = super_step(h);
-    if (rc) return rc;
+  if (h->use_graph && !h->timing && supersteps > 0) {
+    if (!h->step_exec[0]) {
+      const int rc = capture_step_graphs(h);
+      if (rc) return rc;
+    }
+    for (uint32_t i = 0; i < supersteps; ++i) {
+      CB_CUDA(h, cudaGraphLaunch(h->step_exec[h->cur], h->stream));
+      h->cur = 1 - h->cur;
+      h->g += 1;
+      h->launches += h->step_launches;
+    }
+  } else {
+    for (uint32_t i = 0; i < supersteps; ++i) {
+      const int rc = super_step(h);
+      if (rc) return rc;
+    }
   }
   h->stats[5] = h->launches - launches0;
   return CB_OK;
+}
+
+int cb_device_bytes(cb_handle h, int64_t* now, int64_t* peak) {
+  if (!h) return fail(nullptr, CB_EINVAL, "NULL handle");
+  if (now) *now = h->dev_bytes;
+  if (peak) *peak = h->dev_bytes_peak;
+  return CB_OK;
+}
+
+int64_t cb_estimate_bytes(int64_t n, int64_t nnz, int64_t max_degree) {
+  if (n < 0 || nnz < 0 || max_degree < 0) return fail(nullptr, CB_EINVAL, "negative size");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    sms = 152;
+  return estimate_handle_bytes(n, nnz, max_degree, sms);
+}
+
+int cb_graph_count(cb_handle h) {
+  if (!h) return fail(nullptr, CB_EINVAL, "NULL handle");
+  return h->nseg;
+}
+
+int cb_graph_info(cb_handle h, int32_t index, int64_t* n, int64_t* m) {
+  if (!h || index < 0 || index >= h->nseg) return fail(h, CB_EINVAL, "bad handle or graph index");
+  if (n) *n = h->hsegs[index].n;
+  if (m) *m = h->hsegs[index].m;
+  return CB_OK;
+}
+
+int cb_export_graph(cb_handle h, int32_t index, int32_t* edges, int64_t capacity_pairs, int64_t* m_out,
+                    int mem_kind) {
+  if (!h || !m_out || index < 0 || index >= h->nseg) return fail(h, CB_EINVAL, "bad handle, index or m_out");
+  const Seg& S = h->hsegs[index];
+  *m_out = S.m;
+  if (!edges) return CB_OK;
+  if (capacity_pairs < S.m) return fail(h, CB_ESIZE, "capacity below m");
+  if (mem_kind != CB_HOST && mem_kind != CB_DEVICE) return fail(h, CB_EINVAL, "bad mem_kind");
+  if (h->latched) return fail(h, h->latched, "handle has a latched error: " + h->last_error);
+  int rc;
+  if ((rc = ensure_pairs(h))) return rc;
+  return copy_pairs(h, S.pair_off, S.m, edges, mem_kind);
 }
 
 int cb_export_edges(cb_handle h, int32_t* edges, int64_t capacity_pairs, int64_t* m_out, int mem_kind) {
@@ -232,6 +626,10 @@ int cb_export_edges(cb_handle h, int32_t* edges, int64_t capacity_pairs, int64_t
   if (mem_kind != CB_HOST && mem_kind != CB_DEVICE) return fail(h, CB_EINVAL, "bad mem_kind");
   if (h->latched) return fail(h, h->latched, "handle has a latched error: " + h->last_error);
   int rc;
+  if (h->nseg > 1) {   // every graph in turn, local ids
+    if ((rc = ensure_pairs(h))) return rc;
+    return copy_pairs(h, 0, h->m, edges, mem_kind);
+  }
   const int spare = 1 - h->cur;
   if ((rc = invert_permutation(h, h->order[h->cur], h->pos_next))) return rc;
   if ((rc = permute_rows(h, h->n, h->rp[h->cur], h->col[h->cur], h->pos_next, h->order[h->cur], h->rp_id,
@@ -239,14 +637,17 @@ int cb_export_edges(cb_handle h, int32_t* edges, int64_t capacity_pairs, int64_t
     return rc;
   int32_t* pairs = edges;
   if (mem_kind == CB_HOST) {
-    CB_CUDA(h, cudaMalloc(&pairs, sizeof(int32_t) * 2 * std::max<int64_t>(h->m, 1)));
+    CB_CUDA(h, dmalloc(h, reinterpret_cast<void**>(&pairs), sizeof(int32_t) * 2 * std::max<int64_t>(h->m, 1)));
   }
   rc = export_pairs(h, h->rp_id, h->col[spare], pairs);
   if (!rc && mem_kind == CB_HOST && h->m)
     rc = cudaMemcpyAsync(edges, pairs, sizeof(int32_t) * 2 * h->m, cudaMemcpyDeviceToHost, h->stream)
              ? fail(h, CB_ECUDA, "copy to host failed") : CB_OK;
   const int rc2 = check_device_error(h);
-  if (mem_kind == CB_HOST) cudaFree(pairs);
+  if (mem_kind == CB_HOST) {
+    dfree(h, pairs);
+    h->dev_bytes -= static_cast<int64_t>(sizeof(int32_t) * 2 * std::max<int64_t>(h->m, 1));
+  }
   return rc ? rc : rc2;
 }
 
@@ -282,7 +683,7 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind) {
   if (g >= 0xfffffffeull) return fail(h, CB_ERANGE, "step too large");
   int rc;
   // M is free between super steps
-  if ((rc = compute_permutation(h, g, h->M, nullptr))) return rc;
+  if ((rc = compute_permutation(h, 0, static_cast<int64_t>(g), h->M, nullptr))) return rc;
   CB_CUDA(h, cudaMemcpyAsync(order_out, h->M, sizeof(int32_t) * h->n,
                              mem_kind == CB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
   return cb_sync(h);
@@ -325,6 +726,12 @@ int cb_timings(cb_handle h, double* ms, int count) {
 
 int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!h || !key) return fail(h, CB_EINVAL, "bad argument");
+  if (!std::strcmp(key, "cuda_graph")) {
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "cuda_graph is 0 or 1");
+    h->use_graph = value != 0;
+    return CB_OK;
+  }
+  drop_step_graphs(h);   // every other option changes what a super step launches
   if (!std::strcmp(key, "tile_max")) {
     if (value < 0 || value > kTileMaxCap) return fail(h, CB_EINVAL, "tile_max out of range [0, 128]");
     h->tile_max = static_cast<int>(value);
@@ -363,6 +770,65 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     return CB_OK;
   }
   return fail(h, CB_EINVAL, std::string("unknown option ") + key);
+}
+
+int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
+  if (!h || count < 0) return fail(h, CB_EINVAL, "bad argument");
+  if (h->latched) return fail(h, h->latched, "handle has a latched error: " + h->last_error);
+  if (h->g + max_steps >= 0xfffffffeull) return fail(h, CB_ERANGE, "super-step counter would pass 2^32-2");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CB_CUDA(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(h, CB_ECUDA, "cudaEventCreate failed");
+  }
+  drop_step_graphs(h);
+  const bool timing = h->timing;
+  h->timing = false;
+  uint32_t used = 0;
+  int rc = CB_OK;
+  // one super step under the current options; ms = its device time
+  auto trial = [&](float* ms) -> int {
+    if (cudaEventRecord(e0, h->stream) != cudaSuccess) return fail(h, CB_ECUDA, "cudaEventRecord failed");
+    const int r = super_step(h);
+    if (r) return r;
+    if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return fail(h, CB_ECUDA, "event timing failed");
+    ++used;
+    return CB_OK;
+  };
+  struct Knob {
+    int* field;
+    int cand[4];
+    int ncand;
+  };
+  Knob knobs[3] = {{&h->tile_max, {32, 64, 96, 128}, 4},
+                   {&h->block_max, {512, 1024, 2048, 0}, 3},
+                   {&h->queued_passes, {4, 8, 12, 16}, 4}};
+  float ms = 0;
+  if (used < max_steps) rc = trial(&ms);   // first launches load the kernels: not timed as a candidate
+  for (int k = 0; k < 3 && rc == CB_OK; ++k) {
+    int best = *knobs[k].field;
+    float best_ms = 3.4e38f;
+    for (int j = 0; j < knobs[k].ncand && used < max_steps && rc == CB_OK; ++j) {
+      *knobs[k].field = knobs[k].cand[j];
+      rc = trial(&ms);
+      if (rc == CB_OK && ms < best_ms) {
+        best_ms = ms;
+        best = knobs[k].cand[j];
+      }
+    }
+    *knobs[k].field = best;
+  }
+  h->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  const int64_t vals[4] = {h->tile_max, h->block_max, h->queued_passes, static_cast<int64_t>(used)};
+  const int k = chosen ? std::min(count, 4) : 0;
+  for (int i = 0; i < k; ++i) chosen[i] = vals[i];
+  return k;
 }
 
 }  // extern "C"

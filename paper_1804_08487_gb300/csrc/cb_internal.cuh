@@ -26,9 +26,40 @@ constexpr int kBlockThreads = 256;  // CTA size of the block path
 constexpr int kCounters = 32;       // device counters per handle
 constexpr int kPassSlots = 22;      // pass input counts kept for the statistics ([8, 30))
 
+// One independent graph of a handle.  A plain handle holds one; a batch handle
+// holds many side by side: graph i owns node ids and positions [off, off+span),
+// and its keys use local ids and positions with its own seed and step, so it
+// evolves exactly as it would alone.  An odd graph in a batch gets one padding
+// node of degree 0 whose permutation key is the largest possible: it always
+// takes the last position, and its trade with the node before it changes
+// nothing, which is the untraded last position of an odd graph.
+struct Seg {
+  uint64_t seed;
+  int64_t off;           // first node id (= first position)
+  int64_t n;             // real nodes
+  int64_t span;          // n, or n + 1 with a padding node
+  int64_t bucket_base;   // first permutation bucket
+  int64_t m;             // undirected edges
+  int64_t pair_off;      // first exported pair
+  uint32_t g;            // super step (advanced on the device at the end of each step)
+  int32_t B;             // permutation bucket bits
+};
+
 struct Graph {
   int64_t n = 0, nnz = 0, m = 0, T = 0, ntasks = 0;
   uint64_t seed = 0, g = 0;
+  // segments (graphs) of the handle
+  int nseg = 1;
+  Seg* segs = nullptr;            // device table (nseg)
+  int32_t* seg_of = nullptr;      // device: segment of each node id / position (null when nseg == 1)
+  Seg* hsegs = nullptr;           // host copy (g not kept current)
+  int64_t nbuckets = 1;           // permutation buckets over all segments
+  int32_t* pairs = nullptr;       // batch export: every graph's pairs, local ids
+  uint64_t pairs_step = ~0ull;    // super step the pairs were exported at
+  // CUDA graph of one super step per ping-pong parity
+  bool use_graph = false;
+  cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
+  int64_t step_launches = 0;      // kernels in one captured super step
   int64_t maxdeg = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -49,7 +80,7 @@ struct Graph {
   uint64_t* thr_key = nullptr;             // per trade: threshold key
   uint8_t* thr_top = nullptr;              // per trade: top 6 bits of the threshold key
   uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)
-  uint32_t* done = nullptr;                // per trade: stamp g+1 once the threshold is published
+  uint32_t* done = nullptr;                // per trade: 1 once the threshold is published (cleared per step)
   int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (tile, 256, 1024 threads), index order
   int64_t* tile_off = nullptr;             // per tile-class trade: prefix of its weight max(L, 4)
   int32_t* tile_first = nullptr;           // first tile-class trade of each tile (+ end sentinel)
@@ -66,7 +97,8 @@ struct Graph {
   size_t sort_ws_bytes = 0;
   void* scan_ws = nullptr;
   size_t scan_ws_bytes = 0;
-  int64_t* host_counters = nullptr;        // pinned mirror of counters
+  int64_t* host_counters = nullptr;        // host mirror of counters
+  int64_t dev_bytes = 0, dev_bytes_peak = 0;   // device memory held by the handle
   int queued_passes = 12;                  // dependency passes queued per super step before the resolver
   int64_t last_passes_queued = 0;
   int last_in = 0;                         // deferred list the resolver read in the last super step
@@ -112,9 +144,12 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, void*
                                int64_t* launches = nullptr);
 
 // permute.cu
-size_t perm_ws_bytes(int64_t n);
-// order_out[p] = node at position p in super step g; pos_out[x] = position of x (may be null)
-int compute_permutation(Graph* h, uint64_t g, int32_t* order_out, int32_t* pos_out);
+size_t perm_ws_bytes(int64_t n, int64_t nbuckets);
+int bucket_bits(int64_t n);
+// order_out[p] = node at position p; pos_out[x] = position of x (may be null).
+// Each segment uses its device step counter + dg, or the step g_abs for all
+// when g_abs >= 0.
+int compute_permutation(Graph* h, uint32_t dg, int64_t g_abs, int32_t* order_out, int32_t* pos_out);
 // M, deg_next and rp[1-cur] for the step after the current one
 int prepare_next(Graph* h);
 
@@ -129,6 +164,14 @@ int export_pairs(Graph* h, const int64_t* rp, const int32_t* col, int32_t* pairs
 
 // trade.cu
 int super_step(Graph* h);
+int init_trade_kernels(Graph* h);   // one-time kernel attributes (outside stream capture)
+size_t trade_ws_slice_bytes(int64_t max_trade);
+
+// api.cu
+// device bytes a plain handle of n nodes / nnz entries / largest degree takes (upper estimate)
+int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sms);
+// record the CUDA graphs of the super step now (when the cuda_graph option is on)
+int prepare_step_graphs(Graph* h);
 
 }  // namespace cb
 

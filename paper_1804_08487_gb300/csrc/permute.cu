@@ -11,9 +11,6 @@
 #include <mutex>
 
 namespace cb {
-namespace {
-
-constexpr int kPermThreads = 256;
 
 int bucket_bits(int64_t n) {
   int lg = 0;
@@ -21,20 +18,64 @@ int bucket_bits(int64_t n) {
   return lg > 9 ? lg - 9 : 0;
 }
 
+namespace {
+
+constexpr int kPermThreads = 256;
+
 __device__ __forceinline__ uint32_t bucket_of(uint64_t key, int B) {
   return B == 0 ? 0u : static_cast<uint32_t>(key >> (64 - B));
 }
 
-__global__ void k_perm_hist(int64_t n, uint64_t seed, uint32_t g, int B, int32_t* __restrict__ hist) {
+// Where node keys come from: a handle's segment table (each segment at its
+// device step + dg, or every segment at g_abs when use_abs), or one segment
+// passed by value (segs == nullptr).
+struct KeySrc {
+  const Seg* segs;
+  const int32_t* seg_of;
+  Seg s0;
+  uint32_t dg;
+  int use_abs;
+  uint32_t g_abs;
+};
+
+// Permutation key and bucket of node x.  A padding node gets the largest key.
+__device__ __forceinline__ void key_of(const KeySrc& ks, int64_t x, uint64_t& key, uint32_t& bucket) {
+  uint64_t seed;
+  int64_t off, n, base;
+  uint32_t g;
+  int B;
+  if (ks.segs) {
+    const Seg* S = ks.segs + (ks.seg_of ? __ldg(ks.seg_of + x) : 0);
+    seed = __ldg(&S->seed);
+    off = __ldg(&S->off);
+    n = __ldg(&S->n);
+    base = __ldg(&S->bucket_base);
+    g = ks.use_abs ? ks.g_abs : __ldg(&S->g) + ks.dg;
+    B = __ldg(&S->B);
+  } else {
+    seed = ks.s0.seed;
+    off = ks.s0.off;
+    n = ks.s0.n;
+    base = ks.s0.bucket_base;
+    g = ks.use_abs ? ks.g_abs : ks.s0.g + ks.dg;
+    B = ks.s0.B;
+  }
+  const int64_t l = x - off;
+  key = l < n ? node_key(seed, static_cast<uint32_t>(l), g) : ~0ull;
+  bucket = static_cast<uint32_t>(base) + bucket_of(key, B);
+}
+
+__global__ void k_perm_hist(int64_t n, KeySrc ks, int nb, int32_t* __restrict__ hist) {
   extern __shared__ int32_t sh[];
-  const int nb = 1 << B;
   const bool local = nb <= 4096;
   if (local) {
     for (int i = threadIdx.x; i < nb; i += blockDim.x) sh[i] = 0;
     __syncthreads();
   }
   for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
-    const uint32_t b = bucket_of(node_key(seed, static_cast<uint32_t>(x), g), B);
+    uint64_t k;
+    uint32_t b;
+    key_of(ks, x, k, b);
     if (local) atomicAdd(&sh[b], 1); else atomicAdd(&hist[b], 1);
   }
   if (local) {
@@ -44,12 +85,12 @@ __global__ void k_perm_hist(int64_t n, uint64_t seed, uint32_t g, int B, int32_t
   }
 }
 
-__global__ void k_perm_scatter(int64_t n, uint64_t seed, uint32_t g, int B,
-                               const int64_t* __restrict__ boff, int32_t* __restrict__ cursor,
+__global__ void k_perm_scatter(int64_t n, KeySrc ks, const int64_t* __restrict__ boff, int32_t* __restrict__ cursor,
                                uint64_t* __restrict__ bkey, int32_t* __restrict__ bid) {
   for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
-    const uint64_t k = node_key(seed, static_cast<uint32_t>(x), g);
-    const uint32_t b = bucket_of(k, B);
+    uint64_t k;
+    uint32_t b;
+    key_of(ks, x, k, b);
     const int64_t slot = boff[b] + atomicAdd(&cursor[b], 1);
     bkey[slot] = k;
     bid[slot] = static_cast<int32_t>(x);
@@ -147,8 +188,7 @@ struct PermWs {
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-PermWs carve(void* base, int64_t n) {
-  const int64_t nb = int64_t(1) << bucket_bits(n);
+PermWs carve(void* base, int64_t n, int64_t nb) {
   char* p = static_cast<char*>(base);
   PermWs w;
   w.hist = reinterpret_cast<int32_t*>(p); p += align_up(sizeof(int32_t) * nb);
@@ -169,31 +209,34 @@ unsigned grid_for(int64_t work, int threads, int num_sms) {
 
 }  // namespace
 
-size_t perm_ws_bytes(int64_t n) {
-  const int64_t nb = int64_t(1) << bucket_bits(n);
+size_t perm_ws_bytes(int64_t n, int64_t nb) {
   return align_up(sizeof(int32_t) * nb) * 2 + align_up(sizeof(int64_t) * (nb + 1)) +
          align_up(sizeof(int32_t) * (nb + 1)) + align_up(sizeof(uint64_t) * n) +
          align_up(sizeof(int32_t) * n) + scan_ws_bytes(nb + 1) + 256;
 }
 
-int compute_permutation(Graph* h, uint64_t g, int32_t* order_out, int32_t* pos_out) {
+int compute_permutation(Graph* h, uint32_t dg, int64_t g_abs, int32_t* order_out, int32_t* pos_out) {
   const int64_t n = h->n;
   if (n == 0) return CB_OK;
-  const int B = bucket_bits(n);
-  const int nb = 1 << B;
-  PermWs w = carve(h->sort_ws, n);
+  const int64_t nb = h->nbuckets;
+  PermWs w = carve(h->sort_ws, n, nb);
   cudaStream_t s = h->stream;
   CB_CUDA(h, cudaMemsetAsync(w.hist, 0, sizeof(int32_t) * nb, s));
   CB_CUDA(h, cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * nb, s));
   CB_CUDA(h, cudaMemsetAsync(w.overflow, 0, sizeof(int32_t), s));
+  KeySrc ks{};
+  ks.segs = h->segs;
+  ks.seg_of = h->seg_of;
+  ks.dg = dg;
+  ks.use_abs = g_abs >= 0;
+  ks.g_abs = static_cast<uint32_t>(g_abs < 0 ? 0 : g_abs);
   const unsigned grid = grid_for(n, kPermThreads, h->num_sms);
   const size_t hsm = nb <= 4096 ? sizeof(int32_t) * nb : 0;
-  k_perm_hist<<<grid, kPermThreads, hsm, s>>>(n, h->seed, static_cast<uint32_t>(g), B, w.hist);
+  k_perm_hist<<<grid, kPermThreads, hsm, s>>>(n, ks, static_cast<int>(nb), w.hist);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   CB_CUDA(h, exclusive_scan_i32(w.hist, w.boff, nb, w.scan, s, &h->launches));
-  k_perm_scatter<<<grid, kPermThreads, 0, s>>>(n, h->seed, static_cast<uint32_t>(g), B, w.boff, w.cursor,
-                                               w.bkey, w.bid);
+  k_perm_scatter<<<grid, kPermThreads, 0, s>>>(n, ks, w.boff, w.cursor, w.bkey, w.bid);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   const int cap = h->bucket_cap;
@@ -201,8 +244,8 @@ int compute_permutation(Graph* h, uint64_t g, int32_t* order_out, int32_t* pos_o
   while (cap_pow2 < cap) cap_pow2 <<= 1;
   const size_t ssm = static_cast<size_t>(cap_pow2) * (sizeof(uint64_t) + sizeof(int32_t));
   const unsigned sgrid = static_cast<unsigned>(nb < h->num_sms * 8 ? nb : h->num_sms * 8);
-  k_bucket_sort<<<sgrid, kPermThreads, ssm, s>>>(nb, w.boff, w.bkey, w.bid, cap, order_out, pos_out, w.overflow,
-                                                cap_pow2);
+  k_bucket_sort<<<sgrid, kPermThreads, ssm, s>>>(static_cast<int>(nb), w.boff, w.bkey, w.bid, cap, order_out, pos_out,
+                                                w.overflow, cap_pow2);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   k_bucket_overflow<<<64, kPermThreads, 0, s>>>(w.overflow, w.boff, w.bkey, w.bid, order_out, pos_out);
@@ -213,7 +256,7 @@ int compute_permutation(Graph* h, uint64_t g, int32_t* order_out, int32_t* pos_o
 
 int prepare_next(Graph* h) {
   const int nxt = 1 - h->cur;
-  int rc = compute_permutation(h, h->g + 1, h->order[nxt], h->pos_next);
+  int rc = compute_permutation(h, 1, -1, h->order[nxt], h->pos_next);
   if (rc) return rc;
   const unsigned grid = grid_for(h->n, kPermThreads, h->num_sms);
   k_prep_next<<<grid, kPermThreads, 0, h->stream>>>(h->n, h->order[h->cur], h->order[nxt], h->pos_next,
@@ -253,7 +296,7 @@ extern "C" int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32
   if (n > kStaticPermMaxNodes)
     return fail(nullptr, CB_ESIZE, "cb_permutation_static: n exceeds the static scratch limit of 2^20 nodes");
   if (g >= 0xfffffffeull) return fail(nullptr, CB_ERANGE, "cb_permutation_static: step too large");
-  if (perm_ws_bytes(kStaticPermMaxNodes) > kStaticPermBytes)
+  if (perm_ws_bytes(kStaticPermMaxNodes, int64_t(1) << bucket_bits(kStaticPermMaxNodes)) > kStaticPermBytes)
     return fail(nullptr, CB_ECHECK, "cb_permutation_static: static scratch smaller than its limit needs");
   if (n == 0) return CB_OK;
   int dev = 0, num_sms = 0;
@@ -277,7 +320,7 @@ extern "C" int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int B = bucket_bits(n);
   const int nb = 1 << B;
-  PermWs w = carve(base, n);
+  PermWs w = carve(base, n, nb);
   // the scratch keeps the previous call's contents: clear the counters
   if ((e = cudaMemsetAsync(w.hist, 0, sizeof(int32_t) * nb, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(w.cursor, 0, sizeof(int32_t) * nb, s)) != cudaSuccess ||
@@ -285,10 +328,17 @@ extern "C" int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32
     return cuda_fail(nullptr, e, "cudaMemsetAsync");
   const unsigned grid = grid_for(n, kPermThreads, num_sms);
   const size_t hsm = nb <= 4096 ? sizeof(int32_t) * nb : 0;
-  k_perm_hist<<<grid, kPermThreads, hsm, s>>>(n, seed, static_cast<uint32_t>(g), B, w.hist);
+  KeySrc ks{};
+  ks.s0.seed = seed;
+  ks.s0.n = n;
+  ks.s0.span = n;
+  ks.s0.B = B;
+  ks.use_abs = 1;
+  ks.g_abs = static_cast<uint32_t>(g);
+  k_perm_hist<<<grid, kPermThreads, hsm, s>>>(n, ks, nb, w.hist);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_perm_hist");
   if ((e = exclusive_scan_i32(w.hist, w.boff, nb, w.scan, s)) != cudaSuccess) return cuda_fail(nullptr, e, "scan");
-  k_perm_scatter<<<grid, kPermThreads, 0, s>>>(n, seed, static_cast<uint32_t>(g), B, w.boff, w.cursor, w.bkey, w.bid);
+  k_perm_scatter<<<grid, kPermThreads, 0, s>>>(n, ks, w.boff, w.cursor, w.bkey, w.bid);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_perm_scatter");
   const int cap = 2048;
   const size_t ssm = static_cast<size_t>(cap) * (sizeof(uint64_t) + sizeof(int32_t));

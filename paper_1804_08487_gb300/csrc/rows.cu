@@ -117,16 +117,19 @@ __global__ void k_count_upper(int64_t n, const int64_t* __restrict__ rp, const i
   }
 }
 
+// Pairs (x, y) with x < y, ids local to x's graph (both ends share it).
 __global__ void k_write_pairs(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                               const int32_t* __restrict__ cnt, const int64_t* __restrict__ off,
+                              const Seg* __restrict__ segs, const int32_t* __restrict__ seg_of,
                               int32_t* __restrict__ pairs) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < n; x += nw) {
     const int64_t e = rp[x + 1], c = cnt[x], b = e - c, o = off[x];
+    const int32_t base = seg_of ? static_cast<int32_t>(segs[seg_of[x]].off) : 0;
     for (int64_t i = lane; i < c; i += 32) {
-      pairs[2 * (o + i)] = static_cast<int32_t>(x);
-      pairs[2 * (o + i) + 1] = col[b + i];
+      pairs[2 * (o + i)] = static_cast<int32_t>(x) - base;
+      pairs[2 * (o + i) + 1] = col[b + i] - base;
     }
   }
 }
@@ -201,7 +204,8 @@ int export_pairs(Graph* h, const int64_t* rp, const int32_t* col, int32_t* pairs
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   CB_CUDA(h, exclusive_scan_i32(cnt, off, n, h->scan_ws, h->stream, &h->launches));
-  k_write_pairs<<<grid_of(n * 32, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, cnt, off, pairs);
+  k_write_pairs<<<grid_of(n * 32, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, cnt, off, h->segs, h->seg_of,
+                                                                           pairs);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   return CB_OK;

@@ -63,8 +63,9 @@ constexpr int kTileHash = 1 << kTileHashLg;          // > 1.7 x the slots of a t
 
 struct StepCtx {
   int64_t n, T;
-  uint64_t seed;
-  uint32_t g, stamp;
+  uint32_t stamp;
+  const Seg* segs;          // per graph: seed, step, first position
+  const int32_t* seg_of;    // graph of each position (null: one graph)
   const int64_t* rp;
   const int32_t* col;
   uint8_t* stash;
@@ -121,18 +122,34 @@ __device__ __forceinline__ bool at_or_below(uint64_t key, uint64_t tb, uint64_t 
   return key < tk || (key == tk && tb <= tt);
 }
 
+// Key parameters of a trade's graph: its seed, its step and its first
+// position (keys count positions from the start of the graph).  Both ends of
+// an edge are in the same graph.
+struct KeyCtx {
+  uint64_t seed;
+  uint32_t g, off;
+};
+__device__ __forceinline__ KeyCtx key_ctx(const StepCtx& c, int64_t t) {
+  const Seg* S = c.segs + (c.seg_of ? __ldg(c.seg_of + 2 * t) : 0);
+  return {__ldg(&S->seed), __ldg(&S->g), static_cast<uint32_t>(__ldg(&S->off))};
+}
+
 // Both trades' keys of the edge whose step-start positions are lo < hi.
 struct EdgeKeys {
   uint64_t lo_side, hi_side;
 };
-__device__ __forceinline__ EdgeKeys edge_keys(uint64_t seed, uint32_t lo, uint32_t hi, uint32_t g) {
-  const Philox4 r = philox4x32_10(lo, hi, g, 1u, seed);
+__device__ __forceinline__ EdgeKeys edge_keys(const KeyCtx& kc, uint32_t lo, uint32_t hi) {
+  const Philox4 r = philox4x32_10(lo - kc.off, hi - kc.off, kc.g, 1u, kc.seed);
   return {(static_cast<uint64_t>(r.w0) << 32) | r.w1, (static_cast<uint64_t>(r.w2) << 32) | r.w3};
+}
+__device__ __forceinline__ uint64_t side_key(const KeyCtx& kc, uint32_t lo, uint32_t hi, bool lo_side) {
+  return edge_key(kc.seed, lo - kc.off, hi - kc.off, kc.g, lo_side);
 }
 
 // Does trade s send the edge (lo, hi) to its node at position 2s?  Full test.
-__device__ __forceinline__ bool far_keeps_low(const StepCtx& c, int64_t s, uint32_t lo, uint32_t hi) {
-  const uint64_t k = edge_key(c.seed, lo, hi, c.g, (lo >> 1) == static_cast<uint32_t>(s));
+__device__ __forceinline__ bool far_keeps_low(const StepCtx& c, const KeyCtx& kc, int64_t s, uint32_t lo,
+                                              uint32_t hi) {
+  const uint64_t k = side_key(kc, lo, hi, (lo >> 1) == static_cast<uint32_t>(s));
   return at_or_below(k, tie_break(lo, hi), __ldcg(c.thr_key + s), __ldcg(c.thr_tb + s));
 }
 
@@ -221,8 +238,8 @@ __device__ __forceinline__ uint32_t lo_of(int64_t t2, uint8_t m, int32_t y) {
 __device__ __forceinline__ uint32_t hi_of(int64_t t2, uint8_t m, int32_t y) {
   return max(static_cast<uint32_t>(t2 + (m & kR)), static_cast<uint32_t>(y));
 }
-__device__ __forceinline__ uint64_t own_key(const StepCtx& c, int64_t t, uint32_t lo, uint32_t hi) {
-  return edge_key(c.seed, lo, hi, c.g, (lo >> 1) == static_cast<uint32_t>(t));
+__device__ __forceinline__ uint64_t own_key(const KeyCtx& kc, int64_t t, uint32_t lo, uint32_t hi) {
+  return side_key(kc, lo, hi, (lo >> 1) == static_cast<uint32_t>(t));
 }
 
 // One radix digit of the 16-bit key prefixes: histogram of (top >> shift) & 255
@@ -264,7 +281,7 @@ __device__ void radix_digit(Team& tm, const WsA& w, int L, int shift, uint32_t p
 // k-th smallest (1-based) (key, lo, hi) over D: two radix digits on the stored
 // 16-bit key prefixes, then the full keys of the few remaining candidates.
 template <class Team>
-__device__ void select_kth(Team& tm, const StepCtx& c, const WsA& w, int L, int64_t t, int k, SelOut* out) {
+__device__ void select_kth(Team& tm, const KeyCtx& kc, const WsA& w, int L, int64_t t, int k, SelOut* out) {
   const int64_t t2 = 2 * t;
   radix_digit(tm, w, L, 8, 0, k, out);
   const uint32_t b1 = static_cast<uint32_t>(out->bin);
@@ -295,7 +312,7 @@ __device__ void select_kth(Team& tm, const StepCtx& c, const WsA& w, int L, int6
     const uint32_t tp = w.top[i];
     if (full16 ? (tp != prefix) : ((tp >> 8) != b1)) continue;
     const uint32_t lo = lo_of(t2, m, w.y[i]), hi = hi_of(t2, m, w.y[i]);
-    const uint64_t ki = own_key(c, t, lo, hi), tbi = tie_break(lo, hi);
+    const uint64_t ki = own_key(kc, t, lo, hi), tbi = tie_break(lo, hi);
     if (cnt == 1) {            // the only element with this prefix
       out->key = ki;
       out->tb = tbi;
@@ -311,7 +328,7 @@ __device__ void select_kth(Team& tm, const StepCtx& c, const WsA& w, int L, int6
         const uint32_t tj = w.top[j];
         if (full16 ? (tj != prefix) : ((tj >> 8) != b1)) continue;
         const uint32_t loj = lo_of(t2, mj, w.y[j]), hij = hi_of(t2, mj, w.y[j]);
-        const uint64_t kj = own_key(c, t, loj, hij);
+        const uint64_t kj = own_key(kc, t, loj, hij);
         r += (kj < ki || (kj == ki && tie_break(loj, hij) < tbi));
       }
       if (r == kk - 1) {
@@ -338,6 +355,7 @@ __device__ void select_kth(Team& tm, const StepCtx& c, const WsA& w, int L, int6
 template <class Team>
 __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, SelOut* sel) {
   const TradeRows tr = trade_rows(c, t);
+  const KeyCtx kc = key_ctx(c, t);
   const int du = tr.du, dv = tr.dv, L = du + dv;
   const int H = 1 << w.lgH;
   for (int i = tm.rank; i < H; i += Team::N) w.hash[i] = 0ull;
@@ -386,7 +404,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
           int g2 = gam;
           if (cnt_row[rho] == 1) {
             const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(e0 + gam);
-            g2 = far_keeps_low(c, s, min(x, y), max(x, y)) ? 0 : 1;
+            g2 = far_keeps_low(c, kc, s, min(x, y), max(x, y)) ? 0 : 1;
           }
           m1[rho][g2] = 1;
           if (rho == r && gam == (yy & 1)) col_now = g2;
@@ -396,7 +414,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     {  // both trades' keys of this edge: own 16-bit prefix, far 6-bit prefix
       const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
       const uint32_t lo = min(x, y), hi = max(x, y);
-      const EdgeKeys ek = edge_keys(c.seed, lo, hi, c.g);
+      const EdgeKeys ek = edge_keys(kc, lo, hi);
       const bool lo_mine = (lo >> 1) == static_cast<uint32_t>(t);
       w.top[i] = static_cast<uint16_t>((lo_mine ? ek.lo_side : ek.hi_side) >> 48);
       w.far[i] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
@@ -416,7 +434,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   const bool publish_fence = tm.any(has_dependents);
   uint64_t tk = 0, tt = 0;
   if (!tr.single && a > 0) {
-    select_kth(tm, c, w, L, t, a, sel);
+    select_kth(tm, kc, w, L, t, a, sel);
     tk = sel->key;
     tt = sel->tb;
   }
@@ -432,7 +450,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
       low = tp < tk16;
     } else {
       const uint32_t lo = lo_of(t2, m, w.y[i]), hi = hi_of(t2, m, w.y[i]);
-      low = at_or_below(own_key(c, t, lo, hi), tie_break(lo, hi), tk, tt);
+      low = at_or_below(own_key(kc, t, lo, hi), tie_break(lo, hi), tk, tt);
     }
     if ((low ? 0 : 1) != r) {
       w.meta[i] = m | kFlip;
@@ -489,6 +507,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
 template <class Team>
 __device__ void phase_b(Team& tm, const StepCtx& c, int64_t t) {
   const TradeRows tr = trade_rows(c, t);
+  const KeyCtx kc = key_ctx(c, t);
   const int du = tr.du, dv = tr.dv, L = du + dv;
   const int64_t t2 = 2 * t;
   const int32_t pu = c.M[t2];
@@ -523,7 +542,7 @@ __device__ void phase_b(Team& tm, const StepCtx& c, int64_t t) {
           low = ft < tt;
         } else {
           const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-          low = far_keeps_low(c, s, min(x, y), max(x, y));
+          low = far_keeps_low(c, kc, s, min(x, y), max(x, y));
         }
         y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
       }
@@ -593,6 +612,7 @@ __global__ void k_tile_first(const int64_t* __restrict__ tile_off, const int64_t
 // ---------------------------------------------------------------- tile path
 
 struct TileShared {              // per-trade data of the current tile
+  KeyCtx kc[kTileTrades];
   int64_t b0[kTileTrades];
   int64_t ou[kTileTrades], ov[kTileTrades];
   int32_t t[kTileTrades];
@@ -640,6 +660,7 @@ __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& 
     const int32_t t = list[k];
     const TradeRows tr = trade_rows(c, t);
     sh.t[j] = t;
+    sh.kc[j] = key_ctx(c, t);
     sh.b0[j] = tr.b0;
     sh.du[j] = static_cast<int16_t>(tr.du);
     sh.dv[j] = static_cast<int16_t>(tr.dv);
@@ -781,7 +802,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
             int g2 = gam;
             if (cnt_row[rho] == 1) {
               const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(2 * s + gam);
-              g2 = far_keeps_low(c, s, min(x, y), max(x, y)) ? 0 : 1;
+              g2 = far_keeps_low(c, sh.kc[k], s, min(x, y), max(x, y)) ? 0 : 1;
             }
             m1[rho][g2] = 1;
             if (rho == r && gam == (yy & 1)) col_now = g2;
@@ -790,7 +811,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
       }
       const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
       const uint32_t lo = min(x, y), hi = max(x, y);
-      const EdgeKeys ek = edge_keys(c.seed, lo, hi, c.g);
+      const EdgeKeys ek = edge_keys(sh.kc[k], lo, hi);
       const bool lo_mine = (lo >> 1) == static_cast<uint32_t>(t);
       ta.key[e] = lo_mine ? ek.lo_side : ek.hi_side;
       ta.far[e] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
@@ -1040,7 +1061,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
           low = ft < tt;
         } else {
           const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-          low = far_keeps_low(c, s, min(x, y), max(x, y));
+          low = far_keeps_low(c, sh.kc[k], s, min(x, y), max(x, y));
         }
         y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
       }
@@ -1073,7 +1094,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
 // ---------------------------------------------------------------- team paths
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_phase_a_block(StepCtx c, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx c, const int32_t* __restrict__ list,
                                                       const int64_t* __restrict__ count, int smem_max, char* gws,
                                                       size_t slice) {
   extern __shared__ __align__(16) char sbuf[];
@@ -1140,7 +1161,34 @@ __global__ void __launch_bounds__(kBigThreads) k_resolve(StepCtx c, const int32_
   if (threadIdx.x == 0 && *c.def_count != 0) latch(c.err, kErrResolve);
 }
 
+// End of a super step: every graph's step counter moves on.
+__global__ void k_seg_advance(Seg* segs, int nseg) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nseg; i += gridDim.x * blockDim.x) segs[i].g += 1;
+}
+
+int finish_step(Graph* h) {
+  k_seg_advance<<<(h->nseg + 255) / 256, 256, 0, h->stream>>>(h->segs, h->nseg);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  h->cur = 1 - h->cur;
+  h->g += 1;
+  return CB_OK;
+}
+
 }  // namespace
+
+int init_trade_kernels(Graph* h) {
+  // the largest dynamic shared memory any handle may ask of each kernel
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(ws_a_bytes(kBlockMaxCap))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(ws_a_bytes(kSmemMaxCap))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(ws_a_bytes(kSmemMaxCap))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(sizeof(TileA))));
+  return CB_OK;
+}
 
 size_t trade_ws_slice_bytes(int64_t max_trade) {
   return (ws_a_bytes(static_cast<int>(max_trade)) + 255) & ~size_t(255);
@@ -1158,9 +1206,9 @@ int super_step(Graph* h) {
   StepCtx c;
   c.n = h->n;
   c.T = h->T;
-  c.seed = h->seed;
-  c.g = static_cast<uint32_t>(h->g);
-  c.stamp = static_cast<uint32_t>(h->g + 1);
+  c.stamp = 1;   // done flags are cleared at the start of every step
+  c.segs = h->segs;
+  c.seg_of = h->seg_of;
   c.rp = h->rp[h->cur];
   c.col = h->col[h->cur];
   c.stash = h->stash;
@@ -1179,11 +1227,8 @@ int super_step(Graph* h) {
   c.gws_count = ucnt + kCounters - 1;
   CB_CUDA(h, cudaMemsetAsync(cnt, 0, kCounters * sizeof(int64_t), s));
   const int64_t ntasks = h->ntasks;
-  if (ntasks == 0) {
-    h->cur = nxt;
-    h->g += 1;
-    return CB_OK;
-  }
+  if (ntasks == 0) return finish_step(h);
+  CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * ntasks, s));
   const int tile_max = std::min(h->tile_max, kTileMaxCap);
   const int block_max = std::max(h->block_max, tile_max);
   auto grid_n = [&](int64_t work) {
@@ -1209,13 +1254,7 @@ int super_step(Graph* h) {
   }
   const size_t med_smem = ws_a_bytes(std::max(block_max, 1));
   const size_t big_smem = ws_a_bytes(std::max(h->smem_max, 1));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(med_smem)));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(big_smem)));
   const unsigned tgrid = static_cast<unsigned>(h->num_sms * 8);
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(sizeof(TileA))));
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
   char* gws = static_cast<char*>(h->ws_global);
@@ -1266,8 +1305,6 @@ int super_step(Graph* h) {
   // whatever is still deferred runs in index order on one CTA (no host round trip)
   c.def_out = h->list_def[1 - in];   // never written: the resolver defers nothing
   c.def_count = ucnt + kCounters - 2;
-  CB_CUDA(h, cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(big_smem)));
   k_resolve<<<1, kBigThreads, big_smem, s>>>(c, h->list_def[in], cnt + 4 + in, h->list_def[1 - in], h->smem_max,
                                              gws, h->ws_slice);
   CB_CUDA(h, cudaGetLastError());
@@ -1302,9 +1339,7 @@ int super_step(Graph* h) {
     h->phase_ms[2] += d;
     h->phase_ms[3] += tot;
   }
-  h->cur = nxt;
-  h->g += 1;
-  return CB_OK;
+  return finish_step(h);
 }
 
 }  // namespace cb

@@ -119,6 +119,30 @@ PLAIN = {
 }
 
 
+SERVING_RATE = 200.0        # mean arrivals per second (Poisson)
+SERVING_MASTER_SEED = 2018   # drives the inter-arrival times only
+
+
+def serving_request(i: int):
+    """Request i of the serving workload: n log-uniform in [2^12, 2^22], gamma
+    uniform in [2,3], degrees on [4, n/16] (so b = n/16 + 1 exclusive), super
+    steps uniform in [5, 50]; the request index seeds the graph and the chain
+    (stream 3 draws n, gamma and the step count)."""
+    n = int(_load().cb_synth_exp2(12.0 + 10.0 * uniform(i, 3, 0)))
+    n = min(max(n, 1 << 12), 1 << 22)
+    gamma = 2.0 + uniform(i, 3, 1)
+    steps = 5 + min(int(46.0 * uniform(i, 3, 2)), 45)
+    return Workload(f"request[{i}]", n, 4, n // 16 + 1, gamma, i, i, steps)
+
+
+def serving_arrivals(count: int, rate: float = SERVING_RATE, seed: int = SERVING_MASTER_SEED) -> np.ndarray:
+    """Arrival times (seconds from the first) of a Poisson process: exponential
+    inter-arrival gaps -ln(1-U)/rate from stream 4 of the master seed."""
+    gaps = [-np.log1p(-uniform(seed, 4, i)) / rate for i in range(count)]
+    t = np.cumsum([0.0] + gaps[1:])
+    return np.asarray(t, dtype=np.float64)
+
+
 def ensemble_member(i: int):
     """Member i of the 256-graph ensemble: n log-uniform in [2^10, 2^16], gamma
     uniform in [2,3], degrees on [4, n/16), seed 1000+i (stream 3 draws n and gamma)."""
