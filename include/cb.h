@@ -168,9 +168,9 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
  * Counters of the last cb_global_trades call, for tests and tuning
  * (synchronises the handle's stream; out[5] counts the kernels inside the
  * CUDA graphs replayed when "cuda_graph" is on):
- * out[0] = dependency-resolution passes of the last super step (the final
- *          in-order pass counts as one),
- * out[1] = trades deferred to a later pass (summed over its passes),
+ * out[0] = threshold passes of the last super step: 1, or 2 when the first
+ *          pass deferred trades to the in-order pass,
+ * out[1] = trades the first pass deferred,
  * out[2] = trades on the tile path, out[3] = on the 256- and 1024-thread paths,
  * out[4] = trades whose workspace did not fit in shared memory,
  * out[5] = kernel launches issued by the call.
@@ -210,10 +210,6 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               workspace [8192]; 64..8192.
  *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];
  *               larger buckets take the global-memory fallback; 2..4096.
- *   "queued_passes" dependency-resolution passes queued per super step before
- *               the host checks whether any trade is still waiting [12];
- *               0..64 (more passes follow as needed; the result never
- *               depends on this value).
  *   "timing"    1: record CUDA events around the phases of each super step
  *               (adds one stream synchronisation per super step) [0].
  */
@@ -248,9 +244,9 @@ int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_o
  * Pick the fastest work split for this handle: runs up to max_steps real
  * super steps (they advance the chain; the result does not depend on the
  * options), each under one candidate setting of "tile_max", "block_max" and
- * "queued_passes", timed with CUDA events, and keeps the fastest.  chosen
+ * "smem_max", timed with CUDA events, and keeps the fastest.  chosen
  * (may be NULL) receives up to `count` values: tile_max, block_max,
- * queued_passes, super steps used.  Returns the number of values written.
+ * smem_max, super steps used.  Returns the number of values written.
  */
 int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count);
 

@@ -194,7 +194,7 @@ def cb_export_graph(h, index: int, out=None):
 def cb_autotune(h, max_steps: int):
     out = (C.c_int64 * 4)()
     k = _check(load().cb_autotune(h, max_steps, out, 4), h)
-    names = ["tile_max", "block_max", "queued_passes", "steps"]
+    names = ["tile_max", "block_max", "smem_max", "steps"]
     return {names[i]: out[i] for i in range(k)}
 
 

@@ -62,7 +62,7 @@ void release(Graph* h) {
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
                   h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
-                  h->list_def[0], h->list_def[1], h->counters, h->err,
+                  h->counters, h->err,
                   h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs};
   if (h->stream)
     for (void* b : bufs) dfree(h, b);
@@ -230,15 +230,12 @@ int finish_create(Graph* h) {
   }
   h->sort_ws_bytes = perm_ws_bytes(std::max<int64_t>(n, 1), h->nbuckets);
   h->scan_ws_bytes = scan_ws_bytes(std::max<int64_t>(n + 1, h->nbuckets + 1));
-  int64_t def_cap = 1;   // the in-order resolver bitonic-sorts a deferred list padded to a power of two
-  while (def_cap < h->ntasks) def_cap <<= 1;
   if (dalloc(h, &h->order[0], n) || dalloc(h, &h->order[1], n) || dalloc(h, &h->rp[0], n + 1) || dalloc(h, &h->rp[1], n + 1) ||
       dalloc(h, &h->pos_next, n) || dalloc(h, &h->M, n) || dalloc(h, &h->deg_next, n) || dalloc(h, &h->stash, nnz) ||
       dalloc(h, &h->thr_key, h->ntasks) || dalloc(h, &h->thr_tb, h->ntasks) || dalloc(h, &h->done, h->ntasks) ||
       dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->list[0], h->ntasks) || dalloc(h, &h->list[1], h->ntasks) ||
       dalloc(h, &h->list[2], h->ntasks) || dalloc(h, &h->tile_off, h->ntasks) || dalloc(h, &h->tile_first, h->ntasks + 2) ||
       dalloc(h, &h->cls_flag, 4 * h->ntasks) || dalloc(h, &h->cls_scan, 4 * (h->ntasks + 1)) ||
-      dalloc(h, &h->list_def[0], def_cap) || dalloc(h, &h->list_def[1], def_cap) ||
       dmalloc(h, &h->sort_ws, h->sort_ws_bytes) || dmalloc(h, &h->scan_ws, h->scan_ws_bytes))
     return fail(h, CB_ENOMEM, "device allocation failed");
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
@@ -340,13 +337,11 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   // mirrors the allocations of cb_create + finish_create + size_trade_workspace
   // + a host export's temporary pairs (2m int32)
   const int64_t ntasks = n / 2 + (n & 1);
-  int64_t def_cap = 1;
-  while (def_cap < ntasks) def_cap <<= 1;
   const int64_t nb = int64_t(1) << bucket_bits(n);
   int64_t b = 0;
   b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * nnz + 32 + 8 * kCounters;             // cb_create
   b += 2 * 4 * n + 2 * 8 * (n + 1) + 3 * 4 * n + nnz;                                     // per node, stash
-  b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 16 + 32) + 4 * (ntasks + 2) + 32 + 2 * 4 * def_cap;
+  b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 16 + 32) + 4 * (ntasks + 2) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;
   if (max_trade > kSmemMaxCap || maxdeg > 16384) {
@@ -696,19 +691,8 @@ int cb_stats(cb_handle h, int64_t* out, int count) {
                              h->stream));
   CB_CUDA(h, cudaStreamSynchronize(h->stream));
   const int64_t* hc = h->host_counters;
-  int64_t passes = 1, deferred = 0;
-  for (int i = 1; i < kPassSlots && i < h->last_passes_queued; ++i) {
-    if (hc[8 + i] == 0) break;
-    deferred += hc[8 + i];
-    passes = i + 1;
-  }
-  const int64_t left = hc[4 + h->last_in];   // run by the resolver
-  if (left) {
-    deferred += left;
-    passes += 1;
-  }
-  h->stats[0] = passes;
-  h->stats[1] = deferred;
+  h->stats[0] = hc[4] ? 2 : 1;   // the in-order pass runs only what the first pass deferred
+  h->stats[1] = hc[4];
   h->stats[2] = hc[0];
   h->stats[3] = hc[1] + hc[2];
   h->stats[4] = hc[kCounters - 1];
@@ -735,11 +719,6 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!std::strcmp(key, "tile_max")) {
     if (value < 0 || value > kTileMaxCap) return fail(h, CB_EINVAL, "tile_max out of range [0, 128]");
     h->tile_max = static_cast<int>(value);
-    return CB_OK;
-  }
-  if (!std::strcmp(key, "queued_passes")) {
-    if (value < 0 || value > 64) return fail(h, CB_EINVAL, "queued_passes out of range [0, 64]");
-    h->queued_passes = static_cast<int>(value);
     return CB_OK;
   }
   if (!std::strcmp(key, "tile_paths")) {
@@ -805,7 +784,7 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
   };
   Knob knobs[3] = {{&h->tile_max, {32, 64, 96, 128}, 4},
                    {&h->block_max, {512, 1024, 2048, 0}, 3},
-                   {&h->queued_passes, {4, 8, 12, 16}, 4}};
+                   {&h->smem_max, {2048, 4096, 8192, 0}, 3}};
   float ms = 0;
   if (used < max_steps) rc = trial(&ms);   // first launches load the kernels: not timed as a candidate
   for (int k = 0; k < 3 && rc == CB_OK; ++k) {
@@ -813,19 +792,21 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
     float best_ms = 3.4e38f;
     for (int j = 0; j < knobs[k].ncand && used < max_steps && rc == CB_OK; ++j) {
       *knobs[k].field = knobs[k].cand[j];
-      rc = trial(&ms);
+      if (knobs[k].field == &h->smem_max) rc = size_trade_workspace(h);   // the global workspace follows smem_max
+      if (rc == CB_OK) rc = trial(&ms);
       if (rc == CB_OK && ms < best_ms) {
         best_ms = ms;
         best = knobs[k].cand[j];
       }
     }
     *knobs[k].field = best;
+    if (rc == CB_OK && knobs[k].field == &h->smem_max) rc = size_trade_workspace(h);
   }
   h->timing = timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  const int64_t vals[4] = {h->tile_max, h->block_max, h->queued_passes, static_cast<int64_t>(used)};
+  const int64_t vals[4] = {h->tile_max, h->block_max, h->smem_max, static_cast<int64_t>(used)};
   const int k = chosen ? std::min(count, 4) : 0;
   for (int i = 0; i < k; ++i) chosen[i] = vals[i];
   return k;

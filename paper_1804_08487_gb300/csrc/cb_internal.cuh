@@ -16,7 +16,7 @@ enum DevErr : int32_t {
   kErrRowSide = 2,       // entry written to the wrong row of a trade
   kErrValidate = 3,      // input graph not simple / symmetric / in range
   kErrBucket = 4,        // permutation bucket bookkeeping failed
-  kErrResolve = 5,       // a trade could not run in index order
+  kErrResolve = 5,       // a dependency wait of the in-order pass gave up
 };
 
 constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
@@ -24,7 +24,6 @@ constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
 constexpr int kCounters = 32;       // device counters per handle
-constexpr int kPassSlots = 22;      // pass input counts kept for the statistics ([8, 30))
 
 // One independent graph of a handle.  A plain handle holds one; a batch handle
 // holds many side by side: graph i owns node ids and positions [off, off+span),
@@ -86,8 +85,7 @@ struct Graph {
   int32_t* tile_first = nullptr;           // first tile-class trade of each tile (+ end sentinel)
   int32_t* cls_flag = nullptr;             // 4 x ntasks scratch: class flags and tile weights
   int64_t* cls_scan = nullptr;             // 4 x (ntasks+1) scratch: their exclusive scans
-  int32_t* list_def[2] = {nullptr, nullptr};  // deferred trades, ping-pong
-  int64_t* counters = nullptr;             // list lengths, tile weight, deferred counts, pass counts (kCounters)
+  int64_t* counters = nullptr;             // list lengths, tile weight, deferred count, claims (kCounters)
   int32_t* err = nullptr;                  // latched device error
   // workspaces
   void* ws_global = nullptr;               // global workspace for trades too big for smem
@@ -99,9 +97,6 @@ struct Graph {
   size_t scan_ws_bytes = 0;
   int64_t* host_counters = nullptr;        // host mirror of counters
   int64_t dev_bytes = 0, dev_bytes_peak = 0;   // device memory held by the handle
-  int queued_passes = 12;                  // dependency passes queued per super step before the resolver
-  int64_t last_passes_queued = 0;
-  int last_in = 0;                         // deferred list the resolver read in the last super step
 
   // knobs
   int tile_max = kTileMaxCap;

@@ -19,7 +19,8 @@
 //     threshold (key, lo, hi) of its |A_{u-v}|-th smallest element: u keeps
 //     exactly the elements at or below it (Fig. 2: u receives the first
 //     |A_{u-v}| elements of sigma(D)).  A trade whose dependency has not
-//     published yet is deferred to a later pass.  Per entry it stores one
+//     published yet is marked deferred; one more pass runs the deferred
+//     trades in index order (see k_phase_a_inorder).  Per entry it stores one
 //     byte: whether its own trade moves the edge, whether the far trade will
 //     consider the edge, and the top six bits of the far trade's key for it.
 //  B. Every trade writes its two rows for step g+1: each entry goes to u or v
@@ -41,6 +42,9 @@
 
 namespace cb {
 namespace {
+
+constexpr uint32_t kDeferred = 2;              // done[t]: deferred by the first pass
+constexpr uint32_t kWaitLimit = 1u << 24;      // polls of a dependency before giving up (about 2 s)
 
 // meta bits per entry (phase A)
 constexpr uint8_t kR = 1;       // entry sits in v's row
@@ -77,8 +81,8 @@ struct StepCtx {
   const int32_t* M;
   const int64_t* rp_next;
   int32_t* col_next;
-  int32_t* def_out;
-  unsigned long long* def_count;
+  unsigned long long* def_count;   // trades deferred by the first pass
+  uint32_t wait;                   // 0: defer a trade whose dependency is unpublished; 1: wait for it
   unsigned long long* gws_count;
 };
 
@@ -389,8 +393,20 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     const bool dep = !tr.single && s < t && (cu + cv >= 2) && (cu == 1 || cv == 1);
     if (dep) {
       if (ld_acquire(c.done + s) != c.stamp) {
-        defer = true;
-        continue;
+        if (!c.wait) {
+          defer = true;
+          continue;
+        }
+        // in-order pass: s is complete or held by a running CTA that claimed it
+        // earlier, so the wait ends; the limit turns a broken invariant into an error
+        uint32_t polls = 0;
+        while (ld_acquire(c.done + s) != c.stamp) {
+          if (++polls > kWaitLimit) {
+            latch(c.err, kErrResolve);
+            break;
+          }
+          __nanosleep(128);
+        }
       }
       // replay trade s's decisions on this block
       int m1[2][2] = {{0, 0}, {0, 0}};
@@ -426,7 +442,10 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     w.meta[i] = m;
   }
   if (tm.any(defer)) {
-    if (tm.rank == 0) c.def_out[atomicAdd(c.def_count, 1ull)] = static_cast<int32_t>(t);
+    if (tm.rank == 0) {
+      c.done[t] = kDeferred;
+      atomicAdd(c.def_count, 1ull);
+    }
     tm.sync();
     return;
   }
@@ -825,7 +844,10 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
     // deferred trades leave; the others start selecting their a-th smallest key
     for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
       const int32_t t = sh.t[k];
-      if (sh.flags[k] & 1) c.def_out[atomicAdd(c.def_count, 1ull)] = t;
+      if (sh.flags[k] & 1) {
+        c.done[t] = kDeferred;
+        atomicAdd(c.def_count, 1ull);
+      }
       const bool skip = (sh.flags[k] & 1) || sh.acnt[k] == 0 || 2 * int64_t(t) + 1 >= c.n;
       ta.kk[k] = skip ? 0 : sh.acnt[k];
       ta.shift[k] = skip ? -1 : 60;
@@ -1124,41 +1146,53 @@ __global__ void __launch_bounds__(NT) k_phase_b_block(StepCtx c, const int32_t* 
   for (int64_t q = blockIdx.x; q < len; q += gridDim.x) phase_b(tm, c, list[q]);
 }
 
-// Trades still deferred after the queued passes: one CTA sorts them and runs
-// them in index order, so every trade they wait on is complete when they run
-// (the earliest deferred trade's predecessors always are).  Normally empty.
-__global__ void __launch_bounds__(kBigThreads) k_resolve(StepCtx c, const int32_t* __restrict__ list,
-                                                         const int64_t* __restrict__ count, int32_t* __restrict__ sorted,
-                                                         int smem_max, char* gws, size_t slice) {
+// The trades the first pass deferred, in index order.  CTAs claim chunks of
+// trade indices in increasing order and run the deferred trades of a chunk one
+// after another; a trade waits for an unpublished dependency instead of
+// deferring.  A dependency s < t is either complete (first pass) or deferred
+// too, and then it sits in an earlier chunk or earlier in the same chunk:
+// claimed before t by a CTA that is already running.  By induction on the
+// index, the smallest unfinished claimed trade waits for nothing, so every
+// wait ends whatever the residency of the grid.
+__global__ void __launch_bounds__(kBigThreads) k_phase_a_inorder(StepCtx c, int64_t ntasks, int64_t chunk,
+                                                                 unsigned long long* claim, int smem_max,
+                                                                 char* gws, size_t slice) {
   extern __shared__ __align__(16) char sbuf[];
   __shared__ int64_t red[kBigThreads / 32 + 2];
   __shared__ SelOut sel;
+  __shared__ int64_t first;
+  __shared__ int32_t found[kBigThreads];
+  __shared__ int nfound;
   BlockTeam<kBigThreads> tm(red);
-  const int64_t len = *count;
-  if (len == 0) return;
-  int64_t P = 1;
-  while (P < len) P <<= 1;
-  for (int64_t i = threadIdx.x; i < P; i += blockDim.x) sorted[i] = i < len ? list[i] : 0x7fffffff;
-  __syncthreads();
-  for (int64_t k = 2; k <= P; k <<= 1)
-    for (int64_t j = k >> 1; j > 0; j >>= 1) {
-      for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
-        const int64_t l = i ^ j;
-        if (l > i) {
-          const int32_t x = sorted[i], y = sorted[l];
-          if ((x > y) == ((i & k) == 0)) { sorted[i] = y; sorted[l] = x; }
+  for (;;) {
+    if (threadIdx.x == 0) first = static_cast<int64_t>(atomicAdd(claim, 1ull)) * chunk;
+    __syncthreads();
+    const int64_t lo = first;
+    if (lo >= ntasks) return;
+    const int64_t hi = lo + chunk < ntasks ? lo + chunk : ntasks;
+    for (int64_t base = lo; base < hi; base += kBigThreads) {
+      // the deferred trades of this slice of the chunk, in index order
+      const int64_t t0 = base + threadIdx.x;
+      const int mine = (t0 < hi && __ldcg(c.done + t0) == kDeferred) ? 1 : 0;
+      const int before = static_cast<int>(tm.exscan(mine));
+      if (mine) found[before] = static_cast<int32_t>(t0);
+      if (threadIdx.x == kBigThreads - 1) nfound = before + mine;
+      __syncthreads();
+      const int nf = nfound;
+      for (int q = 0; q < nf; ++q) {
+        const int64_t t = found[q];
+        const TradeRows tr = trade_rows(c, t);
+        const int L = tr.du + tr.dv;
+        char* wsb = sbuf;
+        if (L > smem_max) {
+          wsb = gws + slice * blockIdx.x;
+          if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
         }
+        phase_a(tm, c, t, carve_a(wsb, L), &sel);
       }
       __syncthreads();
     }
-  for (int64_t q = 0; q < len; ++q) {
-    const int64_t t = sorted[q];
-    const TradeRows tr = trade_rows(c, t);
-    const int L = tr.du + tr.dv;
-    char* base = L > smem_max ? gws : sbuf;
-    phase_a(tm, c, t, carve_a(base, L), &sel);
   }
-  if (threadIdx.x == 0 && *c.def_count != 0) latch(c.err, kErrResolve);
 }
 
 // End of a super step: every graph's step counter moves on.
@@ -1183,7 +1217,7 @@ int init_trade_kernels(Graph* h) {
                                   static_cast<int>(ws_a_bytes(kBlockMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
-  CB_CUDA(h, cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(TileA))));
@@ -1258,16 +1292,11 @@ int super_step(Graph* h) {
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
   char* gws = static_cast<char*>(h->ws_global);
-  // phase A, first pass: every class; trades whose dependency has not published
-  // yet go to one deferred list, re-run by the 1024-thread kernel in later
-  // passes.  Passes are queued back to back without a host round trip; a pass
-  // over an empty list exits at once.  Counters: [4 + p] deferred list p,
-  // [8 + i] the input count of pass i + 1 (for the statistics).
-  auto defer_to = [&](int out) {
-    c.def_out = h->list_def[out];
-    c.def_count = ucnt + 4 + out;
-  };
-  defer_to(0);
+  // phase A, first pass: every class; a trade whose dependency has not
+  // published yet is marked deferred.  Counters: [4] deferred trades, [5]
+  // chunks claimed by the in-order pass.
+  c.wait = 0;
+  c.def_count = ucnt + 4;
   if (h->tile_paths & 1) {
     k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt);
   } else {
@@ -1284,33 +1313,15 @@ int super_step(Graph* h) {
                                                                    h->ws_slice);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
-  int in = 0;
-  int64_t passes = 1;
-  auto deferred_pass = [&]() -> int {
-    const int out = 1 - in;
-    CB_CUDA(h, cudaMemsetAsync(cnt + 4 + out, 0, sizeof(int64_t), s));
-    if (passes < kPassSlots)
-      CB_CUDA(h, cudaMemcpyAsync(cnt + 8 + passes, cnt + 4 + in, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    defer_to(out);
-    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, h->list_def[in], cnt + 4 + in, h->smem_max,
-                                                                     gws, h->ws_slice);
+  // second pass: the deferred trades in index order, waiting on dependencies
+  c.wait = 1;
+  {
+    const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
+    k_phase_a_inorder<<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + 5, h->smem_max, gws,
+                                                           h->ws_slice);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
-    in = out;
-    ++passes;
-    return CB_OK;
-  };
-  for (int q = 0; q < h->queued_passes; ++q)
-    if ((rc = deferred_pass())) return rc;
-  // whatever is still deferred runs in index order on one CTA (no host round trip)
-  c.def_out = h->list_def[1 - in];   // never written: the resolver defers nothing
-  c.def_count = ucnt + kCounters - 2;
-  k_resolve<<<1, kBigThreads, big_smem, s>>>(c, h->list_def[in], cnt + 4 + in, h->list_def[1 - in], h->smem_max,
-                                             gws, h->ws_slice);
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-  h->last_passes_queued = passes;
-  h->last_in = in;
+  }
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
   // phase B
   if (h->tile_paths & 2) {

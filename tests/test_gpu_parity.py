@@ -121,8 +121,8 @@ def test_dense_graphs_resolve_dependencies(n, a, b, seed):
     _run_pair(g.row_ptr, g.col, seed, 6, check_stats=lambda s: seen.append(s["passes"]))
     _run_pair(g.row_ptr, g.col, seed + 100, 3, options={"tile_max": 32})
     _run_pair(g.row_ptr, g.col, seed + 200, 3, options={"tile_max": 0, "block_max": 0, "smem_max": 64})
-    _run_pair(g.row_ptr, g.col, seed + 300, 3, options={"queued_passes": 0})   # host-checked passes only
-    _run_pair(g.row_ptr, g.col, seed + 400, 3, options={"queued_passes": 1})
+    _run_pair(g.row_ptr, g.col, seed + 300, 3, options={"tile_paths": 0})
+    _run_pair(g.row_ptr, g.col, seed + 400, 3, options={"block_max": 0, "smem_max": 128})
 
 
 def test_dependency_passes_happen():
