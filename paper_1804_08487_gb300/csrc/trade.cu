@@ -522,11 +522,13 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   tm.sync();
 }
 
-// Phase B for trade t: write its two rows in step g+1's layout (no workspace).
+// Phase B for trade t: write its two rows in step g+1's layout.  Rows are
+// sets, so entries take slots in their new row in any order: each warp claims
+// a run of slots per row with one shared-memory atomic (slots[0..1] count the
+// entries placed in u's and v's new rows).
 template <class Team>
-__device__ void phase_b(Team& tm, const StepCtx& c, int64_t t) {
+__device__ void phase_b(Team& tm, const StepCtx& c, int64_t t, int* slots) {
   const TradeRows tr = trade_rows(c, t);
-  const KeyCtx kc = key_ctx(c, t);
   const int du = tr.du, dv = tr.dv, L = du + dv;
   const int64_t t2 = 2 * t;
   const int32_t pu = c.M[t2];
@@ -542,7 +544,13 @@ __device__ void phase_b(Team& tm, const StepCtx& c, int64_t t) {
     if (tm.rank == 0) latch(c.err, kErrRowLength);
     return;
   }
-  int64_t base0 = 0;   // entries already placed in u's new row
+  if (tm.rank == 0) {
+    slots[0] = 0;
+    slots[1] = 0;
+  }
+  tm.sync();
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
   for (int c0 = 0; c0 < L; c0 += Team::N) {
     const int i = c0 + tm.rank;
     int r2 = 2;        // 2: no entry
@@ -561,23 +569,31 @@ __device__ void phase_b(Team& tm, const StepCtx& c, int64_t t) {
           low = ft < tt;
         } else {
           const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-          low = far_keeps_low(c, kc, s, min(x, y), max(x, y));
+          low = far_keeps_low(c, key_ctx(c, t), s, min(x, y), max(x, y));   // prefix tie: 1 in 64
         }
         y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
       }
       out = c.M[y2];
     }
-    const int is0 = (r2 == 0);
-    const int64_t before0 = tm.exscan(is0);
-    const int64_t in0 = tm.sum(is0);
-    if (r2 == 0) {
-      c.col_next[ou + base0 + before0] = out;
-    } else if (r2 == 1) {
-      c.col_next[ov + (static_cast<int64_t>(i) - (base0 + before0))] = out;
+    const unsigned b0 = __ballot_sync(kFull, r2 == 0), b1 = __ballot_sync(kFull, r2 == 1);
+    int base0 = 0, base1 = 0;
+    if (lane == 0) {
+      if (b0) base0 = atomicAdd(&slots[0], __popc(b0));
+      if (b1) base1 = atomicAdd(&slots[1], __popc(b1));
     }
-    base0 += in0;
+    base0 = __shfl_sync(kFull, base0, 0);
+    base1 = __shfl_sync(kFull, base1, 0);
+    if (r2 == 0) {
+      const int p = base0 + __popc(b0 & below);
+      if (p < du) c.col_next[ou + p] = out; else latch(c.err, kErrRowSide);
+    } else if (r2 == 1) {
+      const int p = base1 + __popc(b1 & below);
+      if (p < dv) c.col_next[ov + p] = out; else latch(c.err, kErrRowSide);
+    }
   }
-  if (tm.rank == 0 && base0 != du) latch(c.err, kErrRowSide);
+  tm.sync();
+  if (tm.rank == 0 && slots[0] != du) latch(c.err, kErrRowSide);
+  tm.sync();   // slots are reused by the team's next trade
 }
 
 // ---------------------------------------------------------- classification
@@ -631,14 +647,12 @@ __global__ void k_tile_first(const int64_t* __restrict__ tile_off, const int64_t
 // ---------------------------------------------------------------- tile path
 
 struct TileShared {              // per-trade data of the current tile
-  KeyCtx kc[kTileTrades];
   int64_t b0[kTileTrades];
   int64_t ou[kTileTrades], ov[kTileTrades];
   int32_t t[kTileTrades];
   int32_t acnt[kTileTrades];    // |A_{u-v}| (phase A)
   int32_t flags[kTileTrades];   // bit0 deferred, bit1 has a dependent later trade
   int16_t du[kTileTrades], dv[kTileTrades], lofs[kTileTrades];
-  int32_t scan[kTileThreads / 32 + 2];
   int64_t first, base;
   int32_t ntr, nslots;
 };
@@ -648,6 +662,7 @@ struct TileEntries {
   int32_t* y;
   uint16_t* owner;
   uint8_t* stash;    // loaded only when non-null
+  KeyCtx* kc;        // per trade, filled only when non-null
 };
 
 __device__ __forceinline__ int tile_owner(const TileShared& sh, int e) {
@@ -679,7 +694,7 @@ __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& 
     const int32_t t = list[k];
     const TradeRows tr = trade_rows(c, t);
     sh.t[j] = t;
-    sh.kc[j] = key_ctx(c, t);
+    if (te.kc) te.kc[j] = key_ctx(c, t);
     sh.b0[j] = tr.b0;
     sh.du[j] = static_cast<int16_t>(tr.du);
     sh.dv[j] = static_cast<int16_t>(tr.dv);
@@ -693,7 +708,7 @@ __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& 
     const int i = e - sh.lofs[k];
     if (i < sh.du[k] + sh.dv[k]) {
       te.owner[e] = static_cast<uint16_t>(k);
-      te.y[e] = __ldcg(c.col + sh.b0[k] + i);
+      if (te.y) te.y[e] = __ldcg(c.col + sh.b0[k] + i);
       if (te.stash) te.stash[e] = c.stash[sh.b0[k] + i];
     } else {
       te.owner[e] = kNoOwner;
@@ -708,6 +723,7 @@ __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& 
 // |A_{u-v}|-th smallest key of every trade from a radix select with 4-bit
 // digits that all trades of the tile run together.
 struct TileA {
+  KeyCtx kc[kTileTrades];                 // key parameters of each trade's graph
   uint64_t key[kTileSlots];               // full own key
   unsigned long long hash[kTileHash];     // (key+1) << 16 | flags
   union {
@@ -768,7 +784,8 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (int i = threadIdx.x; i < kTileHash; i += blockDim.x) ta.hash[i] = 0ull;
-    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, nullptr}, list, tile_off, tile_first, ntrades, total_w, tile))
+    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, nullptr, ta.kc}, list, tile_off, tile_first, ntrades, total_w,
+                    tile))
       continue;
     const int E = sh.nslots;
     // entries into the hash: presence bit (row, column) per (trade, far trade)
@@ -821,7 +838,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
             int g2 = gam;
             if (cnt_row[rho] == 1) {
               const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(2 * s + gam);
-              g2 = far_keeps_low(c, sh.kc[k], s, min(x, y), max(x, y)) ? 0 : 1;
+              g2 = far_keeps_low(c, ta.kc[k], s, min(x, y), max(x, y)) ? 0 : 1;
             }
             m1[rho][g2] = 1;
             if (rho == r && gam == (yy & 1)) col_now = g2;
@@ -830,7 +847,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
       }
       const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
       const uint32_t lo = min(x, y), hi = max(x, y);
-      const EdgeKeys ek = edge_keys(sh.kc[k], lo, hi);
+      const EdgeKeys ek = edge_keys(ta.kc[k], lo, hi);
       const bool lo_mine = (lo >> 1) == static_cast<uint32_t>(t);
       ta.key[e] = lo_mine ? ek.lo_side : ek.hi_side;
       ta.far[e] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
@@ -994,51 +1011,14 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
   }
 }
 
-// Exclusive prefix sum over sh.nslots values v(e) held in `val` (uint8), in
-// place into `out` (int32); 256 threads, each over a contiguous chunk.
-__device__ void tile_scan(TileShared& sh, const uint8_t* val, int32_t* out, int E) {
-  const int per = (E + kTileThreads - 1) / kTileThreads;
-  const int b = threadIdx.x * per;
-  int local = 0;
-  for (int j = 0; j < per; ++j)
-    if (b + j < E) local += val[b + j];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int x = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(kFull, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sh.scan[w] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int tv = threadIdx.x < kTileThreads / 32 ? sh.scan[threadIdx.x] : 0;
-    int sv = tv;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(kFull, sv, o);
-      if (threadIdx.x >= o) sv += y;
-    }
-    if (threadIdx.x < kTileThreads / 32) sh.scan[threadIdx.x] = sv - tv;
-  }
-  __syncthreads();
-  int run = x - local + sh.scan[w];
-  for (int j = 0; j < per; ++j)
-    if (b + j < E) {
-      out[b + j] = run;
-      run += val[b + j];
-    }
-  __syncthreads();
-}
-
 struct TileB {
-  int32_t pre[kTileSlots];     // prefix count of entries going to u's new row
-  int32_t y[kTileSlots];       // entries, then their step-(g+1) positions
+  int32_t slot[2 * kTileTrades];   // entries placed so far in each trade's new u / v row
   uint16_t owner[kTileSlots];
-  uint8_t stash[kTileSlots];   // stash byte, then the new side
-  uint8_t to_u[kTileSlots];
 };
 
+// Phase B for a tile of small trades, one thread per entry: each entry is read,
+// resolved and written in one pass; entries of the same trade and side in a
+// warp claim their slots together (match_any + one shared-memory atomic).
 __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const int32_t* __restrict__ list,
                                                                const int64_t* __restrict__ tile_off,
                                                                const int32_t* __restrict__ tile_first,
@@ -1047,8 +1027,11 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
   __shared__ TileB tb;
   const int64_t ntrades = counts[0], total_w = counts[3];
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (!tile_setup(c, sh, TileEntries{tb.y, tb.owner, tb.stash}, list, tile_off, tile_first, ntrades, total_w, tile))
+    if (!tile_setup(c, sh, TileEntries{nullptr, tb.owner, nullptr, nullptr}, list, tile_off, tile_first, ntrades,
+                    total_w, tile))
       continue;
     const int E = sh.nslots;
     for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
@@ -1063,52 +1046,53 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
         bad |= c.rp_next[pv + 1] - sh.ov[k] != sh.dv[k];
       }
       if (bad) latch(c.err, kErrRowLength);
-    }
-    // side and far end of every entry
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = tb.owner[e];
-      tb.to_u[e] = 0;
-      if (k == kNoOwner) continue;
-      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
-      const int r = (e - sh.lofs[k]) >= sh.du[k];
-      const int32_t yy = tb.y[e];
-      const uint8_t st = tb.stash[e];
-      const int r2 = r ^ (st & 1);
-      int32_t y2 = yy;
-      if (st & 2) {
-        const int64_t s = yy >> 1;
-        const uint32_t ft = st >> 2, tt = c.thr_top[s];
-        bool low;
-        if (ft != tt) {
-          low = ft < tt;
-        } else {
-          const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-          low = far_keeps_low(c, sh.kc[k], s, min(x, y), max(x, y));
-        }
-        y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
-      }
-      tb.y[e] = c.M[y2];
-      tb.to_u[e] = static_cast<uint8_t>(r2 == 0);
-      tb.stash[e] = static_cast<uint8_t>(r2);
+      tb.slot[2 * k] = 0;
+      tb.slot[2 * k + 1] = 0;
     }
     __syncthreads();
-    tile_scan(sh, tb.to_u, tb.pre, E);
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = tb.owner[e];
-      if (k == kNoOwner) continue;
-      const int lo0 = sh.lofs[k];
-      const int before0 = tb.pre[e] - tb.pre[lo0];
-      if (tb.stash[e] == 0) {
-        c.col_next[sh.ou[k] + before0] = tb.y[e];
-      } else {
-        c.col_next[sh.ov[k] + (e - lo0 - before0)] = tb.y[e];
+    const int Er = (E + kTileThreads - 1) / kTileThreads * kTileThreads;   // every lane takes part in the match
+    for (int e = threadIdx.x; e < Er; e += blockDim.x) {
+      const int k = e < E ? tb.owner[e] : kNoOwner;
+      int key = -1;     // (local trade, new side) of the entry
+      int32_t out = 0;
+      if (k != kNoOwner) {
+        const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
+        const int i = e - sh.lofs[k];
+        const int r = i >= sh.du[k];
+        const int32_t yy = __ldcg(c.col + sh.b0[k] + i);
+        const uint8_t st = c.stash[sh.b0[k] + i];
+        const int r2 = r ^ (st & 1);
+        int32_t y2 = yy;
+        if (st & 2) {
+          const int64_t s = yy >> 1;
+          const uint32_t ft = st >> 2, tt = c.thr_top[s];
+          bool low;
+          if (ft != tt) {
+            low = ft < tt;
+          } else {
+            const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
+            low = far_keeps_low(c, key_ctx(c, sh.t[k]), s, min(x, y), max(x, y));   // prefix tie: 1 in 64
+          }
+          y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
+        }
+        out = c.M[y2];
+        key = 2 * k + r2;
       }
-      const int L = sh.du[k] + sh.dv[k];
-      if (e == lo0 + L - 1) {   // last entry of the trade: u's row must be exactly full
-        const int n0 = before0 + (tb.stash[e] == 0);
-        if (n0 != sh.du[k]) latch(c.err, kErrRowSide);
+      const unsigned grp = __match_any_sync(kFull, key);
+      const int leader = __ffs(grp) - 1;
+      int base = 0;
+      if (lane == leader && key >= 0) base = atomicAdd(&tb.slot[key], __popc(grp));
+      base = __shfl_sync(kFull, base, leader);
+      if (key >= 0) {
+        const int p = base + __popc(grp & below);
+        const int r2 = key & 1;
+        if (p < (r2 ? sh.dv[k] : sh.du[k])) c.col_next[(r2 ? sh.ov[k] : sh.ou[k]) + p] = out;
+        else latch(c.err, kErrRowSide);
       }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x)   // u's new row must be exactly full
+      if (tb.slot[2 * k] != sh.du[k]) latch(c.err, kErrRowSide);
     __syncthreads();
   }
 }
@@ -1138,12 +1122,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_phase_b_block(StepCtx c, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(NT, NT == 256 ? 8 : 2) k_phase_b_block(StepCtx c, const int32_t* __restrict__ list,
                                                       const int64_t* __restrict__ count) {
   __shared__ int64_t red[NT / 32 + 2];
+  __shared__ int slots[2];
   BlockTeam<NT> tm(red);
   const int64_t len = *count;
-  for (int64_t q = blockIdx.x; q < len; q += gridDim.x) phase_b(tm, c, list[q]);
+  for (int64_t q = blockIdx.x; q < len; q += gridDim.x) phase_b(tm, c, list[q], slots);
 }
 
 // The trades the first pass deferred, in index order.  CTAs claim chunks of
