@@ -158,57 +158,49 @@ __device__ __forceinline__ bool far_keeps_low(const StepCtx& c, const KeyCtx& kc
 }
 
 // ------------------------------------------------------------ hash table
+//
+// One slot per far trade s of the current trade: high word s + 1 (0 = empty);
+// low word bit (2 rho + gamma) = the trade's node at row rho (0: u, 1: v) is
+// adjacent to s's node at position 2s + gamma (the 2x2 block matrix), bit
+// (4 + 2 rho + gamma) = that entry is moved by the trade (its flip).
 
-__device__ __forceinline__ uint32_t hslot(int32_t y, int lgH) {
-  return (static_cast<uint32_t>(y) * 0x9E3779B1u) >> (32 - lgH);
-}
+__device__ __forceinline__ uint32_t hslot(uint32_t s, int lgH) { return (s * 0x9E3779B1u) >> (32 - lgH); }
 
-__device__ __forceinline__ void h_insert(unsigned long long* h, int lgH, int32_t y, uint32_t bit) {
-  const unsigned long long key = static_cast<unsigned long long>(static_cast<uint32_t>(y) + 1u) << 32;
+// Sets `bit` in the slot of far trade s (creating it); returns the slot.
+__device__ __forceinline__ int h_insert(unsigned long long* h, int lgH, uint32_t s, uint32_t bit) {
+  const unsigned long long key = static_cast<unsigned long long>(s + 1u) << 32;
   const uint32_t mask = (1u << lgH) - 1u;
-  uint32_t s = hslot(y, lgH);
+  uint32_t p = hslot(s, lgH);
   for (;;) {
-    unsigned long long cur = h[s];
+    unsigned long long cur = h[p];
     if ((cur >> 32) == 0) {
-      const unsigned long long prev = atomicCAS(&h[s], 0ull, key | bit);
-      if (prev == 0ull) return;
+      const unsigned long long prev = atomicCAS(&h[p], 0ull, key | bit);
+      if (prev == 0ull) return static_cast<int>(p);
       cur = prev;
     }
     if ((cur >> 32) == (key >> 32)) {
-      atomicOr(reinterpret_cast<unsigned int*>(&h[s]), bit);
-      return;
+      atomicOr(reinterpret_cast<unsigned int*>(&h[p]), bit);
+      return static_cast<int>(p);
     }
-    s = (s + 1) & mask;
+    p = (p + 1) & mask;
   }
-}
-
-// Slot of y, or -1 if y is not in the table.
-__device__ __forceinline__ int h_find(const unsigned long long* h, int lgH, int32_t y) {
-  const uint32_t want = static_cast<uint32_t>(y) + 1u;
-  const uint32_t mask = (1u << lgH) - 1u;
-  uint32_t s = hslot(y, lgH);
-  for (;;) {
-    const unsigned long long cur = h[s];
-    const uint32_t k = static_cast<uint32_t>(cur >> 32);
-    if (k == want) return static_cast<int>(s);
-    if (k == 0) return -1;
-    s = (s + 1) & mask;
-  }
-}
-__device__ __forceinline__ uint32_t h_flags(const unsigned long long* h, int lgH, int32_t y) {
-  const int s = h_find(h, lgH, y);
-  return s < 0 ? 0u : static_cast<uint32_t>(h[s]);
 }
 
 // ---------------------------------------------------------- workspace
 
+constexpr int kSelBits = 10;              // first radix digit: top 10 bits of the key
+constexpr int kSelBins = 1 << kSelBits;
+
+// meta bits per entry (team paths add the neighbour's column bit)
+constexpr uint8_t kCol = 16;    // neighbour sits at the odd position 2s+1
+
 struct WsA {
-  int32_t* y;                 // entries (positions)
+  int32_t* slot;              // hash slot of the entry's far trade (-1: the edge {u,v})
   uint16_t* top;              // top 16 bits of the own key
   uint8_t* meta;
   uint8_t* far;               // top 6 bits of the far trade's key
   unsigned long long* hash;   // 2^lgH slots
-  uint32_t* hist;             // 256 bins
+  uint32_t* hist;             // kSelBins bins
   int lgH;
 };
 
@@ -220,7 +212,7 @@ __host__ __device__ inline int hash_lg(int L) {
 }
 __host__ __device__ inline size_t ws_a_bytes(int L) {
   const size_t L16 = (static_cast<size_t>(L) + 15) & ~size_t(15);
-  return (size_t(1) << hash_lg(L)) * 8 + 1024 + L16 * 4 + L16 * 2 + L16 * 2 + 64;
+  return (size_t(1) << hash_lg(L)) * 8 + kSelBins * 4 + L16 * 4 + L16 * 2 + L16 + L16 + 64;
 }
 __device__ inline WsA carve_a(void* base, int L) {
   const size_t L16 = (static_cast<size_t>(L) + 15) & ~size_t(15);
@@ -228,8 +220,8 @@ __device__ inline WsA carve_a(void* base, int L) {
   WsA w;
   w.lgH = hash_lg(L);
   w.hash = reinterpret_cast<unsigned long long*>(p); p += (size_t(1) << w.lgH) * 8;
-  w.hist = reinterpret_cast<uint32_t*>(p); p += 1024;
-  w.y = reinterpret_cast<int32_t*>(p); p += L16 * 4;
+  w.hist = reinterpret_cast<uint32_t*>(p); p += kSelBins * 4;
+  w.slot = reinterpret_cast<int32_t*>(p); p += L16 * 4;
   w.top = reinterpret_cast<uint16_t*>(p); p += L16 * 2;
   w.meta = reinterpret_cast<uint8_t*>(p); p += L16;
   w.far = reinterpret_cast<uint8_t*>(p);
@@ -245,31 +237,37 @@ __device__ __forceinline__ uint32_t hi_of(int64_t t2, uint8_t m, int32_t y) {
 __device__ __forceinline__ uint64_t own_key(const KeyCtx& kc, int64_t t, uint32_t lo, uint32_t hi) {
   return side_key(kc, lo, hi, (lo >> 1) == static_cast<uint32_t>(t));
 }
+// The neighbour position of a team-path entry (its far trade from the hash).
+__device__ __forceinline__ int32_t entry_y(const WsA& w, int64_t t2, int i) {
+  const uint8_t m = w.meta[i];
+  if (m & kUV) return static_cast<int32_t>(t2 + 1 - (m & kR));
+  const uint32_t s = static_cast<uint32_t>(w.hash[w.slot[i]] >> 32) - 1u;
+  return static_cast<int32_t>(2 * s + ((m & kCol) ? 1 : 0));
+}
 
-// One radix digit of the 16-bit key prefixes: histogram of (top >> shift) & 255
-// over elements of D whose high byte equals `pre` (shift 0) or over all of D
-// (shift 8), then the bin holding the kk-th element.
+// One radix digit of the 16-bit key prefixes: histogram of bits
+// [shift, shift + bits) over the elements of D whose bits above equal `pre`
+// (all of D when shift + bits == 16), then the bin holding the kk-th element.
 template <class Team>
-__device__ void radix_digit(Team& tm, const WsA& w, int L, int shift, uint32_t pre, int kk, SelOut* out) {
-  constexpr int BPM = (256 + Team::N - 1) / Team::N;
-  for (int b = tm.rank; b < 256; b += Team::N) w.hist[b] = 0;
+__device__ void radix_digit(Team& tm, const WsA& w, int L, int shift, int bits, uint32_t pre, int kk, SelOut* out) {
+  const int nb = 1 << bits;
+  const int bpm = (nb + Team::N - 1) / Team::N;
+  for (int b = tm.rank; b < nb; b += Team::N) w.hist[b] = 0;
   tm.sync();
   for (int i = tm.rank; i < L; i += Team::N) {
     if (!(w.meta[i] & kInD)) continue;
     const uint32_t tp = w.top[i];
-    if (shift == 8 || (tp >> 8) == pre) atomicAdd(&w.hist[(tp >> shift) & 255u], 1u);
+    if (shift + bits == 16 || (tp >> (shift + bits)) == pre) atomicAdd(&w.hist[(tp >> shift) & (nb - 1)], 1u);
   }
   tm.sync();
-  const int b0 = tm.rank * BPM;
+  const int b0 = tm.rank * bpm;
   int local = 0;
-#pragma unroll
-  for (int j = 0; j < BPM; ++j)
-    if (b0 + j < 256) local += static_cast<int>(w.hist[b0 + j]);
+  for (int j = 0; j < bpm; ++j)
+    if (b0 + j < nb) local += static_cast<int>(w.hist[b0 + j]);
   int below = static_cast<int>(tm.exscan(local));
-#pragma unroll
-  for (int j = 0; j < BPM; ++j) {
+  for (int j = 0; j < bpm; ++j) {
     const int b = b0 + j;
-    if (b < 256) {
+    if (b < nb) {
       const int hc = static_cast<int>(w.hist[b]);
       if (below < kk && kk <= below + hc) {
         out->bin = b;
@@ -282,27 +280,28 @@ __device__ void radix_digit(Team& tm, const WsA& w, int L, int shift, uint32_t p
   tm.sync();
 }
 
-// k-th smallest (1-based) (key, lo, hi) over D: two radix digits on the stored
-// 16-bit key prefixes, then the full keys of the few remaining candidates.
+// k-th smallest (1-based) (key, lo, hi) over D: one 10-bit radix digit on the
+// stored 16-bit key prefixes (keys are uniform, so the chosen bin holds about
+// |D|/1024 elements), a 6-bit digit only if that bin is crowded, then the
+// full keys of the few remaining candidates.
 template <class Team>
 __device__ void select_kth(Team& tm, const KeyCtx& kc, const WsA& w, int L, int64_t t, int k, SelOut* out) {
+  constexpr int kCand = 32;   // candidates ranked in shared memory (the histogram's space)
   const int64_t t2 = 2 * t;
-  radix_digit(tm, w, L, 8, 0, k, out);
-  const uint32_t b1 = static_cast<uint32_t>(out->bin);
+  radix_digit(tm, w, L, 16 - kSelBits, kSelBits, 0, k, out);
+  uint32_t prefix = static_cast<uint32_t>(out->bin);   // of the top `plen` bits
+  int plen = kSelBits;
   int kk = k - out->below;
   int cnt = out->cnt;
   tm.sync();
-  uint32_t prefix = b1 << 8;
-  bool full16 = false;
-  if (cnt > 1) {
-    radix_digit(tm, w, L, 0, b1, kk, out);
-    prefix |= static_cast<uint32_t>(out->bin);
+  if (cnt > kCand) {
+    radix_digit(tm, w, L, 0, 16 - kSelBits, prefix, kk, out);
+    prefix = (prefix << (16 - kSelBits)) | static_cast<uint32_t>(out->bin);
+    plen = 16;
     kk -= out->below;
     cnt = out->cnt;
     tm.sync();
-    full16 = true;
   }
-  constexpr int kCand = 32;   // candidates ranked in shared memory (the histogram's space)
   uint64_t* ck = reinterpret_cast<uint64_t*>(w.hist);
   uint64_t* ctb = ck + kCand;
   int* ncand = reinterpret_cast<int*>(ctb + kCand);
@@ -313,9 +312,9 @@ __device__ void select_kth(Team& tm, const KeyCtx& kc, const WsA& w, int L, int6
   for (int i = tm.rank; i < L; i += Team::N) {
     const uint8_t m = w.meta[i];
     if (!(m & kInD)) continue;
-    const uint32_t tp = w.top[i];
-    if (full16 ? (tp != prefix) : ((tp >> 8) != b1)) continue;
-    const uint32_t lo = lo_of(t2, m, w.y[i]), hi = hi_of(t2, m, w.y[i]);
+    if ((static_cast<uint32_t>(w.top[i]) >> (16 - plen)) != prefix) continue;
+    const int32_t y = entry_y(w, t2, i);
+    const uint32_t lo = lo_of(t2, m, y), hi = hi_of(t2, m, y);
     const uint64_t ki = own_key(kc, t, lo, hi), tbi = tie_break(lo, hi);
     if (cnt == 1) {            // the only element with this prefix
       out->key = ki;
@@ -324,14 +323,14 @@ __device__ void select_kth(Team& tm, const KeyCtx& kc, const WsA& w, int L, int6
       const int q = atomicAdd(ncand, 1);
       ck[q] = ki;
       ctb[q] = tbi;
-    } else {                   // many equal prefixes: rank against every other candidate
+    } else {                   // many equal 16-bit prefixes: rank against every other candidate
       int r = 0;
       for (int j = 0; j < L; ++j) {
         const uint8_t mj = w.meta[j];
         if (j == i || !(mj & kInD)) continue;
-        const uint32_t tj = w.top[j];
-        if (full16 ? (tj != prefix) : ((tj >> 8) != b1)) continue;
-        const uint32_t loj = lo_of(t2, mj, w.y[j]), hij = hi_of(t2, mj, w.y[j]);
+        if ((static_cast<uint32_t>(w.top[j]) >> (16 - plen)) != prefix) continue;
+        const int32_t yj = entry_y(w, t2, j);
+        const uint32_t loj = lo_of(t2, mj, yj), hij = hi_of(t2, mj, yj);
         const uint64_t kj = own_key(kc, t, loj, hij);
         r += (kj < ki || (kj == ki && tie_break(loj, hij) < tbi));
       }
@@ -362,33 +361,43 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   const KeyCtx kc = key_ctx(c, t);
   const int du = tr.du, dv = tr.dv, L = du + dv;
   const int H = 1 << w.lgH;
-  for (int i = tm.rank; i < H; i += Team::N) w.hash[i] = 0ull;
-  for (int i = tm.rank; i < L; i += Team::N) w.y[i] = __ldcg(c.col + tr.b0 + i);
-  tm.sync();
-  for (int i = tm.rank; i < L; i += Team::N) h_insert(w.hash, w.lgH, w.y[i], i >= du ? 2u : 1u);
-  tm.sync();
   const int64_t t2 = 2 * t;
+  for (int i = tm.rank; i < H; i += Team::N) w.hash[i] = 0ull;
+  tm.sync();
+  // entries into the hash: presence bit (row, column) in the far trade's slot
+  for (int i = tm.rank; i < L; i += Team::N) {
+    const int r = i >= du;
+    const int32_t yy = __ldcg(c.col + tr.b0 + i);
+    const int64_t s = yy >> 1;
+    uint8_t m = static_cast<uint8_t>(r | ((yy & 1) ? kCol : 0));
+    if (s == t) {
+      m |= kUV;
+      w.slot[i] = -1;
+    } else {
+      w.slot[i] = h_insert(w.hash, w.lgH, static_cast<uint32_t>(s), 1u << (2 * r + (yy & 1)));
+    }
+    w.meta[i] = m;
+  }
+  tm.sync();
   bool defer = false, has_dependents = false;
   int cnt_a = 0;
   for (int i = tm.rank; i < L; i += Team::N) {
-    const int r = i >= du;
-    const int32_t yy = w.y[i];
-    const int64_t s = yy >> 1;
+    uint8_t m = w.meta[i];
     w.far[i] = 0;
     w.top[i] = 0;
-    if (s == t) {
-      w.meta[i] = static_cast<uint8_t>(r | kUV);
-      continue;
-    }
-    const int32_t e0 = static_cast<int32_t>(2 * s);
-    const uint32_t f0 = h_flags(w.hash, w.lgH, e0), f1 = h_flags(w.hash, w.lgH, e0 + 1);
-    const int u0 = f0 & 1, v0 = (f0 >> 1) & 1, u1 = f1 & 1, v1 = (f1 >> 1) & 1;
+    if (m & kUV) continue;
+    const int r = m & kR;
+    const int colb = (m & kCol) ? 1 : 0;
+    const unsigned long long hv = w.hash[w.slot[i]];
+    const int64_t s = static_cast<int64_t>(hv >> 32) - 1;
+    const uint32_t f = static_cast<uint32_t>(hv);
+    const int u0 = f & 1, u1 = (f >> 1) & 1, v0 = (f >> 2) & 1, v1 = (f >> 3) & 1;
     const int cu = u0 + u1, cv = v0 + v1;
-    uint8_t m = static_cast<uint8_t>(r | (u0 << 4) | (u1 << 5) | (v0 << 6) | (v1 << 7));
+    const int32_t yy = static_cast<int32_t>(2 * s + colb);
     // a later trade s depends on t when it sees >= 2 block edges and one of
     // its own nodes holds exactly one of them
     if (!tr.single && s > t && s < c.T && cu + cv >= 2 && (u0 + v0 == 1 || u1 + v1 == 1)) has_dependents = true;
-    int col_now = yy & 1;                            // s-node of this edge when t acts
+    int col_now = colb;                              // s-node of this edge when t acts
     int other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
     const bool dep = !tr.single && s < t && (cu + cv >= 2) && (cu == 1 || cv == 1);
     if (dep) {
@@ -419,11 +428,11 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
           if (!bits[rho][gam]) continue;
           int g2 = gam;
           if (cnt_row[rho] == 1) {
-            const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(e0 + gam);
+            const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(2 * s + gam);
             g2 = far_keeps_low(c, kc, s, min(x, y), max(x, y)) ? 0 : 1;
           }
           m1[rho][g2] = 1;
-          if (rho == r && gam == (yy & 1)) col_now = g2;
+          if (rho == r && gam == colb) col_now = g2;
         }
       other = m1[1 - r][col_now];
     }
@@ -458,7 +467,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     tt = sel->tb;
   }
   const uint32_t tk16 = static_cast<uint32_t>(tk >> 48);
-  // own decisions; flips are recorded in the hash for the far-side test
+  // own decisions; flips are recorded in the far trade's slot
   for (int i = tm.rank; i < L; i += Team::N) {
     const uint8_t m = w.meta[i];
     if (!(m & kInD)) continue;
@@ -468,13 +477,13 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     if (tp != tk16) {
       low = tp < tk16;
     } else {
-      const uint32_t lo = lo_of(t2, m, w.y[i]), hi = hi_of(t2, m, w.y[i]);
+      const int32_t y = entry_y(w, t2, i);
+      const uint32_t lo = lo_of(t2, m, y), hi = hi_of(t2, m, y);
       low = at_or_below(own_key(kc, t, lo, hi), tie_break(lo, hi), tk, tt);
     }
     if ((low ? 0 : 1) != r) {
       w.meta[i] = m | kFlip;
-      const int slot = h_find(w.hash, w.lgH, w.y[i]);
-      atomicOr(reinterpret_cast<unsigned int*>(&w.hash[slot]), 4u << r);
+      atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
     }
   }
   tm.sync();
@@ -485,25 +494,24 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     int in_far = 0;
     if (!(m & kUV)) {
       const int r = m & kR;
-      const int32_t yy = w.y[i];
-      const int64_t s = yy >> 1;
-      const int u0 = (m >> 4) & 1, u1 = (m >> 5) & 1, v0 = (m >> 6) & 1, v1 = (m >> 7) & 1;
+      const unsigned long long hv = w.hash[w.slot[i]];
+      const int64_t s = static_cast<int64_t>(hv >> 32) - 1;
+      const uint32_t fl = static_cast<uint32_t>(hv);
+      const int u0 = fl & 1, u1 = (fl >> 1) & 1, v0 = (fl >> 2) & 1, v1 = (fl >> 3) & 1;
       const int cr = r ? (v0 + v1) : (u0 + u1);
       if (tr.single || s < t) {
         in_far = (cr == 1);                 // trade s acted before t: initial block
       } else if (s < c.T) {
         if (u0 + u1 + v0 + v1 == 1) {
           in_far = 1;
-        } else {                            // block after t's own decisions
-          const int32_t e0 = static_cast<int32_t>(2 * s);
-          const uint32_t f0 = h_flags(w.hash, w.lgH, e0), f1 = h_flags(w.hash, w.lgH, e0 + 1);
+        } else {                            // block after t's own decisions: presence bits 0..3, flips 4..7
           const int myrow = r ^ f;
           int same = 0;
-          // post-trade row of each block edge: u-row entries move to v when flipped, and back
-          same += (f0 & 1) && (((f0 >> 2) & 1) == myrow);
-          same += ((f0 >> 1) & 1) && ((1 ^ ((f0 >> 3) & 1)) == myrow);
-          same += (f1 & 1) && (((f1 >> 2) & 1) == myrow);
-          same += ((f1 >> 1) & 1) && ((1 ^ ((f1 >> 3) & 1)) == myrow);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (!((fl >> q) & 1)) continue;
+            same += (((q >> 1) ^ ((fl >> (4 + q)) & 1)) == myrow);
+          }
           in_far = (same == 1);
         }
       }
