@@ -654,9 +654,11 @@ __global__ void k_tile_first(const int64_t* __restrict__ tile_off, const int64_t
 
 // ---------------------------------------------------------------- tile path
 
+// Shared memory of the tile kernels is budgeted so that four 256-thread CTAs
+// fit on an SM (228 KB, 1 KB reserved per CTA): the threshold kernel's
+// TileShared + TileA must stay below 56 KB.
 struct TileShared {              // per-trade data of the current tile
   int64_t b0[kTileTrades];
-  int64_t ou[kTileTrades], ov[kTileTrades];
   int32_t t[kTileTrades];
   int32_t acnt[kTileTrades];    // |A_{u-v}| (phase A)
   int32_t flags[kTileTrades];   // bit0 deferred, bit1 has a dependent later trade
@@ -743,9 +745,11 @@ struct TileA {
   uint16_t owner[kTileSlots];
   uint8_t meta[kTileSlots];
   uint8_t far[kTileSlots];
-  int32_t kk[kTileTrades];                // rank still sought (1-based)
+  int16_t kk[kTileTrades];                // rank still sought (1-based; |D| <= 128)
   int8_t shift[kTileTrades];
 };
+
+static_assert(sizeof(TileShared) + sizeof(TileA) + 1024 <= 233472 / 4, "tile threshold kernel: 4 CTAs per SM");
 
 __device__ __forceinline__ uint64_t tile_hkey(int k, int64_t s) {
   return ((static_cast<uint64_t>(k) << 31) | static_cast<uint64_t>(s)) + 1;
@@ -874,7 +878,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
         atomicAdd(c.def_count, 1ull);
       }
       const bool skip = (sh.flags[k] & 1) || sh.acnt[k] == 0 || 2 * int64_t(t) + 1 >= c.n;
-      ta.kk[k] = skip ? 0 : sh.acnt[k];
+      ta.kk[k] = static_cast<int16_t>(skip ? 0 : sh.acnt[k]);
       ta.shift[k] = skip ? -1 : 60;
       ta.prefix[k] = 0;
     }
@@ -903,7 +907,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
           const uint32_t w = ta.hist[k * 8 + (b >> 1)];
           const int cb = static_cast<int>((b & 1) ? (w >> 16) : (w & 0xffffu));
           if (below < kk && kk <= below + cb) {
-            ta.kk[k] = kk - below;
+            ta.kk[k] = static_cast<int16_t>(kk - below);
             ta.prefix[k] |= static_cast<uint64_t>(b) << sft;
             if (cb == 1 || sft == 0) {
               ta.shift[k] = static_cast<int8_t>(-2 - sft);   // resolved; -2 - shift keeps the last shift
@@ -1020,6 +1024,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
 }
 
 struct TileB {
+  int64_t ou[kTileTrades], ov[kTileTrades];   // each trade's new u / v row offsets
   int32_t slot[2 * kTileTrades];   // entries placed so far in each trade's new u / v row
   uint16_t owner[kTileSlots];
 };
@@ -1045,13 +1050,13 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
     for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
       const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
       const int32_t pu = c.M[t2];
-      sh.ou[k] = c.rp_next[pu];
-      bool bad = c.rp_next[pu + 1] - sh.ou[k] != sh.du[k];
-      sh.ov[k] = 0;
+      tb.ou[k] = c.rp_next[pu];
+      bool bad = c.rp_next[pu + 1] - tb.ou[k] != sh.du[k];
+      tb.ov[k] = 0;
       if (sh.dv[k] > 0) {
         const int32_t pv = c.M[t2 + 1];
-        sh.ov[k] = c.rp_next[pv];
-        bad |= c.rp_next[pv + 1] - sh.ov[k] != sh.dv[k];
+        tb.ov[k] = c.rp_next[pv];
+        bad |= c.rp_next[pv + 1] - tb.ov[k] != sh.dv[k];
       }
       if (bad) latch(c.err, kErrRowLength);
       tb.slot[2 * k] = 0;
@@ -1094,7 +1099,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const 
       if (key >= 0) {
         const int p = base + __popc(grp & below);
         const int r2 = key & 1;
-        if (p < (r2 ? sh.dv[k] : sh.du[k])) c.col_next[(r2 ? sh.ov[k] : sh.ou[k]) + p] = out;
+        if (p < (r2 ? sh.dv[k] : sh.du[k])) c.col_next[(r2 ? tb.ov[k] : tb.ou[k]) + p] = out;
         else latch(c.err, kErrRowSide);
       }
     }
@@ -1214,6 +1219,11 @@ int init_trade_kernels(Graph* h) {
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(TileA))));
+  // shared memory, not L1, limits how many CTAs of these kernels an SM holds
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
   return CB_OK;
 }
 
