@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) k_rows_warp(RowArgs a) {
 // Long rows: one CTA per row, shared memory or a global slice per CTA.
 __global__ void __launch_bounds__(256) k_rows_block(RowArgs a, int32_t* gws, int64_t slice) {
   extern __shared__ int32_t sbuf[];
-  __shared__ int64_t red[256 / 32 + 2];
+  __shared__ int64_t red[BlockTeam<256>::kRedSlots];
   BlockTeam<256> tm(red);
   for (int64_t q = blockIdx.x; q < a.nrows; q += gridDim.x) {
     const int64_t len = a.dst_rp[q + 1] - a.dst_rp[q];

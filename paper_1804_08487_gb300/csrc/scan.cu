@@ -14,7 +14,7 @@ constexpr int64_t kScanTile = kScanThreads * kScanItems;
 template <class Tin>
 __global__ void __launch_bounds__(kScanThreads) k_block_sums(const Tin* __restrict__ in, int64_t n,
                                                              int64_t* __restrict__ bsum) {
-  __shared__ int64_t red[kScanThreads / 32 + 2];
+  __shared__ int64_t red[BlockTeam<kScanThreads>::kRedSlots];
   BlockTeam<kScanThreads> tm(red);
   const int64_t base = blockIdx.x * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
   int64_t s = 0;
@@ -29,7 +29,7 @@ template <class Tin>
 __global__ void __launch_bounds__(kScanThreads) k_block_scan(const Tin* __restrict__ in, int64_t n,
                                                              const int64_t* __restrict__ boff,
                                                              int64_t* __restrict__ out) {
-  __shared__ int64_t red[kScanThreads / 32 + 2];
+  __shared__ int64_t red[BlockTeam<kScanThreads>::kRedSlots];
   BlockTeam<kScanThreads> tm(red);
   const int64_t base = blockIdx.x * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
   int64_t v[kScanItems];

@@ -33,31 +33,34 @@ struct WarpTeam {
   __device__ __forceinline__ uint64_t bcast(uint64_t v, int src) const { return __shfl_sync(kFull, v, src); }
 };
 
-// A CTA of NT threads; `red` points at NT/32 + 2 int64 slots of shared memory.
+// A CTA of NT threads; `red` points at kRedSlots int64 slots of shared memory.
+// Reductions take one barrier: warp partials go to one of two buffers in
+// turn, and every warp combines them itself.  A buffer is written again only
+// two calls later, after the middle call's barrier, when every thread has read
+// it.  Every thread must make the same sequence of calls.
 template <int NT>
 struct BlockTeam {
   static constexpr int N = NT;
   static constexpr int NW = NT / 32;
+  static constexpr int kRedSlots = 2 * NW;
   int rank;
+  int buf;
   int64_t* red;
-  __device__ __forceinline__ BlockTeam(int64_t* r) : rank(threadIdx.x), red(r) {}
+  __device__ __forceinline__ BlockTeam(int64_t* r) : rank(threadIdx.x), buf(0), red(r) {}
   __device__ __forceinline__ void sync() const { __syncthreads(); }
   __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p); }
   __device__ int64_t sum(int64_t v) {
+    const int lane = rank & 31;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if ((rank & 31) == 0) red[rank >> 5] = v;
+    int64_t* part = red + buf * NW;
+    if (lane == 0) part[rank >> 5] = v;
     __syncthreads();
-    if (rank < 32) {
-      int64_t x = rank < NW ? red[rank] : 0;
+    buf ^= 1;
+    int64_t x = lane < NW ? part[lane] : 0;
 #pragma unroll
-      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-      if (rank == 0) red[NW] = x;
-    }
-    __syncthreads();
-    const int64_t r = red[NW];
-    __syncthreads();
-    return r;
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
   }
   __device__ int64_t exscan(int64_t v) {
     const int lane = rank & 31, w = rank >> 5;
@@ -67,22 +70,15 @@ struct BlockTeam {
       const int64_t y = __shfl_up_sync(kFull, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) red[w] = x;
+    int64_t* part = red + buf * NW;
+    if (lane == 31) part[w] = x;
     __syncthreads();
-    if (rank < 32) {
-      const int64_t t = rank < NW ? red[rank] : 0;
-      int64_t s = t;
+    buf ^= 1;
+    // warps before w, summed across the lanes of this warp
+    int64_t before = lane < w ? part[lane] : 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(kFull, s, o);
-        if (rank >= o) s += y;
-      }
-      if (rank < NW) red[rank] = s - t;
-    }
-    __syncthreads();
-    const int64_t r = x - v + red[w];
-    __syncthreads();
-    return r;
+    for (int o = 16; o; o >>= 1) before += __shfl_xor_sync(kFull, before, o);
+    return x - v + before;
   }
 };
 

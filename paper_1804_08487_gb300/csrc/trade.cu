@@ -194,7 +194,13 @@ constexpr int kSelBins = 1 << kSelBits;
 // meta bits per entry (team paths add the neighbour's column bit)
 constexpr uint8_t kCol = 16;    // neighbour sits at the odd position 2s+1
 
+constexpr int kCand = 32;       // candidates sharing the threshold's bin, ranked by full key
+
 struct WsA {
+  uint64_t* ck;               // kCand candidate keys
+  uint64_t* ctb;              // their tie-breaks
+  int32_t* cidx;              // their entry indices
+  int32_t* ncand;
   int32_t* slot;              // hash slot of the entry's far trade (-1: the edge {u,v})
   uint16_t* top;              // top 16 bits of the own key
   uint8_t* meta;
@@ -212,7 +218,7 @@ __host__ __device__ inline int hash_lg(int L) {
 }
 __host__ __device__ inline size_t ws_a_bytes(int L) {
   const size_t L16 = (static_cast<size_t>(L) + 15) & ~size_t(15);
-  return (size_t(1) << hash_lg(L)) * 8 + kSelBins * 4 + L16 * 4 + L16 * 2 + L16 + L16 + 64;
+  return (size_t(1) << hash_lg(L)) * 8 + kSelBins * 4 + kCand * 20 + 16 + L16 * 4 + L16 * 2 + L16 + L16 + 64;
 }
 __device__ inline WsA carve_a(void* base, int L) {
   const size_t L16 = (static_cast<size_t>(L) + 15) & ~size_t(15);
@@ -221,6 +227,10 @@ __device__ inline WsA carve_a(void* base, int L) {
   w.lgH = hash_lg(L);
   w.hash = reinterpret_cast<unsigned long long*>(p); p += (size_t(1) << w.lgH) * 8;
   w.hist = reinterpret_cast<uint32_t*>(p); p += kSelBins * 4;
+  w.ck = reinterpret_cast<uint64_t*>(p); p += kCand * 8;
+  w.ctb = reinterpret_cast<uint64_t*>(p); p += kCand * 8;
+  w.cidx = reinterpret_cast<int32_t*>(p); p += kCand * 4;
+  w.ncand = reinterpret_cast<int32_t*>(p); p += 16;
   w.slot = reinterpret_cast<int32_t*>(p); p += L16 * 4;
   w.top = reinterpret_cast<uint16_t*>(p); p += L16 * 2;
   w.meta = reinterpret_cast<uint8_t*>(p); p += L16;
@@ -280,13 +290,13 @@ __device__ void radix_digit(Team& tm, const WsA& w, int L, int shift, int bits, 
   tm.sync();
 }
 
-// k-th smallest (1-based) (key, lo, hi) over D: one 10-bit radix digit on the
+// k-th smallest (1-based) (key, lo, hi) over D, the general procedure (used
+// when more than kCand elements share the threshold's bin): one 10-bit radix digit on the
 // stored 16-bit key prefixes (keys are uniform, so the chosen bin holds about
 // |D|/1024 elements), a 6-bit digit only if that bin is crowded, then the
 // full keys of the few remaining candidates.
 template <class Team>
 __device__ void select_kth(Team& tm, const KeyCtx& kc, const WsA& w, int L, int64_t t, int k, SelOut* out) {
-  constexpr int kCand = 32;   // candidates ranked in shared memory (the histogram's space)
   const int64_t t2 = 2 * t;
   radix_digit(tm, w, L, 16 - kSelBits, kSelBits, 0, k, out);
   uint32_t prefix = static_cast<uint32_t>(out->bin);   // of the top `plen` bits
@@ -363,6 +373,8 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   const int H = 1 << w.lgH;
   const int64_t t2 = 2 * t;
   for (int i = tm.rank; i < H; i += Team::N) w.hash[i] = 0ull;
+  for (int i = tm.rank; i < kSelBins; i += Team::N) w.hist[i] = 0;
+  if (tm.rank == 0) *w.ncand = 0;
   tm.sync();
   // entries into the hash: presence bit (row, column) in the far trade's slot
   for (int i = tm.rank; i < L; i += Team::N) {
@@ -447,46 +459,136 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     if (!other && !tr.single) {
       m |= kInD;
       cnt_a += (r == 0);
+      atomicAdd(&w.hist[w.top[i] >> (16 - kSelBits)], 1u);
     }
     w.meta[i] = m;
   }
-  if (tm.any(defer)) {
+  // one reduction: |A_{u-v}|, any deferral, any later dependent trade
+  const int64_t tot = tm.sum(static_cast<int64_t>(cnt_a) | (static_cast<int64_t>(defer) << 32) |
+                             (static_cast<int64_t>(has_dependents) << 48));
+  if ((tot >> 32) & 0xffff) {
     if (tm.rank == 0) {
       c.done[t] = kDeferred;
       atomicAdd(c.def_count, 1ull);
     }
-    tm.sync();
     return;
   }
-  const int a = static_cast<int>(tm.sum(cnt_a));
-  const bool publish_fence = tm.any(has_dependents);
+  const int a = static_cast<int>(tot & 0xffffffff);
+  const bool publish_fence = (tot >> 48) != 0;
+  const bool no_thr = tr.single || a == 0;   // u keeps nothing of D
+  // the bin of the top kSelBits key bits that holds the a-th smallest element
+  int bin = 0, cnt = 0, below = 0;
+  if (!no_thr) {
+    constexpr int bpm = (kSelBins + Team::N - 1) / Team::N;
+    const int b0 = tm.rank * bpm;
+    int local = 0;
+#pragma unroll
+    for (int j = 0; j < bpm; ++j)
+      if (b0 + j < kSelBins) local += static_cast<int>(w.hist[b0 + j]);
+    int run = static_cast<int>(tm.exscan(local));
+#pragma unroll
+    for (int j = 0; j < bpm; ++j) {
+      const int b = b0 + j;
+      if (b < kSelBins) {
+        const int hc = static_cast<int>(w.hist[b]);
+        if (run < a && a <= run + hc) {
+          sel->bin = b;
+          sel->below = run;
+          sel->cnt = hc;
+        }
+        run += hc;
+      }
+    }
+    tm.sync();
+    bin = sel->bin;
+    below = sel->below;
+    cnt = sel->cnt;
+  }
   uint64_t tk = 0, tt = 0;
-  if (!tr.single && a > 0) {
+  if (cnt <= kCand) {
+    // own decisions: an element below the threshold's bin stays with u, above it
+    // goes to v; in the bin, full keys decide (the only element: the threshold)
+    for (int i = tm.rank; i < L; i += Team::N) {
+      const uint8_t m = w.meta[i];
+      if (!(m & kInD)) continue;
+      const int r = m & kR;
+      const int d = static_cast<int>(w.top[i]) >> (16 - kSelBits);
+      bool low;
+      if (no_thr || d > bin) {
+        low = false;
+      } else if (d < bin) {
+        low = true;
+      } else {
+        const int32_t y = entry_y(w, t2, i);
+        const uint32_t lo = lo_of(t2, m, y), hi = hi_of(t2, m, y);
+        const uint64_t ki = own_key(kc, t, lo, hi), tbi = tie_break(lo, hi);
+        if (cnt == 1) {
+          low = true;
+          sel->key = ki;
+          sel->tb = tbi;
+        } else {
+          const int q = atomicAdd(w.ncand, 1);
+          w.ck[q] = ki;
+          w.ctb[q] = tbi;
+          w.cidx[q] = i;
+          continue;
+        }
+      }
+      if ((low ? 0 : 1) != r) {
+        w.meta[i] = m | kFlip;
+        atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
+      }
+    }
+    tm.sync();
+    if (cnt > 1) {   // rank the elements of the threshold's bin
+      const int kk = a - below;
+      for (int q = tm.rank; q < cnt; q += Team::N) {
+        int rk = 0;
+        for (int j = 0; j < cnt; ++j) rk += (w.ck[j] < w.ck[q] || (w.ck[j] == w.ck[q] && w.ctb[j] < w.ctb[q]));
+        if (rk == kk - 1) {
+          sel->key = w.ck[q];
+          sel->tb = w.ctb[q];
+        }
+        const int i = w.cidx[q];
+        const uint8_t m = w.meta[i];
+        const int r = m & kR;
+        if ((rk < kk ? 0 : 1) != r) {
+          w.meta[i] = m | kFlip;
+          atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
+        }
+      }
+      tm.sync();
+    }
+    if (!no_thr) {
+      tk = sel->key;
+      tt = sel->tb;
+    }
+  } else {
+    // crowded bin (|D| in the tens of thousands): the general selection
     select_kth(tm, kc, w, L, t, a, sel);
     tk = sel->key;
     tt = sel->tb;
-  }
-  const uint32_t tk16 = static_cast<uint32_t>(tk >> 48);
-  // own decisions; flips are recorded in the far trade's slot
-  for (int i = tm.rank; i < L; i += Team::N) {
-    const uint8_t m = w.meta[i];
-    if (!(m & kInD)) continue;
-    const int r = m & kR;
-    const uint32_t tp = w.top[i];
-    bool low;
-    if (tp != tk16) {
-      low = tp < tk16;
-    } else {
-      const int32_t y = entry_y(w, t2, i);
-      const uint32_t lo = lo_of(t2, m, y), hi = hi_of(t2, m, y);
-      low = at_or_below(own_key(kc, t, lo, hi), tie_break(lo, hi), tk, tt);
+    const uint32_t tk16 = static_cast<uint32_t>(tk >> 48);
+    for (int i = tm.rank; i < L; i += Team::N) {
+      const uint8_t m = w.meta[i];
+      if (!(m & kInD)) continue;
+      const int r = m & kR;
+      const uint32_t tp = w.top[i];
+      bool low;
+      if (tp != tk16) {
+        low = tp < tk16;
+      } else {
+        const int32_t y = entry_y(w, t2, i);
+        const uint32_t lo = lo_of(t2, m, y), hi = hi_of(t2, m, y);
+        low = at_or_below(own_key(kc, t, lo, hi), tie_break(lo, hi), tk, tt);
+      }
+      if ((low ? 0 : 1) != r) {
+        w.meta[i] = m | kFlip;
+        atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
+      }
     }
-    if ((low ? 0 : 1) != r) {
-      w.meta[i] = m | kFlip;
-      atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
-    }
+    tm.sync();
   }
-  tm.sync();
   // will the far trade consider this edge?  Write the stash byte.
   for (int i = tm.rank; i < L; i += Team::N) {
     const uint8_t m = w.meta[i];
@@ -1117,7 +1219,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
                                                       const int64_t* __restrict__ count, int smem_max, char* gws,
                                                       size_t slice) {
   extern __shared__ __align__(16) char sbuf[];
-  __shared__ int64_t red[NT / 32 + 2];
+  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ SelOut sel;
   BlockTeam<NT> tm(red);
   const int64_t len = *count;
@@ -1137,7 +1239,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
 template <int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 8 : 2) k_phase_b_block(StepCtx c, const int32_t* __restrict__ list,
                                                       const int64_t* __restrict__ count) {
-  __shared__ int64_t red[NT / 32 + 2];
+  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ int slots[2];
   BlockTeam<NT> tm(red);
   const int64_t len = *count;
@@ -1156,7 +1258,7 @@ __global__ void __launch_bounds__(kBigThreads) k_phase_a_inorder(StepCtx c, int6
                                                                  unsigned long long* claim, int smem_max,
                                                                  char* gws, size_t slice) {
   extern __shared__ __align__(16) char sbuf[];
-  __shared__ int64_t red[kBigThreads / 32 + 2];
+  __shared__ int64_t red[BlockTeam<kBigThreads>::kRedSlots];
   __shared__ SelOut sel;
   __shared__ int64_t first;
   __shared__ int32_t found[kBigThreads];
