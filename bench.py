@@ -164,7 +164,7 @@ def ensemble_graphs(count=ENSEMBLE_GRAPHS):
     return graphs, [w.chain_seed for w in members]
 
 
-def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=12, clocks=None):
+def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=25, clocks=None):
     """Batched: one handle, autotuned (its tuning steps are untimed warm-up),
     CUDA-graph replay, `steps` timed super steps.  Plain: each graph in its
     own handle, `steps` super steps each, timed one after another (device
@@ -297,7 +297,7 @@ def run_ensemble(args):
     value = world * r["m_total"] * K / (t_ms / 1e3)
     line = {
         "metric": METRIC + " (batched ensemble)", "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": 14, "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "warmup": 27, "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": ENSEMBLE_NAME, "graphs": r["graphs"], "n_total": r["n_total"],
                    "m_total": r["m_total"], "l2": "inputs smaller than L2 are re-read every step (no flush)",

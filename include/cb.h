@@ -208,6 +208,10 @@ int cb_timings(cb_handle h, double* ms, int count);
  *   "smem_max"  larger trades run on a 1024-thread CTA and keep up to this
  *               many entries in shared memory, more in a global-memory
  *               workspace [8192]; 64..8192.
+ *   "inorder_threads" CTA size of the pass that runs deferred trades in
+ *               index order: 1024 (large trades in shared memory) or 256
+ *               (four CTAs per SM; trades above block_max from global
+ *               memory) [1024; 256 for cb_create_batch].
  *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];
  *               larger buckets take the global-memory fallback; 2..4096.
  *   "timing"    1: record CUDA events around the phases of each super step
@@ -243,10 +247,12 @@ int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_o
 /*
  * Pick the fastest work split for this handle: runs up to max_steps real
  * super steps (they advance the chain; the result does not depend on the
- * options), each under one candidate setting of "tile_max", "block_max" and
- * "smem_max", timed with CUDA events, and keeps the fastest.  chosen
- * (may be NULL) receives up to `count` values: tile_max, block_max,
- * smem_max, super steps used.  Returns the number of values written.
+ * options): one to load the kernels, then the rest shared evenly by the
+ * candidate settings, one knob at a time, of "tile_max", "block_max",
+ * "smem_max" and "inorder_threads", timed with CUDA events, and keeps the
+ * fastest.  chosen (may be NULL) receives up to `count` values: tile_max,
+ * block_max, smem_max, inorder_threads, super steps used.  Returns the
+ * number of values written.
  */
 int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count);
 

@@ -192,9 +192,9 @@ def cb_export_graph(h, index: int, out=None):
 
 
 def cb_autotune(h, max_steps: int):
-    out = (C.c_int64 * 4)()
-    k = _check(load().cb_autotune(h, max_steps, out, 4), h)
-    names = ["tile_max", "block_max", "smem_max", "steps"]
+    out = (C.c_int64 * 5)()
+    k = _check(load().cb_autotune(h, max_steps, out, 5), h)
+    names = ["tile_max", "block_max", "smem_max", "inorder_threads", "steps"]
     return {names[i]: out[i] for i in range(k)}
 
 

@@ -93,13 +93,16 @@ int size_trade_workspace(Graph* h) {
     h->dev_bytes -= static_cast<int64_t>(h->ws_slice * h->ws_ctas);
     h->ws_global = nullptr;
   }
+  // a slice per CTA for trades whose workspace is not in shared memory: above
+  // smem_max on the 1024-thread path, above block_max in the in-order pass
   const int64_t max_trade = 2 * h->maxdeg;
+  const int64_t block_max = std::max(h->block_max, std::min(h->tile_max, kTileMaxCap));
   h->ws_ctas = h->num_sms * 4;
   h->ws_slice = 0;
-  if (max_trade > h->smem_max || h->maxdeg > 16384) {
+  if (max_trade > std::min<int64_t>(h->smem_max, block_max) || h->maxdeg > 16384) {
     h->ws_slice = trade_ws_slice_bytes(std::max<int64_t>(max_trade, 1));
     const size_t budget = size_t(2) << 30;
-    h->ws_ctas = static_cast<int>(std::max<size_t>(1, std::min<size_t>(h->num_sms * 2, budget / h->ws_slice)));
+    h->ws_ctas = static_cast<int>(std::max<size_t>(1, std::min<size_t>(h->num_sms * 4, budget / h->ws_slice)));
     CB_CUDA(h, dmalloc(h, &h->ws_global, h->ws_slice * h->ws_ctas));
   }
   return CB_OK;
@@ -344,9 +347,9 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 16 + 32) + 4 * (ntasks + 2) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;
-  if (max_trade > kSmemMaxCap || maxdeg > 16384) {
+  if (max_trade > kBlockMaxCap || maxdeg > 16384) {   // default block_max
     const size_t slice = trade_ws_slice_bytes(std::max<int64_t>(max_trade, 1));
-    const size_t ctas = std::max<size_t>(1, std::min<size_t>(num_sms * 2, (size_t(2) << 30) / slice));
+    const size_t ctas = std::max<size_t>(1, std::min<size_t>(num_sms * 4, (size_t(2) << 30) / slice));
     b += static_cast<int64_t>(slice * ctas);
   }
   b += 4 * std::max<int64_t>(nnz, 2);
@@ -502,6 +505,7 @@ int cb_create_batch(int32_t count, const int64_t* n, const int64_t* row_ptr, con
   h->seed = seeds[0];
   h->g = first_step;
   h->nbuckets = base;
+  h->inorder_threads = 256;   // many small graphs: many small deferred trades
   cudaStream_t s = h->stream;
   int64_t* d_rp_in = nullptr;
   int64_t* d_rpo = nullptr;
@@ -719,7 +723,7 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!std::strcmp(key, "tile_max")) {
     if (value < 0 || value > kTileMaxCap) return fail(h, CB_EINVAL, "tile_max out of range [0, 128]");
     h->tile_max = static_cast<int>(value);
-    return CB_OK;
+    return size_trade_workspace(h);
   }
   if (!std::strcmp(key, "tile_paths")) {
     if (value < 0 || value > 3) return fail(h, CB_EINVAL, "tile_paths out of range [0, 3]");
@@ -729,7 +733,7 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!std::strcmp(key, "block_max")) {
     if (value < 0 || value > kBlockMaxCap) return fail(h, CB_EINVAL, "block_max out of range [0, 2048]");
     h->block_max = static_cast<int>(value);
-    return CB_OK;
+    return size_trade_workspace(h);
   }
   if (!std::strcmp(key, "smem_max")) {
     if (value < 64 || value > kSmemMaxCap) return fail(h, CB_EINVAL, "smem_max out of range [64, 8192]");
@@ -741,6 +745,11 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
       for (auto& e : h->ev) CB_CUDA(h, cudaEventCreate(&e));
     }
     h->timing = value != 0;
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "inorder_threads")) {
+    if (value != 256 && value != 1024) return fail(h, CB_EINVAL, "inorder_threads is 256 or 1024");
+    h->inorder_threads = static_cast<int>(value);
     return CB_OK;
   }
   if (!std::strcmp(key, "bucket_cap")) {
@@ -766,15 +775,20 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
   h->timing = false;
   uint32_t used = 0;
   int rc = CB_OK;
-  // one super step under the current options; ms = its device time
+  // `per` super steps under the current options (fewer if the budget ends);
+  // ms = their device time per step
+  uint32_t per = 1;
   auto trial = [&](float* ms) -> int {
     if (cudaEventRecord(e0, h->stream) != cudaSuccess) return fail(h, CB_ECUDA, "cudaEventRecord failed");
-    const int r = super_step(h);
-    if (r) return r;
+    uint32_t k = 0;
+    for (; k < per && used < max_steps; ++k, ++used) {
+      const int r = super_step(h);
+      if (r) return r;
+    }
     if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
         cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
       return fail(h, CB_ECUDA, "event timing failed");
-    ++used;
+    *ms /= static_cast<float>(k ? k : 1);
     return CB_OK;
   };
   struct Knob {
@@ -782,17 +796,23 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
     int cand[4];
     int ncand;
   };
-  Knob knobs[3] = {{&h->tile_max, {32, 64, 96, 128}, 4},
+  Knob knobs[4] = {{&h->tile_max, {32, 64, 96, 128}, 4},
                    {&h->block_max, {512, 1024, 2048, 0}, 3},
-                   {&h->smem_max, {2048, 4096, 8192, 0}, 3}};
+                   {&h->smem_max, {2048, 4096, 8192, 0}, 3},
+                   {&h->inorder_threads, {256, 1024, 0, 0}, 2}};
   float ms = 0;
   if (used < max_steps) rc = trial(&ms);   // first launches load the kernels: not timed as a candidate
-  for (int k = 0; k < 3 && rc == CB_OK; ++k) {
+  {
+    int total = 0;   // candidate settings over all knobs
+    for (const Knob& kn : knobs) total += kn.ncand;
+    if (max_steps > used) per = std::max<uint32_t>(1, (max_steps - used) / static_cast<uint32_t>(total));
+  }
+  for (int k = 0; k < 4 && rc == CB_OK; ++k) {
     int best = *knobs[k].field;
     float best_ms = 3.4e38f;
     for (int j = 0; j < knobs[k].ncand && used < max_steps && rc == CB_OK; ++j) {
       *knobs[k].field = knobs[k].cand[j];
-      if (knobs[k].field == &h->smem_max) rc = size_trade_workspace(h);   // the global workspace follows smem_max
+      rc = size_trade_workspace(h);   // the global workspace follows block_max and smem_max
       if (rc == CB_OK) rc = trial(&ms);
       if (rc == CB_OK && ms < best_ms) {
         best_ms = ms;
@@ -800,14 +820,14 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
       }
     }
     *knobs[k].field = best;
-    if (rc == CB_OK && knobs[k].field == &h->smem_max) rc = size_trade_workspace(h);
+    if (rc == CB_OK) rc = size_trade_workspace(h);
   }
   h->timing = timing;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  const int64_t vals[4] = {h->tile_max, h->block_max, h->smem_max, static_cast<int64_t>(used)};
-  const int k = chosen ? std::min(count, 4) : 0;
+  const int64_t vals[5] = {h->tile_max, h->block_max, h->smem_max, h->inorder_threads, static_cast<int64_t>(used)};
+  const int k = chosen ? std::min(count, 5) : 0;
   for (int i = 0; i < k; ++i) chosen[i] = vals[i];
   return k;
 }

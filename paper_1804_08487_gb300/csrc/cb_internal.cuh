@@ -104,6 +104,7 @@ struct Graph {
   int block_max = kBlockMaxCap;
   int smem_max = kSmemMaxCap;
   int bucket_cap = 2048;
+  int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
 
   // stats of the last cb_global_trades
   int64_t stats[8] = {0};

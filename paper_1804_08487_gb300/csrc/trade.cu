@@ -1254,29 +1254,30 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 8 : 2) k_phase_b_block(StepCtx
 // claimed before t by a CTA that is already running.  By induction on the
 // index, the smallest unfinished claimed trade waits for nothing, so every
 // wait ends whatever the residency of the grid.
-__global__ void __launch_bounds__(kBigThreads) k_phase_a_inorder(StepCtx c, int64_t ntasks, int64_t chunk,
-                                                                 unsigned long long* claim, int smem_max,
-                                                                 char* gws, size_t slice) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_phase_a_inorder(StepCtx c, int64_t ntasks, int64_t chunk,
+                                                        unsigned long long* claim, int smem_max, char* gws,
+                                                        size_t slice) {
   extern __shared__ __align__(16) char sbuf[];
-  __shared__ int64_t red[BlockTeam<kBigThreads>::kRedSlots];
+  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ SelOut sel;
   __shared__ int64_t first;
-  __shared__ int32_t found[kBigThreads];
+  __shared__ int32_t found[NT];
   __shared__ int nfound;
-  BlockTeam<kBigThreads> tm(red);
+  BlockTeam<NT> tm(red);
   for (;;) {
     if (threadIdx.x == 0) first = static_cast<int64_t>(atomicAdd(claim, 1ull)) * chunk;
     __syncthreads();
     const int64_t lo = first;
     if (lo >= ntasks) return;
     const int64_t hi = lo + chunk < ntasks ? lo + chunk : ntasks;
-    for (int64_t base = lo; base < hi; base += kBigThreads) {
+    for (int64_t base = lo; base < hi; base += NT) {
       // the deferred trades of this slice of the chunk, in index order
       const int64_t t0 = base + threadIdx.x;
       const int mine = (t0 < hi && __ldcg(c.done + t0) == kDeferred) ? 1 : 0;
       const int before = static_cast<int>(tm.exscan(mine));
       if (mine) found[before] = static_cast<int32_t>(t0);
-      if (threadIdx.x == kBigThreads - 1) nfound = before + mine;
+      if (threadIdx.x == NT - 1) nfound = before + mine;
       __syncthreads();
       const int nf = nfound;
       for (int q = 0; q < nf; ++q) {
@@ -1317,7 +1318,9 @@ int init_trade_kernels(Graph* h) {
                                   static_cast<int>(ws_a_bytes(kBlockMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(ws_a_bytes(kBlockMaxCap))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(sizeof(TileA))));
@@ -1418,12 +1421,22 @@ int super_step(Graph* h) {
                                                                    h->ws_slice);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
-  // second pass: the deferred trades in index order, waiting on dependencies
+  // second pass: the deferred trades in index order, waiting on dependencies.
+  // 1024-thread CTAs keep large trades in shared memory; 256-thread CTAs (four
+  // per SM) run many small deferred trades at once, large ones from a global
+  // slice.
   c.wait = 1;
-  {
+  if (h->inorder_threads == kBigThreads) {
     const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
-    k_phase_a_inorder<<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + 5, h->smem_max, gws,
-                                                           h->ws_slice);
+    k_phase_a_inorder<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + 5, h->smem_max, gws,
+                                                                       h->ws_slice);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+  } else {
+    const unsigned igrid = static_cast<unsigned>(gws ? std::min(h->num_sms * 4, h->ws_ctas) : h->num_sms * 4);
+    const int64_t chunk = std::max<int64_t>(512, (ntasks + int64_t(igrid) * 4 - 1) / (int64_t(igrid) * 4));
+    k_phase_a_inorder<kMedThreads><<<igrid, kMedThreads, med_smem, s>>>(c, ntasks, chunk, ucnt + 5, block_max, gws,
+                                                                       h->ws_slice);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
   }

@@ -123,6 +123,7 @@ def test_dense_graphs_resolve_dependencies(n, a, b, seed):
     _run_pair(g.row_ptr, g.col, seed + 200, 3, options={"tile_max": 0, "block_max": 0, "smem_max": 64})
     _run_pair(g.row_ptr, g.col, seed + 300, 3, options={"tile_paths": 0})
     _run_pair(g.row_ptr, g.col, seed + 400, 3, options={"block_max": 0, "smem_max": 128})
+    _run_pair(g.row_ptr, g.col, seed + 500, 3, options={"inorder_threads": 256, "block_max": 256})
 
 
 def test_dependency_passes_happen():
