@@ -200,9 +200,9 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               default stream).  Changing any other option re-records.
  *   "tile_max"  trades up to this size run on the flat tile path (one
  *               thread per entry, many trades per CTA) [128]; 0..128.
- *   "tile_paths" bit 0: threshold phase of tile-path trades on the tile
- *               kernel, bit 1: their rebuild phase; a cleared bit runs
- *               that phase on the 256-thread kernel instead [3]; 0..3.
+ *   "tile_paths" 1: threshold phase of tile-path trades on the tile
+ *               kernel; 0: on the 256-thread kernel instead [1].  (The
+ *               rebuild phase is one flat pass over all entries.)
  *   "block_max" trades up to this size run on a 256-thread CTA [2048];
  *               0..2048 (values below tile_max act as tile_max).
  *   "smem_max"  larger trades run on a 1024-thread CTA and keep up to this

@@ -204,6 +204,13 @@ void destroy_graph(Graph* h) {
   delete static_cast<cb_graph*>(h);
 }
 
+// Scratch of 4 int32 per trade: class flags and tile weights, then (phase B)
+// 2 slot counters per trade and the first / last trade of each 2048-entry chunk.
+int64_t cls_flag_count(int64_t ntasks, int64_t nnz) {
+  const int64_t chunks = nnz / 2048 + 1;
+  return std::max<int64_t>(4 * ntasks, 2 * ntasks + 2 * chunks);
+}
+
 // Common part of handle creation.  On entry: n, nnz, the segment table (host
 // and device, seg_of for batches) and the id-space CSR (rp_id, col[0],
 // unsorted rows) are in place.  Validates, sizes the workspaces and lays the
@@ -238,10 +245,14 @@ int finish_create(Graph* h) {
       dalloc(h, &h->thr_key, h->ntasks) || dalloc(h, &h->thr_tb, h->ntasks) || dalloc(h, &h->done, h->ntasks) ||
       dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->list[0], h->ntasks) || dalloc(h, &h->list[1], h->ntasks) ||
       dalloc(h, &h->list[2], h->ntasks) || dalloc(h, &h->tile_off, h->ntasks) || dalloc(h, &h->tile_first, h->ntasks + 2) ||
-      dalloc(h, &h->cls_flag, 4 * h->ntasks) || dalloc(h, &h->cls_scan, 4 * (h->ntasks + 1)) ||
+      dalloc(h, &h->cls_flag, cls_flag_count(h->ntasks, nnz)) || dalloc(h, &h->cls_scan, 4 * (h->ntasks + 1)) ||
       dmalloc(h, &h->sort_ws, h->sort_ws_bytes) || dmalloc(h, &h->scan_ws, h->scan_ws_bytes))
     return fail(h, CB_ENOMEM, "device allocation failed");
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
+  // the flat rebuild reads 8 entries (32 B) and 8 stash bytes per vector load
+  if ((reinterpret_cast<uintptr_t>(h->col[0]) | reinterpret_cast<uintptr_t>(h->col[1])) % 16 ||
+      reinterpret_cast<uintptr_t>(h->stash) % 8)
+    return fail(h, CB_ECUDA, "device allocation not aligned for vector loads");
   if ((rc = size_trade_workspace(h))) return rc;
   // sort every row (id space) into col[1] and validate: simple and symmetric
   if ((rc = permute_rows(h, n, h->rp_id, h->col[0], nullptr, nullptr, h->rp_id, h->col[1]))) return rc;
@@ -344,7 +355,7 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   int64_t b = 0;
   b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * nnz + 32 + 8 * kCounters;             // cb_create
   b += 2 * 4 * n + 2 * 8 * (n + 1) + 3 * 4 * n + nnz;                                     // per node, stash
-  b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 16 + 32) + 4 * (ntasks + 2) + 32;
+  b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 32) + 4 * cls_flag_count(ntasks, nnz) + 4 * (ntasks + 2) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;
   if (max_trade > kBlockMaxCap || maxdeg > 16384) {   // default block_max
@@ -726,7 +737,7 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     return size_trade_workspace(h);
   }
   if (!std::strcmp(key, "tile_paths")) {
-    if (value < 0 || value > 3) return fail(h, CB_EINVAL, "tile_paths out of range [0, 3]");
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "tile_paths is 0 or 1");
     h->tile_paths = static_cast<int>(value);
     return CB_OK;
   }

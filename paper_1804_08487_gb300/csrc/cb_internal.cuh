@@ -100,7 +100,7 @@ struct Graph {
 
   // knobs
   int tile_max = kTileMaxCap;
-  int tile_paths = 3;   // bit0: threshold phase of tile-class trades on the tile kernel, bit1: rebuild phase
+  int tile_paths = 1;   // 1: threshold phase of tile-class trades on the tile kernel
   int block_max = kBlockMaxCap;
   int smem_max = kSmemMaxCap;
   int bucket_cap = 2048;

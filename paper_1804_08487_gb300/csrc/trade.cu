@@ -26,14 +26,13 @@
 //  B. Every trade writes its two rows for step g+1: each entry goes to u or v
 //     by its own trade's bit; its far end is resolved against the far trade's
 //     threshold (six-bit prefix first, the full key only on a prefix tie), and
-//     positions are mapped to step g+1.
+//     positions are mapped to step g+1.  One flat pass over all entries.
 //
-// Trades of at most `tile_max` entries run on the flat tile path: a CTA takes
-// a run of consecutive small trades (about 1024 entries) with one thread per
-// entry and loops over each trade's own entries in shared memory.  Trades up
-// to `block_max` entries run one per 256-thread CTA, larger ones one per
-// 1024-thread CTA with up to `smem_max` entries in shared memory (a
-// global-memory slice above that).
+// Phase A by trade size: trades of at most `tile_max` entries run on the tile
+// path (a CTA takes a run of consecutive small trades, about 1024 entries,
+// one thread per entry); trades up to `block_max` entries run one per
+// 256-thread CTA, larger ones one per 1024-thread CTA with up to `smem_max`
+// entries in shared memory (a global-memory slice above that).
 #include <algorithm>
 
 #include "cb_internal.cuh"
@@ -632,80 +631,6 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   tm.sync();
 }
 
-// Phase B for trade t: write its two rows in step g+1's layout.  Rows are
-// sets, so entries take slots in their new row in any order: each warp claims
-// a run of slots per row with one shared-memory atomic (slots[0..1] count the
-// entries placed in u's and v's new rows).
-template <class Team>
-__device__ void phase_b(Team& tm, const StepCtx& c, int64_t t, int* slots) {
-  const TradeRows tr = trade_rows(c, t);
-  const int du = tr.du, dv = tr.dv, L = du + dv;
-  const int64_t t2 = 2 * t;
-  const int32_t pu = c.M[t2];
-  const int64_t ou = c.rp_next[pu];
-  int64_t ov = 0;
-  bool bad = c.rp_next[pu + 1] - ou != du;
-  if (dv > 0) {
-    const int32_t pv = c.M[t2 + 1];
-    ov = c.rp_next[pv];
-    bad |= c.rp_next[pv + 1] - ov != dv;
-  }
-  if (bad) {
-    if (tm.rank == 0) latch(c.err, kErrRowLength);
-    return;
-  }
-  if (tm.rank == 0) {
-    slots[0] = 0;
-    slots[1] = 0;
-  }
-  tm.sync();
-  const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
-  for (int c0 = 0; c0 < L; c0 += Team::N) {
-    const int i = c0 + tm.rank;
-    int r2 = 2;        // 2: no entry
-    int32_t out = 0;
-    if (i < L) {
-      const int r = i >= du;
-      const int32_t yy = __ldcg(c.col + tr.b0 + i);
-      const uint8_t st = c.stash[tr.b0 + i];
-      r2 = r ^ (st & 1);
-      int32_t y2 = yy;
-      if (st & 2) {
-        const int64_t s = yy >> 1;
-        const uint32_t ft = st >> 2, tt = c.thr_top[s];
-        bool low;
-        if (ft != tt) {
-          low = ft < tt;
-        } else {
-          const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-          low = far_keeps_low(c, key_ctx(c, t), s, min(x, y), max(x, y));   // prefix tie: 1 in 64
-        }
-        y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
-      }
-      out = c.M[y2];
-    }
-    const unsigned b0 = __ballot_sync(kFull, r2 == 0), b1 = __ballot_sync(kFull, r2 == 1);
-    int base0 = 0, base1 = 0;
-    if (lane == 0) {
-      if (b0) base0 = atomicAdd(&slots[0], __popc(b0));
-      if (b1) base1 = atomicAdd(&slots[1], __popc(b1));
-    }
-    base0 = __shfl_sync(kFull, base0, 0);
-    base1 = __shfl_sync(kFull, base1, 0);
-    if (r2 == 0) {
-      const int p = base0 + __popc(b0 & below);
-      if (p < du) c.col_next[ou + p] = out; else latch(c.err, kErrRowSide);
-    } else if (r2 == 1) {
-      const int p = base1 + __popc(b1 & below);
-      if (p < dv) c.col_next[ov + p] = out; else latch(c.err, kErrRowSide);
-    }
-  }
-  tm.sync();
-  if (tm.rank == 0 && slots[0] != du) latch(c.err, kErrRowSide);
-  tm.sync();   // slots are reused by the team's next trade
-}
-
 // ---------------------------------------------------------- classification
 
 // Class of each trade (tile / 256 / 1024 threads) and its tile weight.
@@ -773,7 +698,6 @@ struct TileShared {              // per-trade data of the current tile
 struct TileEntries {
   int32_t* y;
   uint16_t* owner;
-  uint8_t* stash;    // loaded only when non-null
   KeyCtx* kc;        // per trade, filled only when non-null
 };
 
@@ -821,7 +745,6 @@ __device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& 
     if (i < sh.du[k] + sh.dv[k]) {
       te.owner[e] = static_cast<uint16_t>(k);
       if (te.y) te.y[e] = __ldcg(c.col + sh.b0[k] + i);
-      if (te.stash) te.stash[e] = c.stash[sh.b0[k] + i];
     } else {
       te.owner[e] = kNoOwner;
     }
@@ -898,7 +821,7 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     for (int i = threadIdx.x; i < kTileHash; i += blockDim.x) ta.hash[i] = 0ull;
-    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, nullptr, ta.kc}, list, tile_off, tile_first, ntrades, total_w,
+    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, ta.kc}, list, tile_off, tile_first, ntrades, total_w,
                     tile))
       continue;
     const int E = sh.nslots;
@@ -1125,90 +1048,211 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
   }
 }
 
-struct TileB {
-  int64_t ou[kTileTrades], ov[kTileTrades];   // each trade's new u / v row offsets
-  int32_t slot[2 * kTileTrades];   // entries placed so far in each trade's new u / v row
-  uint16_t owner[kTileSlots];
+// --------------------------------------------------------- flat rebuild
+//
+// Phase B over the whole position-space adjacency at once: a CTA takes a
+// chunk of 2048 consecutive entries, each thread 8 consecutive entries.  Trade
+// t owns entries [rp[2t], rp[2t+2]); the trades a chunk touches go to a
+// shared table (start, u/v boundary, new row offsets), or are looked up in
+// global memory when a chunk spans more trades than the table holds (only
+// with many empty trades).  Entries of the same (trade, new side) in a warp
+// claim their slots together with one global atomic on the trade's counter
+// (rows are sets; a counter past the row's degree latches an error).
+
+constexpr int kFlatThreads = 256;
+constexpr int kFlatPer = 8;                              // consecutive entries per thread
+constexpr int kFlatChunk = kFlatThreads * kFlatPer;      // entries per chunk
+constexpr int kFlatTrades = 512;                         // trades in the shared table
+
+struct FlatTrade {
+  int64_t start, b1;    // first entry, first entry of v's row
+  int64_t ou, ov;       // new row offsets of u and v
+  int32_t du, dv;
 };
 
-// Phase B for a tile of small trades, one thread per entry: each entry is read,
-// resolved and written in one pass; entries of the same trade and side in a
-// warp claim their slots together (match_any + one shared-memory atomic).
-__global__ void __launch_bounds__(kTileThreads) k_phase_b_tile(StepCtx c, const int32_t* __restrict__ list,
-                                                               const int64_t* __restrict__ tile_off,
-                                                               const int32_t* __restrict__ tile_first,
-                                                               const int64_t* __restrict__ counts) {
-  __shared__ TileShared sh;
-  __shared__ TileB tb;
-  const int64_t ntrades = counts[0], total_w = counts[3];
-  const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
+__device__ __forceinline__ FlatTrade flat_trade(const StepCtx& c, int64_t t) {
+  FlatTrade f;
+  f.start = c.rp[2 * t];
+  f.b1 = c.rp[2 * t + 1];
+  const bool single = 2 * t + 1 >= c.n;
+  const int64_t end = single ? f.b1 : c.rp[2 * t + 2];
+  f.du = static_cast<int32_t>(f.b1 - f.start);
+  f.dv = static_cast<int32_t>(end - f.b1);
+  const int32_t pu = c.M[2 * t];
+  f.ou = c.rp_next[pu];
+  bool bad = c.rp_next[pu + 1] - f.ou != f.du;
+  f.ov = 0;
+  if (!single) {
+    const int32_t pv = c.M[2 * t + 1];
+    f.ov = c.rp_next[pv];
+    bad |= c.rp_next[pv + 1] - f.ov != f.dv;
+  }
+  if (bad) latch(c.err, kErrRowLength);
+  return f;
+}
+
+// Last trade in [lo, hi] whose first entry is <= e (global row offsets).
+__device__ __forceinline__ int64_t flat_owner(const StepCtx& c, int64_t lo, int64_t hi, int64_t e) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (c.rp[2 * mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The first and last trade with entries in each chunk (one thread per trade:
+// every chunk boundary lies in exactly one non-empty trade).
+__global__ void k_flat_ranges(StepCtx c, int64_t nnz, int64_t ntasks, int32_t* __restrict__ cf,
+                              int32_t* __restrict__ cl) {
+  const int64_t nchunks = (nnz + kFlatChunk - 1) / kFlatChunk;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t b = c.rp[2 * t];
+    const int64_t e = 2 * t + 1 >= c.n ? c.rp[2 * t + 1] : c.rp[2 * t + 2];
+    if (e <= b) continue;
+    // chunks whose first entry lies in [b, e)
+    for (int64_t ch = (b + kFlatChunk - 1) / kFlatChunk; ch < nchunks && ch * kFlatChunk < e; ++ch)
+      cf[ch] = static_cast<int32_t>(t);
+    // chunks whose last entry lies in [b, e)
+    for (int64_t ch = b / kFlatChunk; ch < nchunks; ++ch) {
+      const int64_t last = ((ch + 1) * kFlatChunk < nnz ? (ch + 1) * kFlatChunk : nnz) - 1;
+      if (last >= e) break;
+      if (last >= b) cl[ch] = static_cast<int32_t>(t);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_t nnz, int64_t ntasks,
+                                                               int32_t* __restrict__ slots,
+                                                               const int32_t* __restrict__ cf,
+                                                               const int32_t* __restrict__ cl) {
+  __shared__ FlatTrade tab[kFlatTrades];
+  __shared__ int32_t cnt[2 * kFlatTrades];     // entries of this chunk per (local trade, new side)
+  __shared__ int32_t gbase[2 * kFlatTrades];   // their first slot in the new row
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (!tile_setup(c, sh, TileEntries{nullptr, tb.owner, nullptr, nullptr}, list, tile_off, tile_first, ntrades,
-                    total_w, tile))
-      continue;
-    const int E = sh.nslots;
-    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
-      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
-      const int32_t pu = c.M[t2];
-      tb.ou[k] = c.rp_next[pu];
-      bool bad = c.rp_next[pu + 1] - tb.ou[k] != sh.du[k];
-      tb.ov[k] = 0;
-      if (sh.dv[k] > 0) {
-        const int32_t pv = c.M[t2 + 1];
-        tb.ov[k] = c.rp_next[pv];
-        bad |= c.rp_next[pv + 1] - tb.ov[k] != sh.dv[k];
-      }
-      if (bad) latch(c.err, kErrRowLength);
-      tb.slot[2 * k] = 0;
-      tb.slot[2 * k + 1] = 0;
+  const int64_t nchunks = (nnz + kFlatChunk - 1) / kFlatChunk;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int64_t e0 = ch * kFlatChunk;
+    const int64_t e1 = e0 + kFlatChunk < nnz ? e0 + kFlatChunk : nnz;
+    const int64_t tf = cf[ch], tl = cl[ch];
+    const int ntr = static_cast<int>(tl - tf + 1 < kFlatTrades + 1 ? tl - tf + 1 : kFlatTrades + 1);
+    const bool in_table = ntr <= kFlatTrades;
+    if (in_table) {
+      for (int q = threadIdx.x; q < ntr; q += blockDim.x) tab[q] = flat_trade(c, tf + q);
+      for (int q = threadIdx.x; q < 2 * ntr; q += blockDim.x) cnt[q] = 0;
     }
     __syncthreads();
-    const int Er = (E + kTileThreads - 1) / kTileThreads * kTileThreads;   // every lane takes part in the match
-    for (int e = threadIdx.x; e < Er; e += blockDim.x) {
-      const int k = e < E ? tb.owner[e] : kNoOwner;
-      int key = -1;     // (local trade, new side) of the entry
+    const int64_t base = e0 + static_cast<int64_t>(threadIdx.x) * kFlatPer;
+    // owner of this thread's first entry, then walk forward
+    int64_t q = 0;
+    if (base < e1) {
+      if (in_table) {
+        int lo = 0, hi = ntr - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (tab[mid].start <= base) lo = mid; else hi = mid - 1;
+        }
+        q = lo;
+      } else {
+        q = flat_owner(c, tf, tl, base) - tf;
+      }
+    }
+    FlatTrade ft = in_table ? tab[q] : flat_trade(c, tf + q);
+    int64_t next_start = (tf + q + 1 <= tl) ? (in_table ? tab[q + 1].start : c.rp[2 * (tf + q + 1)]) : INT64_MAX;
+    // the thread's 8 entries and stash bytes (32 B and 8 B, aligned: chunks
+    // start at multiples of 2048 entries); a partial run at the end loads singly
+    int32_t yv[kFlatPer];
+    uint8_t sv[kFlatPer];
+    if (base + kFlatPer <= e1) {
+      const int4 a0 = __ldcs(reinterpret_cast<const int4*>(c.col + base));
+      const int4 a1 = __ldcs(reinterpret_cast<const int4*>(c.col + base) + 1);
+      yv[0] = a0.x; yv[1] = a0.y; yv[2] = a0.z; yv[3] = a0.w;
+      yv[4] = a1.x; yv[5] = a1.y; yv[6] = a1.z; yv[7] = a1.w;
+      const uint2 b = __ldcs(reinterpret_cast<const uint2*>(c.stash + base));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        sv[j] = static_cast<uint8_t>(b.x >> (8 * j));
+        sv[4 + j] = static_cast<uint8_t>(b.y >> (8 * j));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kFlatPer; ++j) {
+        yv[j] = base + j < e1 ? c.col[base + j] : 0;
+        sv[j] = base + j < e1 ? c.stash[base + j] : 0;
+      }
+    }
+    int32_t outv[kFlatPer], keyv[kFlatPer], posv[kFlatPer];
+#pragma unroll
+    for (int j = 0; j < kFlatPer; ++j) {
+      const int64_t e = base + j;
+      const bool valid = e < e1;
+      if (valid) {
+        while (e >= next_start) {   // next non-empty trade (empty trades share its start)
+          ++q;
+          ft = in_table ? tab[q] : flat_trade(c, tf + q);
+          next_start = (tf + q + 1 <= tl) ? (in_table ? tab[q + 1].start : c.rp[2 * (tf + q + 1)]) : INT64_MAX;
+        }
+      }
+      int key = -1;
       int32_t out = 0;
-      if (k != kNoOwner) {
-        const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
-        const int i = e - sh.lofs[k];
-        const int r = i >= sh.du[k];
-        const int32_t yy = __ldcg(c.col + sh.b0[k] + i);
-        const uint8_t st = c.stash[sh.b0[k] + i];
+      if (valid) {
+        const int64_t t = tf + q;
+        const int r = e >= ft.b1;
+        const int32_t yy = yv[j];
+        const uint8_t st = sv[j];
         const int r2 = r ^ (st & 1);
         int32_t y2 = yy;
         if (st & 2) {
-          const int64_t s = yy >> 1;
-          const uint32_t ft = st >> 2, tt = c.thr_top[s];
+          const int32_t s = yy >> 1;
+          const uint32_t fp = st >> 2, tt = c.thr_top[s];
           bool low;
-          if (ft != tt) {
-            low = ft < tt;
+          if (fp != tt) {
+            low = fp < tt;
           } else {
-            const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-            low = far_keeps_low(c, key_ctx(c, sh.t[k]), s, min(x, y), max(x, y));   // prefix tie: 1 in 64
+            const uint32_t x = static_cast<uint32_t>(2 * t + r), y = static_cast<uint32_t>(yy);
+            low = far_keeps_low(c, key_ctx(c, t), s, min(x, y), max(x, y));   // prefix tie: 1 in 64
           }
-          y2 = static_cast<int32_t>(2 * s) + (low ? 0 : 1);
+          y2 = 2 * s + (low ? 0 : 1);
         }
         out = c.M[y2];
-        key = 2 * k + r2;
+        key = static_cast<int>(2 * q + r2);
       }
+      // the entries of one (trade, side) in the warp take consecutive slots
       const unsigned grp = __match_any_sync(kFull, key);
       const int leader = __ffs(grp) - 1;
-      int base = 0;
-      if (lane == leader && key >= 0) base = atomicAdd(&tb.slot[key], __popc(grp));
-      base = __shfl_sync(kFull, base, leader);
-      if (key >= 0) {
-        const int p = base + __popc(grp & below);
+      int slot0 = 0;
+      if (lane == leader && key >= 0)
+        slot0 = in_table ? atomicAdd(&cnt[key], __popc(grp))
+                         : atomicAdd(&slots[2 * (tf + q) + (key & 1)], __popc(grp));
+      slot0 = __shfl_sync(kFull, slot0, leader);
+      outv[j] = out;
+      keyv[j] = key;
+      posv[j] = slot0 + __popc(grp & below);
+      if (!in_table && key >= 0) {   // global slot already final
+        const int p = posv[j];
         const int r2 = key & 1;
-        if (p < (r2 ? sh.dv[k] : sh.du[k])) c.col_next[(r2 ? tb.ov[k] : tb.ou[k]) + p] = out;
+        if (p < (r2 ? ft.dv : ft.du)) c.col_next[(r2 ? ft.ov : ft.ou) + p] = out;
         else latch(c.err, kErrRowSide);
       }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x)   // u's new row must be exactly full
-      if (tb.slot[2 * k] != sh.du[k]) latch(c.err, kErrRowSide);
-    __syncthreads();
+    if (in_table) {
+      // one global reservation per (trade, side) of the chunk, then the writes
+      __syncthreads();
+      for (int k = threadIdx.x; k < 2 * ntr; k += blockDim.x)
+        if (cnt[k]) gbase[k] = atomicAdd(&slots[2 * (tf + (k >> 1)) + (k & 1)], cnt[k]);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kFlatPer; ++j) {
+        const int key = keyv[j];
+        if (key < 0) continue;
+        const FlatTrade& f = tab[key >> 1];
+        const int r2 = key & 1;
+        const int p = gbase[key] + posv[j];
+        if (p < (r2 ? f.dv : f.du)) c.col_next[(r2 ? f.ov : f.ou) + p] = outv[j];
+        else latch(c.err, kErrRowSide);
+      }
+    }
+    __syncthreads();   // the table is reloaded for the next chunk
   }
 }
 
@@ -1234,16 +1278,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
     }
     phase_a(tm, c, t, carve_a(base, L), &sel);
   }
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 8 : 2) k_phase_b_block(StepCtx c, const int32_t* __restrict__ list,
-                                                      const int64_t* __restrict__ count) {
-  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
-  __shared__ int slots[2];
-  BlockTeam<NT> tm(red);
-  const int64_t len = *count;
-  for (int64_t q = blockIdx.x; q < len; q += gridDim.x) phase_b(tm, c, list[q], slots);
 }
 
 // The trades the first pass deferred, in index order.  CTAs claim chunks of
@@ -1441,20 +1475,23 @@ int super_step(Graph* h) {
     ++h->launches;
   }
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
-  // phase B
-  if (h->tile_paths & 2) {
-    k_phase_b_tile<<<tgrid, kTileThreads, 0, s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt);
-  } else {
-    k_phase_b_block<kMedThreads><<<mgrid, kMedThreads, 0, s>>>(c, h->list[0], cnt + 0);
+  // phase B: one flat pass over every entry; per-trade slot counters start at zero
+  {
+    int32_t* slots = h->cls_flag;   // 2 x ntasks, free after the classification
+    int32_t* cf = h->cls_flag + 2 * ntasks;   // chunk ranges (the scratch holds 2 x (nnz / 2048 + 1) more)
+    const int64_t nchunks = (h->nnz + kFlatChunk - 1) / kFlatChunk;
+    int32_t* cl = cf + nchunks;
+    CB_CUDA(h, cudaMemsetAsync(slots, 0, sizeof(int32_t) * 2 * ntasks, s));
+    if (nchunks > 0) {
+      k_flat_ranges<<<grid_n(ntasks), 256, 0, s>>>(c, h->nnz, ntasks, cf, cl);
+      CB_CUDA(h, cudaGetLastError());
+      ++h->launches;
+      const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 8));
+      k_phase_b_flat<<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl);
+      CB_CUDA(h, cudaGetLastError());
+      ++h->launches;
+    }
   }
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-  k_phase_b_block<kMedThreads><<<mgrid, kMedThreads, 0, s>>>(c, h->list[1], cnt + 1);
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-  k_phase_b_block<kBigThreads><<<static_cast<unsigned>(h->num_sms * 2), kBigThreads, 0, s>>>(c, h->list[2], cnt + 2);
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
   if (h->timing) {
     CB_CUDA(h, cudaEventRecord(h->ev[3], s));
     CB_CUDA(h, cudaEventSynchronize(h->ev[3]));

@@ -99,8 +99,8 @@ CASES = [
     (1500, 20, 400, 2.0, 11, {"block_max": 0, "smem_max": 64}),   # global-memory workspace
     (1200, 10, 300, 2.0, 14, {"tile_max": 0, "block_max": 0}),    # everything on the 1024-thread path
     (777, 5, 200, 2.0, 12, {"bucket_cap": 2}),        # permutation sort fallback
-    (2500, 3, 60, 2.0, 15, {"tile_paths": 1}),        # tile thresholds, 256-thread rebuild
-    (2500, 3, 60, 2.0, 16, {"tile_paths": 2}),        # 256-thread thresholds, tile rebuild
+    (2500, 3, 60, 2.0, 15, {"tile_paths": 1}),        # tile thresholds
+    (2500, 3, 60, 2.0, 16, {"tile_paths": 0}),        # 256-thread thresholds for small trades
     (3000, 4, 1500, 2.0, 13, {}),                     # heavy tail: block-path hubs
 ]
 
@@ -262,3 +262,11 @@ def test_plain_n2p20_matches_stored_oracle_hashes():
         c.global_trades(1)
         if str(step) in gold["edge_sha256_after_step"]:
             assert edge_hash(c.edges()) == gold["edge_sha256_after_step"][str(step)], step
+
+
+def test_very_dense_graph_more_chunks_than_trades():
+    """Average degree above 1024: the rebuild's 2048-entry chunks outnumber the
+    trades (its per-chunk scratch must not assume otherwise)."""
+    g = synth.powerlaw_graph(2400, 1100, 2300, 2.0, 5)
+    assert int(g.row_ptr[-1]) // 2048 > 1200
+    _run_pair(g.row_ptr, g.col, 77, 2)
