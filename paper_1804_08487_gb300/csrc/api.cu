@@ -254,21 +254,31 @@ int finish_create(Graph* h) {
       reinterpret_cast<uintptr_t>(h->stash) % 8)
     return fail(h, CB_ECUDA, "device allocation not aligned for vector loads");
   if ((rc = size_trade_workspace(h))) return rc;
-  // sort every row (id space) into col[1] and validate: simple and symmetric
-  if ((rc = permute_rows(h, n, h->rp_id, h->col[0], nullptr, nullptr, h->rp_id, h->col[1]))) return rc;
-  if ((rc = validate_sorted_graph(h, h->rp_id, h->col[1], n))) return rc;
+  // rows in id space, sorted (sorted input is used as it is), then validated:
+  // simple and symmetric
+  bool sorted = false;
+  if ((rc = rows_sorted(h, h->rp_id, h->col[0], n, &sorted))) return rc;
+  int32_t* idcol = h->col[0];
+  if (!sorted) {
+    if ((rc = permute_rows(h, n, h->rp_id, h->col[0], nullptr, nullptr, h->rp_id, h->col[1]))) return rc;
+    idcol = h->col[1];
+  }
+  if ((rc = validate_sorted_graph(h, h->rp_id, idcol, n))) return rc;
   if ((rc = check_device_error(h))) {
     h->last_error = "graph is not simple and symmetric";
     return CB_EINVAL;
   }
-  // position-space layout of the first super step
+  // position-space layout of the first super step (rows are sets: no sort);
+  // the step's adjacency lives in col[cur = 0]
   h->cur = 0;
   if ((rc = compute_permutation(h, 0, -1, h->order[0], h->pos_next))) return rc;
   if (n) k_gather_deg<<<grid1d(n, h->num_sms), 256, 0, s>>>(n, h->order[0], h->deg_id, h->deg_next);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   CB_CUDA(h, exclusive_scan_i32(h->deg_next, h->rp[0], n, h->scan_ws, s, &h->launches));
-  if ((rc = permute_rows(h, n, h->rp_id, h->col[1], h->order[0], h->pos_next, h->rp[0], h->col[0]))) return rc;
+  int32_t* pcol = idcol == h->col[0] ? h->col[1] : h->col[0];
+  if ((rc = relabel_rows(h, n, h->rp_id, idcol, h->order[0], h->pos_next, h->rp[0], pcol))) return rc;
+  if (pcol != h->col[0]) std::swap(h->col[0], h->col[1]);
   return check_device_error(h);
 }
 

@@ -153,7 +153,12 @@ int prepare_next(Graph* h);
 // dst row q <- src row rowmap[q] with values mapped through valmap (identity if null), ascending
 int permute_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* src_col,
                  const int32_t* rowmap, const int32_t* valmap, const int64_t* dst_rp, int32_t* dst_col);
-int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n);
+int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n);   // synchronises
+// *sorted = every row strictly increasing (synchronises)
+int rows_sorted(Graph* h, const int64_t* rp, const int32_t* col, int64_t n, bool* sorted);
+// like permute_rows without sorting (rows keep their order)
+int relabel_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* src_col, const int32_t* rowmap,
+                 const int32_t* valmap, const int64_t* dst_rp, int32_t* dst_col);
 int check_row_offsets(Graph* h, const int64_t* rp, int64_t n);
 int invert_permutation(Graph* h, const int32_t* order, int32_t* pos);
 int export_pairs(Graph* h, const int64_t* rp, const int32_t* col, int32_t* pairs);

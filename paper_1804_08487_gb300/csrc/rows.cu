@@ -10,6 +10,8 @@
 namespace cb {
 namespace {
 
+const int32_t kErrValidateHost = kErrValidate;
+
 constexpr int kRowWarpMax = 256;     // rows up to this length: one warp
 constexpr int kRowBlockSmem = 16384; // rows up to this length: one CTA in shared memory
 
@@ -83,21 +85,70 @@ __global__ void k_check_rp(int64_t n, const int64_t* __restrict__ rp, int32_t* e
 }
 
 // Rows sorted: strictly increasing, in range, no self loop, and symmetric.
+// Symmetry with half the searches: every entry y > x must find x in row y;
+// those mirrors are distinct entries below the diagonal, so the graph is
+// symmetric exactly when, in addition, there are as many entries below the
+// diagonal as above (counted into ud[0] and ud[1]).
 __global__ void k_validate(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                           int32_t* err) {
+                           int32_t* err, unsigned long long* ud) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  unsigned long long up = 0, down = 0;
   for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < n; x += nw) {
     const int64_t b = rp[x], e = rp[x + 1];
     for (int64_t i = b + lane; i < e; i += 32) {
       const int32_t y = col[i];
       bool bad = y < 0 || y >= n || y == x || (i > b && col[i - 1] >= y);
-      if (!bad) {
+      if (!bad && y > x) {
+        ++up;
         const int64_t yb = rp[y], ye = rp[y + 1];
         const int k = lower_bound(col + yb, static_cast<int>(ye - yb), static_cast<int32_t>(x));
         bad = (yb + k >= ye) || col[yb + k] != x;
+      } else if (!bad) {
+        ++down;
       }
       if (bad) latch(err, kErrValidate);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    up += __shfl_xor_sync(kFull, up, o);
+    down += __shfl_xor_sync(kFull, down, o);
+  }
+  if (lane == 0) {
+    if (up) atomicAdd(&ud[0], up);
+    if (down) atomicAdd(&ud[1], down);
+  }
+}
+
+// err <- kErrValidate unless every row is strictly increasing (sorted input).
+__global__ void k_rows_sorted(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              int32_t* flag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  bool unsorted = false;
+  for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < n; x += nw) {
+    const int64_t b = rp[x], e = rp[x + 1];
+    for (int64_t i = b + 1 + lane; i < e; i += 32) unsorted |= col[i - 1] >= col[i];
+  }
+  if (__any_sync(kFull, unsorted) && lane == 0) atomicExch(flag, 1);
+}
+
+// dst row q <- src row rowmap[q], values mapped through valmap, order kept.
+__global__ void k_relabel(RowArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t q = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; q < a.nrows; q += nw) {
+    const int64_t x = a.rowmap ? a.rowmap[q] : q;
+    const int64_t s0 = a.src_rp[x], len = a.src_rp[x + 1] - s0;
+    const int64_t d0 = a.dst_rp[q];
+    if (len != a.dst_rp[q + 1] - d0) {
+      if (lane == 0) latch(a.err, kErrRowLength);
+      continue;
+    }
+    for (int64_t i = lane; i < len; i += 32) {
+      const int32_t v = a.src_col[s0 + i];
+      a.dst_col[d0 + i] = a.valmap ? a.valmap[v] : v;
     }
   }
 }
@@ -173,7 +224,40 @@ int permute_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* 
 
 int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n) {
   if (n == 0) return CB_OK;
-  k_validate<<<grid_of(n * 32, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, h->err);
+  unsigned long long* ud = reinterpret_cast<unsigned long long*>(h->counters) + 6;
+  CB_CUDA(h, cudaMemsetAsync(ud, 0, 2 * sizeof(unsigned long long), h->stream));
+  k_validate<<<grid_of(n * 32, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, h->err, ud);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  unsigned long long hud[2] = {0, 0};
+  CB_CUDA(h, cudaMemcpyAsync(hud, ud, sizeof(hud), cudaMemcpyDeviceToHost, h->stream));
+  CB_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (hud[0] != hud[1]) {
+    CB_CUDA(h, cudaMemcpyAsync(h->err, &kErrValidateHost, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  }
+  return CB_OK;
+}
+
+int rows_sorted(Graph* h, const int64_t* rp, const int32_t* col, int64_t n, bool* sorted) {
+  *sorted = true;
+  if (n == 0) return CB_OK;
+  int32_t* flag = reinterpret_cast<int32_t*>(h->counters + 8);
+  CB_CUDA(h, cudaMemsetAsync(flag, 0, sizeof(int32_t), h->stream));
+  k_rows_sorted<<<grid_of(n * 32, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, flag);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  int32_t hf = 0;
+  CB_CUDA(h, cudaMemcpyAsync(&hf, flag, sizeof(hf), cudaMemcpyDeviceToHost, h->stream));
+  CB_CUDA(h, cudaStreamSynchronize(h->stream));
+  *sorted = hf == 0;
+  return CB_OK;
+}
+
+int relabel_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* src_col, const int32_t* rowmap,
+                 const int32_t* valmap, const int64_t* dst_rp, int32_t* dst_col) {
+  if (nrows == 0) return CB_OK;
+  RowArgs a{nrows, src_rp, src_col, rowmap, valmap, dst_rp, dst_col, h->err};
+  k_relabel<<<grid_of(nrows * 32, 256, h->num_sms), 256, 0, h->stream>>>(a);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   return CB_OK;

@@ -216,6 +216,16 @@ def test_rejects_invalid_graphs():
         Curveball(dup_rp, np.array([1, 1, 0, 0], dtype=np.int32), 1)  # multi-edge
     with pytest.raises(CbError):
         Curveball(np.array([0, 1, 2], dtype=np.int64), np.array([5, 0], dtype=np.int32), 1)  # out of range
+    # entries below the diagonal without a mirror above it (2 -> 0 and 2 -> 1):
+    # every entry above the diagonal finds its mirror, the counts differ
+    with pytest.raises(CbError) as e:
+        Curveball(np.array([0, 1, 2, 4], dtype=np.int64), np.array([1, 0, 0, 1], dtype=np.int32), 1)
+    assert e.value.code == CB_EINVAL
+    # an entry above the diagonal without its mirror (0 -> 2) while the counts
+    # above and below agree (3 -> 0 has no mirror either)
+    with pytest.raises(CbError) as e:
+        Curveball(np.array([0, 2, 3, 4, 6], dtype=np.int64), np.array([1, 2, 0, 3, 0, 2], dtype=np.int32), 1)
+    assert e.value.code == CB_EINVAL
 
 
 def test_export_capacity_checked():
