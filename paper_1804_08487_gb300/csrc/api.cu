@@ -35,6 +35,10 @@ unsigned grid1d(int64_t work, int num_sms) {
   return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(num_sms) * 16)));
 }
 
+// Spare entries after each adjacency buffer: a bulk copy of a trade's row
+// range moves whole 16-byte units and may read up to 3 entries past the end.
+constexpr int64_t kColPad = 16;
+
 // Device memory of a handle is stream-ordered (the device's memory pool, on
 // the handle's stream): creating and destroying handles never waits for work
 // of other streams, so many handles can come and go while others run.
@@ -363,7 +367,7 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   const int64_t ntasks = n / 2 + (n & 1);
   const int64_t nb = int64_t(1) << bucket_bits(n);
   int64_t b = 0;
-  b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * nnz + 32 + 8 * kCounters;             // cb_create
+  b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * (nnz + kColPad) + 32 + 8 * kCounters;   // cb_create
   b += 2 * 4 * n + 2 * 8 * (n + 1) + 3 * 4 * n + nnz;                                     // per node, stash
   b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 32) + 4 * cls_flag_count(ntasks, nnz) + 4 * (ntasks + 2) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
@@ -434,8 +438,8 @@ int cb_create(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t se
     h->nbuckets = int64_t(1) << S.B;
   }
   cudaStream_t s = h->stream;
-  if (dalloc(h, &h->segs, 1) || dalloc(h, &h->rp_id, n + 1) || dalloc(h, &h->deg_id, n) || dalloc(h, &h->col[0], nnz) ||
-      dalloc(h, &h->col[1], nnz) || dalloc(h, &h->err, 8) || dalloc(h, &h->counters, kCounters) ||
+  if (dalloc(h, &h->segs, 1) || dalloc(h, &h->rp_id, n + 1) || dalloc(h, &h->deg_id, n) || dalloc(h, &h->col[0], nnz + kColPad) ||
+      dalloc(h, &h->col[1], nnz + kColPad) || dalloc(h, &h->err, 8) || dalloc(h, &h->counters, kCounters) ||
       !(h->host_counters = new (std::nothrow) int64_t[kCounters]))
     return bail(fail(h, CB_ENOMEM, "device allocation failed"));
   CB_CUDA(h, cudaMemsetAsync(h->err, 0, 8 * sizeof(int32_t), s));
@@ -531,7 +535,7 @@ int cb_create_batch(int32_t count, const int64_t* n, const int64_t* row_ptr, con
   int64_t* d_rp_in = nullptr;
   int64_t* d_rpo = nullptr;
   if (dalloc(h, &h->segs, count) || dalloc(h, &h->seg_of, N) || dalloc(h, &h->rp_id, N + 1) || dalloc(h, &h->deg_id, N) ||
-      dalloc(h, &h->col[0], e) || dalloc(h, &h->col[1], e) || dalloc(h, &h->err, 8) || dalloc(h, &h->counters, kCounters) ||
+      dalloc(h, &h->col[0], e + kColPad) || dalloc(h, &h->col[1], e + kColPad) || dalloc(h, &h->err, 8) || dalloc(h, &h->counters, kCounters) ||
       !(h->host_counters = new (std::nothrow) int64_t[kCounters]) || dalloc(h, &d_rp_in, nrp) ||
       dalloc(h, &d_rpo, 2 * static_cast<int64_t>(count))) {
     delete[] rpo;

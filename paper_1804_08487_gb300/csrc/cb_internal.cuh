@@ -17,6 +17,7 @@ enum DevErr : int32_t {
   kErrValidate = 3,      // input graph not simple / symmetric / in range
   kErrBucket = 4,        // permutation bucket bookkeeping failed
   kErrResolve = 5,       // a dependency wait of the in-order pass gave up
+  kErrStage = 6,         // a bulk copy into shared memory did not complete in time
 };
 
 constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path

@@ -117,6 +117,62 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
 }
 __device__ __forceinline__ void latch(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
 
+// ------------------------------------------------- bulk copies (TMA engine)
+//
+// A trade's entries are staged into shared memory by one cp.async.bulk copy
+// that completes on an mbarrier.  The copy moves whole 16-byte units, so it
+// starts at the entry rounded down to a multiple of 4 and covers a multiple
+// of 4 entries; the adjacency buffers carry 16 spare entries at their end, so
+// the copy never leaves its allocation.
+
+constexpr uint32_t kTmaWaitLimit = 1u << 23;   // polls of an mbarrier before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(m))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* m, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of m (non-blocking polls with a short
+// sleep, about a second at most); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
+  for (uint32_t it = 0; it < kTmaWaitLimit; ++it) {
+    if (mbar_test_wait(m, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// Entries [b0, b0 + L) of col staged at buf + stage_off(b0).
+__device__ __forceinline__ int stage_off(int64_t b0) { return static_cast<int>(b0 & 3); }
+__device__ __forceinline__ void stage_issue(const int32_t* col, int64_t b0, int L, int32_t* buf, uint64_t* m) {
+  const int64_t a0 = b0 & ~int64_t(3);
+  const uint32_t bytes = static_cast<uint32_t>(((b0 + L - a0) + 3) & ~int64_t(3)) * 4u;
+  fence_proxy_async();   // earlier generic reads of buf come before the copy's writes
+  mbar_expect_tx(m, bytes);
+  bulk_g2s(buf, col + a0, bytes, m);
+}
+
 __device__ __forceinline__ uint64_t tie_break(uint32_t lo, uint32_t hi) {
   return (static_cast<uint64_t>(lo) << 32) | hi;
 }
@@ -158,27 +214,30 @@ __device__ __forceinline__ bool far_keeps_low(const StepCtx& c, const KeyCtx& kc
 
 // ------------------------------------------------------------ hash table
 //
-// One slot per far trade s of the current trade: high word s + 1 (0 = empty);
-// low word bit (2 rho + gamma) = the trade's node at row rho (0: u, 1: v) is
+// One slot per far trade s of the current trade: key s + 1 (0 = empty) and a
+// flag byte: bit (2 rho + gamma) = the trade's node at row rho (0: u, 1: v) is
 // adjacent to s's node at position 2s + gamma (the 2x2 block matrix), bit
 // (4 + 2 rho + gamma) = that entry is moved by the trade (its flip).
 
 __device__ __forceinline__ uint32_t hslot(uint32_t s, int lgH) { return (s * 0x9E3779B1u) >> (32 - lgH); }
 
+__device__ __forceinline__ void flag_or(uint8_t* fl, int p, uint32_t bits) {
+  atomicOr(reinterpret_cast<unsigned int*>(fl + (p & ~3)), bits << (8 * (p & 3)));
+}
+
 // Sets `bit` in the slot of far trade s (creating it); returns the slot.
-__device__ __forceinline__ int h_insert(unsigned long long* h, int lgH, uint32_t s, uint32_t bit) {
-  const unsigned long long key = static_cast<unsigned long long>(s + 1u) << 32;
+__device__ __forceinline__ int h_insert(uint32_t* hk, uint8_t* fl, int lgH, uint32_t s, uint32_t bit) {
+  const uint32_t key = s + 1u;
   const uint32_t mask = (1u << lgH) - 1u;
   uint32_t p = hslot(s, lgH);
   for (;;) {
-    unsigned long long cur = h[p];
-    if ((cur >> 32) == 0) {
-      const unsigned long long prev = atomicCAS(&h[p], 0ull, key | bit);
-      if (prev == 0ull) return static_cast<int>(p);
-      cur = prev;
+    uint32_t cur = hk[p];
+    if (cur == 0) {
+      cur = atomicCAS(&hk[p], 0u, key);
+      if (cur == 0) cur = key;
     }
-    if ((cur >> 32) == (key >> 32)) {
-      atomicOr(reinterpret_cast<unsigned int*>(&h[p]), bit);
+    if (cur == key) {
+      flag_or(fl, static_cast<int>(p), bit);
       return static_cast<int>(p);
     }
     p = (p + 1) & mask;
@@ -204,7 +263,8 @@ struct WsA {
   uint16_t* top;              // top 16 bits of the own key
   uint8_t* meta;
   uint8_t* far;               // top 6 bits of the far trade's key
-  unsigned long long* hash;   // 2^lgH slots
+  uint32_t* hkey;             // 2^lgH slot keys
+  uint8_t* hflag;             // 2^lgH slot flag bytes
   uint32_t* hist;             // kSelBins bins
   int lgH;
 };
@@ -217,14 +277,23 @@ __host__ __device__ inline int hash_lg(int L) {
 }
 __host__ __device__ inline size_t ws_a_bytes(int L) {
   const size_t L16 = (static_cast<size_t>(L) + 15) & ~size_t(15);
-  return (size_t(1) << hash_lg(L)) * 8 + kSelBins * 4 + kCand * 20 + 16 + L16 * 4 + L16 * 2 + L16 + L16 + 64;
+  const size_t H = size_t(1) << hash_lg(L);
+  return H * 4 + ((H + 15) & ~size_t(15)) + kSelBins * 4 + kCand * 20 + 16 + L16 * 4 + L16 * 2 + L16 + L16 + 64;
 }
+// Dynamic shared memory of k_phase_a_block: workspace for `cap` entries, then
+// the staging buffer of a trade's entries.
+inline size_t block_smem_bytes(int cap) {
+  return ((ws_a_bytes(cap) + 127) & ~size_t(127)) + (static_cast<size_t>(cap) + 8) * 4;
+}
+
 __device__ inline WsA carve_a(void* base, int L) {
   const size_t L16 = (static_cast<size_t>(L) + 15) & ~size_t(15);
   char* p = static_cast<char*>(base);
   WsA w;
   w.lgH = hash_lg(L);
-  w.hash = reinterpret_cast<unsigned long long*>(p); p += (size_t(1) << w.lgH) * 8;
+  const size_t H = size_t(1) << w.lgH;
+  w.hkey = reinterpret_cast<uint32_t*>(p); p += H * 4;
+  w.hflag = reinterpret_cast<uint8_t*>(p); p += (H + 15) & ~size_t(15);
   w.hist = reinterpret_cast<uint32_t*>(p); p += kSelBins * 4;
   w.ck = reinterpret_cast<uint64_t*>(p); p += kCand * 8;
   w.ctb = reinterpret_cast<uint64_t*>(p); p += kCand * 8;
@@ -250,7 +319,7 @@ __device__ __forceinline__ uint64_t own_key(const KeyCtx& kc, int64_t t, uint32_
 __device__ __forceinline__ int32_t entry_y(const WsA& w, int64_t t2, int i) {
   const uint8_t m = w.meta[i];
   if (m & kUV) return static_cast<int32_t>(t2 + 1 - (m & kR));
-  const uint32_t s = static_cast<uint32_t>(w.hash[w.slot[i]] >> 32) - 1u;
+  const uint32_t s = w.hkey[w.slot[i]] - 1u;
   return static_cast<int32_t>(2 * s + ((m & kCol) ? 1 : 0));
 }
 
@@ -364,32 +433,45 @@ __device__ void select_kth(Team& tm, const KeyCtx& kc, const WsA& w, int L, int6
 }
 
 // Phase A for trade t.
+// The next trade's bulk copy, issued by member 0 as soon as the current trade
+// has read its staged entries (the same buffer is reused).
+struct StageNext {
+  bool issue;
+  int64_t b0;
+  int L;
+  int32_t* buf;
+  uint64_t* mbar;
+};
+
 template <class Team>
-__device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, SelOut* sel) {
+__device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, SelOut* sel,
+                        const int32_t* ystage = nullptr, StageNext sn = StageNext{false, 0, 0, nullptr, nullptr}) {
   const TradeRows tr = trade_rows(c, t);
   const KeyCtx kc = key_ctx(c, t);
   const int du = tr.du, dv = tr.dv, L = du + dv;
   const int H = 1 << w.lgH;
   const int64_t t2 = 2 * t;
-  for (int i = tm.rank; i < H; i += Team::N) w.hash[i] = 0ull;
+  for (int i = tm.rank; i < H; i += Team::N) w.hkey[i] = 0u;
+  for (int i = tm.rank; i < ((H + 15) & ~15) / 4; i += Team::N) reinterpret_cast<uint32_t*>(w.hflag)[i] = 0u;
   for (int i = tm.rank; i < kSelBins; i += Team::N) w.hist[i] = 0;
   if (tm.rank == 0) *w.ncand = 0;
   tm.sync();
   // entries into the hash: presence bit (row, column) in the far trade's slot
   for (int i = tm.rank; i < L; i += Team::N) {
     const int r = i >= du;
-    const int32_t yy = __ldcg(c.col + tr.b0 + i);
+    const int32_t yy = ystage ? ystage[i] : __ldcg(c.col + tr.b0 + i);
     const int64_t s = yy >> 1;
     uint8_t m = static_cast<uint8_t>(r | ((yy & 1) ? kCol : 0));
     if (s == t) {
       m |= kUV;
       w.slot[i] = -1;
     } else {
-      w.slot[i] = h_insert(w.hash, w.lgH, static_cast<uint32_t>(s), 1u << (2 * r + (yy & 1)));
+      w.slot[i] = h_insert(w.hkey, w.hflag, w.lgH, static_cast<uint32_t>(s), 1u << (2 * r + (yy & 1)));
     }
     w.meta[i] = m;
   }
   tm.sync();
+  if (sn.issue && tm.rank == 0) stage_issue(c.col, sn.b0, sn.L, sn.buf, sn.mbar);
   bool defer = false, has_dependents = false;
   int cnt_a = 0;
   for (int i = tm.rank; i < L; i += Team::N) {
@@ -399,9 +481,9 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     if (m & kUV) continue;
     const int r = m & kR;
     const int colb = (m & kCol) ? 1 : 0;
-    const unsigned long long hv = w.hash[w.slot[i]];
-    const int64_t s = static_cast<int64_t>(hv >> 32) - 1;
-    const uint32_t f = static_cast<uint32_t>(hv);
+    const int sl = w.slot[i];
+    const int64_t s = static_cast<int64_t>(w.hkey[sl]) - 1;
+    const uint32_t f = w.hflag[sl];
     const int u0 = f & 1, u1 = (f >> 1) & 1, v0 = (f >> 2) & 1, v1 = (f >> 3) & 1;
     const int cu = u0 + u1, cv = v0 + v1;
     const int32_t yy = static_cast<int32_t>(2 * s + colb);
@@ -535,7 +617,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
       }
       if ((low ? 0 : 1) != r) {
         w.meta[i] = m | kFlip;
-        atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
+        flag_or(w.hflag, w.slot[i], 16u << (2 * r + ((m & kCol) ? 1 : 0)));
       }
     }
     tm.sync();
@@ -553,7 +635,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
         const int r = m & kR;
         if ((rk < kk ? 0 : 1) != r) {
           w.meta[i] = m | kFlip;
-          atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
+          flag_or(w.hflag, w.slot[i], 16u << (2 * r + ((m & kCol) ? 1 : 0)));
         }
       }
       tm.sync();
@@ -583,7 +665,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
       }
       if ((low ? 0 : 1) != r) {
         w.meta[i] = m | kFlip;
-        atomicOr(reinterpret_cast<unsigned int*>(&w.hash[w.slot[i]]), 16u << (2 * r + ((m & kCol) ? 1 : 0)));
+        flag_or(w.hflag, w.slot[i], 16u << (2 * r + ((m & kCol) ? 1 : 0)));
       }
     }
     tm.sync();
@@ -595,9 +677,8 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     int in_far = 0;
     if (!(m & kUV)) {
       const int r = m & kR;
-      const unsigned long long hv = w.hash[w.slot[i]];
-      const int64_t s = static_cast<int64_t>(hv >> 32) - 1;
-      const uint32_t fl = static_cast<uint32_t>(hv);
+      const int64_t s = static_cast<int64_t>(w.hkey[w.slot[i]]) - 1;
+      const uint32_t fl = w.hflag[w.slot[i]];
       const int u0 = fl & 1, u1 = (fl >> 1) & 1, v0 = (fl >> 2) & 1, v1 = (fl >> 3) & 1;
       const int cr = r ? (v0 + v1) : (u0 + u1);
       if (tr.single || s < t) {
@@ -1261,12 +1342,40 @@ __global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_
 template <int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx c, const int32_t* __restrict__ list,
                                                       const int64_t* __restrict__ count, int smem_max, char* gws,
-                                                      size_t slice) {
+                                                      size_t slice, int stage_cap) {
+  // dynamic shared memory: the workspace, then the staging buffer of a
+  // trade's entries (stage_cap + 8 int32, 16-byte aligned)
   extern __shared__ __align__(16) char sbuf[];
   __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ SelOut sel;
+  __shared__ uint64_t mbar;
   BlockTeam<NT> tm(red);
   const int64_t len = *count;
+  int32_t* stage = reinterpret_cast<int32_t*>(sbuf + ((ws_a_bytes(smem_max) + 127) & ~size_t(127)));
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  // member 0 reads the next trade's row range at the start of each trade; the
+  // copy goes out once the current trade has read its staged entries
+  auto range_of = [&](int64_t q, int64_t* b0, int* L) {
+    const int64_t t = list[q];
+    const TradeRows tr = trade_rows(c, t);
+    *b0 = tr.b0;
+    *L = tr.du + tr.dv;
+  };
+  int64_t nb0 = 0;
+  int nL = 0;
+  // a trade is staged when it has entries and fits the buffer (every thread
+  // applies the same test to the same trade)
+  auto staged = [&](int L) { return L > 0 && L <= stage_cap; };
+  if (threadIdx.x == 0 && blockIdx.x < len) {
+    range_of(blockIdx.x, &nb0, &nL);
+    if (staged(nL)) stage_issue(c.col, nb0, nL, stage, &mbar);
+  }
+  bool failed = false;
   for (int64_t q = blockIdx.x; q < len; q += gridDim.x) {
     const int64_t t = list[q];
     const TradeRows tr = trade_rows(c, t);
@@ -1276,7 +1385,28 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
       base = gws + slice * blockIdx.x;
       if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
     }
-    phase_a(tm, c, t, carve_a(base, L), &sel);
+    StageNext sn{false, 0, 0, stage, &mbar};
+    if (threadIdx.x == 0 && q + gridDim.x < len) {
+      range_of(q + gridDim.x, &nb0, &nL);
+      sn.issue = staged(nL);
+      sn.b0 = nb0;
+      sn.L = nL;
+    }
+    const int32_t* ys = nullptr;
+    if (staged(L)) {   // this trade's entries were staged by the previous one (or the prologue)
+      const bool late = !mbar_wait(&mbar, parity);
+      parity ^= 1;
+      if (__syncthreads_or(late)) {
+        failed = true;
+        break;
+      }
+      ys = stage + stage_off(tr.b0);
+    }
+    phase_a(tm, c, t, carve_a(base, L), &sel, ys, sn);
+  }
+  if (failed) {   // a copy did not complete in time: report, let it land, leave
+    if (threadIdx.x == 0) latch(c.err, kErrStage);
+    mbar_wait(&mbar, parity ^ 1);
   }
 }
 
@@ -1289,7 +1419,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
 // index, the smallest unfinished claimed trade waits for nothing, so every
 // wait ends whatever the residency of the grid.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_phase_a_inorder(StepCtx c, int64_t ntasks, int64_t chunk,
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_inorder(StepCtx c, int64_t ntasks, int64_t chunk,
                                                         unsigned long long* claim, int smem_max, char* gws,
                                                         size_t slice) {
   extern __shared__ __align__(16) char sbuf[];
@@ -1349,9 +1479,9 @@ int finish_step(Graph* h) {
 int init_trade_kernels(Graph* h) {
   // the largest dynamic shared memory any handle may ask of each kernel
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(ws_a_bytes(kBlockMaxCap))));
+                                  static_cast<int>(block_smem_bytes(kBlockMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(ws_a_bytes(kSmemMaxCap))));
+                                  static_cast<int>(block_smem_bytes(kSmemMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kBlockMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1428,8 +1558,10 @@ int super_step(Graph* h) {
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
   }
-  const size_t med_smem = ws_a_bytes(std::max(block_max, 1));
+  const size_t med_smem = ws_a_bytes(std::max(block_max, 1));      // in-order pass (no staging)
   const size_t big_smem = ws_a_bytes(std::max(h->smem_max, 1));
+  const size_t med_smem_st = block_smem_bytes(std::max(block_max, 1));   // threshold kernels with staging
+  const size_t big_smem_st = block_smem_bytes(std::max(h->smem_max, 1));
   const unsigned tgrid = static_cast<unsigned>(h->num_sms * 8);
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
@@ -1442,17 +1574,17 @@ int super_step(Graph* h) {
   if (h->tile_paths & 1) {
     k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt);
   } else {
-    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem, s>>>(c, h->list[0], cnt + 0, block_max, gws,
-                                                                     h->ws_slice);
+    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[0], cnt + 0, block_max, gws,
+                                                                        h->ws_slice, block_max);
   }
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
-  k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem, s>>>(c, h->list[1], cnt + 1, block_max, gws,
-                                                                   h->ws_slice);
+  k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[1], cnt + 1, block_max, gws,
+                                                                      h->ws_slice, block_max);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
-  k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, h->list[2], cnt + 2, h->smem_max, gws,
-                                                                   h->ws_slice);
+  k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, h->list[2], cnt + 2, h->smem_max, gws,
+                                                                      h->ws_slice, h->smem_max);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   // second pass: the deferred trades in index order, waiting on dependencies.
