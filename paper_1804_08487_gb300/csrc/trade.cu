@@ -472,6 +472,9 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   }
   tm.sync();
   if (sn.issue && tm.rank == 0) stage_issue(c.col, sn.b0, sn.L, sn.buf, sn.mbar);
+  // trade and position indices fit 32 bits (n < 2^31)
+  const uint32_t t32 = static_cast<uint32_t>(t), T32 = static_cast<uint32_t>(c.T);
+  const uint32_t t2u = 2u * t32;
   bool defer = false, has_dependents = false;
   int cnt_a = 0;
   for (int i = tm.rank; i < L; i += Team::N) {
@@ -480,67 +483,70 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     w.top[i] = 0;
     if (m & kUV) continue;
     const int r = m & kR;
-    const int colb = (m & kCol) ? 1 : 0;
+    const uint32_t colb = (m & kCol) ? 1u : 0u;
     const int sl = w.slot[i];
-    const int64_t s = static_cast<int64_t>(w.hkey[sl]) - 1;
-    const uint32_t f = w.hflag[sl];
-    const int u0 = f & 1, u1 = (f >> 1) & 1, v0 = (f >> 2) & 1, v1 = (f >> 3) & 1;
-    const int cu = u0 + u1, cv = v0 + v1;
-    const int32_t yy = static_cast<int32_t>(2 * s + colb);
-    // a later trade s depends on t when it sees >= 2 block edges and one of
-    // its own nodes holds exactly one of them
-    if (!tr.single && s > t && s < c.T && cu + cv >= 2 && (u0 + v0 == 1 || u1 + v1 == 1)) has_dependents = true;
-    int col_now = colb;                              // s-node of this edge when t acts
-    int other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
-    const bool dep = !tr.single && s < t && (cu + cv >= 2) && (cu == 1 || cv == 1);
-    if (dep) {
-      if (ld_acquire(c.done + s) != c.stamp) {
-        if (!c.wait) {
-          defer = true;
-          continue;
-        }
-        // in-order pass: s is complete or held by a running CTA that claimed it
-        // earlier, so the wait ends; the limit turns a broken invariant into an error
-        uint32_t polls = 0;
-        while (ld_acquire(c.done + s) != c.stamp) {
-          if (++polls > kWaitLimit) {
-            latch(c.err, kErrResolve);
-            break;
+    const uint32_t s = w.hkey[sl] - 1u;
+    const uint32_t f = w.hflag[sl] & 15u;
+    int other = 0;   // the other row is adjacent to this neighbour (a common neighbour)
+    if (f & (f - 1u)) {
+      // a block of two or more edges: common neighbours and dependencies
+      const int u0 = f & 1, u1 = (f >> 1) & 1, v0 = (f >> 2) & 1, v1 = (f >> 3) & 1;
+      const int cu = u0 + u1, cv = v0 + v1;
+      // a later trade s depends on t when one of its own nodes holds exactly
+      // one of the block's edges
+      if (!tr.single && s > t32 && s < T32 && (u0 + v0 == 1 || u1 + v1 == 1)) has_dependents = true;
+      int col_now = static_cast<int>(colb);          // s-node of this edge when t acts
+      other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
+      const bool dep = !tr.single && s < t32 && (cu == 1 || cv == 1);
+      if (dep) {
+        if (ld_acquire(c.done + s) != c.stamp) {
+          if (!c.wait) {
+            defer = true;
+            continue;
           }
-          __nanosleep(128);
+          // in-order pass: s is complete or held by a running CTA that claimed it
+          // earlier, so the wait ends; the limit turns a broken invariant into an error
+          uint32_t polls = 0;
+          while (ld_acquire(c.done + s) != c.stamp) {
+            if (++polls > kWaitLimit) {
+              latch(c.err, kErrResolve);
+              break;
+            }
+            __nanosleep(128);
+          }
         }
+        // replay trade s's decisions on this block
+        int m1[2][2] = {{0, 0}, {0, 0}};
+        const int bits[2][2] = {{u0, u1}, {v0, v1}};
+        const int cnt_row[2] = {cu, cv};
+#pragma unroll
+        for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+          for (int gam = 0; gam < 2; ++gam) {
+            if (!bits[rho][gam]) continue;
+            int g2 = gam;
+            if (cnt_row[rho] == 1) {
+              const uint32_t x = t2u + rho, y = 2u * s + gam;
+              g2 = far_keeps_low(c, kc, s, min(x, y), max(x, y)) ? 0 : 1;
+            }
+            m1[rho][g2] = 1;
+            if (rho == r && gam == static_cast<int>(colb)) col_now = g2;
+          }
+        other = m1[1 - r][col_now];
       }
-      // replay trade s's decisions on this block
-      int m1[2][2] = {{0, 0}, {0, 0}};
-      const int bits[2][2] = {{u0, u1}, {v0, v1}};
-      const int cnt_row[2] = {cu, cv};
-#pragma unroll
-      for (int rho = 0; rho < 2; ++rho)
-#pragma unroll
-        for (int gam = 0; gam < 2; ++gam) {
-          if (!bits[rho][gam]) continue;
-          int g2 = gam;
-          if (cnt_row[rho] == 1) {
-            const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(2 * s + gam);
-            g2 = far_keeps_low(c, kc, s, min(x, y), max(x, y)) ? 0 : 1;
-          }
-          m1[rho][g2] = 1;
-          if (rho == r && gam == colb) col_now = g2;
-        }
-      other = m1[1 - r][col_now];
     }
-    {  // both trades' keys of this edge: own 16-bit prefix, far 6-bit prefix
-      const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-      const uint32_t lo = min(x, y), hi = max(x, y);
-      const EdgeKeys ek = edge_keys(kc, lo, hi);
-      const bool lo_mine = (lo >> 1) == static_cast<uint32_t>(t);
-      w.top[i] = static_cast<uint16_t>((lo_mine ? ek.lo_side : ek.hi_side) >> 48);
-      w.far[i] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
-    }
+    // both trades' keys of this edge: own 16-bit prefix, far 6-bit prefix
+    const uint32_t x = t2u + r, y = 2u * s + colb;
+    const uint32_t lo = min(x, y), hi = max(x, y);
+    const EdgeKeys ek = edge_keys(kc, lo, hi);
+    const bool lo_mine = (lo >> 1) == t32;
+    const uint32_t top = static_cast<uint32_t>((lo_mine ? ek.lo_side : ek.hi_side) >> 48);
+    w.top[i] = static_cast<uint16_t>(top);
+    w.far[i] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
     if (!other && !tr.single) {
       m |= kInD;
       cnt_a += (r == 0);
-      atomicAdd(&w.hist[w.top[i] >> (16 - kSelBits)], 1u);
+      atomicAdd(&w.hist[top >> (16 - kSelBits)], 1u);
     }
     w.meta[i] = m;
   }
@@ -677,13 +683,14 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     int in_far = 0;
     if (!(m & kUV)) {
       const int r = m & kR;
-      const int64_t s = static_cast<int64_t>(w.hkey[w.slot[i]]) - 1;
-      const uint32_t fl = w.hflag[w.slot[i]];
+      const int sl = w.slot[i];
+      const uint32_t s = w.hkey[sl] - 1u;
+      const uint32_t fl = w.hflag[sl];
       const int u0 = fl & 1, u1 = (fl >> 1) & 1, v0 = (fl >> 2) & 1, v1 = (fl >> 3) & 1;
       const int cr = r ? (v0 + v1) : (u0 + u1);
-      if (tr.single || s < t) {
+      if (tr.single || s < t32) {
         in_far = (cr == 1);                 // trade s acted before t: initial block
-      } else if (s < c.T) {
+      } else if (s < T32) {
         if (u0 + u1 + v0 + v1 == 1) {
           in_far = 1;
         } else {                            // block after t's own decisions: presence bits 0..3, flips 4..7
@@ -932,15 +939,16 @@ __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const 
         continue;
       }
       const int slot = tile_hfind(ta.hash, tile_hkey(k, s));
-      const uint32_t bits = static_cast<uint32_t>(ta.hash[slot]);
+      const uint32_t bits = static_cast<uint32_t>(ta.hash[slot]) & 15u;
       const int u0 = bits & 1, u1 = (bits >> 1) & 1, v0 = (bits >> 2) & 1, v1 = (bits >> 3) & 1;
       const int cu = u0 + u1, cv = v0 + v1;
       uint8_t m = static_cast<uint8_t>(r | (u0 << 4) | (u1 << 5) | (v0 << 6) | (v1 << 7));
-      if (!single && s > t && s < c.T && cu + cv >= 2 && (u0 + v0 == 1 || u1 + v1 == 1))
-        atomicOr(&sh.flags[k], 2);
+      const bool multi = (bits & (bits - 1u)) != 0;   // two or more block edges (rare)
+      if (multi && !single && s > t && s < c.T && (u0 + v0 == 1 || u1 + v1 == 1)) atomicOr(&sh.flags[k], 2);
       int col_now = yy & 1;
-      int other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
-      if (!single && s < t && (cu + cv >= 2) && (cu == 1 || cv == 1)) {
+      int other = 0;   // a single edge leaves the other row without this neighbour
+      if (multi) other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
+      if (multi && !single && s < t && (cu == 1 || cv == 1)) {
         if (ld_acquire(c.done + s) != c.stamp) {
           atomicOr(&sh.flags[k], 1);
           continue;
