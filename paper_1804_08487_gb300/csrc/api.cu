@@ -67,7 +67,7 @@ void release(Graph* h) {
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
                   h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
                   h->counters, h->err,
-                  h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs};
+                  h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs, h->far_pack};
   if (h->stream)
     for (void* b : bufs) dfree(h, b);
   for (auto& x : h->step_exec)
@@ -247,6 +247,7 @@ int finish_create(Graph* h) {
   if (dalloc(h, &h->order[0], n) || dalloc(h, &h->order[1], n) || dalloc(h, &h->rp[0], n + 1) || dalloc(h, &h->rp[1], n + 1) ||
       dalloc(h, &h->pos_next, n) || dalloc(h, &h->M, n) || dalloc(h, &h->deg_next, n) || dalloc(h, &h->stash, nnz) ||
       dalloc(h, &h->thr_key, h->ntasks) || dalloc(h, &h->thr_tb, h->ntasks) || dalloc(h, &h->done, h->ntasks) ||
+      dalloc(h, &h->far_pack, h->ntasks) ||
       dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->list[0], h->ntasks) || dalloc(h, &h->list[1], h->ntasks) ||
       dalloc(h, &h->list[2], h->ntasks) || dalloc(h, &h->tile_off, h->ntasks) || dalloc(h, &h->tile_first, h->ntasks + 2) ||
       dalloc(h, &h->cls_flag, cls_flag_count(h->ntasks, nnz)) || dalloc(h, &h->cls_scan, 4 * (h->ntasks + 1)) ||
@@ -369,7 +370,7 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   int64_t b = 0;
   b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * (nnz + kColPad) + 32 + 8 * kCounters;   // cb_create
   b += 2 * 4 * n + 2 * 8 * (n + 1) + 3 * 4 * n + nnz;                                     // per node, stash
-  b += ntasks * (8 + 8 + 4 + 1 + 3 * 4 + 8 + 32) + 4 * cls_flag_count(ntasks, nnz) + 4 * (ntasks + 2) + 32;
+  b += ntasks * (8 + 8 + 4 + 16 + 1 + 3 * 4 + 8 + 32) + 4 * cls_flag_count(ntasks, nnz) + 4 * (ntasks + 2) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;
   if (max_trade > kBlockMaxCap || maxdeg > 16384) {   // default block_max

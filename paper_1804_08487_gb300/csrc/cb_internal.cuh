@@ -81,6 +81,7 @@ struct Graph {
   uint8_t* thr_top = nullptr;              // per trade: top 6 bits of the threshold key
   uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)
   uint32_t* done = nullptr;                // per trade: 1 once the threshold is published (cleared per step)
+  int4* far_pack = nullptr;                // per trade: new positions of its nodes, threshold prefix (rebuild)
   int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (tile, 256, 1024 threads), index order
   int64_t* tile_off = nullptr;             // per tile-class trade: prefix of its weight max(L, 4)
   int32_t* tile_first = nullptr;           // first tile-class trade of each tile (+ end sentinel)

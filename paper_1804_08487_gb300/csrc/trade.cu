@@ -1189,6 +1189,19 @@ __device__ __forceinline__ int64_t flat_owner(const StepCtx& c, int64_t lo, int6
   return lo;
 }
 
+// What the rebuild needs of a far trade s, in one 16-byte record: the new
+// positions of its two nodes and the top 6 bits of its threshold key.
+__global__ void k_far_pack(StepCtx c, int64_t ntasks, int4* __restrict__ pack) {
+  for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < ntasks; s += int64_t(gridDim.x) * blockDim.x) {
+    int4 p;
+    p.x = c.M[2 * s];
+    p.y = 2 * s + 1 < c.n ? c.M[2 * s + 1] : 0;
+    p.z = c.thr_top[s];
+    p.w = 0;
+    pack[s] = p;
+  }
+}
+
 // The first and last trade with entries in each chunk (one thread per trade:
 // every chunk boundary lies in exactly one non-empty trade).
 __global__ void k_flat_ranges(StepCtx c, int64_t nnz, int64_t ntasks, int32_t* __restrict__ cf,
@@ -1213,7 +1226,8 @@ __global__ void k_flat_ranges(StepCtx c, int64_t nnz, int64_t ntasks, int32_t* _
 __global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_t nnz, int64_t ntasks,
                                                                int32_t* __restrict__ slots,
                                                                const int32_t* __restrict__ cf,
-                                                               const int32_t* __restrict__ cl) {
+                                                               const int32_t* __restrict__ cl,
+                                                               const int4* __restrict__ pack) {
   __shared__ FlatTrade tab[kFlatTrades];
   __shared__ int32_t cnt[2 * kFlatTrades];     // entries of this chunk per (local trade, new side)
   __shared__ int32_t gbase[2 * kFlatTrades];   // their first slot in the new row
@@ -1290,10 +1304,11 @@ __global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_
         const int32_t yy = yv[j];
         const uint8_t st = sv[j];
         const int r2 = r ^ (st & 1);
-        int32_t y2 = yy;
+        const int32_t s = yy >> 1;
+        const int4 fs = __ldg(pack + s);   // one gather: the far trade's new positions and threshold prefix
+        int hi_node = yy & 1;
         if (st & 2) {
-          const int32_t s = yy >> 1;
-          const uint32_t fp = st >> 2, tt = c.thr_top[s];
+          const uint32_t fp = st >> 2, tt = static_cast<uint32_t>(fs.z);
           bool low;
           if (fp != tt) {
             low = fp < tt;
@@ -1301,9 +1316,9 @@ __global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_
             const uint32_t x = static_cast<uint32_t>(2 * t + r), y = static_cast<uint32_t>(yy);
             low = far_keeps_low(c, key_ctx(c, t), s, min(x, y), max(x, y));   // prefix tie: 1 in 64
           }
-          y2 = 2 * s + (low ? 0 : 1);
+          hi_node = low ? 0 : 1;
         }
-        out = c.M[y2];
+        out = hi_node ? fs.y : fs.x;
         key = static_cast<int>(2 * q + r2);
       }
       // the entries of one (trade, side) in the warp take consecutive slots
@@ -1626,8 +1641,11 @@ int super_step(Graph* h) {
       k_flat_ranges<<<grid_n(ntasks), 256, 0, s>>>(c, h->nnz, ntasks, cf, cl);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
+      k_far_pack<<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, h->far_pack);
+      CB_CUDA(h, cudaGetLastError());
+      ++h->launches;
       const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 8));
-      k_phase_b_flat<<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl);
+      k_phase_b_flat<<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl, h->far_pack);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
     }
