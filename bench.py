@@ -116,6 +116,23 @@ def workload(name):
     return synth.PLAIN[name]
 
 
+def measured_traffic():
+    """DRAM bytes per super step of the threshold phase at n=2^25 from the
+    committed ncu summary, or None if the trade kernels changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic_plain_n2p25.md")
+    src = os.path.join(ROOT, "paper_1804_08487_gb300", "csrc", "trade.cu")
+    try:
+        text = open(path).read()
+        vals = dict(line.split(": ", 1) for line in text.splitlines()
+                    if line.startswith(("traffic_threshold_bytes_per_step", "source_sha256_trade_cu")))
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != vals["source_sha256_trade_cu"].strip():
+            return None
+        return float(vals["traffic_threshold_bytes_per_step"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -537,8 +554,9 @@ def run_ours(args):
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic", "config": config_of(w, g, world),
         "roofline": {"bound": "hbm", "kernel": f"{dom} phase", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": f"{peak_kind} hbm_gbs"},
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": measured_traffic() if (dom == "threshold" and args.workload == "n2^25") else None,
+                     "traffic_unit": "bytes per super step", "peak_source": f"{peak_kind} hbm_gbs"},
         "roofline_step": {"bytes_min": b_min, "achieved": step_gbs, "peak": peak, "unit": "GB/s",
                           "frac": step_gbs / peak},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc},
