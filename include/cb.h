@@ -212,6 +212,8 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               index order: 1024 (large trades in shared memory) or 256
  *               (four CTAs per SM; trades above block_max from global
  *               memory) [1024; 256 for cb_create_batch].
+ *   "wide_pack" 1: the rebuild reads 16-byte far-trade records even when
+ *               n <= 2^29 would allow 8-byte ones (a test knob) [0].
  *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];
  *               larger buckets take the global-memory fallback; 2..4096.
  *   "timing"    1: record CUDA events around the phases of each super step

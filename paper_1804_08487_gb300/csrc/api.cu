@@ -778,6 +778,11 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     h->inorder_threads = static_cast<int>(value);
     return CB_OK;
   }
+  if (!std::strcmp(key, "wide_pack")) {
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "wide_pack is 0 or 1");
+    h->wide_pack = value != 0;
+    return CB_OK;
+  }
   if (!std::strcmp(key, "bucket_cap")) {
     if (value < 2 || value > 4096) return fail(h, CB_EINVAL, "bucket_cap out of range [2, 4096]");
     h->bucket_cap = static_cast<int>(value);

@@ -107,6 +107,7 @@ struct Graph {
   int smem_max = kSmemMaxCap;
   int bucket_cap = 2048;
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
+  bool wide_pack = false;       // 16-byte far-trade records even when 8 bytes would do (tests)
 
   // stats of the last cb_global_trades
   int64_t stats[8] = {0};

@@ -1189,16 +1189,40 @@ __device__ __forceinline__ int64_t flat_owner(const StepCtx& c, int64_t lo, int6
   return lo;
 }
 
-// What the rebuild needs of a far trade s, in one 16-byte record: the new
-// positions of its two nodes and the top 6 bits of its threshold key.
-__global__ void k_far_pack(StepCtx c, int64_t ntasks, int4* __restrict__ pack) {
+// What the rebuild needs of a far trade s, in one record: the new positions
+// of its two nodes and the top 6 bits of its threshold key.  Up to 2^29
+// positions it fits 8 bytes (29 + 29 + 6 bits), else 16.
+constexpr int64_t kNarrowPackMax = int64_t(1) << 29;
+
+struct FarTrade {
+  int32_t x, y;    // new positions of nodes 2s and 2s+1
+  uint32_t top;    // threshold prefix
+};
+
+template <bool kNarrow>
+__global__ void k_far_pack(StepCtx c, int64_t ntasks, void* __restrict__ pack) {
   for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < ntasks; s += int64_t(gridDim.x) * blockDim.x) {
-    int4 p;
-    p.x = c.M[2 * s];
-    p.y = 2 * s + 1 < c.n ? c.M[2 * s + 1] : 0;
-    p.z = c.thr_top[s];
-    p.w = 0;
-    pack[s] = p;
+    const uint32_t x = static_cast<uint32_t>(c.M[2 * s]);
+    const uint32_t y = 2 * s + 1 < c.n ? static_cast<uint32_t>(c.M[2 * s + 1]) : 0u;
+    const uint32_t top = c.thr_top[s];
+    if constexpr (kNarrow) {
+      static_cast<uint64_t*>(pack)[s] = uint64_t(x) | (uint64_t(y) << 29) | (uint64_t(top) << 58);
+    } else {
+      static_cast<int4*>(pack)[s] = make_int4(static_cast<int32_t>(x), static_cast<int32_t>(y),
+                                              static_cast<int32_t>(top), 0);
+    }
+  }
+}
+
+template <bool kNarrow>
+__device__ __forceinline__ FarTrade far_trade(const void* pack, int32_t s) {
+  if constexpr (kNarrow) {
+    const uint64_t v = __ldg(static_cast<const unsigned long long*>(pack) + s);
+    return {static_cast<int32_t>(v & 0x1FFFFFFFu), static_cast<int32_t>((v >> 29) & 0x1FFFFFFFu),
+            static_cast<uint32_t>(v >> 58)};
+  } else {
+    const int4 v = __ldg(static_cast<const int4*>(pack) + s);
+    return {v.x, v.y, static_cast<uint32_t>(v.z)};
   }
 }
 
@@ -1223,11 +1247,12 @@ __global__ void k_flat_ranges(StepCtx c, int64_t nnz, int64_t ntasks, int32_t* _
   }
 }
 
+template <bool kNarrow>
 __global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_t nnz, int64_t ntasks,
                                                                int32_t* __restrict__ slots,
                                                                const int32_t* __restrict__ cf,
                                                                const int32_t* __restrict__ cl,
-                                                               const int4* __restrict__ pack) {
+                                                               const void* __restrict__ pack) {
   __shared__ FlatTrade tab[kFlatTrades];
   __shared__ int32_t cnt[2 * kFlatTrades];     // entries of this chunk per (local trade, new side)
   __shared__ int32_t gbase[2 * kFlatTrades];   // their first slot in the new row
@@ -1305,10 +1330,10 @@ __global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_
         const uint8_t st = sv[j];
         const int r2 = r ^ (st & 1);
         const int32_t s = yy >> 1;
-        const int4 fs = __ldg(pack + s);   // one gather: the far trade's new positions and threshold prefix
+        const FarTrade fs = far_trade<kNarrow>(pack, s);   // one gather: new positions, threshold prefix
         int hi_node = yy & 1;
         if (st & 2) {
-          const uint32_t fp = st >> 2, tt = static_cast<uint32_t>(fs.z);
+          const uint32_t fp = st >> 2, tt = fs.top;
           bool low;
           if (fp != tt) {
             low = fp < tt;
@@ -1641,11 +1666,14 @@ int super_step(Graph* h) {
       k_flat_ranges<<<grid_n(ntasks), 256, 0, s>>>(c, h->nnz, ntasks, cf, cl);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
-      k_far_pack<<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, h->far_pack);
+      const bool narrow = h->n <= kNarrowPackMax && !h->wide_pack;
+      if (narrow) k_far_pack<true><<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, h->far_pack);
+      else k_far_pack<false><<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, h->far_pack);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
       const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 8));
-      k_phase_b_flat<<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl, h->far_pack);
+      if (narrow) k_phase_b_flat<true><<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl, h->far_pack);
+      else k_phase_b_flat<false><<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl, h->far_pack);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
     }

@@ -101,6 +101,7 @@ CASES = [
     (777, 5, 200, 2.0, 12, {"bucket_cap": 2}),        # permutation sort fallback
     (2500, 3, 60, 2.0, 15, {"tile_paths": 1}),        # tile thresholds
     (2500, 3, 60, 2.0, 16, {"tile_paths": 0}),        # 256-thread thresholds for small trades
+    (3001, 3, 300, 2.0, 18, {"wide_pack": 1}),        # 16-byte far-trade records (n > 2^29 layout)
     (3000, 4, 1500, 2.0, 13, {}),                     # heavy tail: block-path hubs
 ]
 
