@@ -32,6 +32,13 @@
  *  - Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As
  *    Easy as 1, 2, 3" (SC'11); key words (k0, k1) = (low, high) 32 bits of the
  *    seed; philox64 = (r0 << 32) | r1.
+ *  - Relaxed global trade (Def. "Relaxed global trade", Appendix EM-GCB; the
+ *    linear congruential maps of Section 4.3 and the Appendix "Linear
+ *    congruential maps"), when switched on: super step g draws
+ *    h(x) = (a x + b) mod p, p the smallest prime >= n, from Philox4x32-10 on
+ *    counter (0, 0, g, 4) = r0..r3: a = 1 + ((r0<<32|r1) mod (p-1)),
+ *    b = (r2<<32|r3) mod p.  The nodes in order of h(x) (injective on [n])
+ *    form the trades, as a permutation does.
  *
  * Data structure: the edge list E (two endpoint fields per edge, plus the
  * edge's identity at the start of the current super step) and, per node, the
@@ -83,6 +90,7 @@ typedef struct {
   int64_t* pos;            /* position of each node in the current step */
   int64_t* order;          /* node at each position */
   int64_t maxdeg;
+  int relaxed;             /* 1: permutations from linear congruential maps */
   /* per-trade scratch */
   void* scratch;
 } or_state;
@@ -208,14 +216,45 @@ uint64_t or_step(void* hp) { return ((or_state*)hp)->g; }
 int64_t or_num_edges(void* hp) { return ((or_state*)hp)->m; }
 int64_t or_num_nodes(void* hp) { return ((or_state*)hp)->n; }
 
+/* Smallest prime p >= n (trial division; p = 2 for n <= 2). */
+static uint64_t next_prime(uint64_t n) {
+  for (uint64_t p = n < 2 ? 2 : n;; p++) {
+    int prime = 1;
+    for (uint64_t d = 2; d * d <= p; d++)
+      if (p % d == 0) { prime = 0; break; }
+    if (prime) return p;
+  }
+}
+
+/* The linear congruential map h(x) = (a x + b) mod p of super step g. */
+static void lcg_params(const or_state* h, uint64_t g, uint64_t* p, uint64_t* a, uint64_t* b) {
+  uint32_t ctr[4] = {0u, 0u, (uint32_t)g, 4u}, r[4];
+  philox4x32_10(ctr, h->seed, r);
+  *p = next_prime((uint64_t)h->n);
+  *a = 1 + ((((uint64_t)r[0] << 32) | r[1]) % (*p - 1));
+  *b = (((uint64_t)r[2] << 32) | r[3]) % *p;
+}
+
+void or_lcg_params(void* hp, uint64_t g, uint64_t* p, uint64_t* a, uint64_t* b) {
+  lcg_params((or_state*)hp, g, p, a, b);
+}
+
+void or_set_relaxed(void* hp, int on) { ((or_state*)hp)->relaxed = on != 0; }
+
 /* Permutation pi for super step g: positions of all nodes. */
 static int compute_permutation(or_state* h, uint64_t g) {
   keyid* ki = (keyid*)malloc(sizeof(keyid) * (size_t)(h->n ? h->n : 1));
   if (!ki) return OR_ENOMEM;
+  uint64_t p = 0, a = 0, b = 0;
+  if (h->relaxed) lcg_params(h, g, &p, &a, &b);
   for (int64_t x = 0; x < h->n; x++) {
-    uint32_t ctr[4] = {(uint32_t)x, 0u, (uint32_t)g, 0u}, r[4];
-    philox4x32_10(ctr, h->seed, r);
-    ki[x].key = ((uint64_t)r[0] << 32) | r[1];
+    if (h->relaxed) {
+      ki[x].key = (a * (uint64_t)x + b) % p;   /* the image h(x): distinct for x < n <= p */
+    } else {
+      uint32_t ctr[4] = {(uint32_t)x, 0u, (uint32_t)g, 0u}, r[4];
+      philox4x32_10(ctr, h->seed, r);
+      ki[x].key = ((uint64_t)r[0] << 32) | r[1];
+    }
     ki[x].id = x;
   }
   qsort(ki, (size_t)h->n, sizeof(keyid), cmp_keyid);
@@ -406,5 +445,6 @@ void* or_clone(void* hp, int* rc) {
   }
   void* c = or_create(h->n, h->row_ptr, col, h->seed, h->g, rc);
   free(col); free(fill);
+  if (c) ((or_state*)c)->relaxed = h->relaxed;
   return c;
 }

@@ -38,6 +38,8 @@ def _load():
         lib.or_clone.restype = vp
         lib.or_clone.argtypes = [vp, ip]
         lib.or_philox4x32_10.argtypes = [vp, u64, vp]
+        lib.or_set_relaxed.argtypes = [vp, C.c_int]
+        lib.or_lcg_params.argtypes = [vp, u64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
         _lib = lib
     return _lib
 
@@ -128,6 +130,16 @@ class Oracle:
         if nd < 0:
             raise ValueError(nd)
         return out[:nd].copy(), int(a.value)
+
+    def set_relaxed(self, on: bool = True) -> None:
+        """Permutations from linear congruential maps (Def. "Relaxed global trade")."""
+        _load().or_set_relaxed(self._h, 1 if on else 0)
+
+    def lcg_params(self, g: int):
+        """(p, a, b) of super step g's map h(x) = (a x + b) mod p."""
+        p, a, b = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0)
+        _load().or_lcg_params(self._h, g, C.byref(p), C.byref(a), C.byref(b))
+        return p.value, a.value, b.value
 
     def clone(self) -> "Oracle":
         rc = C.c_int(0)

@@ -115,3 +115,31 @@ def to_csr(state, n):
     rp[1:] = np.cumsum([len(adj[x]) for x in range(n)])
     col = np.array([y for x in range(n) for y in sorted(adj[x])], dtype=np.int32)
     return rp, col
+
+
+def next_prime(n):
+    """Smallest prime p >= n (p = 2 for n <= 2), by trial division."""
+    p = max(n, 2)
+    while any(p % d == 0 for d in range(2, int(p ** 0.5) + 1)):
+        p += 1
+    return p
+
+
+def lcg_orders(n):
+    """Every order of [n] induced by a linear congruential map
+    h(x) = (a x + b) mod p, 1 <= a < p, 0 <= b < p, p the smallest prime >= n
+    (Def. "Relaxed global trade": nodes in order of their image), one per map."""
+    p = next_prime(n)
+    return [sorted(range(n), key=lambda x: (a * x + b) % p) for a in range(1, p) for b in range(p)]
+
+
+def relaxed_global_trade_row(state, n):
+    """Exact transition probabilities of one relaxed global trade: the map
+    drawn uniformly from the family, then the trades of its order."""
+    row = {}
+    orders = lcg_orders(n)
+    w = Fraction(1, len(orders))
+    for order in orders:
+        for s2, q in global_trade_outcomes(state, n, order).items():
+            row[s2] = row.get(s2, 0) + w * q
+    return row

@@ -363,3 +363,119 @@ def test_long_run_is_uniform_on_omega(deg, seed):
         if t % 3 == 2:
             visits[idx[frozenset(tuple(e) for e in o.edges().tolist())]] += 1
     assert chisquare(visits).pvalue > 1e-4
+
+
+# ------------------------------------------- relaxed global trade (LCG maps)
+# Def. "Relaxed global trade" (Appendix EM-GCB) with linear congruential maps
+# h(x) = (a x + b) mod p (Section 4.3, Appendix "Linear congruential maps").
+
+def _is_prime(q):
+    return q >= 2 and all(q % d for d in range(2, int(q ** 0.5) + 1))
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 6, 7, 8, 24, 97, 1000, 65536, 1 << 20])
+def test_lcg_prime_and_parameters(n):
+    o = Oracle(np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32), 11)
+    for g in range(3):
+        p, a, b = o.lcg_params(g)
+        assert _is_prime(p) and p >= max(n, 2)
+        assert all(not _is_prime(q) for q in range(max(n, 2), p))   # the smallest such prime
+        assert 1 <= a < p and 0 <= b < p
+
+
+@pytest.mark.parametrize("p", [2, 3, 7, 11, 101])
+def test_lcg_is_a_bijection_with_the_stated_inverse(p):
+    """Prop. "congruentialbijective": h is a bijection of Z_p and
+    h^{-1}(y) = a^{-1} (y - b) mod p."""
+    rng = np.random.default_rng(p)
+    for _ in range(10):
+        a = int(rng.integers(1, p)) if p > 2 else 1
+        b = int(rng.integers(0, p))
+        image = [(a * x + b) % p for x in range(p)]
+        assert sorted(image) == list(range(p))
+        ainv = pow(a, p - 2, p)
+        assert all((ainv * (image[x] - b)) % p == x for x in range(p))
+
+
+@pytest.mark.parametrize("p", [5, 7, 11])
+def test_lcg_family_is_pairwise_uniform(p):
+    """Lemma "statrandom": over all maps of the family, every pair of distinct
+    keys goes to every pair of distinct values exactly once (the maps are
+    bijections, so equal values never occur)."""
+    for x1 in range(p):
+        for x2 in range(p):
+            if x1 == x2:
+                continue
+            cnt = {}
+            for a in range(1, p):
+                for b in range(p):
+                    key = ((a * x1 + b) % p, (a * x2 + b) % p)
+                    cnt[key] = cnt.get(key, 0) + 1
+            assert all(y1 != y2 for (y1, y2) in cnt)
+            assert len(cnt) == p * (p - 1) and set(cnt.values()) == {1}
+
+
+def _rank_bounds(pi, x, xp, y):
+    return y - (pi[xp] - xp), y - (pi[x] - x)
+
+
+def test_sorted_rank_map_worked_example():
+    """The paper's example for Prop. "bounds": im(h) = {0,1,2,3,5,6} (n = 6,
+    p = 7; here a = 1, b = 5), pi(0) = 0 and pi(5) = 6 bound the rank of 2 to
+    {1, 2}; its rank is 2."""
+    n, p, a, b = 6, 7, 1, 5
+    pi = sorted((a * x + b) % p for x in range(n))
+    assert pi == [0, 1, 2, 3, 5, 6]
+    assert pi[0] == 0 and pi[5] == 6
+    lo, hi = _rank_bounds(pi, 0, 5, 2)
+    assert (lo, hi) == (1, 2) and lo <= pi.index(2) <= hi
+
+
+def test_sorted_rank_map_bounds_hold():
+    """Prop. "bounds": for ranks x <= x' with pi(x) <= y <= pi(x'), the rank of
+    y lies in [y - (pi(x') - x'), y - (pi(x) - x)]."""
+    rng = np.random.default_rng(3)
+    for n in [5, 30, 200, 1000]:
+        p = next((q for q in range(max(n, 2), 2 * n + 10) if _is_prime(q)))
+        for _ in range(20):
+            a, b = int(rng.integers(1, p)), int(rng.integers(0, p))
+            pi = sorted((a * x + b) % p for x in range(n))
+            for _ in range(20):
+                x, xp = sorted(int(v) for v in rng.integers(0, n, size=2))
+                r = int(rng.integers(x, xp + 1))
+                lo, hi = _rank_bounds(pi, x, xp, pi[r])
+                assert lo <= r <= hi
+
+
+def test_relaxed_oracle_orders_nodes_by_the_map():
+    g = synth.powerlaw_graph(3001, 3, 80, 2.0, 2)
+    o = Oracle(g.row_ptr, g.col, 17)
+    o.set_relaxed(True)
+    for step in range(3):
+        p, a, b = o.lcg_params(step)
+        want = np.argsort([(a * x + b) % p for x in range(g.n)], kind="stable")
+        assert np.array_equal(o.permutation(step), want)
+    deg0 = np.diff(g.row_ptr)
+    o.superstep(4)
+    e = o.edges()
+    check_simple_canonical(e, g.n)
+    assert np.array_equal(degrees(e, g.n), deg0)
+
+
+@pytest.mark.parametrize("deg", [[1] * 4, [2, 2, 1, 1, 0], [2] * 6])
+def test_relaxed_chain_is_symmetric(deg):
+    """Each global trade for a fixed order is a symmetric transition (Thm
+    "globaltrades"), so the relaxed chain, which draws the order from the LCG
+    family, has a symmetric stochastic matrix on Omega_G: uniform is
+    stationary.  Checked exactly by enumerating every map of the family."""
+    states = exact.omega(deg)
+    n = len(deg)
+    idx = {s: i for i, s in enumerate(states)}
+    P = np.zeros((len(states), len(states)), dtype=object)
+    for s in states:
+        for s2, q in exact.relaxed_global_trade_row(s, n).items():
+            P[idx[s], idx[s2]] = q
+    for i in range(len(states)):
+        assert sum(P[i, :]) == 1
+        for j in range(len(states)):
+            assert P[i, j] == P[j, i]
