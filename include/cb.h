@@ -212,6 +212,14 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               index order: 1024 (large trades in shared memory) or 256
  *               (four CTAs per SM; trades above block_max from global
  *               memory) [1024; 256 for cb_create_batch].
+ *   "relaxed"   1: relaxed global trades (Def. "Relaxed global trade",
+ *               Appendix EM-GCB): super step g orders the nodes by
+ *               h(x) = (a x + b) mod p, p the smallest prime >= n, with
+ *               a = 1 + (philox64(seed; 0, 0, g, 4) mod (p - 1)) and b =
+ *               (r2<<32|r3 of the same call) mod p, computed without a sort;
+ *               0: the Philox key sort [0].  May be switched between super
+ *               steps (the current step is laid out again).  Handles of one
+ *               graph only (CB_EINVAL for cb_create_batch).
  *   "wide_pack" 1: the rebuild reads 16-byte far-trade records even when
  *               n <= 2^29 would allow 8-byte ones (a test knob) [0].
  *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];

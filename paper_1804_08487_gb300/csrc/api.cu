@@ -67,7 +67,8 @@ void release(Graph* h) {
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
                   h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
                   h->counters, h->err,
-                  h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs, h->far_pack};
+                  h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs, h->far_pack,
+                  h->lcg_ab, h->lcg_gaps};
   if (h->stream)
     for (void* b : bufs) dfree(h, b);
   for (auto& x : h->step_exec)
@@ -353,6 +354,55 @@ int copy_pairs(Graph* h, int64_t first, int64_t count, int32_t* edges, int mem_k
                              mem_kind == CB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
   CB_CUDA(h, cudaStreamSynchronize(h->stream));
   return CB_OK;
+}
+
+uint64_t next_prime_host(uint64_t n) {
+  for (uint64_t p = n < 2 ? 2 : n;; ++p) {
+    bool prime = true;
+    for (uint64_t d = 2; d * d <= p; ++d)
+      if (p % d == 0) {
+        prime = false;
+        break;
+      }
+    if (prime) return p;
+  }
+}
+
+// Switch between permutations by Philox key sort and by a linear congruential
+// map (Def. "Relaxed global trade") between super steps: the current graph is
+// taken back to node-id rows, the current step's permutation is drawn in the
+// new mode, and the rows are laid out again.  The chain state is the graph
+// and the step index, so the switch is seamless.
+int set_relaxed(Graph* h, bool on) {
+  if (h->nseg != 1) return fail(h, CB_EINVAL, "relaxed permutations are for handles of one graph");
+  if (on == h->relaxed) return CB_OK;
+  const int64_t n = h->n;
+  cudaStream_t s = h->stream;
+  int rc;
+  if (on && !h->lcg_ab) {
+    h->lcg_p = next_prime_host(static_cast<uint64_t>(std::max<int64_t>(n, 2)));
+    if (h->lcg_p - static_cast<uint64_t>(n) >= static_cast<uint64_t>(kMaxLcgGaps))
+      return fail(h, CB_EINVAL, "prime gap above the relaxed permutation's limit");
+    if (dalloc(h, &h->lcg_ab, 2) || dalloc(h, &h->lcg_gaps, kMaxLcgGaps + 1))
+      return fail(h, CB_ENOMEM, "device allocation failed");
+  }
+  const int spare = 1 - h->cur;
+  // node-id rows of the current graph into col[spare]
+  if ((rc = invert_permutation(h, h->order[h->cur], h->pos_next))) return rc;
+  if ((rc = permute_rows(h, n, h->rp[h->cur], h->col[h->cur], h->pos_next, h->order[h->cur], h->rp_id,
+                         h->col[spare])))
+    return rc;
+  h->relaxed = on;
+  if ((rc = compute_permutation(h, 0, -1, h->order[h->cur], h->pos_next))) return rc;
+  if (n) k_gather_deg<<<grid1d(n, h->num_sms), 256, 0, s>>>(n, h->order[h->cur], h->deg_id, h->deg_next);
+  CB_CUDA(h, cudaGetLastError());
+  ++h->launches;
+  CB_CUDA(h, exclusive_scan_i32(h->deg_next, h->rp[h->cur], n, h->scan_ws, s, &h->launches));
+  if ((rc = relabel_rows(h, n, h->rp_id, h->col[spare], h->order[h->cur], h->pos_next, h->rp[h->cur],
+                         h->col[h->cur])))
+    return rc;
+  h->pairs_step = ~0ull;
+  return check_device_error(h);
 }
 
 int upload_segs(Graph* h) {
@@ -777,6 +827,10 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     if (value != 256 && value != 1024) return fail(h, CB_EINVAL, "inorder_threads is 256 or 1024");
     h->inorder_threads = static_cast<int>(value);
     return CB_OK;
+  }
+  if (!std::strcmp(key, "relaxed")) {
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "relaxed is 0 or 1");
+    return set_relaxed(h, value != 0);
   }
   if (!std::strcmp(key, "wide_pack")) {
     if (value < 0 || value > 1) return fail(h, CB_EINVAL, "wide_pack is 0 or 1");

@@ -25,6 +25,7 @@ constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
 constexpr int kCounters = 32;       // device counters per handle
+constexpr int kMaxLcgGaps = 1024;   // p - n for the relaxed permutation (prime gaps below 2^31 are far smaller)
 
 // One independent graph of a handle.  A plain handle holds one; a batch handle
 // holds many side by side: graph i owns node ids and positions [off, off+span),
@@ -108,6 +109,11 @@ struct Graph {
   int bucket_cap = 2048;
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
   bool wide_pack = false;       // 16-byte far-trade records even when 8 bytes would do (tests)
+  // relaxed global trade: permutations from h(x) = (a x + b) mod p
+  bool relaxed = false;
+  uint64_t lcg_p = 0;           // smallest prime >= n
+  uint64_t* lcg_ab = nullptr;   // device: a, b of the step being prepared
+  int64_t* lcg_gaps = nullptr;  // device: gap count, then the sorted gap values
 
   // stats of the last cb_global_trades
   int64_t stats[8] = {0};

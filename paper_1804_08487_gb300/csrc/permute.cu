@@ -97,6 +97,74 @@ __global__ void k_perm_scatter(int64_t n, KeySrc ks, const int64_t* __restrict__
   }
 }
 
+// ------------------------------------------- relaxed global trade (no sort)
+//
+// Def. "Relaxed global trade" with a linear congruential map
+// h(x) = (a x + b) mod p, p the smallest prime >= n: the nodes in order of
+// h(x).  The image of [n] is Z_p minus the p - n values h takes on [n, p)
+// (the gaps; p - n is below a few hundred for any n < 2^31), so node x sits
+// at position h(x) - #{gaps below h(x)}, with no sort.  (a, b) come from
+// Philox4x32-10 on counter (0, 0, g, 4): a = 1 + (r0r1 mod (p-1)),
+// b = r2r3 mod p.
+
+__device__ __forceinline__ uint64_t mulmod(uint64_t x, uint64_t y, uint64_t p) { return (x * y) % p; }
+
+// One CTA: (a, b) of the step, the gap values h(x), n <= x < p, sorted into gaps[1..]
+// (gaps[0] = their count).
+__global__ void k_lcg_gaps(int64_t n, uint64_t p, KeySrc ks, uint64_t* __restrict__ ab, int64_t* __restrict__ gaps) {
+  __shared__ int64_t sg[kMaxLcgGaps];
+  const uint64_t seed = ks.segs ? ks.segs[0].seed : ks.s0.seed;
+  const uint32_t g = ks.use_abs ? ks.g_abs : (ks.segs ? ks.segs[0].g : ks.s0.g) + ks.dg;
+  const Philox4 r = philox4x32_10(0u, 0u, g, 4u, seed);
+  const uint64_t a = 1 + (((static_cast<uint64_t>(r.w0) << 32) | r.w1) % (p - 1));
+  const uint64_t b = ((static_cast<uint64_t>(r.w2) << 32) | r.w3) % p;
+  const int ng = static_cast<int>(p - static_cast<uint64_t>(n));
+  int P = 1;
+  while (P < ng) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x)
+    sg[i] = i < ng ? static_cast<int64_t>((mulmod(a, static_cast<uint64_t>(n + i), p) + b) % p) : INT64_MAX;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int64_t x = sg[i], y = sg[l];
+          if ((x > y) == ((i & k) == 0)) { sg[i] = y; sg[l] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < ng; i += blockDim.x) gaps[1 + i] = sg[i];
+  if (threadIdx.x == 0) {
+    gaps[0] = ng;
+    ab[0] = a;
+    ab[1] = b;
+  }
+}
+
+// Node x goes to position h(x) - #{gaps < h(x)}.
+__global__ void k_lcg_positions(int64_t n, uint64_t p, const uint64_t* __restrict__ ab,
+                                const int64_t* __restrict__ gaps, int32_t* __restrict__ order,
+                                int32_t* __restrict__ pos) {
+  __shared__ int64_t sg[kMaxLcgGaps];
+  const int ng = static_cast<int>(gaps[0]);
+  for (int i = threadIdx.x; i < ng; i += blockDim.x) sg[i] = gaps[1 + i];
+  __syncthreads();
+  const uint64_t a = ab[0], b = ab[1];
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t y = static_cast<int64_t>((mulmod(a, static_cast<uint64_t>(x), p) + b) % p);
+    int lo = 0, hi = ng;   // gaps below y
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sg[mid] < y) lo = mid + 1; else hi = mid;
+    }
+    const int64_t q = y - lo;
+    order[q] = static_cast<int32_t>(x);
+    if (pos) pos[x] = static_cast<int32_t>(q);
+  }
+}
+
 __device__ __forceinline__ bool pair_less(uint64_t ka, int32_t ia, uint64_t kb, int32_t ib) {
   return ka < kb || (ka == kb && ia < ib);
 }
@@ -218,6 +286,21 @@ size_t perm_ws_bytes(int64_t n, int64_t nb) {
 int compute_permutation(Graph* h, uint32_t dg, int64_t g_abs, int32_t* order_out, int32_t* pos_out) {
   const int64_t n = h->n;
   if (n == 0) return CB_OK;
+  if (h->relaxed) {
+    KeySrc ks{};
+    ks.segs = h->segs;
+    ks.dg = dg;
+    ks.use_abs = g_abs >= 0;
+    ks.g_abs = static_cast<uint32_t>(g_abs < 0 ? 0 : g_abs);
+    k_lcg_gaps<<<1, 256, 0, h->stream>>>(n, h->lcg_p, ks, h->lcg_ab, h->lcg_gaps);
+    CB_CUDA(h, cudaGetLastError());
+    k_lcg_positions<<<grid_for(n, kPermThreads, h->num_sms), kPermThreads, 0, h->stream>>>(n, h->lcg_p, h->lcg_ab,
+                                                                                          h->lcg_gaps, order_out,
+                                                                                          pos_out);
+    CB_CUDA(h, cudaGetLastError());
+    h->launches += 2;
+    return CB_OK;
+  }
   const int64_t nb = h->nbuckets;
   PermWs w = carve(h->sort_ws, n, nb);
   cudaStream_t s = h->stream;
