@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default="n2^25")
     ap.add_argument("--batched", type=int, default=1, help="1: add the batched-ensemble comparison to the line")
     ap.add_argument("--requests", type=int, default=200, help="serving workload: number of requests replayed")
+    ap.add_argument("--perm", default="sort", choices=["sort", "relaxed"],
+                    help="relaxed: permutations from linear congruential maps (Def. 'Relaxed global trade')")
     return ap.parse_args()
 
 
@@ -142,13 +144,15 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def cpu_sample(w, steps=1, log2n=19):
+def cpu_sample(w, steps=1, log2n=19, perm="sort"):
     """Oracle on a bounded sample of the workload family: the same degree law
     at n=2^log2n, `steps` super steps, one host core (the chain is sequential)."""
     from oracle import Oracle
     from paper_1804_08487_gb300 import synth
     g = synth.powerlaw_graph(1 << log2n, w.a, w.b, w.gamma, w.degree_seed)
     o = Oracle(g.row_ptr, g.col, w.chain_seed)
+    if perm == "relaxed":
+        o.set_relaxed(True)
     t0 = time.perf_counter()
     o.superstep(steps)
     dt = time.perf_counter() - t0
@@ -157,8 +161,9 @@ def cpu_sample(w, steps=1, log2n=19):
     return g.m * steps / dt, desc, g.m, dt
 
 
-def config_of(w, g, world):
-    return {"workload": w.name, "n": g.n, "m": g.m, "degree_seed": g.degree_seed, "chain_seed": w.chain_seed,
+def config_of(w, g, world, perm="sort"):
+    return {"workload": w.name + (" relaxed (linear congruential maps)" if perm == "relaxed" else ""),
+            "n": g.n, "m": g.m, "degree_seed": g.degree_seed, "chain_seed": w.chain_seed,
             "l2": "inputs larger than L2 (adjacency %.1f GB vs 129 MB L2)" % (g.m * 8 / 1e9),
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -473,6 +478,8 @@ def run_ours(args):
     seed = w.chain_seed + rank          # each replica its own chain
     stream = torch.cuda.Stream()
     c = cb.Curveball(g.row_ptr, g.col, seed, stream=stream)
+    if args.perm == "relaxed":
+        c.set_option("relaxed", 1)
     c.set_option("timing", 1)
     c.global_trades(args.warmup)
     c.sync()
@@ -514,6 +521,8 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     c2 = cb.Curveball(rp_h, col_h, seed, stream=stream)
+    if args.perm == "relaxed":
+        c2.set_option("relaxed", 1)
     c2.global_trades(args.steps)
     c2.edges(out_h)
     c2.sync()
@@ -548,11 +557,11 @@ def run_ours(args):
     achieved = phase_bytes[dom] / (phase_ms[dom] / 1e3) / 1e9
     b_min = 16 * g.m + 24 * g.n
     step_gbs = b_min / (t_max / K / 1e3) / 1e9
-    cpu_v, cpu_desc, _, _ = cpu_sample(w)
+    cpu_v, cpu_desc, _, _ = cpu_sample(w, perm=args.perm)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32", "data": "synthetic", "config": config_of(w, g, world),
+        "dtype": "int32", "data": "synthetic", "config": config_of(w, g, world, args.perm),
         "roofline": {"bound": "hbm", "kernel": f"{dom} phase", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": measured_traffic() if (dom == "threshold" and args.workload == "n2^25") else None,
