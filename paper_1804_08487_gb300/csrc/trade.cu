@@ -898,16 +898,26 @@ __device__ __forceinline__ int tile_hfind(const unsigned long long* h, uint64_t 
   }
 }
 
+// Tile order: round robin over the CTAs (`blocked` = 0), or each CTA a run of
+// consecutive tiles (`blocked` = 1).  A trade defers when a trade it depends
+// on has not published yet: in one large graph those are spread over all
+// earlier indices, and round robin finishes them first; in a batch of small
+// graphs they sit in the tiles just before, which a CTA running consecutive
+// tiles has already done.
 __global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const int32_t* __restrict__ list,
                                                                const int64_t* __restrict__ tile_off,
                                                                const int32_t* __restrict__ tile_first,
-                                                               const int64_t* __restrict__ counts) {
+                                                               const int64_t* __restrict__ counts, int blocked) {
   __shared__ TileShared sh;
   extern __shared__ __align__(16) char dsm[];
   TileA& ta = *reinterpret_cast<TileA*>(dsm);
   const int64_t ntrades = counts[0], total_w = counts[3];
   const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;   // tiles per CTA when blocked
+  for (int64_t i = 0;; ++i) {
+    if (blocked && i >= per) break;
+    const int64_t tile = blocked ? blockIdx.x * per + i : blockIdx.x + i * gridDim.x;
+    if (tile >= ntiles) break;
     for (int i = threadIdx.x; i < kTileHash; i += blockDim.x) ta.hash[i] = 0ull;
     if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, ta.kc}, list, tile_off, tile_first, ntrades, total_w,
                     tile))
@@ -1620,7 +1630,8 @@ int super_step(Graph* h) {
   c.wait = 0;
   c.def_count = ucnt + 4;
   if (h->tile_paths & 1) {
-    k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt);
+    k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt,
+                                                              h->nseg > 1 ? 1 : 0);
   } else {
     k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[0], cnt + 0, block_max, gws,
                                                                         h->ws_slice, block_max);
