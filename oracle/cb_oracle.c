@@ -32,6 +32,15 @@
  *  - Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As
  *    Easy as 1, 2, 3" (SC'11); key words (k0, k1) = (low, high) 32 bits of the
  *    seed; philox64 = (r0 << 32) | r1.
+ *  - Uniform single trades (Simple Undirected Curveball, Section 3.2, the
+ *    paragraph after Fig. 2; the trade sequence T of Section 4.1): trade i
+ *    (0-based, 64-bit) draws Philox4x32-10 on counter (i_lo, i_hi, 0, 5) =
+ *    r0..r3; u = floor(r0 n / 2^32), w = floor(r1 (n-1) / 2^32) and
+ *    v = w + (w >= u), so u != v and every ordered pair has probability
+ *    1/(n(n-1)) up to a relative 2^-32.  sigma: disjoint neighbour x (node
+ *    id) is keyed by (r0<<32|r1) of Philox4x32-10 on counter
+ *    (x, i_lo, i_hi, 6); sigma(D) is D sorted by (key, x).  The trades apply
+ *    one after the other in index order.
  *  - Relaxed global trade (Def. "Relaxed global trade", Appendix EM-GCB; the
  *    linear congruential maps of Section 4.3 and the Appendix "Linear
  *    congruential maps"), when switched on: super step g draws
@@ -91,6 +100,7 @@ typedef struct {
   int64_t* order;          /* node at each position */
   int64_t maxdeg;
   int relaxed;             /* 1: permutations from linear congruential maps */
+  uint64_t uni;            /* index of the next uniform single trade */
   /* per-trade scratch */
   void* scratch;
 } or_state;
@@ -413,6 +423,78 @@ int64_t or_disjoint(void* hp, int64_t u, int64_t v, int32_t* out, int64_t cap, i
   return nd;
 }
 
+/* ------------------------------------------------- uniform single trades */
+
+/* The node pair of uniform trade i on n >= 2 nodes (see the header). */
+void or_uniform_pair(uint64_t seed, int64_t n, uint64_t i, int64_t* u, int64_t* v) {
+  uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(i >> 32), 0u, 5u}, r[4];
+  philox4x32_10(ctr, seed, r);
+  int64_t a = (int64_t)(((uint64_t)r[0] * (uint64_t)n) >> 32);
+  int64_t w = (int64_t)(((uint64_t)r[1] * (uint64_t)(n - 1)) >> 32);
+  *u = a;
+  *v = w + (w >= a);
+}
+
+static int cmp_key_x(const void* p, const void* q) {
+  const elem* a = (const elem*)p; const elem* b = (const elem*)q;
+  if (a->key != b->key) return (a->key > b->key) - (a->key < b->key);
+  return (a->x > b->x) - (a->x < b->x);
+}
+
+/* Uniform trade i: the drawn pair, D, sigma(D) by the keys of trade i, Fig. 2. */
+static void uniform_trade(or_state* h, uint64_t i) {
+  scratch_t* s = (scratch_t*)h->scratch;
+  int64_t u, v, a;
+  or_uniform_pair(h->seed, h->n, i, &u, &v);
+  int64_t nd = disjoint_set(h, u, v, s->d, &a);
+  for (int64_t k = 0; k < nd; k++) {
+    uint32_t ctr[4] = {(uint32_t)s->d[k].x, (uint32_t)i, (uint32_t)(i >> 32), 6u}, r[4];
+    philox4x32_10(ctr, h->seed, r);
+    s->d[k].key = ((uint64_t)r[0] << 32) | r[1];
+  }
+  qsort(s->d, (size_t)nd, sizeof(elem), cmp_key_x);   /* sigma(D) */
+  apply_sigma(h, u, v, s->d, nd, a);
+}
+
+/* Apply the next `count` uniform trades (none exist for n < 2: only the index advances). */
+int or_uniform_trades(void* hp, uint64_t count) {
+  or_state* h = (or_state*)hp;
+  for (uint64_t c = 0; c < count; c++) {
+    if (h->n >= 2) uniform_trade(h, h->uni);
+    h->uni++;
+  }
+  return OR_OK;
+}
+
+uint64_t or_uniform_next(void* hp) { return ((or_state*)hp)->uni; }
+void or_set_uniform_next(void* hp, uint64_t i) { ((or_state*)hp)->uni = i; }
+
+/*
+ * Successor lists of a trade sequence (Section 4.1): for each node x the
+ * increasing indices i of the trades t_i = {pairs[2i], pairs[2i+1]} that
+ * contain x, in suc[begin[x] .. begin[x+1]); the closing "infinity" of the
+ * paper is the end of the range.  Returns OR_EINVAL for a node outside [0, n)
+ * or a pair of equal nodes.
+ */
+int or_successors(int64_t n, const int32_t* pairs, int64_t count, int64_t* begin, int32_t* suc) {
+  for (int64_t x = 0; x <= n; x++) begin[x] = 0;
+  for (int64_t i = 0; i < count; i++) {
+    int32_t a = pairs[2 * i], b = pairs[2 * i + 1];
+    if (a < 0 || b < 0 || a >= n || b >= n || a == b) return OR_EINVAL;
+    begin[a + 1]++; begin[b + 1]++;
+  }
+  for (int64_t x = 0; x < n; x++) begin[x + 1] += begin[x];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+  if (!fill) return OR_ENOMEM;
+  for (int64_t x = 0; x < n; x++) fill[x] = begin[x];
+  for (int64_t i = 0; i < count; i++) {   /* increasing i: each list comes out sorted */
+    suc[fill[pairs[2 * i]]++] = (int32_t)i;
+    suc[fill[pairs[2 * i + 1]]++] = (int32_t)i;
+  }
+  free(fill);
+  return OR_OK;
+}
+
 /* Canonical edge list: pairs [a,b] with a<b, sorted lexicographically. */
 int64_t or_export(void* hp, int32_t* pairs, int64_t cap_pairs) {
   or_state* h = (or_state*)hp;
@@ -445,6 +527,6 @@ void* or_clone(void* hp, int* rc) {
   }
   void* c = or_create(h->n, h->row_ptr, col, h->seed, h->g, rc);
   free(col); free(fill);
-  if (c) ((or_state*)c)->relaxed = h->relaxed;
+  if (c) { ((or_state*)c)->relaxed = h->relaxed; ((or_state*)c)->uni = h->uni; }
   return c;
 }

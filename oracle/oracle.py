@@ -39,6 +39,14 @@ def _load():
         lib.or_clone.argtypes = [vp, ip]
         lib.or_philox4x32_10.argtypes = [vp, u64, vp]
         lib.or_set_relaxed.argtypes = [vp, C.c_int]
+        lib.or_uniform_pair.argtypes = [u64, i64, u64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        lib.or_uniform_trades.restype = C.c_int
+        lib.or_uniform_trades.argtypes = [vp, u64]
+        lib.or_uniform_next.restype = u64
+        lib.or_uniform_next.argtypes = [vp]
+        lib.or_set_uniform_next.argtypes = [vp, u64]
+        lib.or_successors.restype = C.c_int
+        lib.or_successors.argtypes = [i64, vp, i64, vp, vp]
         lib.or_lcg_params.argtypes = [vp, u64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
         _lib = lib
     return _lib
@@ -51,6 +59,25 @@ def philox4x32_10(ctr, seed: int) -> np.ndarray:
     out = np.zeros(4, dtype=np.uint32)
     lib.or_philox4x32_10(c.ctypes.data, C.c_uint64(seed & (2**64 - 1)), out.ctypes.data)
     return out
+
+
+def uniform_pair(seed: int, n: int, i: int):
+    """Node pair (u, v) of uniform trade i on n >= 2 nodes (the oracle's draw)."""
+    u, v = C.c_int64(0), C.c_int64(0)
+    _load().or_uniform_pair(C.c_uint64(seed & (2**64 - 1)), n, C.c_uint64(i), C.byref(u), C.byref(v))
+    return u.value, v.value
+
+
+def successors(n: int, pairs):
+    """Successor lists of a trade sequence (Section 4.1): (begin, suc) with
+    node x's increasing trade indices in suc[begin[x]:begin[x+1]]."""
+    p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    begin = np.zeros(n + 1, dtype=np.int64)
+    suc = np.zeros(max(2 * len(p), 1), dtype=np.int32)
+    rc = _load().or_successors(n, p.ctypes.data, len(p), begin.ctypes.data, suc.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle rejected the trade sequence (code {rc})")
+    return begin, suc[:2 * len(p)]
 
 
 class Oracle:
@@ -140,6 +167,19 @@ class Oracle:
         p, a, b = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0)
         _load().or_lcg_params(self._h, g, C.byref(p), C.byref(a), C.byref(b))
         return p.value, a.value, b.value
+
+    def uniform_trades(self, count: int = 1, first=None) -> None:
+        """Apply the next `count` uniform single trades (Section 3.2); with
+        `first`, the sequence continues from trade index `first`."""
+        if first is not None:
+            _load().or_set_uniform_next(self._h, C.c_uint64(first))
+        rc = _load().or_uniform_trades(self._h, C.c_uint64(count))
+        if rc:
+            raise RuntimeError(f"oracle uniform trades failed (code {rc})")
+
+    @property
+    def uniform_next(self) -> int:
+        return int(_load().or_uniform_next(self._h))
 
     def clone(self) -> "Oracle":
         rc = C.c_int(0)

@@ -7,6 +7,8 @@ the edge {u, v}, and gives u a uniformly random |A_{u-v}|-subset of the disjoint
 set D (Section 4: "draw |A_u n D| nodes from D for u uniformly at random").  A
 global trade (Def. "Undirected Global Trade", Section 3.3) draws a uniform
 permutation pi and applies the floor(n/2) trades {pi(2i-1), pi(2i)} in order.
+`imcb` restates a given trade sequence in the manner of IM-CB (Section 4.2),
+with sigma supplied by the caller.
 """
 from fractions import Fraction
 from itertools import combinations, permutations
@@ -143,3 +145,63 @@ def relaxed_global_trade_row(state, n):
         for s2, q in global_trade_outcomes(state, n, order).items():
             row[s2] = row.get(s2, 0) + w * q
     return row
+
+
+def imcb(n, edges, pairs, sigma):
+    """The trade sequence `pairs` applied in the manner of the paper's IM-CB
+    (Section 4.2 and its appendix algorithm): successor lists Suc, every edge
+    kept once, in the buffer of the endpoint whose next trade comes first; a
+    trade gathers the buffers of its two nodes, reassigns the disjoint
+    neighbours and pushes every resulting edge to the endpoint traded next.
+
+    sigma(i, u, v, d, a) returns sigma(D) for trade i, given D sorted by node
+    id and a = |A_{u-v}|; u receives its first a elements (Fig. 2)."""
+    inf = len(pairs)
+    suc = [[] for _ in range(n)]
+    for i, (u, v) in enumerate(pairs):
+        suc[u].append(i)
+        suc[v].append(i)
+    idx = [0] * n
+
+    def tau(x):
+        return suc[x][idx[x]] if idx[x] < len(suc[x]) else inf
+
+    buf = [[] for _ in range(n)]
+
+    def push(a, b):
+        if tau(a) <= tau(b):
+            buf[a].append(b)
+        else:
+            buf[b].append(a)
+
+    for a, b in edges:
+        push(a, b)
+    for i, (u, v) in enumerate(pairs):
+        assert tau(u) == i and tau(v) == i
+        nu, nv = set(buf[u]), set(buf[v])
+        # the edge {u, v}, if present, sits in exactly one of the two buffers
+        if u in nv:
+            nu.add(v)
+        if v in nu:
+            nv.add(u)
+        buf[u], buf[v] = [], []
+        idx[u] += 1
+        idx[v] += 1
+        auv = nu - nv - {v}
+        avu = nv - nu - {u}
+        d = sorted(auv | avu)
+        order = sigma(i, u, v, d, len(auv))
+        assert sorted(order) == d
+        new_u = (nu - auv) | set(order[:len(auv)])
+        new_v = (nv - avu) | set(order[len(auv):])
+        for x in new_u:
+            push(u, x)
+        for x in new_v:
+            if x != u:
+                push(v, x)
+    out = set()
+    for a in range(n):
+        for b in buf[a]:
+            out.add((min(a, b), max(a, b)))
+    assert sum(len(b) for b in buf) == len(out) == len(edges)
+    return sorted(out)
