@@ -104,6 +104,14 @@ def load():
     lib.cb_server_stats.argtypes = [vp, C.POINTER(i64), i32]
     lib.cb_server_destroy.restype = None
     lib.cb_server_destroy.argtypes = [vp]
+    lib.cb_uniform_trades.restype = i32
+    lib.cb_uniform_trades.argtypes = [vp, u64]
+    lib.cb_uniform_next.restype = i32
+    lib.cb_uniform_next.argtypes = [vp, C.POINTER(u64)]
+    lib.cb_uniform_pairs.restype = i32
+    lib.cb_uniform_pairs.argtypes = [u64, i64, u64, i64, vp, vp]
+    lib.cb_successors.restype = i32
+    lib.cb_successors.argtypes = [i64, vp, i64, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -260,6 +268,44 @@ def cb_permutation_static(n: int, seed: int, g: int, order_out, stream=None):
     return _check(load().cb_permutation_static(n, C.c_uint64(seed & (2**64 - 1)), C.c_uint64(g), p, s))
 
 
+def _stream(stream):
+    return None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def cb_uniform_trades(h, count: int):
+    """Apply the handle's next `count` uniform single trades (Section 3.2)."""
+    return _check(load().cb_uniform_trades(h, C.c_uint64(count)), h)
+
+
+def cb_uniform_next(h) -> int:
+    v = C.c_uint64(0)
+    _check(load().cb_uniform_next(h, C.byref(v)), h)
+    return v.value
+
+
+def cb_uniform_pairs(seed: int, n: int, first: int, count: int, pairs_out, stream=None):
+    """Node pairs of uniform trades first..first+count-1 into `pairs_out` (an
+    int32 CUDA tensor of 2*count entries)."""
+    p, kind, _ = _ptr(pairs_out)
+    if kind != CB_DEVICE:
+        raise ValueError("pairs_out must be device memory")
+    return _check(load().cb_uniform_pairs(C.c_uint64(seed & (2**64 - 1)), n, C.c_uint64(first), count, p,
+                                          _stream(stream)))
+
+
+def cb_successors(n: int, pairs, suc_begin_out, suc_out, stream=None):
+    """Successor lists (Section 4.1) of the trade sequence in `pairs` (int32
+    CUDA tensor, 2 per trade) into suc_begin_out (int64, n+1) and suc_out
+    (int32, 2 per trade), all device memory."""
+    pp, k1, _ = _ptr(pairs)
+    pb, k2, _ = _ptr(suc_begin_out)
+    ps, k3, _ = _ptr(suc_out)
+    if CB_HOST in (k2,) or (pp is not None and k1 != CB_DEVICE) or (ps is not None and k3 != CB_DEVICE):
+        raise ValueError("cb_successors takes device memory")
+    count = pairs.numel() // 2
+    return _check(load().cb_successors(n, pp, count, pb, ps, _stream(stream)))
+
+
 def cb_stats(h):
     out = (C.c_int64 * 8)()
     k = _check(load().cb_stats(h, out, 8), h)
@@ -309,6 +355,13 @@ class Curveball:
 
     def autotune(self, max_steps: int):
         return cb_autotune(self.h, max_steps)
+
+    def uniform_trades(self, count: int = 1):
+        cb_uniform_trades(self.h, count)
+
+    @property
+    def uniform_next(self) -> int:
+        return cb_uniform_next(self.h)
 
     def sync(self):
         cb_sync(self.h)

@@ -63,6 +63,7 @@ void dfree(Graph* h, void* p) {
 void release(Graph* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  free_uniform(h);
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
                   h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
@@ -81,7 +82,7 @@ void release(Graph* h) {
 }
 
 // Read the latched device error word; synchronises the stream.
-int check_device_error(Graph* h) {
+int read_device_error(Graph* h) {
   int32_t e = 0;
   CB_CUDA(h, cudaMemcpyAsync(&e, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CB_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -114,6 +115,10 @@ int size_trade_workspace(Graph* h) {
 }
 
 }  // namespace
+
+int check_device_error(Graph* h) { return read_device_error(h); }
+
+cudaError_t dev_alloc(Graph* h, void** p, size_t bytes) { return dmalloc(h, p, bytes); }
 
 int fail(Graph* g, int code, const std::string& msg) {
   if (g) g->last_error = msg;
@@ -288,7 +293,7 @@ int finish_create(Graph* h) {
   return check_device_error(h);
 }
 
-void drop_step_graphs(Graph* h) {
+void drop_graphs(Graph* h) {
   for (auto& x : h->step_exec)
     if (x) {
       cudaGraphExecDestroy(x);
@@ -436,6 +441,8 @@ int prepare_step_graphs(Graph* h) {
   if (!h->use_graph || h->step_exec[0]) return CB_OK;
   return capture_step_graphs(h);
 }
+
+void drop_step_graphs(Graph* h) { drop_graphs(h); }
 
 }  // namespace cb
 

@@ -18,7 +18,11 @@ enum DevErr : int32_t {
   kErrBucket = 4,        // permutation bucket bookkeeping failed
   kErrResolve = 5,       // a dependency wait of the in-order pass gave up
   kErrStage = 6,         // a bulk copy into shared memory did not complete in time
+  kErrUniform = 7,       // uniform trades: an inbox or the run queue overflowed, or a message missed its trade
+  kErrUniformWait = 8,   // uniform trades: a wait for a queued trade or an inbox entry gave up
 };
+
+struct UniBufs;   // uniform-trade buffers (uniform.cu)
 
 constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
 constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
@@ -115,6 +119,10 @@ struct Graph {
   uint64_t* lcg_ab = nullptr;   // device: a, b of the step being prepared
   int64_t* lcg_gaps = nullptr;  // device: gap count, then the sorted gap values
 
+  // uniform single trades (uniform.cu)
+  UniBufs* uni = nullptr;
+  uint64_t uni_next = 0;        // index of the next uniform trade
+
   // stats of the last cb_global_trades
   int64_t stats[8] = {0};
   int64_t launches = 0;                    // kernel launches issued by this handle
@@ -178,6 +186,17 @@ int init_trade_kernels(Graph* h);   // one-time kernel attributes (outside strea
 size_t trade_ws_slice_bytes(int64_t max_trade);
 
 // api.cu
+// stream-ordered device allocation counted in the handle's device bytes
+cudaError_t dev_alloc(Graph* h, void** p, size_t bytes);
+// read the latched device error word (synchronises the stream)
+int check_device_error(Graph* h);
+// forget the recorded super-step graphs (they are recorded again when next needed)
+void drop_step_graphs(Graph* h);
+
+// uniform.cu
+int uniform_trades(Graph* h, uint64_t count);
+void free_uniform(Graph* h);
+
 // device bytes a plain handle of n nodes / nnz entries / largest degree takes (upper estimate)
 int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sms);
 // record the CUDA graphs of the super step now (when the cuda_graph option is on)
