@@ -2,7 +2,7 @@
 """Throughput of the global Curveball super step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload n2^25|n2^20|n2^21|n4096|ensemble]
+                    [--workload n2^25|n2^20|n2^21|n4096|ensemble|serving|uniform]
 
 One "step" is one global super step (Def. "Undirected Global Trade",
 Section 3.3) over the whole graph.  The metric is edge-trades/s = m * steps /
@@ -20,6 +20,10 @@ graphs, n log-uniform in [2^10, 2^16], 50 super steps each) run as one batch
 handle (one CUDA-graph launch per super step, autotuned work split) against
 256 sequential plain runs on the same GPU.  --workload ensemble makes that
 the headline of the line.
+
+--workload uniform times uniform single trades instead (Simple Undirected
+Curveball, Section 3.2): one step is n/2 trades on the --uniform-graph graph,
+run as the successor-list dataflow.
 """
 import argparse
 import json
@@ -46,6 +50,8 @@ def parse():
     ap.add_argument("--workload", default="n2^25")
     ap.add_argument("--batched", type=int, default=1, help="1: add the batched-ensemble comparison to the line")
     ap.add_argument("--requests", type=int, default=200, help="serving workload: number of requests replayed")
+    ap.add_argument("--uniform-graph", default="n2^25",
+                    help="uniform workload: the plain graph the uniform single trades run on")
     ap.add_argument("--perm", default="sort", choices=["sort", "relaxed"],
                     help="relaxed: permutations from linear congruential maps (Def. 'Relaxed global trade')")
     return ap.parse_args()
@@ -461,6 +467,117 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- uniform single trades
+
+UNIFORM_METRIC = "edge-trades/s per n/2 uniform single trades"
+
+
+def uniform_cpu_sample(w, log2n=19):
+    """Oracle's uniform single trades on a bounded sample: the same degree law
+    at n=2^log2n, n/2 trades, one host core (the sequence is sequential)."""
+    from oracle import Oracle
+    from paper_1804_08487_gb300 import synth
+    g = synth.powerlaw_graph(1 << log2n, w.a, w.b, w.gamma, w.degree_seed)
+    o = Oracle(g.row_ptr, g.col, w.chain_seed)
+    t0 = time.perf_counter()
+    o.uniform_trades(g.n // 2)
+    dt = time.perf_counter() - t0
+    desc = (f"oracle, n=2^{log2n} PLD([{w.a},{w.b}),{w.gamma:g}) Havel-Hakimi graph (m={g.m}), "
+            f"n/2 uniform single trades, sequential")
+    return g.m / dt, desc
+
+
+def run_uniform(args):
+    """One step = n/2 uniform single trades (Section 3.2; as many trades as one
+    global trade) on the plain workload graph, run as the Suc dataflow."""
+    import torch
+    from paper_1804_08487_gb300 import cb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args.uniform_graph)
+    g = w.graph()
+    seed = w.chain_seed + rank
+    stream = torch.cuda.Stream()
+    half = g.n // 2
+    c = cb.Curveball(g.row_ptr, g.col, seed, stream=stream)
+    c.uniform_trades(half * args.warmup)
+    c.sync()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        c.uniform_trades(half)
+        launches += int(c.stats().get("launches", 0))
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    t_max = t_ms
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    K = args.steps
+    value = world * g.m * K / (t_max / 1e3)
+    # end to end through the C ABI with host buffers
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    out_h = torch.empty(2 * g.m, dtype=torch.int32).pin_memory()
+    c.close()
+    barrier()
+    t0 = time.perf_counter()
+    c2 = cb.Curveball(rp_h, col_h, seed, stream=stream)
+    c2.uniform_trades(half * K)
+    c2.edges(out_h)
+    c2.sync()
+    e2e_s = time.perf_counter() - t0
+    c2.close()
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    b_min = 16 * g.m + 24 * g.n
+    gbs = b_min / (t_max / K / 1e3) / 1e9
+    cpu_v, cpu_desc = uniform_cpu_sample(w)
+    line = {
+        "metric": UNIFORM_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": dict(config_of(w, g, world), workload=w.name + ", n/2 uniform single trades per step"),
+        "roofline": {"bound": "hbm", "kernel": "uniform trades (whole step)", "achieved": gbs, "peak": peak,
+                     "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "note": "B_min = 16m + 24n per step; the dataflow is bound by its chain of dependent trades"},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc},
+        "e2e": {"value": world * g.m * K / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": (g.row_ptr.nbytes + g.col.nbytes) / K, "d2h_bytes_per_step": 2 * g.m * 4 / K},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args):
@@ -603,6 +720,23 @@ def run_reference(args):
         }
         print(json.dumps(line), flush=True)
         return
+    if args.workload == "uniform":
+        w = workload(args.uniform_graph)
+        vals = []
+        for _ in range(max(args.steps, 1)):
+            v, sample = uniform_cpu_sample(w, log2n=17)
+            vals.append(v)
+        value = statistics.median(vals)
+        line = {
+            "impl": "reference", "metric": UNIFORM_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w.name + ", n/2 uniform single trades per step", "parallelism": "single"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     w = workload(args.workload)
     from paper_1804_08487_gb300 import synth
     from oracle import Oracle
@@ -637,6 +771,8 @@ def main():
         run_ensemble(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "uniform":
+        run_uniform(args)
     else:
         run_ours(args)
 

@@ -173,7 +173,8 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
  * out[1] = trades the first pass deferred,
  * out[2] = trades on the tile path, out[3] = on the 256- and 1024-thread paths,
  * out[4] = trades whose workspace did not fit in shared memory,
- * out[5] = kernel launches issued by the call.
+ * out[5] = kernel launches issued by the last cb_global_trades or
+ *          cb_uniform_trades call.
  * `count` = capacity of out; returns the number of counters written.
  */
 int cb_stats(cb_handle h, int64_t* out, int count);

@@ -44,11 +44,11 @@ struct UniBufs {
   int32_t* suc = nullptr;      // 2L: slot ids grouped by node, increasing
   int32_t* nxt = nullptr;      // 2L: next trade of the slot's node after its trade
   unsigned long long* fill = nullptr;   // L: inbox counts (side 0 low, side 1 high)
-  int32_t* queue = nullptr;    // L: runnable trades in the order they became runnable
+  int32_t* queue = nullptr;    // L: runnable trades; small ones from the front, big ones from the back
   int32_t* occ = nullptr;      // n: occurrences, then fill cursors
   int64_t* sbeg = nullptr;     // n+1: Suc offsets
   int32_t* ocur = nullptr;     // n: output row cursors
-  unsigned long long* ctr = nullptr;   // [0] queue head, [1] queue tail
+  unsigned long long* ctr = nullptr;   // run queue head and tail, a cache line apart
   void* scan_ws = nullptr;
   int2* inbox = nullptr;
   int64_t inbox_cap = 0;
@@ -203,13 +203,39 @@ struct UniCtx {
   int64_t slice_elems;
 };
 
+// The run queue: a ticket (kHead) takes the next slot, a push (kTail)
+// fills the next slot; the two counters sit on different cache lines.
+// Every trade is queued exactly once, so every ticket below L ends.
+constexpr int kHead = 0, kTail = 16, kCtrWords = 32;
+
 __device__ __forceinline__ void push(const UniCtx& c, int64_t k) {
-  const unsigned long long q = atomicAdd(&c.ctr[1], 1ull);
+  const unsigned long long q = atomicAdd(&c.ctr[kTail], 1ull);
   if (q >= static_cast<unsigned long long>(c.L)) {
     latch(c.err, kErrUniform);
     return;
   }
   st_relaxed_i32(c.queue + q, static_cast<int32_t>(k));
+}
+
+// The next queued trade, or -1 when every slot is taken or a wait gave up.
+__device__ int64_t take_ticket(const UniCtx& c) {
+  const unsigned long long q = atomicAdd(&c.ctr[kHead], 1ull);
+  if (q >= static_cast<unsigned long long>(c.L)) return -1;
+  int32_t t = ld_relaxed_i32(c.queue + q);
+  if (t < 0) {
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+      __nanosleep(200);
+      t = ld_relaxed_i32(c.queue + q);
+      if (t >= 0) break;
+      if (ld_volatile_i32(c.err) != 0) return -1;
+      if (globaltimer() - t0 > kUniWaitNs) {
+        latch(c.err, kErrUniformWait);
+        return -1;
+      }
+    }
+  }
+  return t;
 }
 
 // Append (other, other_tau) to node x's inbox at trade d.
@@ -280,8 +306,8 @@ __global__ void k_uni_route(UniCtx c, int64_t n, const int32_t* __restrict__ col
   }
 }
 
-// Bounded wait for an inbox entry still being written.
-__device__ __forceinline__ bool wait_entry(const int2* p, const int32_t* err, int2* out) {
+// Bounded wait for an inbox entry still being written (the cold path).
+__device__ __noinline__ bool wait_entry(const int2* p, const int32_t* err, int2* out) {
   int2 m = ld_relaxed_v2(p);
   if (m.x != -1) {
     *out = m;
@@ -301,22 +327,35 @@ __device__ __forceinline__ bool wait_entry(const int2* p, const int32_t* err, in
 
 // Per-trade work space: the gathered entries (neighbour, its next trade),
 // their shuffle keys, flags and a hash of u's neighbours.
+template <class HT>
 struct TradeWs {
   int2* ent;
   uint64_t* key;
-  int32_t* hash;
+  HT* hash;        // entry index + 1 of u's neighbours, 0 = empty
   uint8_t* flag;   // bit 0 side (0: u's inbox, 1: v's), bit 1 common, bit 2 the edge {u, v}, bit 3 to u
 };
 
+// Big trades keep their entries in global memory but hash u's neighbours in
+// the (then unused) shared memory with 16-bit slots, up to this degree of u
+// at a load factor of at most 3/4.
+constexpr int kHash16MaxDu = 12288;
+
 constexpr size_t kWsBytesPerElem = sizeof(int2) + sizeof(uint64_t) + 2 * sizeof(int32_t) + 1;
 
-__device__ __forceinline__ TradeWs carve_ws(char* base, int64_t cap) {
-  TradeWs w;
+__device__ __forceinline__ TradeWs<int32_t> carve_ws(char* base, int64_t cap) {
+  TradeWs<int32_t> w;
   w.ent = reinterpret_cast<int2*>(base);
   w.key = reinterpret_cast<uint64_t*>(base + sizeof(int2) * cap);
   w.hash = reinterpret_cast<int32_t*>(base + (sizeof(int2) + sizeof(uint64_t)) * cap);
   w.flag = reinterpret_cast<uint8_t*>(base + (sizeof(int2) + sizeof(uint64_t) + 2 * sizeof(int32_t)) * cap);
   return w;
+}
+
+// log2 of the smallest power of two >= max(want, 2)
+__device__ __forceinline__ int hash_bits(int64_t want) {
+  int b = 1;
+  while ((int64_t(1) << b) < want) ++b;
+  return b;
 }
 
 __device__ __forceinline__ uint32_t hash_slot(int32_t x, int hbits) {
@@ -384,26 +423,39 @@ __device__ void deliver(const UniCtx& c, const Msg& m) {
   if (m.old + inc == ((dv << 32) | du)) push(c, d);
 }
 
-constexpr int kMsgBatch = 4;   // messages per thread with their atomics in flight together
+// Elements of D with the same full key as entry e and a smaller node id
+// (ties of 64-bit keys: practically never, hence the plain loop).
+__device__ __noinline__ int tied_before(const UniCtx& c, const int2* ent, const uint64_t* key, const uint8_t* flag,
+                                        int E, int e) {
+  const uint32_t id = static_cast<uint32_t>(c.order[ent[e].x]);
+  int before = 0;
+  for (int q = 0; q < E; ++q)
+    if ((flag[q] & 6) == 0 && key[q] == key[e] && static_cast<uint32_t>(c.order[ent[q].x]) < id) ++before;
+  return before;
+}
+
+constexpr int kMsgBatch = 2;   // messages per thread with their atomics in flight together
 
 // One trade by the whole CTA.  Returns false when a wait gave up.
-__device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k, const TradeWs& w,
+template <class HT>
+__device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k, const TradeWs<HT>& w, int hbits,
                           int32_t* hist, int64_t* s_sel, int* s_abort) {
   const int32_t u = c.tp[2 * k], v = c.tp[2 * k + 1];
   const int du = static_cast<int>(c.rp[u + 1] - c.rp[u]), dv = static_cast<int>(c.rp[v + 1] - c.rp[v]);
   const int32_t nu = c.nxt[2 * k], nv = c.nxt[2 * k + 1];
   const int E = du + dv;
-  int hbits = 1;
-  while ((1 << hbits) < 2 * du) ++hbits;
   const int H = 1 << hbits;
   const int2* inu = c.inbox + c.ib[2 * k];
   const int2* inv = c.inbox + c.ib[2 * k + 1];
-  // 1. gather both inboxes (entries may still be in flight); clear the hash
+  // 1. gather both inboxes: plain L2 loads, and a bounded wait only for an
+  //    entry still in flight; clear the hash
   bool ok = true;
+#pragma unroll 4
   for (int e = tm.rank; e < E; e += kUniThreads) {
     const int side = e >= du;
-    int2 m;
-    if (!wait_entry(side ? inv + (e - du) : inu + e, c.err, &m)) {
+    const int2* p = side ? inv + (e - du) : inu + e;
+    int2 m = __ldcg(p);
+    if (m.x == -1 && !wait_entry(p, c.err, &m)) {
       ok = false;
       m = make_int2(0, kInf);
     }
@@ -417,7 +469,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   // 2. u's neighbours into the hash (entry index + 1)
   for (int e = tm.rank; e < du; e += kUniThreads) {
     uint32_t s = hash_slot(w.ent[e].x, hbits);
-    while (atomicCAS(&w.hash[s], 0, e + 1) != 0) s = (s + 1) & (H - 1);
+    while (atomicCAS(&w.hash[s], HT(0), static_cast<HT>(e + 1)) != HT(0)) s = (s + 1) & (H - 1);
   }
   tm.sync();
   // 3. v's neighbours look themselves up: common neighbours and the edge {u, v}
@@ -427,7 +479,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
     if (x == u) f |= 4;
     uint32_t s = hash_slot(x, hbits);
     for (;;) {
-      const int32_t h = w.hash[s];
+      const int32_t h = static_cast<int32_t>(w.hash[s]);
       if (h == 0) break;
       if (w.ent[h - 1].x == x) {
         f |= 2;
@@ -442,6 +494,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   // 4. D = the rest, keyed by trade k's shuffle keys (Philox on (node id, k))
   const uint64_t gi = c.first + static_cast<uint64_t>(k);
   int64_t cnt = 0;
+#pragma unroll 4
   for (int e = tm.rank; e < E; e += kUniThreads) {
     uint8_t f = w.flag[e];
     if (f == 0 && w.ent[e].x == v) w.flag[e] = f = 4;
@@ -463,6 +516,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
     for (int shift = 56;; shift -= 8) {
       for (int b = tm.rank; b < 256; b += kUniThreads) hist[b] = 0;
       tm.sync();
+#pragma unroll 4
       for (int e = tm.rank; e < E; e += kUniThreads)
         if ((w.flag[e] & 6) == 0 && (w.key[e] & mask) == prefix) atomicAdd(&hist[(w.key[e] >> shift) & 255], 1);
       tm.sync();
@@ -486,6 +540,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
     }
   }
   // decision: below the threshold's bucket to u, above to v, within it by rank
+#pragma unroll 2
   for (int e = tm.rank; e < E; e += kUniThreads) {
     const uint8_t f = w.flag[e];
     if (f & 6) continue;
@@ -497,14 +552,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
       if (km != prefix) to_u = km < prefix;
       else if (!tie) to_u = r >= 1;   // the single element of the last bucket is the na-th
       else {
-        // rank among the tied elements by node id (ties of 64-bit keys: practically never)
-        const uint32_t id = static_cast<uint32_t>(c.order[w.ent[e].x]);
-        int before = 0;
-        for (int q = 0; q < E; ++q)
-          if ((w.flag[q] & 6) == 0 && w.key[q] == w.key[e] &&
-              static_cast<uint32_t>(c.order[w.ent[q].x]) < id)
-            ++before;
-        to_u = before < r;
+        to_u = tied_before(c, w.ent, w.key, w.flag, E, e) < r;
       }
     }
     if (to_u) w.flag[e] = f | 8;
@@ -543,7 +591,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   return true;
 }
 
-__global__ void __launch_bounds__(kUniThreads, 4) k_uni_exec(UniCtx c) {
+__global__ void __launch_bounds__(kUniThreads, 3) k_uni_exec(UniCtx c) {
   extern __shared__ __align__(16) char usm[];
   __shared__ int64_t red[BlockTeam<kUniThreads>::kRedSlots];
   __shared__ int32_t hist[256];
@@ -557,34 +605,23 @@ __global__ void __launch_bounds__(kUniThreads, 4) k_uni_exec(UniCtx c) {
       c.gslice ? carve_ws(c.gslice + static_cast<size_t>(blockIdx.x) * c.slice_elems * kWsBytesPerElem, c.slice_elems)
                : ws_smem;
   for (;;) {
-    if (threadIdx.x == 0) {
-      int64_t k = -1;
-      const unsigned long long q = atomicAdd(&c.ctr[0], 1ull);
-      if (q < static_cast<unsigned long long>(c.L)) {
-        int32_t t = ld_relaxed_i32(c.queue + q);
-        if (t < 0) {
-          const uint64_t t0 = globaltimer();
-          for (;;) {
-            __nanosleep(200);
-            t = ld_relaxed_i32(c.queue + q);
-            if (t >= 0) break;
-            if (ld_volatile_i32(c.err) != 0) break;
-            if (globaltimer() - t0 > kUniWaitNs) {
-              latch(c.err, kErrUniformWait);
-              break;
-            }
-          }
-        }
-        k = t;
-      }
-      s_k = k;
-    }
+    if (threadIdx.x == 0) s_k = take_ticket(c);
     tm.sync();
     const int64_t k = s_k;
     if (k < 0) break;
     const int32_t u = c.tp[2 * k], v = c.tp[2 * k + 1];
-    const int64_t E = (c.rp[u + 1] - c.rp[u]) + (c.rp[v + 1] - c.rp[v]);
-    if (!uni_trade(tm, c, k, E <= kUniSmemElems ? ws_smem : ws_glob, hist, s_sel, &s_abort)) {
+    const int64_t du = c.rp[u + 1] - c.rp[u];
+    const int64_t E = du + (c.rp[v + 1] - c.rp[v]);
+    bool ok;
+    if (E <= kUniSmemElems) {
+      ok = uni_trade(tm, c, k, ws_smem, hash_bits(2 * du), hist, s_sel, &s_abort);
+    } else if (du <= kHash16MaxDu) {
+      TradeWs<uint16_t> w16{ws_glob.ent, ws_glob.key, reinterpret_cast<uint16_t*>(usm), ws_glob.flag};
+      ok = uni_trade(tm, c, k, w16, hash_bits((4 * du + 2) / 3), hist, s_sel, &s_abort);
+    } else {
+      ok = uni_trade(tm, c, k, ws_glob, hash_bits(2 * du), hist, s_sel, &s_abort);
+    }
+    if (!ok) {
       if (threadIdx.x == 0) latch(c.err, kErrUniformWait);
       break;
     }
@@ -592,7 +629,13 @@ __global__ void __launch_bounds__(kUniThreads, 4) k_uni_exec(UniCtx c) {
 }
 
 // Every output row full.
-__global__ void k_uni_check(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ocur, int32_t* err) {
+// Every output row full, and every trade queued and taken exactly once.
+__global__ void k_uni_check(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ocur,
+                            const unsigned long long* __restrict__ ctr, int64_t L, int32_t* err) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long l = static_cast<unsigned long long>(L);
+    if (ctr[kTail] != l) latch(err, kErrUniform);
+  }
   for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x)
     if (ocur[x] != rp[x + 1] - rp[x]) latch(err, kErrRowLength);
 }
@@ -627,7 +670,7 @@ int uni_buffers(Graph* h, int64_t L) {
   if (grow(h, &b->tp, 2 * L, by) || grow(h, &b->dslot, 2 * L, by) || grow(h, &b->ib, 2 * L + 1, by) ||
       grow(h, &b->suc, 2 * L, by) || grow(h, &b->nxt, 2 * L, by) || grow(h, &b->fill, L, by) ||
       grow(h, &b->queue, L, by) || grow(h, &b->occ, n, by) || grow(h, &b->sbeg, n + 1, by) ||
-      grow(h, &b->ocur, n, by) || grow(h, &b->ctr, 2, by))
+      grow(h, &b->ocur, n, by) || grow(h, &b->ctr, kCtrWords, by))
     return fail(h, CB_ENOMEM, "device allocation failed (uniform trades)");
   const size_t ws = std::max(scan_ws_bytes(n), scan_ws_bytes(2 * L));
   void* q = nullptr;
@@ -663,6 +706,7 @@ int uniform_trades(Graph* h, uint64_t count) {
     return CB_OK;
   }
   cudaStream_t s = h->stream;
+  const int64_t launches0 = h->launches;
   const int64_t chunk = std::max<int64_t>(n / 2, kUniChunkMin);
   int rc;
   if ((rc = uni_buffers(h, std::min<int64_t>(chunk, static_cast<int64_t>(std::min<uint64_t>(count, 1ull << 40))))))
@@ -734,7 +778,7 @@ int uniform_trades(Graph* h, uint64_t count) {
     if (total) CB_CUDA(h, cudaMemsetAsync(b->inbox, 0xff, sizeof(int2) * static_cast<size_t>(total), s));
     CB_CUDA(h, cudaMemsetAsync(b->fill, 0, sizeof(unsigned long long) * L, s));
     CB_CUDA(h, cudaMemsetAsync(b->queue, 0xff, sizeof(int32_t) * L, s));
-    CB_CUDA(h, cudaMemsetAsync(b->ctr, 0, sizeof(unsigned long long) * 2, s));
+    CB_CUDA(h, cudaMemsetAsync(b->ctr, 0, sizeof(unsigned long long) * kCtrWords, s));
     CB_CUDA(h, cudaMemsetAsync(b->ocur, 0, sizeof(int32_t) * n, s));
     const int spare = 1 - h->cur;
     UniCtx c;
@@ -761,14 +805,15 @@ int uniform_trades(Graph* h, uint64_t count) {
     CB_CUDA(h, cudaGetLastError());
     k_uni_exec<<<ctas, kUniThreads, smem, s>>>(c);
     CB_CUDA(h, cudaGetLastError());
-    k_uni_check<<<g1, 256, 0, s>>>(n, c.rp, b->ocur, h->err);
+    k_uni_check<<<g1, 256, 0, s>>>(n, c.rp, b->ocur, b->ctr, L, h->err);
     CB_CUDA(h, cudaGetLastError());
-    h->launches += 9;
+    h->launches += 7;
     if ((rc = check_device_error(h))) return rc;
     std::swap(h->col[h->cur], h->col[spare]);
     done += static_cast<uint64_t>(L);
   }
   h->uni_next += count;
+  h->stats[5] = h->launches - launches0;
   // the recorded super steps name the old adjacency buffers; exports are stale
   drop_step_graphs(h);
   h->pairs_step = ~0ull;
