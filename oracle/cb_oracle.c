@@ -41,6 +41,10 @@
  *    id) is keyed by (r0<<32|r1) of Philox4x32-10 on counter
  *    (x, i_lo, i_hi, 6); sigma(D) is D sorted by (key, x).  The trades apply
  *    one after the other in index order.
+ *  - Swap counts (Appendix "Swaps performed by Curveball and Global
+ *    Curveball"): a trade performs as many neighbourhood swaps as edge ends
+ *    that change node (twice the pairs of neighbours exchanged; Fig. 2's
+ *    sigma exchanges four edges), out of deg(u) + deg(v) possible.
  *  - Relaxed global trade (Def. "Relaxed global trade", Appendix EM-GCB; the
  *    linear congruential maps of Section 4.3 and the Appendix "Linear
  *    congruential maps"), when switched on: super step g draws
@@ -101,6 +105,8 @@ typedef struct {
   int64_t maxdeg;
   int relaxed;             /* 1: permutations from linear congruential maps */
   uint64_t uni;            /* index of the next uniform single trade */
+  int64_t swaps_done;      /* edge ends that changed node in a trade (2 per exchanged pair) */
+  int64_t swaps_all;       /* deg(u) + deg(v) summed over the trades */
   /* per-trade scratch */
   void* scratch;
 } or_state;
@@ -342,8 +348,10 @@ static void apply_sigma(or_state* h, int64_t u, int64_t v, elem* sig, int64_t nd
     if (h->end[2 * (int64_t)y->e] == v) h->end[2 * (int64_t)y->e] = (int32_t)u; else h->end[2 * (int64_t)y->e + 1] = (int32_t)u;
     h->inc[x->slot] = y->e;   /* slot in u's list now holds the edge arriving at u */
     h->inc[y->slot] = x->e;   /* slot in v's list now holds the edge arriving at v */
+    h->swaps_done += 2;
     p++; q++;
   }
+  h->swaps_all += (h->row_ptr[u + 1] - h->row_ptr[u]) + (h->row_ptr[v + 1] - h->row_ptr[v]);
 }
 
 /* One trade of the global trade: sigma drawn from the edge keys of step g. */
@@ -468,6 +476,14 @@ int or_uniform_trades(void* hp, uint64_t count) {
 
 uint64_t or_uniform_next(void* hp) { return ((or_state*)hp)->uni; }
 void or_set_uniform_next(void* hp, uint64_t i) { ((or_state*)hp)->uni = i; }
+
+/* Swap counts since creation or the last reset (see the header). */
+void or_swap_counts(void* hp, int64_t* performed, int64_t* possible, int reset) {
+  or_state* h = (or_state*)hp;
+  *performed = h->swaps_done;
+  *possible = h->swaps_all;
+  if (reset) { h->swaps_done = 0; h->swaps_all = 0; }
+}
 
 /*
  * Successor lists of a trade sequence (Section 4.1): for each node x the

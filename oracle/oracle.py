@@ -45,6 +45,7 @@ def _load():
         lib.or_uniform_next.restype = u64
         lib.or_uniform_next.argtypes = [vp]
         lib.or_set_uniform_next.argtypes = [vp, u64]
+        lib.or_swap_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.c_int]
         lib.or_successors.restype = C.c_int
         lib.or_successors.argtypes = [i64, vp, i64, vp, vp]
         lib.or_lcg_params.argtypes = [vp, u64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
@@ -176,6 +177,13 @@ class Oracle:
         rc = _load().or_uniform_trades(self._h, C.c_uint64(count))
         if rc:
             raise RuntimeError(f"oracle uniform trades failed (code {rc})")
+
+    def swap_counts(self, reset: bool = False):
+        """(performed, possible) neighbourhood swaps since creation or the last
+        reset: edge ends that changed node, and deg(u) + deg(v) per trade."""
+        a, b = C.c_int64(0), C.c_int64(0)
+        _load().or_swap_counts(self._h, C.byref(a), C.byref(b), 1 if reset else 0)
+        return a.value, b.value
 
     @property
     def uniform_next(self) -> int:
