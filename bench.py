@@ -535,6 +535,9 @@ def run_uniform(args):
         t_max = float(tt.item())
     K = args.steps
     value = world * g.m * K / (t_max / 1e3)
+    c.set_option("swap_stats", 1)   # one more, untimed step for the swap fraction
+    c.uniform_trades(half)
+    sw_done, sw_all = c.swap_counts()
     # end to end through the C ABI with host buffers
     rp_h = torch.from_numpy(g.row_ptr).pin_memory()
     col_h = torch.from_numpy(g.col).pin_memory()
@@ -571,6 +574,8 @@ def run_uniform(args):
                 "h2d_bytes_per_step": (g.row_ptr.nbytes + g.col.nbytes) / K, "d2h_bytes_per_step": 2 * g.m * 4 / K},
         "gpu_launches": launches,
         "clocks": clk,
+        "swap_fraction": {"performed": sw_done, "possible": sw_all,
+                          "fraction": sw_done / sw_all if sw_all else None, "of": "n/2 uniform single trades"},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -621,6 +626,11 @@ def run_ours(args):
     t_ms = e0.elapsed_time(e1)
     stats = c.stats()
     phases = c.timings()
+    # swap fraction of one more (untimed) super step (Appendix "Swaps performed
+    # by Curveball and Global Curveball")
+    c.set_option("swap_stats", 1)
+    c.global_trades(1)
+    sw_done, sw_all = c.swap_counts()
     t_max = t_ms
     if world > 1:
         import torch.distributed as dist
@@ -693,6 +703,8 @@ def run_ours(args):
         "phase_ms_per_step": {"permutation": phases["permutation_ms"] / K, "threshold": phase_ms["threshold"],
                               "rebuild": phase_ms["rebuild"], "step": phases["step_ms"] / K},
         "dependency_passes_last_step": stats.get("passes"),
+        "swap_fraction": {"performed": sw_done, "possible": sw_all,
+                          "fraction": sw_done / sw_all if sw_all else None, "of": "one global trade"},
     }
     if batched is not None:
         line["batched"] = batched

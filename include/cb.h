@@ -227,8 +227,26 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               larger buckets take the global-memory fallback; 2..4096.
  *   "timing"    1: record CUDA events around the phases of each super step
  *               (adds one stream synchronisation per super step) [0].
+ *   "swap_stats" 1: count neighbourhood swaps (see cb_swap_counts) from zero
+ *               in every later super step and uniform trade; super steps
+ *               then run without the recorded CUDA graphs, plus one counting
+ *               kernel each.  0: stop counting [0].  Handles of one graph
+ *               only (CB_EINVAL for cb_create_batch).
  */
 int cb_set_option(cb_handle h, const char* key, int64_t value);
+
+/*
+ * Swap counts since "swap_stats" was last set to 1 (Appendix "Swaps
+ * performed by Curveball and Global Curveball").
+ *   - A trade of u and v performs as many neighbourhood swaps as edge ends
+ *     that change node: twice the pairs of disjoint neighbours it exchanges.
+ *     Fig. 2's sigma exchanges four edges.
+ *   - deg(u) + deg(v) swaps are possible.
+ *   - For odd n the untraded node of a global trade counts in neither.
+ * *performed / *possible is the fraction the appendix plots.  Both are 0
+ * when counting was never on.  Synchronises the handle's stream.
+ */
+int cb_swap_counts(cb_handle h, int64_t* performed, int64_t* possible);
 
 /*
  * The permutation of super step g for n nodes and `seed` (the same order as

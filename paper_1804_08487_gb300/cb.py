@@ -104,6 +104,8 @@ def load():
     lib.cb_server_stats.argtypes = [vp, C.POINTER(i64), i32]
     lib.cb_server_destroy.restype = None
     lib.cb_server_destroy.argtypes = [vp]
+    lib.cb_swap_counts.restype = i32
+    lib.cb_swap_counts.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     lib.cb_uniform_trades.restype = i32
     lib.cb_uniform_trades.argtypes = [vp, u64]
     lib.cb_uniform_next.restype = i32
@@ -272,6 +274,13 @@ def _stream(stream):
     return None if stream is None else C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
 
 
+def cb_swap_counts(h):
+    """(performed, possible) neighbourhood swaps since "swap_stats" was set."""
+    a, b = C.c_int64(0), C.c_int64(0)
+    _check(load().cb_swap_counts(h, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
+
+
 def cb_uniform_trades(h, count: int):
     """Apply the handle's next `count` uniform single trades (Section 3.2)."""
     return _check(load().cb_uniform_trades(h, C.c_uint64(count)), h)
@@ -358,6 +367,9 @@ class Curveball:
 
     def uniform_trades(self, count: int = 1):
         cb_uniform_trades(self.h, count)
+
+    def swap_counts(self):
+        return cb_swap_counts(self.h)
 
     @property
     def uniform_next(self) -> int:

@@ -69,7 +69,7 @@ void release(Graph* h) {
                   h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
                   h->counters, h->err,
                   h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs, h->far_pack,
-                  h->lcg_ab, h->lcg_gaps};
+                  h->lcg_ab, h->lcg_gaps, h->swaps};
   if (h->stream)
     for (void* b : bufs) dfree(h, b);
   for (auto& x : h->step_exec)
@@ -638,7 +638,7 @@ int cb_global_trades(cb_handle h, uint32_t supersteps) {
   if (h->g + supersteps >= 0xfffffffeull) return fail(h, CB_ERANGE, "super-step counter would pass 2^32-2");
   const int64_t launches0 = h->launches;
   for (double& v : h->phase_ms) v = 0;
-  if (h->use_graph && !h->timing && supersteps > 0) {
+  if (h->use_graph && !h->timing && !h->swap_stats && supersteps > 0) {
     if (!h->step_exec[0]) {
       const int rc = capture_step_graphs(h);
       if (rc) return rc;
@@ -651,7 +651,8 @@ int cb_global_trades(cb_handle h, uint32_t supersteps) {
     }
   } else {
     for (uint32_t i = 0; i < supersteps; ++i) {
-      const int rc = super_step(h);
+      int rc = super_step(h);
+      if (!rc && h->swap_stats) rc = count_swaps(h);
       if (rc) return rc;
     }
   }
@@ -838,6 +839,10 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!std::strcmp(key, "relaxed")) {
     if (value < 0 || value > 1) return fail(h, CB_EINVAL, "relaxed is 0 or 1");
     return set_relaxed(h, value != 0);
+  }
+  if (!std::strcmp(key, "swap_stats")) {
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "swap_stats is 0 or 1");
+    return set_swap_stats(h, value != 0);
   }
   if (!std::strcmp(key, "wide_pack")) {
     if (value < 0 || value > 1) return fail(h, CB_EINVAL, "wide_pack is 0 or 1");

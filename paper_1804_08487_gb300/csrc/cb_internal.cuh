@@ -122,6 +122,9 @@ struct Graph {
   // uniform single trades (uniform.cu)
   UniBufs* uni = nullptr;
   uint64_t uni_next = 0;        // index of the next uniform trade
+  // swap counts (swaps.cu): device pair (performed, possible), when on
+  bool swap_stats = false;
+  int64_t* swaps = nullptr;
 
   // stats of the last cb_global_trades
   int64_t stats[8] = {0};
@@ -192,6 +195,10 @@ cudaError_t dev_alloc(Graph* h, void** p, size_t bytes);
 int check_device_error(Graph* h);
 // forget the recorded super-step graphs (they are recorded again when next needed)
 void drop_step_graphs(Graph* h);
+
+// swaps.cu
+int count_swaps(Graph* h);                 // add the last super step's counts
+int set_swap_stats(Graph* h, bool on);     // on: counts from zero
 
 // uniform.cu
 int uniform_trades(Graph* h, uint64_t count);

@@ -201,6 +201,7 @@ struct UniCtx {
   int32_t* err;
   char* gslice;
   int64_t slice_elems;
+  unsigned long long* swaps;   // (performed, possible) swap counts, or null
 };
 
 // The run queue: a ticket (kHead) takes the next slot, a push (kTail)
@@ -540,6 +541,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
     }
   }
   // decision: below the threshold's bucket to u, above to v, within it by rank
+  int moved = 0;
 #pragma unroll 2
   for (int e = tm.rank; e < E; e += kUniThreads) {
     const uint8_t f = w.flag[e];
@@ -556,6 +558,11 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
       }
     }
     if (to_u) w.flag[e] = f | 8;
+    moved += to_u == ((f & 1) != 0);   // an edge end that changes node
+  }
+  if (c.swaps) {
+    if (moved) atomicAdd(&c.swaps[0], static_cast<unsigned long long>(moved));
+    if (tm.rank == 0) atomicAdd(&c.swaps[1], static_cast<unsigned long long>(E));
   }
   tm.sync();
   // 6. every resulting edge goes on: common neighbours and the edge {u, v}
@@ -801,6 +808,7 @@ int uniform_trades(Graph* h, uint64_t count) {
     c.err = h->err;
     c.gslice = b->gslice;
     c.slice_elems = b->slice_elems;
+    c.swaps = h->swap_stats ? reinterpret_cast<unsigned long long*>(h->swaps) : nullptr;
     k_uni_route<<<grid_for_work(n * 32, h->num_sms), 256, 0, s>>>(c, n, h->col[h->cur]);
     CB_CUDA(h, cudaGetLastError());
     k_uni_exec<<<ctas, kUniThreads, smem, s>>>(c);

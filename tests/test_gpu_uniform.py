@@ -160,3 +160,38 @@ def exact_edges(g):
     rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
     keep = rows < g.col
     return np.stack([rows[keep], g.col[keep]], axis=1)
+
+
+@pytest.mark.parametrize("n,a,b,seed", [(3001, 3, 300, 41), (2000, 10, 11, 42), (5001, 2, 2500, 43)])
+def test_swap_counts_match_oracle(n, a, b, seed):
+    """Swap counts (Appendix "Swaps performed by Curveball and Global
+    Curveball") of global super steps and of uniform trades equal the
+    oracle's exactly."""
+    g = synth.powerlaw_graph(n, a, b, 2.0, seed)
+    c = Curveball(g.row_ptr, g.col, seed)
+    o = Oracle(g.row_ptr, g.col, seed)
+    c.global_trades(1)
+    o.superstep(1)
+    c.set_option("swap_stats", 1)
+    o.swap_counts(reset=True)
+    c.global_trades(2)
+    o.superstep(2)
+    assert c.swap_counts() == o.swap_counts()
+    c.uniform_trades(n)
+    o.uniform_trades(n)
+    assert c.swap_counts() == o.swap_counts()
+    assert np.array_equal(c.edges(), o.edges())
+    c.set_option("swap_stats", 1)   # from zero again
+    c.global_trades(1)
+    o.swap_counts(reset=True)
+    o.superstep(1)
+    performed, possible = c.swap_counts()
+    assert (performed, possible) == o.swap_counts() and 0 < performed <= possible
+
+
+def test_swap_counts_refuse_batches():
+    g1 = exact.to_csr(frozenset({(0, 1)}), 3)
+    ens = Ensemble([g1, g1], [1, 2])
+    with pytest.raises(CbError) as e:
+        ens.set_option("swap_stats", 1)
+    assert e.value.code == CB_EINVAL
