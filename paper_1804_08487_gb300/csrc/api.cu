@@ -274,7 +274,7 @@ int finish_create(Graph* h) {
     if ((rc = permute_rows(h, n, h->rp_id, h->col[0], nullptr, nullptr, h->rp_id, h->col[1]))) return rc;
     idcol = h->col[1];
   }
-  if ((rc = validate_sorted_graph(h, h->rp_id, idcol, n))) return rc;
+  if ((rc = validate_sorted_graph(h, h->rp_id, idcol, n, idcol == h->col[0] ? h->col[1] : h->col[0]))) return rc;
   if ((rc = check_device_error(h))) {
     h->last_error = "graph is not simple and symmetric";
     return CB_EINVAL;
@@ -342,12 +342,7 @@ int ensure_pairs(Graph* h) {
   if (!h->pairs && dalloc(h, &h->pairs, 2 * std::max<int64_t>(h->m, 1)))
     return fail(h, CB_ENOMEM, "device allocation failed");
   int rc;
-  const int spare = 1 - h->cur;
-  if ((rc = invert_permutation(h, h->order[h->cur], h->pos_next))) return rc;
-  if ((rc = permute_rows(h, h->n, h->rp[h->cur], h->col[h->cur], h->pos_next, h->order[h->cur], h->rp_id,
-                         h->col[spare])))
-    return rc;
-  if ((rc = export_pairs(h, h->rp_id, h->col[spare], h->pairs))) return rc;
+  if ((rc = export_sorted_pairs(h, h->pairs))) return rc;
   if ((rc = check_device_error(h))) return rc;
   h->pairs_step = h->g;
   return CB_OK;
@@ -713,16 +708,11 @@ int cb_export_edges(cb_handle h, int32_t* edges, int64_t capacity_pairs, int64_t
     if ((rc = ensure_pairs(h))) return rc;
     return copy_pairs(h, 0, h->m, edges, mem_kind);
   }
-  const int spare = 1 - h->cur;
-  if ((rc = invert_permutation(h, h->order[h->cur], h->pos_next))) return rc;
-  if ((rc = permute_rows(h, h->n, h->rp[h->cur], h->col[h->cur], h->pos_next, h->order[h->cur], h->rp_id,
-                         h->col[spare])))
-    return rc;
   int32_t* pairs = edges;
   if (mem_kind == CB_HOST) {
     CB_CUDA(h, dmalloc(h, reinterpret_cast<void**>(&pairs), sizeof(int32_t) * 2 * std::max<int64_t>(h->m, 1)));
   }
-  rc = export_pairs(h, h->rp_id, h->col[spare], pairs);
+  rc = export_sorted_pairs(h, pairs);
   if (!rc && mem_kind == CB_HOST && h->m)
     rc = cudaMemcpyAsync(edges, pairs, sizeof(int32_t) * 2 * h->m, cudaMemcpyDeviceToHost, h->stream)
              ? fail(h, CB_ECUDA, "copy to host failed") : CB_OK;

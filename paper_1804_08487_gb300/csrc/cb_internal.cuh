@@ -173,7 +173,9 @@ int prepare_next(Graph* h);
 // dst row q <- src row rowmap[q] with values mapped through valmap (identity if null), ascending
 int permute_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* src_col,
                  const int32_t* rowmap, const int32_t* valmap, const int64_t* dst_rp, int32_t* dst_col);
-int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n);   // synchronises
+// simple and symmetric, or kErrValidate latched; `grouped` is scratch of
+// row_ptr[n] int32 (not synchronising)
+int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n, int32_t* grouped);
 // *sorted = every row strictly increasing (synchronises)
 int rows_sorted(Graph* h, const int64_t* rp, const int32_t* col, int64_t n, bool* sorted);
 // like permute_rows without sorting (rows keep their order)
@@ -181,7 +183,9 @@ int relabel_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* 
                  const int32_t* valmap, const int64_t* dst_rp, int32_t* dst_col);
 int check_row_offsets(Graph* h, const int64_t* rp, int64_t n);
 int invert_permutation(Graph* h, const int32_t* order, int32_t* pos);
-int export_pairs(Graph* h, const int64_t* rp, const int32_t* col, int32_t* pairs);
+// canonical pairs (x < y, sorted, local ids) of the current step into `pairs`
+// (2m int32, device); uses the spare adjacency buffer
+int export_sorted_pairs(Graph* h, int32_t* pairs);
 
 // trade.cu
 int super_step(Graph* h);

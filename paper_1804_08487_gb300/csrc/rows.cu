@@ -10,8 +10,6 @@
 namespace cb {
 namespace {
 
-const int32_t kErrValidateHost = kErrValidate;
-
 constexpr int kRowWarpMax = 256;     // rows up to this length: one warp
 constexpr int kRowBlockSmem = 16384; // rows up to this length: one CTA in shared memory
 
@@ -84,40 +82,61 @@ __global__ void k_check_rp(int64_t n, const int64_t* __restrict__ rp, int32_t* e
   }
 }
 
-// Rows sorted: strictly increasing, in range, no self loop, and symmetric.
-// Symmetry with half the searches: every entry y > x must find x in row y;
-// those mirrors are distinct entries below the diagonal, so the graph is
-// symmetric exactly when, in addition, there are as many entries below the
-// diagonal as above (counted into ud[0] and ud[1]).
-__global__ void k_validate(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                           int32_t* err, unsigned long long* ud) {
+// Validation of sorted rows: strictly increasing, in range, no self loop,
+// and symmetric.  Symmetry is checked exactly by grouping: every entry y > x
+// of row x is placed in a group of row y, sized by the entries of row y below
+// the diagonal (L_y).  The graph is symmetric exactly when every group is
+// full and each member x is in L_y: the members are distinct (rows are
+// strictly increasing), so a full group of members of L_y is L_y.  The checks
+// of a group all search the same row, which stays in cache.
+
+// low[x] = entries of row x below x (a lower bound in the sorted row)
+__global__ void k_lower_count(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              int32_t* __restrict__ low) {
+  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x)
+    low[x] = lower_bound(col + rp[x], static_cast<int>(rp[x + 1] - rp[x]), static_cast<int32_t>(x));
+}
+
+// Row checks, and every entry y > x of row x into row y's group
+__global__ void k_sym_scatter(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const int32_t* __restrict__ low, const int64_t* __restrict__ grp,
+                              int32_t* __restrict__ cursor, int32_t* __restrict__ grouped, int32_t* err) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
-  unsigned long long up = 0, down = 0;
   for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < n; x += nw) {
     const int64_t b = rp[x], e = rp[x + 1];
     for (int64_t i = b + lane; i < e; i += 32) {
       const int32_t y = col[i];
       bool bad = y < 0 || y >= n || y == x || (i > b && col[i - 1] >= y);
       if (!bad && y > x) {
-        ++up;
-        const int64_t yb = rp[y], ye = rp[y + 1];
-        const int k = lower_bound(col + yb, static_cast<int>(ye - yb), static_cast<int32_t>(x));
-        bad = (yb + k >= ye) || col[yb + k] != x;
-      } else if (!bad) {
-        ++down;
+        const int32_t slot = atomicAdd(&cursor[y], 1);
+        if (slot < low[y]) grouped[grp[y] + slot] = static_cast<int32_t>(x);
+        else bad = true;   // more entries point down into row y than it has below its diagonal
       }
       if (bad) latch(err, kErrValidate);
     }
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    up += __shfl_xor_sync(kFull, up, o);
-    down += __shfl_xor_sync(kFull, down, o);
-  }
-  if (lane == 0) {
-    if (up) atomicAdd(&ud[0], up);
-    if (down) atomicAdd(&ud[1], down);
+}
+
+// Every group full, and each member x in L_y (binary search in row y)
+__global__ void k_sym_check(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ low, const int64_t* __restrict__ grp,
+                            const int32_t* __restrict__ cursor, const int32_t* __restrict__ grouped, int32_t* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t y = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; y < n; y += nw) {
+    const int ly = low[y];
+    if (cursor[y] != ly) {
+      if (lane == 0) latch(err, kErrValidate);
+      continue;
+    }
+    const int32_t* row = col + rp[y];
+    const int32_t* g = grouped + grp[y];
+    for (int j = lane; j < ly; j += 32) {
+      const int32_t x = g[j];
+      const int k = lower_bound(row, ly, x);
+      if (k >= ly || row[k] != x) latch(err, kErrValidate);
+    }
   }
 }
 
@@ -158,30 +177,84 @@ __global__ void k_invert(int64_t n, const int32_t* __restrict__ order, int32_t* 
     pos[order[p]] = static_cast<int32_t>(p);
 }
 
-// entries of row x greater than x (rows sorted ascending)
-__global__ void k_count_upper(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              int32_t* __restrict__ cnt) {
-  for (int64_t x = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; x < n; x += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t b = rp[x], len = rp[x + 1] - b;
-    const int k = lower_bound(col + b, static_cast<int>(len), static_cast<int32_t>(x + 1));
-    cnt[x] = static_cast<int32_t>(len - k);
-  }
-}
+// ---- canonical export: only the entries above the diagonal are sorted
 
-// Pairs (x, y) with x < y, ids local to x's graph (both ends share it).
-__global__ void k_write_pairs(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              const int32_t* __restrict__ cnt, const int64_t* __restrict__ off,
-                              const Seg* __restrict__ segs, const int32_t* __restrict__ seg_of,
-                              int32_t* __restrict__ pairs) {
+// cnt[x] = entries of (unsorted) row x greater than x
+__global__ void k_count_above(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              int32_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < n; x += nw) {
-    const int64_t e = rp[x + 1], c = cnt[x], b = e - c, o = off[x];
-    const int32_t base = seg_of ? static_cast<int32_t>(segs[seg_of[x]].off) : 0;
-    for (int64_t i = lane; i < c; i += 32) {
-      pairs[2 * (o + i)] = static_cast<int32_t>(x) - base;
-      pairs[2 * (o + i) + 1] = col[b + i] - base;
-    }
+    int c = 0;
+    for (int64_t i = rp[x] + lane; i < rp[x + 1]; i += 32) c += col[i] > x;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if (lane == 0) cnt[x] = c;
+  }
+}
+
+struct AboveArgs {
+  int64_t n;
+  const int64_t* rp;
+  const int32_t* col;
+  const int32_t* cnt;
+  const int64_t* off;
+  const Seg* segs;
+  const int32_t* seg_of;
+  int32_t* pairs;
+  int32_t* err;
+};
+
+// Row x's entries above x, compacted into buf, sorted, written as pairs
+// (x, y) with ids local to x's graph.
+template <class Team>
+__device__ void sort_above(Team& tm, const AboveArgs& a, int64_t x, int32_t* buf) {
+  const int64_t b = a.rp[x], len = a.rp[x + 1] - b;
+  const int c = a.cnt[x];
+  const int P = next_pow2(c > 1 ? c : 1);
+  int64_t base = 0;
+  for (int64_t r0 = 0; r0 < len; r0 += Team::N) {
+    const int64_t i = r0 + tm.rank;
+    const int32_t v = i < len ? a.col[b + i] : -1;
+    const bool up = v > x;
+    const int64_t pos = tm.exscan(up ? 1 : 0);
+    if (up && base + pos < c) buf[base + pos] = v;
+    base += tm.sum(up ? 1 : 0);
+  }
+  if (base != c && tm.rank == 0) latch(a.err, kErrRowLength);
+  for (int i = c + tm.rank; i < P; i += Team::N) buf[i] = 0x7fffffff;
+  tm.sync();
+  team_bitonic_sort(tm, buf, P);
+  const int32_t sb = a.seg_of ? static_cast<int32_t>(a.segs[a.seg_of[x]].off) : 0;
+  const int64_t o = a.off[x];
+  for (int i = tm.rank; i < c; i += Team::N) {
+    a.pairs[2 * (o + i)] = static_cast<int32_t>(x) - sb;
+    a.pairs[2 * (o + i) + 1] = buf[i] - sb;
+  }
+  tm.sync();
+}
+
+// rows with at most kRowWarpMax entries above the diagonal: one warp each
+__global__ void __launch_bounds__(256) k_above_warp(AboveArgs a) {
+  __shared__ int32_t buf[8][kRowWarpMax];
+  WarpTeam tm;
+  const int w = threadIdx.x >> 5;
+  const int64_t nw = int64_t(gridDim.x) * 8;
+  for (int64_t x = blockIdx.x * int64_t(8) + w; x < a.n; x += nw)
+    if (a.cnt[x] <= kRowWarpMax) sort_above(tm, a, x, buf[w]);
+}
+
+// rows with lo < entries above the diagonal <= hi: one CTA each, in `cap`
+// ints of shared memory or, above that, a global slice per CTA
+__global__ void __launch_bounds__(256) k_above_block(AboveArgs a, int lo, int64_t hi, int cap, int32_t* gws,
+                                                     int64_t slice) {
+  extern __shared__ int32_t sbuf[];
+  __shared__ int64_t red[BlockTeam<256>::kRedSlots];
+  BlockTeam<256> tm(red);
+  for (int64_t x = blockIdx.x; x < a.n; x += gridDim.x) {
+    const int c = a.cnt[x];
+    if (c <= lo || c > hi) continue;
+    sort_above(tm, a, x, c <= cap ? sbuf : gws + slice * blockIdx.x);
   }
 }
 
@@ -222,19 +295,24 @@ int permute_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* 
   return CB_OK;
 }
 
-int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n) {
+int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n, int32_t* grouped) {
   if (n == 0) return CB_OK;
-  unsigned long long* ud = reinterpret_cast<unsigned long long*>(h->counters) + 6;
-  CB_CUDA(h, cudaMemsetAsync(ud, 0, 2 * sizeof(unsigned long long), h->stream));
-  k_validate<<<grid_of(n * 32, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, h->err, ud);
+  // scratch: low and cursors in step buffers of n int32, group offsets in
+  // rp[1] (n+1 int64); none is in use before the first super step
+  int32_t* low = h->M;
+  int32_t* cursor = h->deg_next;
+  int64_t* grp = h->rp[1];
+  cudaStream_t s = h->stream;
+  k_lower_count<<<grid_of(n, 256, h->num_sms), 256, 0, s>>>(n, rp, col, low);
   CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-  unsigned long long hud[2] = {0, 0};
-  CB_CUDA(h, cudaMemcpyAsync(hud, ud, sizeof(hud), cudaMemcpyDeviceToHost, h->stream));
-  CB_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (hud[0] != hud[1]) {
-    CB_CUDA(h, cudaMemcpyAsync(h->err, &kErrValidateHost, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
-  }
+  CB_CUDA(h, exclusive_scan_i32(low, grp, n, h->scan_ws, s, &h->launches));
+  CB_CUDA(h, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, s));
+  const unsigned wgrid = grid_of(n * 32, 256, h->num_sms);
+  k_sym_scatter<<<wgrid, 256, 0, s>>>(n, rp, col, low, grp, cursor, grouped, h->err);
+  CB_CUDA(h, cudaGetLastError());
+  k_sym_check<<<wgrid, 256, 0, s>>>(n, rp, col, low, grp, cursor, grouped, h->err);
+  CB_CUDA(h, cudaGetLastError());
+  h->launches += 3;
   return CB_OK;
 }
 
@@ -279,19 +357,51 @@ int invert_permutation(Graph* h, const int32_t* order, int32_t* pos) {
   return CB_OK;
 }
 
-int export_pairs(Graph* h, const int64_t* rp, const int32_t* col, int32_t* pairs) {
+// Canonical pairs of the current step: id-space rows (unsorted), the count
+// above the diagonal per row, and each row's upper part sorted into place.
+int export_sorted_pairs(Graph* h, int32_t* pairs) {
   const int64_t n = h->n;
   if (n == 0) return CB_OK;
+  int rc;
+  const int spare = 1 - h->cur;
+  if ((rc = invert_permutation(h, h->order[h->cur], h->pos_next))) return rc;
+  if ((rc = relabel_rows(h, n, h->rp[h->cur], h->col[h->cur], h->pos_next, h->order[h->cur], h->rp_id,
+                         h->col[spare])))
+    return rc;
   int32_t* cnt = h->deg_next;      // free between super steps
-  int64_t* off = h->rp[1 - h->cur];
-  k_count_upper<<<grid_of(n, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, cnt);
+  int64_t* off = h->rp[spare];
+  cudaStream_t s = h->stream;
+  const unsigned wgrid = grid_of(n * 32, 256, h->num_sms);
+  k_count_above<<<wgrid, 256, 0, s>>>(n, h->rp_id, h->col[spare], cnt);
   CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-  CB_CUDA(h, exclusive_scan_i32(cnt, off, n, h->scan_ws, h->stream, &h->launches));
-  k_write_pairs<<<grid_of(n * 32, 256, h->num_sms), 256, 0, h->stream>>>(n, rp, col, cnt, off, h->segs, h->seg_of,
-                                                                           pairs);
+  CB_CUDA(h, exclusive_scan_i32(cnt, off, n, h->scan_ws, s, &h->launches));
+  AboveArgs a{n, h->rp_id, h->col[spare], cnt, off, h->segs, h->seg_of, pairs, h->err};
+  k_above_warp<<<grid_of(n, 8, h->num_sms), 256, 0, s>>>(a);
   CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
+  h->launches += 2;
+  if (h->maxdeg > kRowWarpMax) {
+    constexpr int kMid = 2048;
+    k_above_block<<<h->num_sms * 8, 256, kMid * 4, s>>>(a, kRowWarpMax, kMid, kMid, nullptr, 0);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    if (h->maxdeg > kMid) {
+      int64_t slice = 0;
+      int ctas = h->num_sms * 2;
+      int32_t* gws = nullptr;
+      if (h->maxdeg > kRowBlockSmem) {
+        slice = next_pow2_host(h->maxdeg);
+        const size_t budget = h->ws_slice * static_cast<size_t>(h->ws_ctas);
+        if (budget < static_cast<size_t>(slice) * 4) return fail(h, CB_ENOMEM, "row workspace too small");
+        ctas = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ctas, budget / (slice * 4))));
+        gws = static_cast<int32_t*>(h->ws_global);
+      }
+      CB_CUDA(h, cudaFuncSetAttribute(k_above_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kRowBlockSmem * 4));
+      k_above_block<<<ctas, 256, kRowBlockSmem * 4, s>>>(a, kMid, INT64_MAX, kRowBlockSmem, gws, slice);
+      CB_CUDA(h, cudaGetLastError());
+      ++h->launches;
+    }
+  }
   return CB_OK;
 }
 

@@ -229,6 +229,33 @@ def test_rejects_invalid_graphs():
     assert e.value.code == CB_EINVAL
 
 
+def test_rejects_single_asymmetric_entry_in_large_graphs():
+    """One entry of a valid graph moved to another neighbour id (row kept
+    sorted and simple) breaks symmetry, whether it lies above or below the
+    diagonal; validation must catch each one."""
+    g = synth.powerlaw_graph(20000, 3, 800, 2.0, 77)
+    rng = np.random.default_rng(5)
+    caught = 0
+    for _ in range(12):
+        col = g.col.copy()
+        x = int(rng.integers(g.n))
+        b, e = int(g.row_ptr[x]), int(g.row_ptr[x + 1])
+        if e == b:
+            continue
+        row = set(col[b:e].tolist())
+        i = int(rng.integers(b, e))
+        y = int(rng.integers(g.n))
+        while y == x or y in row:
+            y = int(rng.integers(g.n))
+        col[i] = y
+        col[b:e] = np.sort(col[b:e])
+        with pytest.raises(CbError) as err:
+            Curveball(g.row_ptr, col, 1)
+        assert err.value.code == CB_EINVAL
+        caught += 1
+    assert caught >= 8
+
+
 def test_export_capacity_checked():
     import ctypes
     from paper_1804_08487_gb300 import cb as cbmod
