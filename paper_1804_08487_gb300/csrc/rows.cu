@@ -83,12 +83,29 @@ __global__ void k_check_rp(int64_t n, const int64_t* __restrict__ rp, int32_t* e
 }
 
 // Validation of sorted rows: strictly increasing, in range, no self loop,
-// and symmetric.  Symmetry is checked exactly by grouping: every entry y > x
-// of row x is placed in a group of row y, sized by the entries of row y below
-// the diagonal (L_y).  The graph is symmetric exactly when every group is
-// full and each member x is in L_y: the members are distinct (rows are
-// strictly increasing), so a full group of members of L_y is L_y.  The checks
-// of a group all search the same row, which stays in cache.
+// and symmetric.  Symmetry is checked exactly:
+//   - every entry y > x of row x must be found among the entries of row y
+//     below the diagonal (L_y);
+//   - the entries above the diagonal, summed over all rows, must be as many
+//     as those below.
+// The found entries are distinct (rows are strictly increasing), so each L_y
+// holds at least as many as point into it, and the totals force equality.
+// For locality the upper entries are first partitioned into buckets of
+// target rows, with one reservation per bucket and CTA. Each bucket's
+// searches then stay within a few MB of rows that L2 holds.
+
+constexpr int kVBuckets = 4096;     // target-row buckets of the partition
+
+// Entry i of row x (rows [b, e)): its id if it lies above the diagonal and
+// the row is well formed up to it, -1 otherwise; *bad for a malformed entry.
+// Every pass of the partition uses this one predicate, so counts, space and
+// writes agree on any input.
+__device__ __forceinline__ int32_t upper_entry(const int32_t* __restrict__ col, int64_t b, int64_t i, int64_t x,
+                                               int64_t n, bool* bad) {
+  const int32_t y = col[i];
+  *bad = y < 0 || y >= n || y == x || (i > b && col[i - 1] >= y);
+  return (!*bad && y > x) ? y : -1;
+}
 
 // low[x] = entries of row x below x (a lower bound in the sorted row)
 __global__ void k_lower_count(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
@@ -97,47 +114,95 @@ __global__ void k_lower_count(int64_t n, const int64_t* __restrict__ rp, const i
     low[x] = lower_bound(col + rp[x], static_cast<int>(rp[x + 1] - rp[x]), static_cast<int32_t>(x));
 }
 
-// Row checks, and every entry y > x of row x into row y's group
-__global__ void k_sym_scatter(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              const int32_t* __restrict__ low, const int64_t* __restrict__ grp,
-                              int32_t* __restrict__ cursor, int32_t* __restrict__ grouped, int32_t* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < n; x += nw) {
+// Row checks and the partition: each CTA takes a contiguous range of rows,
+// counts its upper entries per bucket, reserves their space with one atomic
+// per bucket, and writes (x, y) into it.
+__global__ void __launch_bounds__(256) k_vpart(int64_t n, const int64_t* __restrict__ rp,
+                                               const int32_t* __restrict__ col, int sh,
+                                               unsigned long long* __restrict__ cursor, int2* __restrict__ part,
+                                               unsigned long long cap, int32_t* err) {
+  __shared__ int32_t cnt[kVBuckets];
+  __shared__ unsigned long long base[kVBuckets];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = blockIdx.x * per, r1 = r0 + per < n ? r0 + per : n;
+  for (int b = threadIdx.x; b < kVBuckets; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  for (int64_t x = r0 + w; x < r1; x += blockDim.x >> 5) {
     const int64_t b = rp[x], e = rp[x + 1];
     for (int64_t i = b + lane; i < e; i += 32) {
-      const int32_t y = col[i];
-      bool bad = y < 0 || y >= n || y == x || (i > b && col[i - 1] >= y);
-      if (!bad && y > x) {
-        const int32_t slot = atomicAdd(&cursor[y], 1);
-        if (slot < low[y]) grouped[grp[y] + slot] = static_cast<int32_t>(x);
-        else bad = true;   // more entries point down into row y than it has below its diagonal
-      }
+      bool bad;
+      const int32_t y = upper_entry(col, b, i, x, n, &bad);
       if (bad) latch(err, kErrValidate);
+      else if (y >= 0) atomicAdd(&cnt[y >> sh], 1);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kVBuckets; b += blockDim.x) {
+    base[b] = cnt[b] ? atomicAdd(&cursor[b], static_cast<unsigned long long>(cnt[b])) : 0;
+    cnt[b] = 0;
+  }
+  __syncthreads();
+  for (int64_t x = r0 + w; x < r1; x += blockDim.x >> 5) {
+    const int64_t b = rp[x], e = rp[x + 1];
+    for (int64_t i = b + lane; i < e; i += 32) {
+      bool bad;
+      const int32_t y = upper_entry(col, b, i, x, n, &bad);
+      if (y >= 0) {
+        const int k = y >> sh;
+        const unsigned long long slot = base[k] + static_cast<unsigned long long>(atomicAdd(&cnt[k], 1));
+        if (slot < cap) part[slot] = make_int2(static_cast<int32_t>(x), y);
+        else latch(err, kErrValidate);   // more entries above the diagonal than a symmetric graph has
+      }
     }
   }
 }
 
-// Every group full, and each member x in L_y (binary search in row y)
-__global__ void k_sym_check(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                            const int32_t* __restrict__ low, const int64_t* __restrict__ grp,
-                            const int32_t* __restrict__ cursor, const int32_t* __restrict__ grouped, int32_t* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t y = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; y < n; y += nw) {
-    const int ly = low[y];
-    if (cursor[y] != ly) {
-      if (lane == 0) latch(err, kErrValidate);
+// Every partitioned (x, y) found in L_y; and as many entries above the
+// diagonal as below (bucket space boff[nb] against the scan of low, grp[n]).
+__global__ void k_vcheck(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                         const int32_t* __restrict__ low, const int2* __restrict__ part,
+                         const int64_t* __restrict__ boff, int nb, const int64_t* __restrict__ grp, int64_t cap,
+                         int32_t* err) {
+  const int64_t all = boff[nb];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && all != grp[n]) latch(err, kErrValidate);
+  const int64_t total = all < cap ? all : cap;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int2 p = part[i];
+    if (p.x < 0 || p.y <= p.x || p.y >= n) {   // a slot no valid entry wrote (malformed input)
+      latch(err, kErrValidate);
       continue;
     }
-    const int32_t* row = col + rp[y];
-    const int32_t* g = grouped + grp[y];
-    for (int j = lane; j < ly; j += 32) {
-      const int32_t x = g[j];
-      const int k = lower_bound(row, ly, x);
-      if (k >= ly || row[k] != x) latch(err, kErrValidate);
-    }
+    const int32_t* row = col + rp[p.y];
+    const int ly = low[p.y];
+    const int k = lower_bound(row, ly, p.x);
+    if (k >= ly || row[k] != p.x) latch(err, kErrValidate);
   }
+}
+
+// bucket offsets from the scanned counts; the cursor starts at each offset
+__global__ void k_vcursor(int nb, const int64_t* __restrict__ boff, unsigned long long* __restrict__ cursor) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+    cursor[b] = static_cast<unsigned long long>(boff[b]);
+}
+
+// upper entries per bucket (row checks come with the partition)
+__global__ void __launch_bounds__(256) k_vcount(int64_t n, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, int sh, int32_t* __restrict__ hist) {
+  __shared__ int32_t cnt[kVBuckets];
+  for (int b = threadIdx.x; b < kVBuckets; b += blockDim.x) cnt[b] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t x = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; x < n; x += nw)
+    for (int64_t i = rp[x] + lane; i < rp[x + 1]; i += 32) {
+      bool bad;
+      const int32_t y = upper_entry(col, rp[x], i, x, n, &bad);
+      if (y >= 0) atomicAdd(&cnt[y >> sh], 1);
+    }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kVBuckets; b += blockDim.x)
+    if (cnt[b]) atomicAdd(&hist[b], cnt[b]);
 }
 
 // err <- kErrValidate unless every row is strictly increasing (sorted input).
@@ -297,23 +362,49 @@ int permute_rows(Graph* h, int64_t nrows, const int64_t* src_rp, const int32_t* 
 
 int validate_sorted_graph(Graph* h, const int64_t* rp, const int32_t* col, int64_t n, int32_t* grouped) {
   if (n == 0) return CB_OK;
-  // scratch: low and cursors in step buffers of n int32, group offsets in
-  // rp[1] (n+1 int64); none is in use before the first super step
-  int32_t* low = h->M;
-  int32_t* cursor = h->deg_next;
-  int64_t* grp = h->rp[1];
   cudaStream_t s = h->stream;
-  k_lower_count<<<grid_of(n, 256, h->num_sms), 256, 0, s>>>(n, rp, col, low);
-  CB_CUDA(h, cudaGetLastError());
-  CB_CUDA(h, exclusive_scan_i32(low, grp, n, h->scan_ws, s, &h->launches));
-  CB_CUDA(h, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n, s));
+  // scratch: low in a step buffer of n int32, its scan in rp[1] (n+1 int64),
+  // none in use before the first super step; the partition in `grouped`
+  int32_t* low = h->M;
+  int64_t* grp = h->rp[1];
+  int sh = 0;
+  while (((n - 1) >> sh) >= kVBuckets) ++sh;
+  const int nb = static_cast<int>(((n - 1) >> sh) + 1);
+  char* ws = nullptr;
+  const size_t ws_bytes = sizeof(int32_t) * kVBuckets + sizeof(int64_t) * (kVBuckets + 1) +
+                          sizeof(unsigned long long) * kVBuckets + scan_ws_bytes(kVBuckets) + 64;
+  CB_CUDA(h, dev_alloc(h, reinterpret_cast<void**>(&ws), ws_bytes));
+  int32_t* hist = reinterpret_cast<int32_t*>(ws);
+  int64_t* boff = reinterpret_cast<int64_t*>(ws + sizeof(int32_t) * kVBuckets);
+  unsigned long long* cursor =
+      reinterpret_cast<unsigned long long*>(ws + sizeof(int32_t) * kVBuckets + sizeof(int64_t) * (kVBuckets + 1));
+  void* scan = ws + ((sizeof(int32_t) * kVBuckets + sizeof(int64_t) * (kVBuckets + 1) +
+                      sizeof(unsigned long long) * kVBuckets + 15) & ~size_t(15));
+  int rc = CB_OK;
+  cudaError_t e = cudaSuccess;
+  const unsigned g = grid_of(n, 256, h->num_sms);
   const unsigned wgrid = grid_of(n * 32, 256, h->num_sms);
-  k_sym_scatter<<<wgrid, 256, 0, s>>>(n, rp, col, low, grp, cursor, grouped, h->err);
-  CB_CUDA(h, cudaGetLastError());
-  k_sym_check<<<wgrid, 256, 0, s>>>(n, rp, col, low, grp, cursor, grouped, h->err);
-  CB_CUDA(h, cudaGetLastError());
-  h->launches += 3;
-  return CB_OK;
+  k_lower_count<<<g, 256, 0, s>>>(n, rp, col, low);
+  if ((e = exclusive_scan_i32(low, grp, n, h->scan_ws, s, &h->launches)) == cudaSuccess &&
+      (e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * kVBuckets, s)) == cudaSuccess) {
+    k_vcount<<<wgrid, 256, 0, s>>>(n, rp, col, sh, hist);
+    if ((e = exclusive_scan_i32(hist, boff, nb, scan, s, &h->launches)) == cudaSuccess) {
+      k_vcursor<<<(nb + 255) / 256, 256, 0, s>>>(nb, boff, cursor);
+      // the scratch holds row_ptr[n] int32: room for row_ptr[n] / 2 pairs,
+      // exactly the entries above the diagonal of a symmetric graph
+      const int64_t cap = h->nnz / 2;
+      k_vpart<<<h->num_sms * 4, 256, 0, s>>>(n, rp, col, sh, cursor, reinterpret_cast<int2*>(grouped),
+                                             static_cast<unsigned long long>(cap), h->err);
+      k_vcheck<<<g, 256, 0, s>>>(n, rp, col, low, reinterpret_cast<const int2*>(grouped), boff, nb, grp, cap,
+                                 h->err);
+      e = cudaGetLastError();
+      h->launches += 5;
+    }
+  }
+  if (e != cudaSuccess) rc = cuda_fail(h, e, "validation");
+  cudaFreeAsync(ws, s);
+  h->dev_bytes -= static_cast<int64_t>(ws_bytes);
+  return rc;
 }
 
 int rows_sorted(Graph* h, const int64_t* rp, const int32_t* col, int64_t n, bool* sorted) {
