@@ -19,7 +19,7 @@
  *  - Section 4 (trading procedure): sigma is chosen by the algorithm for each
  *    trade, uniformly; |A_u n D| elements of D go to u.
  *
- * Readings where the paper leaves the choice open (each listed in the design doc):
+ * Readings where the paper leaves the choice open:
  *  - pi: node x gets the 64-bit key philox64(seed; x, 0, g, 0) (counter
  *    words c0..c3), nodes are sorted by (key, id), 0-based positions, and
  *    trade t (0-based) is (order[2t], order[2t+1]).
