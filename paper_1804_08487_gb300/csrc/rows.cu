@@ -160,6 +160,10 @@ __global__ void __launch_bounds__(256) k_vpart(int64_t n, const int64_t* __restr
 
 // Every partitioned (x, y) found in L_y; and as many entries above the
 // diagonal as below (bucket space boff[nb] against the scan of low, grp[n]).
+// A thread runs kSearchLanes binary searches in lockstep, so that many loads
+// are in flight per step: a single search is a chain of dependent L2 reads.
+constexpr int kSearchLanes = 4;
+
 __global__ void k_vcheck(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                          const int32_t* __restrict__ low, const int2* __restrict__ part,
                          const int64_t* __restrict__ boff, int nb, const int64_t* __restrict__ grp, int64_t cap,
@@ -167,16 +171,47 @@ __global__ void k_vcheck(int64_t n, const int64_t* __restrict__ rp, const int32_
   const int64_t all = boff[nb];
   if (blockIdx.x == 0 && threadIdx.x == 0 && all != grp[n]) latch(err, kErrValidate);
   const int64_t total = all < cap ? all : cap;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    const int2 p = part[i];
-    if (p.x < 0 || p.y <= p.x || p.y >= n) {   // a slot no valid entry wrote (malformed input)
-      latch(err, kErrValidate);
-      continue;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x * kSearchLanes;
+  for (int64_t i0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * kSearchLanes; i0 < total; i0 += stride) {
+    const int32_t* row[kSearchLanes];
+    int32_t key[kSearchLanes];
+    int lo[kSearchLanes], hi[kSearchLanes], ly[kSearchLanes];
+#pragma unroll
+    for (int j = 0; j < kSearchLanes; ++j) {
+      lo[j] = 0;
+      hi[j] = 0;
+      ly[j] = 0;
+      key[j] = 0;
+      row[j] = col;
+      if (i0 + j >= total) continue;
+      const int2 p = part[i0 + j];
+      if (p.x < 0 || p.y <= p.x || p.y >= n) {   // a slot no valid entry wrote (malformed input)
+        latch(err, kErrValidate);
+        continue;
+      }
+      row[j] = col + rp[p.y];
+      key[j] = p.x;
+      ly[j] = low[p.y];
+      hi[j] = ly[j];
+      lo[j] = 0;
+      if (ly[j] == 0) latch(err, kErrValidate);   // nothing below the diagonal to find x in
     }
-    const int32_t* row = col + rp[p.y];
-    const int ly = low[p.y];
-    const int k = lower_bound(row, ly, p.x);
-    if (k >= ly || row[k] != p.x) latch(err, kErrValidate);
+    for (;;) {
+      bool more = false;
+#pragma unroll
+      for (int j = 0; j < kSearchLanes; ++j) {
+        if (lo[j] < hi[j]) {
+          more = true;
+          const int mid = (lo[j] + hi[j]) >> 1;
+          if (row[j][mid] < key[j]) lo[j] = mid + 1;
+          else hi[j] = mid;
+        }
+      }
+      if (!more) break;
+    }
+#pragma unroll
+    for (int j = 0; j < kSearchLanes; ++j)
+      if (ly[j] > 0 && (lo[j] >= ly[j] || row[j][lo[j]] != key[j])) latch(err, kErrValidate);
   }
 }
 
