@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_vpart(int64_t n, const int64_t* __restr
 // diagonal as below (bucket space boff[nb] against the scan of low, grp[n]).
 // A thread runs kSearchLanes binary searches in lockstep, so that many loads
 // are in flight per step: a single search is a chain of dependent L2 reads.
-constexpr int kSearchLanes = 4;
+constexpr int kSearchLanes = 8;
 
 __global__ void k_vcheck(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                          const int32_t* __restrict__ low, const int2* __restrict__ part,
