@@ -103,6 +103,7 @@ CASES = [
     (2500, 3, 60, 2.0, 16, {"tile_paths": 0}),        # 256-thread thresholds for small trades
     (3001, 3, 300, 2.0, 18, {"wide_pack": 1}),        # 16-byte far-trade records (n > 2^29 layout)
     (3000, 4, 1500, 2.0, 13, {}),                     # heavy tail: block-path hubs
+    (20000, 1, 3, 2.0, 23, {}),                       # degrees 1-2: rebuild chunks beyond the 512-trade table
 ]
 
 
