@@ -205,3 +205,73 @@ def imcb(n, edges, pairs, sigma):
             out.add((min(a, b), max(a, b)))
     assert sum(len(b) for b in buf) == len(out) == len(edges)
     return sorted(out)
+
+
+def global_trade_by_edge_keys(n, edges, order, edge_key, trade_order=None):
+    """One global trade (Def. "Undirected Global Trade", Section 3.3) with
+    sigma drawn from edge keys, the trades applied in `trade_order` (index
+    order by default).
+
+    Every edge keeps, for the whole step, the identity (lo, hi) of its
+    endpoints' positions at the step's start.  edge_key(t, lo, hi) is trade
+    t's key of such an edge; sigma(D) sorts D by (key, lo, hi) and u
+    receives the first |A_{u-v}| (Fig. 2)."""
+    pos = {x: p for p, x in enumerate(order)}
+    ends = [list(e) for e in edges]
+    ident = [tuple(sorted((pos[a], pos[b]))) for a, b in edges]
+    inc = [set() for _ in range(n)]
+    for e, (a, b) in enumerate(edges):
+        inc[a].add(e)
+        inc[b].add(e)
+
+    def other(e, x):
+        a, b = ends[e]
+        return b if a == x else a
+
+    T = n // 2
+    for t in (range(T) if trade_order is None else trade_order):
+        u, v = order[2 * t], order[2 * t + 1]
+        nu = {other(e, u): e for e in inc[u]}
+        nv = {other(e, v): e for e in inc[v]}
+        auv = [x for x in nu if x not in nv and x != v]
+        avu = [x for x in nv if x not in nu and x != u]
+        d = [(x, nu[x], 0) for x in auv] + [(x, nv[x], 1) for x in avu]
+        d.sort(key=lambda r: (edge_key(t, *ident[r[1]]), ident[r[1]]))
+        a = len(auv)
+        for k, (x, e, side) in enumerate(d):
+            to_u = k < a
+            if to_u and side == 1:      # edge {v, x} becomes {u, x}
+                ends[e] = [u if y == v else y for y in ends[e]]
+                inc[v].discard(e)
+                inc[u].add(e)
+            elif not to_u and side == 0:  # edge {u, x} becomes {v, x}
+                ends[e] = [v if y == u else y for y in ends[e]]
+                inc[u].discard(e)
+                inc[v].add(e)
+    return sorted(tuple(sorted(e)) for e in ends)
+
+
+def random_topological_trade_order(n, edges, order, rng):
+    """An order of the trades of one global trade in which two trades joined
+    by an edge keep their index order.  Trades touch only edges at their own
+    nodes, and a trade moves an edge from one of its nodes to the other, so
+    which trades are joined does not change during the step; trades that
+    are not joined commute."""
+    pos = {x: p for p, x in enumerate(order)}
+    T = n // 2
+    preds = [set() for _ in range(T)]
+    for a, b in edges:
+        s, t = pos[a] >> 1, pos[b] >> 1
+        if s != t and s < T and t < T:
+            preds[max(s, t)].add(min(s, t))
+    done, out = set(), []
+    ready = [t for t in range(T) if not preds[t]]
+    while ready:
+        t = ready.pop(rng.randrange(len(ready)))
+        out.append(t)
+        done.add(t)
+        for w in range(T):
+            if w not in done and w not in ready and w not in out and preds[w] <= done:
+                ready.append(w)
+    assert len(out) == T
+    return out

@@ -479,3 +479,35 @@ def test_relaxed_chain_is_symmetric(deg):
         assert sum(P[i, :]) == 1
         for j in range(len(states)):
             assert P[i, j] == P[j, i]
+
+
+@pytest.mark.parametrize("n,a,b,seed", [(60, 2, 20, 1), (41, 3, 30, 2), (24, 5, 20, 3)])
+def test_global_trade_is_order_independent(n, a, b, seed):
+    """Applying one global trade's trades in any topological order of the
+    'joined by an edge' relation gives the index-order result, which is the
+    oracle's.  The GPU threshold pass rests on this: it runs all trades at
+    once and orders only those joined by an edge."""
+    import random
+    from paper_1804_08487_gb300 import synth
+    from oracle import philox4x32_10
+    g = synth.powerlaw_graph(n, a, b, 2.0, seed)
+    o = Oracle(g.row_ptr, g.col, seed)
+    edges = [tuple(e) for e in o.edges().tolist()]
+    order = [int(x) for x in o.permutation(0)]
+
+    def edge_key(t, lo, hi):
+        r = philox4x32_10([lo, hi, 0, 1], seed)
+        w = (r[0], r[1]) if (lo >> 1) == t else (r[2], r[3])
+        return (int(w[0]) << 32) | int(w[1])
+
+    want_index = exact.global_trade_by_edge_keys(n, edges, order, edge_key)
+    o.superstep(1)
+    assert want_index == [tuple(e) for e in o.edges().tolist()]
+    rng = random.Random(seed)
+    differs = 0
+    for _ in range(5):
+        topo = exact.random_topological_trade_order(n, edges, order, rng)
+        differs += topo != list(range(n // 2))
+        assert exact.global_trade_by_edge_keys(n, edges, order, edge_key, topo) == want_index
+    if a <= 3:   # sparse graphs leave room for other orders (the dense one may not)
+        assert differs > 0
