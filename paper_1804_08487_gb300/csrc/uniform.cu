@@ -598,7 +598,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   return true;
 }
 
-__global__ void __launch_bounds__(kUniThreads, 3) k_uni_exec(UniCtx c) {
+__global__ void __launch_bounds__(kUniThreads, 2) k_uni_exec(UniCtx c) {
   extern __shared__ __align__(16) char usm[];
   __shared__ int64_t red[BlockTeam<kUniThreads>::kRedSlots];
   __shared__ int32_t hist[256];
