@@ -275,3 +275,86 @@ def random_topological_trade_order(n, edges, order, rng):
                 ready.append(w)
     assert len(out) == T
     return out
+
+
+def uniform_dataflow(n, edges, pairs, sigma, rng):
+    """The device protocol for a uniform trade sequence, run sequentially in a
+    random order of runnable trades:
+      - trade i has one inbox per endpoint, full at that endpoint's degree;
+      - every edge goes to min(next trade of a, next trade of b), into the
+        inbox of each endpoint that trades there, carrying the other
+        endpoint and its next trade; if neither endpoint trades again it is
+        final;
+      - a trade runs once both inboxes are full, and sends every resulting
+        edge on the same way.
+    Returns the final edges and the number of trades that ran (all of them
+    unless the protocol deadlocks)."""
+    L = len(pairs)
+    inf = L
+    deg = [0] * n
+    for a, b in edges:
+        deg[a] += 1
+        deg[b] += 1
+    suc = [[] for _ in range(n)]
+    for i, (u, v) in enumerate(pairs):
+        suc[u].append(i)
+        suc[v].append(i)
+
+    def nxt(x, i):   # next trade of x after trade i (i = -1: its first)
+        for j in suc[x]:
+            if j > i:
+                return j
+        return inf
+
+    inbox = {(i, s): [] for i in range(L) for s in (0, 1)}
+    out = set()
+    ready = []
+
+    def full(d):
+        u, v = pairs[d]
+        return len(inbox[(d, 0)]) == deg[u] and len(inbox[(d, 1)]) == deg[v]
+
+    def route(a, ta, b, tb):
+        d = min(ta, tb)
+        if d == inf:
+            out.add((min(a, b), max(a, b)))
+            return
+        u, v = pairs[d]
+        if ta == d:
+            inbox[(d, 0 if a == u else 1)].append((b, tb))
+        if tb == d:
+            inbox[(d, 0 if b == u else 1)].append((a, ta))
+        if full(d):
+            ready.append(d)
+
+    for d in range(L):
+        u, v = pairs[d]
+        if deg[u] == 0 and deg[v] == 0:
+            ready.append(d)
+    for a, b in edges:
+        route(a, nxt(a, -1), b, nxt(b, -1))
+    ran = 0
+    while ready:
+        d = ready.pop(rng.randrange(len(ready)))
+        ran += 1
+        u, v = pairs[d]
+        A = dict(inbox[(d, 0)])
+        B = dict(inbox[(d, 1)])
+        nu, nv = nxt(u, d), nxt(v, d)
+        auv = sorted(x for x in A if x not in B and x != v)
+        avu = sorted(x for x in B if x not in A and x != u)
+        order = sigma(d, u, v, sorted(auv + avu), len(auv))
+        to_u = set(order[:len(auv)])
+        for x in A:
+            if x in B:
+                route(u, nu, x, A[x])
+                route(v, nv, x, B[x])
+        if v in A:
+            route(u, nu, v, nv)
+        for x in auv + avu:
+            tau = A[x] if x in A else B[x]
+            if x in to_u:
+                route(u, nu, x, tau)
+            else:
+                route(v, nv, x, tau)
+    return sorted(out), ran

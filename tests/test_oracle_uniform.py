@@ -192,3 +192,27 @@ def test_uniform_trades_on_tiny_graphs(edges, n):
     assert o.uniform_next == 25
     # with at most one other node, D has at most one element per side and degrees pin the graph
     assert sorted(tuple(e) for e in o.edges().tolist()) == sorted(edges)
+
+
+@pytest.mark.parametrize("n,a,b,seed,count", [(50, 2, 15, 1, 300), (30, 6, 25, 2, 200), (120, 1, 10, 3, 500),
+                                              (6, 1, 5, 4, 100)])
+def test_device_protocol_runs_every_trade_and_equals_oracle(n, a, b, seed, count):
+    """The device's inbox protocol for uniform trades (per-endpoint inboxes
+    sized by degree, each edge sent to the next trade of either endpoint, a
+    trade runs once both inboxes are full), modelled sequentially with the
+    runnable trades taken in random orders: it never deadlocks and always
+    ends in the oracle's graph."""
+    import random
+    g = synth.powerlaw_graph(n, a, b, 2.0, seed)
+    o = Oracle(g.row_ptr, g.col, seed)
+    edges = [tuple(e) for e in o.edges().tolist()]
+    o.uniform_trades(count)
+    want = [tuple(e) for e in o.edges().tolist()]
+    pairs = [uniform_pair(seed, n, k) for k in range(count)]
+    sig = _sigma_from_keys(seed)
+    rng = random.Random(seed)
+    for _ in range(3):
+        got, ran = exact.uniform_dataflow(n, edges, pairs, sig, rng)
+        assert ran == count
+        assert got == want
+
