@@ -2,7 +2,7 @@
 """Throughput of the global Curveball super step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload n2^25|n2^20|n2^21|n4096|ensemble|serving|uniform]
+                    [--workload n2^25|n2^20|n2^21|n4096|ensemble|serving|uniform|swaps]
 
 One "step" is one global super step (Def. "Undirected Global Trade",
 Section 3.3) over the whole graph.  The metric is edge-trades/s = m * steps /
@@ -23,7 +23,8 @@ the headline of the line.
 
 --workload uniform times uniform single trades instead (Simple Undirected
 Curveball, Section 3.2): one step is n/2 trades on the --uniform-graph graph,
-run as the successor-list dataflow.
+run as the successor-list dataflow.  --workload swaps prints the appendix's
+swap-fraction series (uniform trades against global trades as n grows).
 """
 import argparse
 import json
@@ -583,6 +584,54 @@ def run_uniform(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------- swap fraction
+
+def run_swaps(args):
+    """The appendix experiment "Swaps performed by Curveball and Global
+    Curveball": the fraction of performed to possible neighbourhood swaps of
+    n/2 uniform trades and of one global trade, on 10-regular graphs and on
+    PLD([10, n/20), 2) graphs (Havel-Hakimi) for growing n.  Each graph first
+    takes 10 global super steps away from its structured start; both kinds of
+    step then run from that same state (two handles, same seed)."""
+    import torch
+    from paper_1804_08487_gb300 import cb, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    series = []
+    t0 = time.perf_counter()
+    for log2n in range(10, 21, 2):
+        n = 1 << log2n
+        for kind, (a, b) in (("10-regular", (10, 11)), ("PLD([10,n/20),2)", (10, max(n // 20, 11)))):
+            g = synth.powerlaw_graph(n, a, b, 2.0, 100 + log2n)
+            row = {"graph": kind, "n": n, "m": g.m}
+            for how in ("global", "uniform"):
+                c = cb.Curveball(g.row_ptr, g.col, 7 + log2n)
+                c.global_trades(10)
+                c.set_option("swap_stats", 1)
+                if how == "global":
+                    c.global_trades(1)
+                else:
+                    c.uniform_trades(n // 2)
+                done, possible = c.swap_counts()
+                row[how] = done / possible if possible else None
+                c.close()
+            series.append(row)
+    dt = time.perf_counter() - t0
+    reg = [r for r in series if r["graph"] == "10-regular"]
+    line = {
+        "metric": "fraction of performed neighbourhood swaps", "value": reg[-1]["global"], "unit": "fraction",
+        "n_gpus": 1, "steps": 1, "warmup": 10, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "swap fractions: 10-regular and PLD([10,n/20),2) graphs, n = 2^10..2^20, "
+                               "one global trade vs n/2 uniform trades after 10 global super steps",
+                   "parallelism": "single"},
+        "series": series, "seconds": dt,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args):
@@ -785,6 +834,8 @@ def main():
         run_serving(args)
     elif args.workload == "uniform":
         run_uniform(args)
+    elif args.workload == "swaps":
+        run_swaps(args)
     else:
         run_ours(args)
 

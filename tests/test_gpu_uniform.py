@@ -112,6 +112,23 @@ def test_uniform_trades_tiny_graphs(edges, n):
     _run_pair(rp, col, 11, [1, 5, 200])
 
 
+def test_uniform_trades_with_hubs_above_the_shared_hash():
+    """Two hubs of 14000 and 13000 neighbours in a sparse graph: trades whose
+    u has more than 12288 neighbours hash them in global memory, and trades
+    above 2048 entries keep them in a per-CTA global slice.  The seed puts a
+    hub in u's place in trades 1164, 9949 and 15107."""
+    n = 20000
+    g = synth.powerlaw_graph(n, 2, 20, 2.0, 61)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.row_ptr))
+    edges = {(int(a), int(b)) for a, b in zip(rows, g.col) if a < b}
+    edges |= {(0, x) for x in range(2, 14002)} | {(1, x) for x in range(5000, 18000)}
+    rp, col = exact.to_csr(frozenset(edges), n)
+    assert np.diff(rp)[0] > 12288 and np.diff(rp)[1] > 12288
+    hub_u = [k for k in range(n) if uniform_pair(1, n, k)[0] in (0, 1)]
+    assert hub_u[:3] == [1164, 9949, 15107]
+    _run_pair(rp, col, 1, [n // 2, n // 2])
+
+
 def test_uniform_and_global_steps_alternate():
     g = synth.powerlaw_graph(3000, 3, 300, 2.0, 8)
     _run_pair(g.row_ptr, g.col, 21, [500, 1500, 1], steps_between=2)
