@@ -781,6 +781,69 @@ def run_reference(args):
         }
         print(json.dumps(line), flush=True)
         return
+    if args.workload == "swaps":
+        from oracle import Oracle
+        from paper_1804_08487_gb300 import synth
+        series = []
+        t0 = time.perf_counter()
+        for log2n in range(10, 15, 2):
+            n = 1 << log2n
+            for kind, (a, b) in (("10-regular", (10, 11)), ("PLD([10,n/20),2)", (10, max(n // 20, 11)))):
+                g = synth.powerlaw_graph(n, a, b, 2.0, 100 + log2n)
+                row = {"graph": kind, "n": n, "m": g.m}
+                for how in ("global", "uniform"):
+                    o = Oracle(g.row_ptr, g.col, 7 + log2n)
+                    o.superstep(10)
+                    o.swap_counts(reset=True)
+                    if how == "global":
+                        o.superstep(1)
+                    else:
+                        o.uniform_trades(n // 2)
+                    done, possible = o.swap_counts()
+                    row[how] = done / possible if possible else None
+                series.append(row)
+        dt = time.perf_counter() - t0
+        reg = [r for r in series if r["graph"] == "10-regular"]
+        line = {
+            "impl": "reference", "metric": "fraction of performed neighbourhood swaps", "value": reg[-1]["global"],
+            "unit": "fraction", "n_gpus": world, "steps": 1, "warmup": 10, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "swap fractions (oracle sample: n = 2^10..2^14)", "parallelism": "single"},
+            "series": series,
+            "cpu_baseline": {"value": reg[-1]["global"], "unit": "fraction", "cores": 1, "kind": "oracle",
+                             "sample": f"n = 2^10..2^14, {dt:.1f} s"},
+            "e2e": {"value": reg[-1]["global"], "unit": "fraction", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
+    if args.workload == "serving":
+        from oracle import Oracle
+        from paper_1804_08487_gb300 import synth
+        work, t0, used = 0, time.perf_counter(), 0
+        for i in range(10000):
+            if used >= 16 or time.perf_counter() - t0 > 10.0:
+                break
+            w = synth.serving_request(i)
+            if w.n > (1 << 16):
+                continue
+            g = w.graph()
+            o = Oracle(g.row_ptr, g.col, w.chain_seed)
+            o.superstep(w.supersteps)
+            work += g.m * w.supersteps
+            used += 1
+        dt = time.perf_counter() - t0
+        value = work / dt
+        sample = f"oracle, serving requests with n <= 2^16 among the first ones ({used} requests), sequential"
+        line = {
+            "impl": "reference", "metric": METRIC + " (serving)", "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": used, "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": SERVING_NAME, "sample": sample, "parallelism": "single"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "uniform":
         w = workload(args.uniform_graph)
         vals = []
