@@ -65,6 +65,36 @@ def dist_env():
     return rank, world, local
 
 
+# Replicas: one chain does not shard, so every rank randomises its own replica
+# of the workload; the job's time is its slowest rank's, and its throughput
+# counts the work of all ranks.
+
+def replica_seed(seed, rank):
+    """The chain seed of rank `rank`'s replica."""
+    return seed + rank
+
+
+def ensemble_replica_seeds(seeds, rank):
+    """Every graph's chain seed in rank `rank`'s replica of an ensemble."""
+    return [s + 1000003 * rank for s in seeds]
+
+
+def max_over_ranks(x, world, device="cuda"):
+    """The largest x over all ranks (a collective when world > 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, t_max_s):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / t_max_s
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -290,15 +320,10 @@ def run_ensemble(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     graphs, seeds = ensemble_graphs()
-    seeds = [s + 1000003 * rank for s in seeds]   # each replica its own chains
+    seeds = ensemble_replica_seeds(seeds, rank)   # each replica its own chains
     stream = torch.cuda.Stream()
     r = measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, clocks=ClockSampler(local))
-    t_ms = r["batched_ms"]
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(r["batched_ms"], world)
     # end to end: create from pinned host buffers, the super steps, every
     # graph's edge list back to pinned host memory
     rp_all = torch.from_numpy(__import__("numpy").concatenate([g[0] for g in graphs])).pin_memory()
@@ -312,7 +337,7 @@ def run_ensemble(args):
     cb.cb_global_trades(h, ENSEMBLE_STEPS)
     cb.cb_export_edges(h, out_h)
     cb.cb_sync(h)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     cb.cb_destroy(h)
     if rank != 0:
         if world > 1:
@@ -323,7 +348,7 @@ def run_ensemble(args):
     K = ENSEMBLE_STEPS
     b_min = 16 * r["m_total"] + 24 * r["n_total"]
     gbs = b_min / (t_ms / K / 1e3) / 1e9
-    value = world * r["m_total"] * K / (t_ms / 1e3)
+    value = job_rate(world, r["m_total"] * K, t_ms / 1e3)
     line = {
         "metric": METRIC + " (batched ensemble)", "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": 27, "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -336,7 +361,7 @@ def run_ensemble(args):
         "batched_vs_plain": r["speedup_vs_plain"],
         "batched": r,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_desc},
-        "e2e": {"value": world * r["m_total"] * K / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_rate(world, r["m_total"] * K, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": (rp_all.numel() * 8 + col_all.numel() * 4) / K,
                 "d2h_bytes_per_step": out_h.numel() * 4 / K},
         "gpu_launches": r["batched_launches"],
@@ -500,7 +525,7 @@ def run_uniform(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload(args.uniform_graph)
     g = w.graph()
-    seed = w.chain_seed + rank
+    seed = replica_seed(w.chain_seed, rank)
     stream = torch.cuda.Stream()
     half = g.n // 2
     c = cb.Curveball(g.row_ptr, g.col, seed, stream=stream)
@@ -528,14 +553,9 @@ def run_uniform(args):
     barrier()
     clk = clocks.stop()
     t_ms = e0.elapsed_time(e1)
-    t_max = t_ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_ms, world)
     K = args.steps
-    value = world * g.m * K / (t_max / 1e3)
+    value = job_rate(world, g.m * K, t_max / 1e3)
     c.set_option("swap_stats", 1)   # one more, untimed step for the swap fraction
     c.uniform_trades(half)
     sw_done, sw_all = c.swap_counts()
@@ -550,7 +570,7 @@ def run_uniform(args):
     c2.uniform_trades(half * K)
     c2.edges(out_h)
     c2.sync()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     c2.close()
     if rank != 0:
         if world > 1:
@@ -571,7 +591,7 @@ def run_uniform(args):
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "note": "B_min = 16m + 24n per step; the dataflow is bound by its chain of dependent trades"},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc},
-        "e2e": {"value": world * g.m * K / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_rate(world, g.m * K, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": (g.row_ptr.nbytes + g.col.nbytes) / K, "d2h_bytes_per_step": 2 * g.m * 4 / K},
         "gpu_launches": launches,
         "clocks": clk,
@@ -646,7 +666,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = workload(args.workload)
     g = w.graph()
-    seed = w.chain_seed + rank          # each replica its own chain
+    seed = replica_seed(w.chain_seed, rank)          # each replica its own chain
     stream = torch.cuda.Stream()
     c = cb.Curveball(g.row_ptr, g.col, seed, stream=stream)
     if args.perm == "relaxed":
@@ -680,13 +700,8 @@ def run_ours(args):
     c.set_option("swap_stats", 1)
     c.global_trades(1)
     sw_done, sw_all = c.swap_counts()
-    t_max = t_ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * g.m * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(t_ms, world)
+    value = job_rate(world, g.m * args.steps, t_max / 1e3)
 
     # end to end through the C ABI with host buffers: create from pinned host
     # CSR (H2D inside), the same super steps, export to a pinned host buffer (D2H)
@@ -704,12 +719,7 @@ def run_ours(args):
     c2.sync()
     e2e_s = time.perf_counter() - t0
     c2.close()
-    e2e_max = e2e_s
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_max = float(tt.item())
+    e2e_max = max_over_ranks(e2e_s, world)
     h2d = (g.row_ptr.nbytes + g.col.nbytes) / args.steps
     d2h = (2 * g.m * 4) / args.steps
     batched = None
@@ -745,7 +755,7 @@ def run_ours(args):
         "roofline_step": {"bytes_min": b_min, "achieved": step_gbs, "peak": peak, "unit": "GB/s",
                           "frac": step_gbs / peak},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc},
-        "e2e": {"value": world * g.m * K / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_rate(world, g.m * K, e2e_max), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(stats.get("launches", 0)),
         "clocks": clk,
