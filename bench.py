@@ -172,6 +172,25 @@ def measured_traffic():
         return None
 
 
+def verify_step1(name, c, m):
+    """{"step1": bool, "against": ...}: the handle's edge list after its first
+    super step compared with the oracle's sha256 stored in tests/golden for
+    this workload (None when no digest is stored)."""
+    import hashlib
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"plain_{name.replace('^', 'p')}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        want = json.load(f)["edge_sha256_after_step"].get("1")
+    if want is None:
+        return None
+    out = np.empty((m, 2), dtype=np.int32)
+    c.edges(out)
+    got = hashlib.sha256(memoryview(out).cast("B")).hexdigest()
+    return {"step1": got == want, "against": os.path.relpath(path, ROOT) + " (oracle digest)"}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -672,7 +691,15 @@ def run_ours(args):
     if args.perm == "relaxed":
         c.set_option("relaxed", 1)
     c.set_option("timing", 1)
-    c.global_trades(args.warmup)
+    # verify leg (untimed, inside the warm-up): the edge list after super step 1
+    # of this chain against the oracle's stored digest for the workload
+    parity = None
+    if args.warmup >= 1 and rank == 0 and args.perm == "sort":
+        c.global_trades(1)
+        parity = verify_step1(args.workload, c, g.m)
+        c.global_trades(args.warmup - 1)
+    else:
+        c.global_trades(args.warmup)
     c.sync()
 
     def barrier():
@@ -762,6 +789,7 @@ def run_ours(args):
         "phase_ms_per_step": {"permutation": phases["permutation_ms"] / K, "threshold": phase_ms["threshold"],
                               "rebuild": phase_ms["rebuild"], "step": phases["step_ms"] / K},
         "dependency_passes_last_step": stats.get("passes"),
+        "parity": parity,
         "swap_fraction": {"performed": sw_done, "possible": sw_all,
                           "fraction": sw_done / sw_all if sw_all else None, "of": "one global trade"},
     }

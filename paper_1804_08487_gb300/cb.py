@@ -131,6 +131,11 @@ def _ptr(x):
     return x.data_ptr(), (CB_DEVICE if x.is_cuda else CB_HOST), x
 
 
+def _numel(x) -> int:
+    """Element count of a numpy array or a torch tensor."""
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
 def _check(rc: int, h=None):
     if rc < 0:
         msg = load().cb_last_error(h).decode(errors="replace")
@@ -197,7 +202,7 @@ def cb_export_graph(h, index: int, out=None):
             _check(lib.cb_export_graph(h, index, arr.ctypes.data, m.value, C.byref(m), CB_HOST), h)
         return arr
     p, kind, _ = _ptr(out)
-    _check(lib.cb_export_graph(h, index, p, out.numel() // 2, C.byref(m), kind), h)
+    _check(lib.cb_export_graph(h, index, p, _numel(out) // 2, C.byref(m), kind), h)
     return out
 
 
@@ -214,7 +219,7 @@ def cb_global_trades(h, supersteps: int):
 
 def cb_export_edges(h, out=None):
     """Canonical edge list: numpy int32 (m, 2) on the host, or into `out`
-    (an int32 CUDA tensor with at least 2m entries)."""
+    (a numpy array or a torch tensor, int32, with at least 2m entries)."""
     lib = load()
     m = C.c_int64(0)
     _check(lib.cb_export_edges(h, None, 0, C.byref(m), CB_HOST), h)
@@ -224,7 +229,7 @@ def cb_export_edges(h, out=None):
             _check(lib.cb_export_edges(h, arr.ctypes.data, m.value, C.byref(m), CB_HOST), h)
         return arr
     p, kind, _ = _ptr(out)
-    _check(lib.cb_export_edges(h, p, out.numel() // 2, C.byref(m), kind), h)
+    _check(lib.cb_export_edges(h, p, _numel(out) // 2, C.byref(m), kind), h)
     return out
 
 

@@ -7,7 +7,15 @@ import numpy as np
 def edge_hash(edges: np.ndarray) -> str:
     """sha256 of a canonical edge list (int32 pairs a<b, lexicographic), little endian."""
     e = np.ascontiguousarray(edges, dtype="<i4")
-    return hashlib.sha256(e.tobytes()).hexdigest()
+    return hashlib.sha256(memoryview(e).cast("B")).hexdigest()
+
+
+def graph_hash(row_ptr: np.ndarray, col: np.ndarray) -> str:
+    """sha256 of a CSR: row_ptr as int64 then col as int32, little endian."""
+    h = hashlib.sha256()
+    h.update(memoryview(np.ascontiguousarray(row_ptr, dtype="<i8")).cast("B"))
+    h.update(memoryview(np.ascontiguousarray(col, dtype="<i4")).cast("B"))
+    return h.hexdigest()
 
 
 def csr_from_edges(edges: np.ndarray, n: int):
