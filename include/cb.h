@@ -25,7 +25,12 @@
  *     e.g. a torch tensor's data_ptr()).
  *   - Return codes: CB_OK (0) or a negative CB_E* code.  Nothing aborts or
  *     traps; after an error cb_last_error() describes it.  An error latched
- *     by a device check (CB_ECHECK) makes later calls on the handle fail.
+ *     by a device check (CB_ECHECK) or by a device wait that ran out
+ *     (CB_ETIMEOUT) makes later calls on the handle fail; cb_destroy still
+ *     releases it.  Every device-side wait (a trade waiting for the trade it
+ *     depends on, a bulk copy into shared memory, the uniform-trade
+ *     executor's run queue and inboxes) is bounded in time (option
+ *     "wait_ms"); the kernel then records the error and returns.
  *   - One host thread at a time per handle.  Work is issued on the handle's
  *     stream; calls that return data to the caller synchronise that stream.
  */
@@ -45,6 +50,7 @@ extern "C" {
 #define CB_ECHECK (-5)   /* a device-side invariant check failed */
 #define CB_ESIZE (-6)    /* caller buffer too small (size reported) */
 #define CB_ERANGE (-7)   /* super-step counter would exceed 2^32 - 2 */
+#define CB_ETIMEOUT (-8) /* a bounded device wait ran out (the handle stays destroyable) */
 
 #define CB_HOST 0
 #define CB_DEVICE 1
@@ -199,16 +205,24 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               graph launch per super step [0].  Not while "timing" is on.
  *               The handle's stream must support capture (not the legacy
  *               default stream).  Changing any other option re-records.
- *   "tile_max"  trades up to this size run on the flat tile path (one
- *               thread per entry, many trades per CTA) [128]; 0..128.
- *   "tile_paths" 1: threshold phase of tile-path trades on the tile
- *               kernel; 0: on the 256-thread kernel instead [1].  (The
- *               rebuild phase is one flat pass over all entries.)
- *   "block_max" trades up to this size run on a 256-thread CTA [2048];
+ *   "tile_max"  trades up to this size are "small" [128]; 0..128.
+ *   "tile_paths" threshold phase of small trades: 2 one warp per trade
+ *               with its entries in registers; 1 the flat tile kernel (one
+ *               thread per entry, many trades per CTA); 0 the 256-thread
+ *               kernel [2].  (The rebuild phase is one flat pass over all
+ *               entries.)
+ *   "block_max" trades up to this size run on a 256-thread CTA [1024];
  *               0..2048 (values below tile_max act as tile_max).
- *   "smem_max"  larger trades run on a 1024-thread CTA and keep up to this
- *               many entries in shared memory, more in a global-memory
- *               workspace [8192]; 64..8192.
+ *   "smem_max"  larger trades run on a 1024-thread CTA; with "cta_paths" 1
+ *               up to min(4096, smem_max) entries in registers, with 0 up
+ *               to smem_max entries in shared memory; more in a
+ *               global-memory workspace [8192]; 64..8192.
+ *   "cta_paths" 1: threshold phase of the 256- and 1024-thread classes with
+ *               the entries in registers (4 per thread); 0: in shared
+ *               memory [1].
+ *   "cand_max"  register paths: when at most this many elements share the
+ *               threshold's leading key bits they are ranked directly,
+ *               else more radix digits follow [32]; 1..32 (a test knob).
  *   "inorder_threads" CTA size of the pass that runs deferred trades in
  *               index order: 1024 (large trades in shared memory) or 256
  *               (four CTAs per SM; trades above block_max from global
@@ -227,6 +241,18 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               larger buckets take the global-memory fallback; 2..4096.
  *   "timing"    1: record CUDA events around the phases of each super step
  *               (adds one stream synchronisation per super step) [0].
+ *   "wait_ms"   longest single device wait, in milliseconds [1000 for a
+ *               super step, 20000 for uniform trades]; 1..600000.  A wait
+ *               that runs out makes the call (or the next cb_sync) return
+ *               CB_ETIMEOUT.
+ *   "hold_publish" 1: trades never publish that their threshold is ready,
+ *               so a trade that depends on another waits until "wait_ms"
+ *               runs out (a test of the timeout path) [0].
+ *   "hold_trade" uniform trades: messages to this trade (index within the
+ *               call) are dropped, so it never runs and the executor's
+ *               waits run out (a test of the timeout path); -1: none [-1].
+ *   "fix_passes" passes of the rebuild over slices of the far trades (0:
+ *               as many as keep one slice's records in L2) [0]; 0..64.
  *   "swap_stats" 1: count neighbourhood swaps (see cb_swap_counts) from zero
  *               in every later super step and uniform trade; super steps
  *               then run without the recorded CUDA graphs, plus one counting

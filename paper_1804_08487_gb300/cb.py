@@ -21,6 +21,7 @@ CB_ECUDA = -3
 CB_ECHECK = -5
 CB_ESIZE = -6
 CB_ERANGE = -7
+CB_ETIMEOUT = -8
 CB_HOST = 0
 CB_DEVICE = 1
 

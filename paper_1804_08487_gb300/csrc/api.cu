@@ -66,7 +66,7 @@ void release(Graph* h) {
   free_uniform(h);
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
-                  h->list[0], h->list[1], h->list[2], h->tile_off, h->tile_first, h->cls_flag, h->cls_scan,
+                  h->list[0], h->list[1], h->list[2], h->Minv, h->cls_flag, h->cls_scan,
                   h->counters, h->err,
                   h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs, h->far_pack,
                   h->lcg_ab, h->lcg_gaps, h->swaps};
@@ -87,6 +87,10 @@ int read_device_error(Graph* h) {
   CB_CUDA(h, cudaMemcpyAsync(&e, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CB_CUDA(h, cudaStreamSynchronize(h->stream));
   if (e != kErrNone) {
+    if (is_timeout(e)) {
+      h->latched = CB_ETIMEOUT;
+      return fail(h, CB_ETIMEOUT, "a bounded device wait ran out (code " + std::to_string(e) + ")");
+    }
     h->latched = CB_ECHECK;
     return fail(h, CB_ECHECK, "device check failed (code " + std::to_string(e) + ")");
   }
@@ -214,11 +218,11 @@ void destroy_graph(Graph* h) {
   delete static_cast<cb_graph*>(h);
 }
 
-// Scratch of 4 int32 per trade: class flags and tile weights, then (phase B)
-// 2 slot counters per trade and the first / last trade of each 2048-entry chunk.
+// Scratch of 3 int32 per trade (class flags), then (rebuild) the first row
+// of each 2048-entry chunk plus one.
 int64_t cls_flag_count(int64_t ntasks, int64_t nnz) {
   const int64_t chunks = nnz / 2048 + 1;
-  return std::max<int64_t>(4 * ntasks, 2 * ntasks + 2 * chunks);
+  return std::max<int64_t>(3 * ntasks, chunks + 1);
 }
 
 // Common part of handle creation.  On entry: n, nnz, the segment table (host
@@ -251,16 +255,17 @@ int finish_create(Graph* h) {
   h->sort_ws_bytes = perm_ws_bytes(std::max<int64_t>(n, 1), h->nbuckets);
   h->scan_ws_bytes = scan_ws_bytes(std::max<int64_t>(n + 1, h->nbuckets + 1));
   if (dalloc(h, &h->order[0], n) || dalloc(h, &h->order[1], n) || dalloc(h, &h->rp[0], n + 1) || dalloc(h, &h->rp[1], n + 1) ||
-      dalloc(h, &h->pos_next, n) || dalloc(h, &h->M, n) || dalloc(h, &h->deg_next, n) || dalloc(h, &h->stash, nnz) ||
+      dalloc(h, &h->pos_next, n) || dalloc(h, &h->M, n) || dalloc(h, &h->Minv, n) || dalloc(h, &h->deg_next, n) ||
+      dalloc(h, &h->stash, nnz) ||
       dalloc(h, &h->thr_key, h->ntasks) || dalloc(h, &h->thr_tb, h->ntasks) || dalloc(h, &h->done, h->ntasks) ||
       dalloc(h, &h->far_pack, h->ntasks) ||
       dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->list[0], h->ntasks) || dalloc(h, &h->list[1], h->ntasks) ||
-      dalloc(h, &h->list[2], h->ntasks) || dalloc(h, &h->tile_off, h->ntasks) || dalloc(h, &h->tile_first, h->ntasks + 2) ||
-      dalloc(h, &h->cls_flag, cls_flag_count(h->ntasks, nnz)) || dalloc(h, &h->cls_scan, 4 * (h->ntasks + 1)) ||
+      dalloc(h, &h->list[2], h->ntasks) ||
+      dalloc(h, &h->cls_flag, cls_flag_count(h->ntasks, nnz)) || dalloc(h, &h->cls_scan, 3 * (h->ntasks + 1)) ||
       dmalloc(h, &h->sort_ws, h->sort_ws_bytes) || dmalloc(h, &h->scan_ws, h->scan_ws_bytes))
     return fail(h, CB_ENOMEM, "device allocation failed");
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
-  // the flat rebuild reads 8 entries (32 B) and 8 stash bytes per vector load
+  // the rebuild reads 8 placeholders (32 B) and 8 side bytes per vector load
   if ((reinterpret_cast<uintptr_t>(h->col[0]) | reinterpret_cast<uintptr_t>(h->col[1])) % 16 ||
       reinterpret_cast<uintptr_t>(h->stash) % 8)
     return fail(h, CB_ECUDA, "device allocation not aligned for vector loads");
@@ -309,9 +314,15 @@ int capture_step_graphs(Graph* h) {
   const int cur0 = h->cur;
   const uint64_t g0 = h->g;
   const int64_t l0 = h->launches;
+  // a super step leaves its output in the buffer it read (col[cur] before
+  // and after), so parity p is recorded with that buffer as col[p]
+  int32_t* const adj = h->col[cur0];
+  int32_t* const spare = h->col[1 - cur0];
   int rc = CB_OK;
   for (int p = 0; p < 2 && rc == CB_OK; ++p) {
     h->cur = p;
+    h->col[p] = adj;
+    h->col[1 - p] = spare;
     const int64_t lb = h->launches;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
@@ -331,6 +342,8 @@ int capture_step_graphs(Graph* h) {
     h->cur = cur0;
     h->g = g0;
   }
+  h->col[cur0] = adj;
+  h->col[1 - cur0] = spare;
   h->launches = l0;
   if (rc) drop_step_graphs(h);
   return rc;
@@ -419,11 +432,11 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   const int64_t nb = int64_t(1) << bucket_bits(n);
   int64_t b = 0;
   b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * (nnz + kColPad) + 32 + 8 * kCounters;   // cb_create
-  b += 2 * 4 * n + 2 * 8 * (n + 1) + 3 * 4 * n + nnz;                                     // per node, stash
-  b += ntasks * (8 + 8 + 4 + 16 + 1 + 3 * 4 + 8 + 32) + 4 * cls_flag_count(ntasks, nnz) + 4 * (ntasks + 2) + 32;
+  b += 2 * 4 * n + 2 * 8 * (n + 1) + 4 * 4 * n + nnz;                                     // per node, side bytes
+  b += ntasks * (8 + 8 + 4 + 16 + 1 + 3 * 4 + 24) + 4 * cls_flag_count(ntasks, nnz) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;
-  if (max_trade > kBlockMaxCap || maxdeg > 16384) {   // default block_max
+  if (max_trade > kBlockMaxDefault || maxdeg > 16384) {   // default block_max
     const size_t slice = trade_ws_slice_bytes(std::max<int64_t>(max_trade, 1));
     const size_t ctas = std::max<size_t>(1, std::min<size_t>(num_sms * 4, (size_t(2) << 30) / slice));
     b += static_cast<int64_t>(slice * ctas);
@@ -640,6 +653,7 @@ int cb_global_trades(cb_handle h, uint32_t supersteps) {
     }
     for (uint32_t i = 0; i < supersteps; ++i) {
       CB_CUDA(h, cudaGraphLaunch(h->step_exec[h->cur], h->stream));
+      std::swap(h->col[0], h->col[1]);   // as super_step does
       h->cur = 1 - h->cur;
       h->g += 1;
       h->launches += h->step_launches;
@@ -802,6 +816,36 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
   if (!std::strcmp(key, "tile_paths")) {
     if (value < 0 || value > 1) return fail(h, CB_EINVAL, "tile_paths is 0 or 1");
     h->tile_paths = static_cast<int>(value);
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "wait_ms")) {
+    if (value < 1 || value > 600000) return fail(h, CB_EINVAL, "wait_ms out of range [1, 600000]");
+    h->wait_ns = h->uni_wait_ns = static_cast<uint64_t>(value) * 1000000ull;
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "hold_publish")) {
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "hold_publish is 0 or 1");
+    h->hold_publish = static_cast<int>(value);
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "hold_trade")) {
+    if (value < -1) return fail(h, CB_EINVAL, "hold_trade is -1 or a trade index");
+    h->hold_trade = value;
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "fix_passes")) {
+    if (value < 0 || value > 64) return fail(h, CB_EINVAL, "fix_passes out of range [0, 64]");
+    h->fix_passes = static_cast<int>(value);
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "cta_paths")) {
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "cta_paths is 0 or 1");
+    h->cta_paths = static_cast<int>(value);
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "cand_max")) {
+    if (value < 1 || value > 32) return fail(h, CB_EINVAL, "cand_max out of range [1, 32]");
+    h->cand_max = static_cast<int>(value);
     return CB_OK;
   }
   if (!std::strcmp(key, "block_max")) {

@@ -21,11 +21,14 @@ enum DevErr : int32_t {
   kErrUniform = 7,       // uniform trades: an inbox or the run queue overflowed, or a message missed its trade
   kErrUniformWait = 8,   // uniform trades: a wait for a queued trade or an inbox entry gave up
 };
+// The codes that report a bounded wait running out (CB_ETIMEOUT).
+inline bool is_timeout(int32_t e) { return e == kErrResolve || e == kErrStage || e == kErrUniformWait; }
 
 struct UniBufs;   // uniform-trade buffers (uniform.cu)
 
 constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
 constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
+constexpr int kBlockMaxDefault = 1024;   // default of the "block_max" option
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
 constexpr int kCounters = 32;       // device counters per handle
@@ -80,19 +83,18 @@ struct Graph {
   int32_t* col[2] = {nullptr, nullptr};    // position-space rows, ascending
   int32_t* pos_next = nullptr;             // position of each node id in step g+1
   int32_t* M = nullptr;                    // step-g position -> step-(g+1) position
+  int32_t* Minv = nullptr;                 // step-(g+1) position -> step-g position
   int32_t* deg_next = nullptr;             // degree by step-(g+1) position
-  uint8_t* stash = nullptr;                // per entry: bit0 own flip, bit1 in far trade's D
+  uint8_t* stash = nullptr;                // per placed entry (step g+1 layout): bit0 own flip, bits 1..7 far key prefix
   uint64_t* thr_key = nullptr;             // per trade: threshold key
   uint8_t* thr_top = nullptr;              // per trade: top 6 bits of the threshold key
   uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)
   uint32_t* done = nullptr;                // per trade: 1 once the threshold is published (cleared per step)
   int4* far_pack = nullptr;                // per trade: new positions of its nodes, threshold prefix (rebuild)
-  int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (tile, 256, 1024 threads), index order
-  int64_t* tile_off = nullptr;             // per tile-class trade: prefix of its weight max(L, 4)
-  int32_t* tile_first = nullptr;           // first tile-class trade of each tile (+ end sentinel)
-  int32_t* cls_flag = nullptr;             // 4 x ntasks scratch: class flags and tile weights
-  int64_t* cls_scan = nullptr;             // 4 x (ntasks+1) scratch: their exclusive scans
-  int64_t* counters = nullptr;             // list lengths, tile weight, deferred count, claims (kCounters)
+  int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (warp, 256, 1024 threads), index order
+  int32_t* cls_flag = nullptr;             // scratch: 3 x ntasks class flags, then the rebuild's chunk rows
+  int64_t* cls_scan = nullptr;             // 3 x (ntasks+1) scratch: exclusive scans of the class flags
+  int64_t* counters = nullptr;             // list lengths, deferred count, claims (kCounters)
   int32_t* err = nullptr;                  // latched device error
   // workspaces
   void* ws_global = nullptr;               // global workspace for trades too big for smem
@@ -107,8 +109,15 @@ struct Graph {
 
   // knobs
   int tile_max = kTileMaxCap;
-  int tile_paths = 1;   // 1: threshold phase of tile-class trades on the tile kernel
-  int block_max = kBlockMaxCap;
+  int tile_paths = 1;   // threshold phase of small trades: 1 one warp per trade, 0 256-thread CTAs
+  int fix_passes = 0;   // passes of the rebuild's fix-up over slices of the far trades (0: sized for L2)
+  int cta_paths = 1;    // threshold phase of larger trades: 1 register-resident CTA kernels, 0 shared-memory ones
+  int cand_max = 32;    // register paths: candidates ranked directly (tests lower it to force radix digits)
+  uint64_t wait_ns = 1000000000ull;       // longest single wait of a super step (dependency, bulk copy)
+  uint64_t uni_wait_ns = 20000000000ull;  // longest single wait of the uniform-trade executor
+  int hold_publish = 0;                   // test hook: trades never publish their done flags
+  int64_t hold_trade = -1;                // test hook: uniform trade whose messages are dropped
+  int block_max = kBlockMaxDefault;
   int smem_max = kSmemMaxCap;
   int bucket_cap = 2048;
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)

@@ -237,9 +237,11 @@ __global__ void k_bucket_overflow(const int32_t* __restrict__ overflow, const in
 
 __global__ void k_prep_next(int64_t n, const int32_t* __restrict__ order_cur, const int32_t* __restrict__ order_next,
                             const int32_t* __restrict__ pos_next, const int32_t* __restrict__ deg_id,
-                            int32_t* __restrict__ M, int32_t* __restrict__ deg_next) {
+                            int32_t* __restrict__ M, int32_t* __restrict__ Minv, int32_t* __restrict__ deg_next) {
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
-    M[p] = pos_next[order_cur[p]];
+    const int32_t q = pos_next[order_cur[p]];
+    M[p] = q;
+    Minv[q] = static_cast<int32_t>(p);
     deg_next[p] = deg_id[order_next[p]];
   }
 }
@@ -343,7 +345,7 @@ int prepare_next(Graph* h) {
   if (rc) return rc;
   const unsigned grid = grid_for(h->n, kPermThreads, h->num_sms);
   k_prep_next<<<grid, kPermThreads, 0, h->stream>>>(h->n, h->order[h->cur], h->order[nxt], h->pos_next,
-                                                    h->deg_id, h->M, h->deg_next);
+                                                    h->deg_id, h->M, h->Minv, h->deg_next);
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
   CB_CUDA(h, exclusive_scan_i32(h->deg_next, h->rp[nxt], h->n, h->scan_ws, h->stream, &h->launches));

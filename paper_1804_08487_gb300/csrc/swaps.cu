@@ -2,19 +2,20 @@
 // a trade performs as many neighbourhood swaps as edge ends that change node
 // (twice the pairs of neighbours it exchanges), out of deg(u) + deg(v)
 // possible.  With the "swap_stats" option on, every global super step adds
-// its counts: the entries whose stash byte marks a move to the other node
-// of their trade, and the degrees of the traded positions.  Uniform trades
-// add theirs in the executor (uniform.cu).
+// its counts: the entries whose side byte marks a move to the other node of
+// their trade (the untraded node of an odd n never moves), and the degrees
+// of the traded positions.  Uniform trades add theirs in the executor
+// (uniform.cu).
 #include "cb_internal.cuh"
 
 namespace cb {
 namespace {
 
-// out[0] += moved entries among the first rp[two_t] (the traded positions'
-// rows), out[1] += rp[two_t].
-__global__ void k_count_flips(const uint8_t* __restrict__ stash, const int64_t* __restrict__ rp, int64_t two_t,
-                              unsigned long long* out) {
-  const int64_t end = rp[two_t];
+// out[0] += moved entries among all nnz, out[1] += rp[two_t] (the entries of
+// the traded positions' rows in the step just done).
+__global__ void k_count_flips(const uint8_t* __restrict__ stash, int64_t nnz, const int64_t* __restrict__ rp,
+                              int64_t two_t, unsigned long long* out) {
+  const int64_t end = nnz;
   const int64_t words = end >> 2;
   const int64_t tid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -25,7 +26,7 @@ __global__ void k_count_flips(const uint8_t* __restrict__ stash, const int64_t* 
 #pragma unroll
   for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(&out[0], local);
-  if (tid == 0) atomicAdd(&out[1], static_cast<unsigned long long>(end));
+  if (tid == 0) atomicAdd(&out[1], static_cast<unsigned long long>(rp[two_t]));
 }
 
 }  // namespace
@@ -35,7 +36,7 @@ int count_swaps(Graph* h) {
   // the step just done read the rows of the other ping-pong side
   const int64_t two_t = 2 * (h->n / 2);
   const unsigned grid = static_cast<unsigned>(h->num_sms * 4);
-  k_count_flips<<<grid, 256, 0, h->stream>>>(h->stash, h->rp[1 - h->cur], two_t,
+  k_count_flips<<<grid, 256, 0, h->stream>>>(h->stash, h->nnz, h->rp[1 - h->cur], two_t,
                                              reinterpret_cast<unsigned long long*>(h->swaps));
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;

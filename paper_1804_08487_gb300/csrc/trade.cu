@@ -43,7 +43,6 @@ namespace cb {
 namespace {
 
 constexpr uint32_t kDeferred = 2;              // done[t]: deferred by the first pass
-constexpr uint32_t kWaitLimit = 1u << 24;      // polls of a dependency before giving up (about 2 s)
 
 // meta bits per entry (phase A)
 constexpr uint8_t kR = 1;       // entry sits in v's row
@@ -56,13 +55,6 @@ constexpr uint8_t kUV = 8;      // the edge {u_t, v_t}
 // row, bit1 in v's row, bit2 the u-row entry flips, bit3 the v-row entry flips
 constexpr int kMedThreads = 256;
 constexpr int kBigThreads = 1024;
-constexpr int kTileThreads = 256;
-constexpr int kTileCap = 1024;                       // weight units per tile (weight = max(L, 4))
-constexpr int kTileTrades = kTileCap / 4;            // so at most 256 trades per tile
-constexpr int kTileSlots = kTileCap + kTileMaxCap;   // a trade may start just before the cap
-constexpr int kNoOwner = 0xFFFF;
-constexpr int kTileHashLg = 11;
-constexpr int kTileHash = 1 << kTileHashLg;          // > 1.7 x the slots of a tile
 
 struct StepCtx {
   int64_t n, T;
@@ -71,7 +63,9 @@ struct StepCtx {
   const int32_t* seg_of;    // graph of each position (null: one graph)
   const int64_t* rp;
   const int32_t* col;
-  uint8_t* stash;
+  uint8_t* fb;              // side byte of every placed entry (step g+1 layout)
+  int32_t* ph;              // placeholders of every entry in its new row (step g+1 layout)
+  const int32_t* Minv;      // step-(g+1) position -> step-g position
   uint64_t* thr_key;
   uint64_t* thr_tb;
   uint8_t* thr_top;
@@ -79,10 +73,12 @@ struct StepCtx {
   int32_t* err;
   const int32_t* M;
   const int64_t* rp_next;
-  int32_t* col_next;
   unsigned long long* def_count;   // trades deferred by the first pass
   uint32_t wait;                   // 0: defer a trade whose dependency is unpublished; 1: wait for it
   unsigned long long* gws_count;
+  int cand_max;                    // register paths: most candidates ranked directly (else more radix digits)
+  uint64_t wait_ns;                // longest single wait on a dependency or a bulk copy
+  int hold_publish;                // test hook: no trade publishes its done flag (waits run out)
 };
 
 struct SelOut {
@@ -116,6 +112,14 @@ __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void latch(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {
+  return *reinterpret_cast<const volatile int32_t*>(p);
+}
 
 // ------------------------------------------------- bulk copies (TMA engine)
 //
@@ -125,7 +129,6 @@ __device__ __forceinline__ void latch(int32_t* err, int32_t code) { atomicCAS(er
 // of 4 entries; the adjacency buffers carry 16 spare entries at their end, so
 // the copy never leaves its allocation.
 
-constexpr uint32_t kTmaWaitLimit = 1u << 23;   // polls of an mbarrier before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -154,13 +157,15 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* m, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for phase `parity` of m (non-blocking polls with a short
-// sleep, about a second at most); false if it did not complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
-  for (uint32_t it = 0; it < kTmaWaitLimit; ++it) {
-    if (mbar_test_wait(m, parity)) return true;
+// sleep, at most wait_ns); false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, uint64_t wait_ns) {
+  if (mbar_test_wait(m, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (;;) {
     __nanosleep(64);
+    if (mbar_test_wait(m, parity)) return true;
+    if (globaltimer() - t0 > wait_ns) return false;
   }
-  return false;
 }
 
 // Entries [b0, b0 + L) of col staged at buf + stage_off(b0).
@@ -505,10 +510,12 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
             continue;
           }
           // in-order pass: s is complete or held by a running CTA that claimed it
-          // earlier, so the wait ends; the limit turns a broken invariant into an error
-          uint32_t polls = 0;
+          // earlier, so the wait ends; the time limit turns a broken invariant
+          // into an error, after which every other wait gives up at once
+          const uint64_t t0 = globaltimer();
           while (ld_acquire(c.done + s) != c.stamp) {
-            if (++polls > kWaitLimit) {
+            if (ld_volatile_i32(c.err) != 0) break;
+            if (globaltimer() - t0 > c.wait_ns) {
               latch(c.err, kErrResolve);
               break;
             }
@@ -542,7 +549,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     const bool lo_mine = (lo >> 1) == t32;
     const uint32_t top = static_cast<uint32_t>((lo_mine ? ek.lo_side : ek.hi_side) >> 48);
     w.top[i] = static_cast<uint16_t>(top);
-    w.far[i] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
+    w.far[i] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 57);
     if (!other && !tr.single) {
       m |= kInD;
       cnt_a += (r == 0);
@@ -676,12 +683,25 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     }
     tm.sync();
   }
-  // will the far trade consider this edge?  Write the stash byte.
+  // placement: each entry goes into the new row of its node after the trade
+  // (u's or v's row of step g+1) at a slot given by a scan over the team
+  int n0 = 0, n1 = 0;
+  for (int i = tm.rank; i < L; i += Team::N) {
+    const uint8_t m = w.meta[i];
+    const int side = (m & kR) ^ ((m & kFlip) ? 1 : 0);
+    n0 += side == 0;
+    n1 += side;
+  }
+  const int64_t pre = tm.exscan(static_cast<int64_t>(n0) | (static_cast<int64_t>(n1) << 32));
+  int s0 = static_cast<int>(pre & 0xffffffff), s1 = static_cast<int>(pre >> 32);
+  if (tm.rank == Team::N - 1 && (s0 + n0 != du || s1 + n1 != dv)) latch(c.err, kErrRowLength);
+  const int64_t ou = c.rp_next[c.M[2 * t]];
+  const int64_t ov = tr.single ? 0 : c.rp_next[c.M[2 * t + 1]];
   for (int i = tm.rank; i < L; i += Team::N) {
     const uint8_t m = w.meta[i];
     const int f = (m & kFlip) ? 1 : 0;
     int in_far = 0;
-    if (!(m & kUV)) {
+    if (!(m & kUV)) {   // will the far trade decide this edge?
       const int r = m & kR;
       const int sl = w.slot[i];
       const uint32_t s = w.hkey[sl] - 1u;
@@ -705,13 +725,18 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
         }
       }
     }
-    c.stash[tr.b0 + i] = static_cast<uint8_t>(f | (in_far << 1) | (in_far ? (w.far[i] << 2) : 0));
+    const int side = (m & kR) ^ f;
+    const int k = side ? s1++ : s0++;
+    if (k >= (side ? dv : du)) continue;   // counts checked above: never write outside the row
+    const int64_t slot = (side ? ov : ou) + k;
+    c.ph[slot] = entry_y(w, t2, i) | (in_far ? static_cast<int32_t>(0x80000000u) : 0);
+    c.fb[slot] = static_cast<uint8_t>(f | (in_far ? (w.far[i] << 1) : 0));
   }
   if (tm.rank == 0 && !tr.single) {
     c.thr_key[t] = tk;
     c.thr_tb[t] = tt;
-    c.thr_top[t] = static_cast<uint8_t>(tk >> 58);
-    if (publish_fence) {
+    c.thr_top[t] = static_cast<uint8_t>(tk >> 56);
+    if (publish_fence && !c.hold_publish) {
       __threadfence();
       st_release(c.done + t, c.stamp);
     }
@@ -719,9 +744,476 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   tm.sync();
 }
 
+// ------------------------------------------------ register-resident phase A
+//
+// The same decisions as phase_a for a trade whose L = deg u + deg v entries
+// fit the team's registers (J entries per member, entry i held by member
+// i mod N): each member keeps its entries' neighbour positions, key bits and
+// flags in registers across the passes, so the only shared-memory traffic is
+// the far-trade hash, one histogram and the few candidates of the threshold's
+// bin.  Used by the first pass only: a trade whose dependency has not
+// published yet is deferred to the in-order pass.
+
+// per-entry meta word
+constexpr uint32_t kMSlot = 0xFFFFu;        // hash slot of the far trade
+constexpr uint32_t kMR = 1u << 16;          // entry sits in v's row
+constexpr uint32_t kMCol = 1u << 17;        // neighbour at the odd position 2s+1
+constexpr uint32_t kMUV = 1u << 18;         // the edge {u, v}
+constexpr uint32_t kMInD = 1u << 19;        // element of D
+constexpr uint32_t kMFlip = 1u << 20;       // the trade moves the edge to its other node
+constexpr uint32_t kMValid = 1u << 21;      // an entry of the trade
+constexpr uint32_t kMMulti = 1u << 22;      // block of two or more edges
+constexpr int kMFarShift = 24;              // bits 24..30: top 7 bits of the far trade's key
+
+__host__ __device__ constexpr int hash_lg_c(int L) {
+  int lg = 1;
+  while ((1 << lg) < 2 * L) ++lg;
+  return lg;
+}
+
+// One team's workspace: a base address and a compile-time layout for trades
+// of at most LMAX entries and 2^B histogram bins.
+template <int LMAX, int B>
+struct RegWs {
+  static constexpr int kH = 1 << hash_lg_c(LMAX);
+  static constexpr size_t kCk = 0;                              // candidate keys
+  static constexpr size_t kCtb = kCk + kCand * 8;               // candidate tie-breaks
+  static constexpr size_t kSel = kCtb + kCand * 8;              // selection results shared by the team
+  static constexpr size_t kPw = kSel + ((sizeof(SelOut) + 15) & ~size_t(15));   // radix prefix (4 words)
+  static constexpr size_t kNc = kPw + 16;                       // candidate count
+  static constexpr size_t kHk = kNc + 16;                       // hash slot keys (far trade + 1; 0 = empty)
+  static constexpr size_t kHist = kHk + size_t(kH) * 4;         // radix histogram
+  static constexpr size_t kHf = kHist + (size_t(1) << B) * 4;   // slot flags: block matrix 0..3, flips 4..7
+  static constexpr size_t kBytes = (kHf + size_t(kH) + 15) & ~size_t(15);
+  char* base;
+  __device__ __forceinline__ uint64_t* ck() const { return reinterpret_cast<uint64_t*>(base + kCk); }
+  __device__ __forceinline__ uint64_t* ctb() const { return reinterpret_cast<uint64_t*>(base + kCtb); }
+  __device__ __forceinline__ SelOut* sel() const { return reinterpret_cast<SelOut*>(base + kSel); }
+  __device__ __forceinline__ uint32_t* pw() const { return reinterpret_cast<uint32_t*>(base + kPw); }
+  __device__ __forceinline__ int32_t* ncand() const { return reinterpret_cast<int32_t*>(base + kNc); }
+  __device__ __forceinline__ uint32_t* hk() const { return reinterpret_cast<uint32_t*>(base + kHk); }
+  __device__ __forceinline__ uint32_t* hist() const { return reinterpret_cast<uint32_t*>(base + kHist); }
+  __device__ __forceinline__ uint8_t* hf() const { return reinterpret_cast<uint8_t*>(base + kHf); }
+};
+
+// Word d of an element's 128-bit order (key, lo, hi): key high, key low, lo, hi.
+__device__ __forceinline__ uint32_t sel_word(int d, uint64_t key, uint32_t lo, uint32_t hi) {
+  return d == 0 ? static_cast<uint32_t>(key >> 32) : d == 1 ? static_cast<uint32_t>(key) : d == 2 ? lo : hi;
+}
+// B bits of the 128-bit order starting q bits below its top.
+__device__ __forceinline__ uint32_t sel_digit(int q, int B, uint64_t key, uint32_t lo, uint32_t hi) {
+  const int w = q >> 5, off = q & 31;
+  const uint64_t x = (static_cast<uint64_t>(sel_word(w, key, lo, hi)) << 32) |
+                     (w < 3 ? sel_word(w + 1, key, lo, hi) : 0u);
+  return static_cast<uint32_t>((x << off) >> (64 - B));
+}
+// Do the top q bits of the element's order equal those of the prefix pw?
+__device__ __forceinline__ bool sel_match(int q, const uint32_t* pw, uint64_t key, uint32_t lo, uint32_t hi) {
+  for (int d = 0; d < 4 && 32 * d < q; ++d) {
+    const uint32_t a = sel_word(d, key, lo, hi), b = pw[d];
+    const int bits = min(32, q - 32 * d);
+    if (bits == 32 ? a != b : (a >> (32 - bits)) != (b >> (32 - bits))) return false;
+  }
+  return true;
+}
+
+// The step-start positions (lo, hi) of an entry's edge.
+__device__ __forceinline__ void entry_lo_hi(uint32_t t2u, uint32_t m, uint32_t y, uint32_t* lo, uint32_t* hi) {
+  const uint32_t x = t2u + ((m & kMR) ? 1u : 0u);
+  *lo = min(x, y);
+  *hi = max(x, y);
+}
+
+template <class Team, int J, int B, bool kKeepKey, class Ws>
+__device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) {
+  static_assert(Team::N <= 2048 && Team::N * J < (1 << 20), "reduction fields: 20-bit count, 12-bit flags");
+  constexpr int NB = 1 << B;
+  const TradeRows tr = trade_rows(c, t);
+  const KeyCtx kc = key_ctx(c, t);
+  const int du = tr.du, L = tr.du + tr.dv;
+  const int lgH = hash_lg(L);
+  const int H = 1 << lgH;
+  const uint32_t t32 = static_cast<uint32_t>(t), T32 = static_cast<uint32_t>(c.T);
+  const uint32_t t2u = 2u * t32;
+  for (int i = tm.rank; i < H; i += Team::N) w.hk()[i] = 0u;
+  for (int i = tm.rank; i < (H + 3) / 4; i += Team::N) reinterpret_cast<uint32_t*>(w.hf())[i] = 0u;
+  for (int i = tm.rank; i < NB; i += Team::N) w.hist()[i] = 0u;
+  if (tm.rank == 0) *w.ncand() = 0;
+  tm.sync();
+  // entries into the hash: presence bit (row, column) in the far trade's slot
+  uint32_t y[J], mt[J], kt[J], kl[kKeepKey ? J : 1];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int i = tm.rank + j * Team::N;
+    y[j] = 0;
+    mt[j] = 0;
+    kt[j] = 0;
+    if (kKeepKey) kl[j] = 0;
+    if (i < L) {
+      const int32_t yy = __ldcg(c.col + tr.b0 + i);
+      const uint32_t r = i >= du ? 1u : 0u;
+      const uint32_t s = static_cast<uint32_t>(yy) >> 1;
+      uint32_t m = kMValid | (r ? kMR : 0u) | ((yy & 1) ? kMCol : 0u);
+      if (s == t32) m |= kMUV;
+      else m |= static_cast<uint32_t>(h_insert(w.hk(), w.hf(), lgH, s, 1u << (2 * r + (yy & 1))));
+      y[j] = static_cast<uint32_t>(yy);
+      mt[j] = m;
+    }
+  }
+  tm.sync();
+  // block analysis, keys, histogram of the first radix digit
+  bool defer = false, has_dependents = false, any_multi = false;
+  int cnt_a = 0;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    uint32_t m = mt[j];
+    if (!(m & kMValid) || (m & kMUV)) continue;
+    const int r = (m & kMR) ? 1 : 0;
+    const uint32_t colb = (m & kMCol) ? 1u : 0u;
+    const uint32_t s = y[j] >> 1;
+    const uint32_t f = w.hf()[m & kMSlot] & 15u;
+    int other = 0;   // the other row is adjacent to this neighbour when t acts
+    if (f & (f - 1u)) {
+      // a block of two or more edges: common neighbours and dependencies
+      m |= kMMulti;
+      any_multi = true;
+      const int u0 = f & 1, u1 = (f >> 1) & 1, v0 = (f >> 2) & 1, v1 = (f >> 3) & 1;
+      const int cu = u0 + u1, cv = v0 + v1;
+      if (!tr.single && s > t32 && s < T32 && (u0 + v0 == 1 || u1 + v1 == 1)) has_dependents = true;
+      int col_now = static_cast<int>(colb);
+      other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
+      if (!tr.single && s < t32 && (cu == 1 || cv == 1)) {
+        if (ld_acquire(c.done + s) != c.stamp) {   // first pass: leave it to the in-order pass
+          defer = true;
+          mt[j] = m;
+          continue;
+        }
+        // replay trade s's decisions on this block
+        int m1[2][2] = {{0, 0}, {0, 0}};
+        const int bits[2][2] = {{u0, u1}, {v0, v1}};
+        const int cnt_row[2] = {cu, cv};
+#pragma unroll
+        for (int rho = 0; rho < 2; ++rho)
+#pragma unroll
+          for (int gam = 0; gam < 2; ++gam) {
+            if (!bits[rho][gam]) continue;
+            int g2 = gam;
+            if (cnt_row[rho] == 1) {
+              const uint32_t x = t2u + rho, yb = 2u * s + gam;
+              g2 = far_keeps_low(c, kc, s, min(x, yb), max(x, yb)) ? 0 : 1;
+            }
+            m1[rho][g2] = 1;
+            if (rho == r && gam == static_cast<int>(colb)) col_now = g2;
+          }
+        other = m1[1 - r][col_now];
+      }
+    }
+    // both trades' keys of this edge (step-start positions)
+    const uint32_t x = t2u + r, yb = y[j];
+    const uint32_t lo = min(x, yb), hi = max(x, yb);
+    const EdgeKeys ek = edge_keys(kc, lo, hi);
+    const bool lo_mine = (lo >> 1) == t32;
+    const uint64_t own = lo_mine ? ek.lo_side : ek.hi_side;
+    const uint64_t far = lo_mine ? ek.hi_side : ek.lo_side;
+    kt[j] = static_cast<uint32_t>(own >> 32);
+    if (kKeepKey) kl[j] = static_cast<uint32_t>(own);
+    m |= static_cast<uint32_t>(far >> 57) << kMFarShift;
+    if (!other && !tr.single) {
+      m |= kMInD;
+      cnt_a += (r == 0);
+      atomicAdd(&w.hist()[kt[j] >> (32 - B)], 1u);
+    }
+    mt[j] = m;
+  }
+  // one reduction: |A_{u-v}| (bits 0..19) and, in 12-bit fields that hold a
+  // count over up to 1024 members, the members that saw a deferral, a later
+  // dependent trade, a multi-edge block
+  const int64_t tot = tm.sum(static_cast<int64_t>(cnt_a) | (static_cast<int64_t>(defer) << 20) |
+                             (static_cast<int64_t>(has_dependents) << 32) | (static_cast<int64_t>(any_multi) << 44));
+  if ((tot >> 20) & 0xfff) {
+    if (tm.rank == 0) {
+      c.done[t] = kDeferred;
+      atomicAdd(c.def_count, 1ull);
+    }
+    tm.sync();
+    return;
+  }
+  const int a = static_cast<int>(tot & 0xfffff);
+  const bool publish_fence = ((tot >> 32) & 0xfff) != 0;
+  const bool multi_any = ((tot >> 44) & 0xfff) != 0;
+  const bool no_thr = tr.single || a == 0;   // u keeps nothing of D
+  uint64_t tk = 0, tt = 0;
+  if (!no_thr) {
+    // the bin of the first digit (top B key bits) that holds the a-th smallest element
+    constexpr int BPM = (NB + Team::N - 1) / Team::N;
+    {
+      const int b0 = tm.rank * BPM;
+      int local = 0;
+#pragma unroll
+      for (int q = 0; q < BPM; ++q)
+        if (b0 + q < NB) local += static_cast<int>(w.hist()[b0 + q]);
+      int run = static_cast<int>(tm.exscan(local));
+#pragma unroll
+      for (int q = 0; q < BPM; ++q) {
+        const int b = b0 + q;
+        if (b < NB) {
+          const int hc = static_cast<int>(w.hist()[b]);
+          if (run < a && a <= run + hc) {
+            w.sel()->bin = b;
+            w.sel()->below = run;
+            w.sel()->cnt = hc;
+          }
+          run += hc;
+        }
+      }
+    }
+    tm.sync();
+    int qbits = B;              // top bits of the order fixed so far
+    int kk = a - w.sel()->below;  // rank sought among the elements sharing them
+    int cnt = w.sel()->cnt;
+    if (tm.rank == 0) {
+      w.pw()[0] = static_cast<uint32_t>(w.sel()->bin) << (32 - B);
+      w.pw()[1] = w.pw()[2] = w.pw()[3] = 0u;
+    }
+    tm.sync();
+    // more elements share the prefix than the candidate list holds (or the
+    // list is disabled): further B-bit digits of (key, lo, hi)
+    while (cnt > c.cand_max) {
+      for (int i = tm.rank; i < NB; i += Team::N) w.hist()[i] = 0u;
+      tm.sync();
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        if (!(mt[j] & kMInD)) continue;
+        uint32_t lo, hi;
+        entry_lo_hi(t2u, mt[j], y[j], &lo, &hi);
+        const uint64_t key = kKeepKey ? ((static_cast<uint64_t>(kt[j]) << 32) | kl[j]) : own_key(kc, t, lo, hi);
+        if (sel_match(qbits, w.pw(), key, lo, hi)) atomicAdd(&w.hist()[sel_digit(qbits, B, key, lo, hi)], 1u);
+      }
+      tm.sync();
+      {
+        const int b0 = tm.rank * BPM;
+        int local = 0;
+#pragma unroll
+        for (int q = 0; q < BPM; ++q)
+          if (b0 + q < NB) local += static_cast<int>(w.hist()[b0 + q]);
+        int run = static_cast<int>(tm.exscan(local));
+#pragma unroll
+        for (int q = 0; q < BPM; ++q) {
+          const int b = b0 + q;
+          if (b < NB) {
+            const int hc = static_cast<int>(w.hist()[b]);
+            if (run < kk && kk <= run + hc) {
+              w.sel()->bin = b;
+              w.sel()->below = run;
+              w.sel()->cnt = hc;
+            }
+            run += hc;
+          }
+        }
+      }
+      tm.sync();
+      const uint32_t dig = static_cast<uint32_t>(w.sel()->bin);
+      kk -= w.sel()->below;
+      cnt = w.sel()->cnt;
+      tm.sync();
+      if (tm.rank == 0) {   // append the digit to the prefix (it may straddle two words)
+        const int wd = qbits >> 5, off = qbits & 31;
+        const uint64_t d64 = static_cast<uint64_t>(dig) << (64 - B - off);
+        w.pw()[wd] |= static_cast<uint32_t>(d64 >> 32);
+        if (wd < 3) w.pw()[wd + 1] |= static_cast<uint32_t>(d64);
+      }
+      qbits += B;
+      tm.sync();
+    }
+    // rank the few elements that share the prefix by their full order
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if (!(mt[j] & kMInD)) continue;
+      if (qbits == B && (kt[j] >> (32 - B)) != (w.pw()[0] >> (32 - B))) continue;
+      uint32_t lo, hi;
+      entry_lo_hi(t2u, mt[j], y[j], &lo, &hi);
+      const uint64_t key = kKeepKey ? ((static_cast<uint64_t>(kt[j]) << 32) | kl[j]) : own_key(kc, t, lo, hi);
+      if (qbits > B && !sel_match(qbits, w.pw(), key, lo, hi)) continue;
+      if (cnt == 1) {
+        w.sel()->key = key;
+        w.sel()->tb = tie_break(lo, hi);
+      } else {
+        const int q = atomicAdd(w.ncand(), 1);
+        w.ck()[q] = key;
+        w.ctb()[q] = tie_break(lo, hi);
+      }
+    }
+    tm.sync();
+    if (cnt > 1) {
+      for (int q = tm.rank; q < cnt; q += Team::N) {
+        int rk = 0;
+        for (int p = 0; p < cnt; ++p) rk += (w.ck()[p] < w.ck()[q] || (w.ck()[p] == w.ck()[q] && w.ctb()[p] < w.ctb()[q]));
+        if (rk == kk - 1) {
+          w.sel()->key = w.ck()[q];
+          w.sel()->tb = w.ctb()[q];
+        }
+      }
+      tm.sync();
+    }
+    tk = w.sel()->key;
+    tt = w.sel()->tb;
+  }
+  // own decisions: u keeps the elements at or below the threshold
+  const uint32_t tk32 = static_cast<uint32_t>(tk >> 32);
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const uint32_t m = mt[j];
+    if (!(m & kMInD)) continue;
+    const int r = (m & kMR) ? 1 : 0;
+    bool low;
+    if (no_thr) {
+      low = false;
+    } else if (kt[j] != tk32) {
+      low = kt[j] < tk32;
+    } else {
+      uint32_t lo, hi;
+      entry_lo_hi(t2u, m, y[j], &lo, &hi);
+      const uint64_t key = kKeepKey ? ((static_cast<uint64_t>(kt[j]) << 32) | kl[j]) : own_key(kc, t, lo, hi);
+      low = at_or_below(key, tie_break(lo, hi), tk, tt);
+    }
+    if ((low ? 0 : 1) != r) {
+      mt[j] = m | kMFlip;
+      if (m & kMMulti) flag_or(w.hf(), static_cast<int>(m & kMSlot), 16u << (2 * r + ((m & kMCol) ? 1 : 0)));
+    }
+  }
+  if (multi_any) tm.sync();
+  // placement: each entry goes into the new row of its node after the trade
+  // (u's or v's row of step g+1) at a slot given by a scan over the team
+  int n0 = 0, n1 = 0;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const uint32_t m = mt[j];
+    if (!(m & kMValid)) continue;
+    const int side = ((m & kMR) ? 1 : 0) ^ ((m & kMFlip) ? 1 : 0);
+    n0 += side == 0;
+    n1 += side;
+  }
+  const int64_t pre = tm.exscan(static_cast<int64_t>(n0) | (static_cast<int64_t>(n1) << 32));
+  int s0 = static_cast<int>(pre & 0xffffffff), s1 = static_cast<int>(pre >> 32);
+  if (tm.rank == Team::N - 1 && (s0 + n0 != du || s1 + n1 != tr.dv)) latch(c.err, kErrRowLength);
+  const int64_t ou = c.rp_next[c.M[2 * t]];
+  const int64_t ov = tr.single ? 0 : c.rp_next[c.M[2 * t + 1]];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const uint32_t m = mt[j];
+    if (!(m & kMValid)) continue;
+    const int r = (m & kMR) ? 1 : 0;
+    const int f = (m & kMFlip) ? 1 : 0;
+    // will the far trade decide this edge?
+    int in_far = 0;
+    if (!(m & kMUV)) {
+      const uint32_t s = y[j] >> 1;
+      if (tr.single || s < t32) {
+        const uint32_t fl = w.hf()[m & kMSlot];
+        in_far = __popc(r ? (fl & 12u) : (fl & 3u)) == 1;   // trade s acted before t: initial block
+      } else if (s < T32) {
+        if (!(m & kMMulti)) {
+          in_far = 1;
+        } else {                           // block after t's own decisions: presence bits 0..3, flips 4..7
+          const uint32_t fl = w.hf()[m & kMSlot];
+          const int myrow = r ^ f;
+          int same = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (!((fl >> q) & 1)) continue;
+            same += (((q >> 1) ^ ((fl >> (4 + q)) & 1)) == myrow);
+          }
+          in_far = (same == 1);
+        }
+      }
+    }
+    const int side = r ^ f;
+    const int k = side ? s1++ : s0++;
+    if (k >= (side ? tr.dv : du)) continue;   // counts checked above: never write outside the row
+    const int64_t slot = (side ? ov : ou) + k;
+    c.ph[slot] = static_cast<int32_t>(y[j] | (static_cast<uint32_t>(in_far) << 31));
+    c.fb[slot] = static_cast<uint8_t>(f | (in_far ? (((m >> kMFarShift) & 127u) << 1) : 0u));
+  }
+  if (tm.rank == 0 && !tr.single) {
+    c.thr_key[t] = tk;
+    c.thr_tb[t] = tt;
+    c.thr_top[t] = static_cast<uint8_t>(tk >> 56);
+    if (publish_fence && !c.hold_publish) {
+      __threadfence();
+      st_release(c.done + t, c.stamp);
+    }
+  }
+  tm.sync();
+}
+
+// Phase A of small trades, one warp per trade (L <= 32 J): eight independent
+// warps per CTA, each with its own workspace; no CTA barriers.
+constexpr int kWarpJ = 4;                       // entries per lane: trades up to 128 entries
+constexpr int kWarpB = 7;                       // first radix digit: 128 bins
+constexpr int kWarpWarps = 8;                   // warps per CTA
+using WarpWs = RegWs<32 * kWarpJ, kWarpB>;
+
+__global__ void __launch_bounds__(32 * kWarpWarps) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ list,
+                                                                  const int64_t* __restrict__ count) {
+  extern __shared__ __align__(16) char wsm[];
+  const int wid = threadIdx.x >> 5;
+  const WarpWs w{wsm + WarpWs::kBytes * wid};
+  WarpTeam tm;
+  const int64_t len = *count;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * kWarpWarps;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * kWarpWarps + wid; q < len; q += step)
+    phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, list[q], w);
+}
+
+
+// Phase A of larger trades, one CTA of NT threads per trade (J entries per
+// thread in registers, so L <= NT J): trades of `list` with lmin < L <= lmax;
+// the others are left to another launch.
+template <int NT, int J, int B>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_cta(StepCtx c, const int32_t* __restrict__ list,
+                                                                     const int64_t* __restrict__ count, int lmin,
+                                                                     int lmax) {
+  extern __shared__ __align__(16) char csm[];
+  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
+  BlockTeam<NT> tm(red);
+  const RegWs<NT * J, B> w{csm};
+  const int64_t len = *count;
+  for (int64_t q = blockIdx.x; q < len; q += gridDim.x) {
+    const int64_t t = list[q];
+    const TradeRows tr = trade_rows(c, t);
+    const int L = tr.du + tr.dv;
+    if (L <= lmin || L > lmax) continue;   // the same test in every thread
+    phase_a_reg<BlockTeam<NT>, J, B, false>(tm, c, t, w);
+  }
+}
+constexpr int kCtaJ = 4;         // entries per thread: up to 1024 on 256 threads, 4096 on 1024
+constexpr int kCta256B = 10;     // 1024 bins
+constexpr int kCta1024B = 12;    // 4096 bins
+constexpr size_t kCta256Ws = RegWs<256 * kCtaJ, kCta256B>::kBytes;
+constexpr size_t kCta1024Ws = RegWs<1024 * kCtaJ, kCta1024B>::kBytes;
+
+// Phase A of the largest trades (L > lmin) with the general procedure:
+// entries, keys and flags in a global-memory workspace slice per CTA.
+__global__ void __launch_bounds__(kBigThreads, 1) k_phase_a_huge(StepCtx c, const int32_t* __restrict__ list,
+                                                                const int64_t* __restrict__ count, int lmin,
+                                                                char* gws, size_t slice) {
+  __shared__ int64_t red[BlockTeam<kBigThreads>::kRedSlots];
+  __shared__ SelOut sel;
+  BlockTeam<kBigThreads> tm(red);
+  const int64_t len = *count;
+  for (int64_t q = blockIdx.x; q < len; q += gridDim.x) {
+    const int64_t t = list[q];
+    const TradeRows tr = trade_rows(c, t);
+    const int L = tr.du + tr.dv;
+    if (L <= lmin) continue;
+    if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
+    phase_a(tm, c, t, carve_a(gws + slice * blockIdx.x, L), &sel);
+  }
+}
+
 // ---------------------------------------------------------- classification
 
-// Class of each trade (tile / 256 / 1024 threads) and its tile weight.
+// Class of each trade: small (one warp), medium (256 threads), large (1024).
 __global__ void k_class_flags(StepCtx c, int64_t ntasks, int tile_max, int block_max, int32_t* __restrict__ f) {
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
     const TradeRows tr = trade_rows(c, t);
@@ -730,483 +1222,61 @@ __global__ void k_class_flags(StepCtx c, int64_t ntasks, int tile_max, int block
     f[t] = cls == 0;
     f[ntasks + t] = cls == 1;
     f[2 * ntasks + t] = cls == 2;
-    f[3 * ntasks + t] = cls == 0 ? max(L, kTileCap / kTileTrades) : 0;
   }
 }
 
-// Stable compaction of each class into index order, plus tile offsets.
+// Stable compaction of each class into index order.
 __global__ void k_class_scatter(int64_t ntasks, const int32_t* __restrict__ f, const int64_t* __restrict__ sc,
-                                int32_t* __restrict__ l0, int32_t* __restrict__ l1, int32_t* __restrict__ l2,
-                                int64_t* __restrict__ tile_off) {
+                                int32_t* __restrict__ l0, int32_t* __restrict__ l1, int32_t* __restrict__ l2) {
   const int64_t n1 = ntasks + 1;
   for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
-    if (f[t]) {
-      const int64_t k = sc[t];
-      l0[k] = static_cast<int32_t>(t);
-      tile_off[k] = sc[3 * n1 + t];
-    } else if (f[ntasks + t]) {
-      l1[sc[n1 + t]] = static_cast<int32_t>(t);
-    } else {
-      l2[sc[2 * n1 + t]] = static_cast<int32_t>(t);
-    }
+    if (f[t]) l0[sc[t]] = static_cast<int32_t>(t);
+    else if (f[ntasks + t]) l1[sc[n1 + t]] = static_cast<int32_t>(t);
+    else l2[sc[2 * n1 + t]] = static_cast<int32_t>(t);
   }
 }
 
-// First tile-class trade of every tile (tile i = weight offsets [i C, (i+1) C)),
-// plus the end sentinel; one thread per tile-class trade.
-__global__ void k_tile_first(const int64_t* __restrict__ tile_off, const int64_t* __restrict__ counts,
-                             int32_t* __restrict__ tile_first) {
-  const int64_t ntr = counts[0], total_w = counts[3];
-  const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
-  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < ntr; k += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t cur = tile_off[k] / kTileCap;
-    const int64_t prev = k ? tile_off[k - 1] / kTileCap : -1;
-    for (int64_t i = prev + 1; i <= cur; ++i) tile_first[i] = static_cast<int32_t>(k);
-    if (k == ntr - 1)
-      for (int64_t i = cur + 1; i <= ntiles; ++i) tile_first[i] = static_cast<int32_t>(ntr);
-  }
-}
-
-// ---------------------------------------------------------------- tile path
-
-// Shared memory of the tile kernels is budgeted so that four 256-thread CTAs
-// fit on an SM (228 KB, 1 KB reserved per CTA): the threshold kernel's
-// TileShared + TileA must stay below 56 KB.
-struct TileShared {              // per-trade data of the current tile
-  int64_t b0[kTileTrades];
-  int32_t t[kTileTrades];
-  int32_t acnt[kTileTrades];    // |A_{u-v}| (phase A)
-  int32_t flags[kTileTrades];   // bit0 deferred, bit1 has a dependent later trade
-  int16_t du[kTileTrades], dv[kTileTrades], lofs[kTileTrades];
-  int64_t first, base;
-  int32_t ntr, nslots;
-};
-
-// Per-entry arrays of a tile (phase-specific layouts provide them).
-struct TileEntries {
-  int32_t* y;
-  uint16_t* owner;
-  KeyCtx* kc;        // per trade, filled only when non-null
-};
-
-__device__ __forceinline__ int tile_owner(const TileShared& sh, int e) {
-  int lo = 0, hi = sh.ntr;   // last local trade with lofs <= e
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (sh.lofs[mid] <= e) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-// Set up tile `tile`: its trades and entries (y) in shared memory.  Returns
-// false when the tile is empty.
-__device__ bool tile_setup(const StepCtx& c, TileShared& sh, const TileEntries& te, const int32_t* list,
-                           const int64_t* tile_off, const int32_t* tile_first, int64_t ntrades, int64_t total_w,
-                           int64_t tile) {
-  if (threadIdx.x == 0) {
-    const int64_t a = tile_first[tile];
-    const int64_t b = tile_first[tile + 1];
-    sh.first = a;
-    sh.ntr = static_cast<int32_t>(b - a);
-    sh.base = a < ntrades ? tile_off[a] : 0;
-    sh.nslots = static_cast<int32_t>((b < ntrades ? tile_off[b] : total_w) - sh.base);
-  }
-  __syncthreads();
-  if (sh.ntr == 0) return false;
-  for (int j = threadIdx.x; j < sh.ntr; j += blockDim.x) {
-    const int64_t k = sh.first + j;
-    const int32_t t = list[k];
-    const TradeRows tr = trade_rows(c, t);
-    sh.t[j] = t;
-    if (te.kc) te.kc[j] = key_ctx(c, t);
-    sh.b0[j] = tr.b0;
-    sh.du[j] = static_cast<int16_t>(tr.du);
-    sh.dv[j] = static_cast<int16_t>(tr.dv);
-    sh.lofs[j] = static_cast<int16_t>(tile_off[k] - sh.base);
-    sh.acnt[j] = 0;
-    sh.flags[j] = 0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < sh.nslots; e += blockDim.x) {
-    const int k = tile_owner(sh, e);
-    const int i = e - sh.lofs[k];
-    if (i < sh.du[k] + sh.dv[k]) {
-      te.owner[e] = static_cast<uint16_t>(k);
-      if (te.y) te.y[e] = __ldcg(c.col + sh.b0[k] + i);
-    } else {
-      te.owner[e] = kNoOwner;
-    }
-  }
-  __syncthreads();
-  return true;
-}
-
-// Phase A for a tile of small trades, one thread per entry.  The 2x2 block
-// matrices come from a hash keyed by (local trade, far trade), the
-// |A_{u-v}|-th smallest key of every trade from a radix select with 4-bit
-// digits that all trades of the tile run together.
-struct TileA {
-  KeyCtx kc[kTileTrades];                 // key parameters of each trade's graph
-  uint64_t key[kTileSlots];               // full own key
-  unsigned long long hash[kTileHash];     // (key+1) << 16 | flags
-  union {
-    uint32_t hist[kTileTrades * 8];       // 16 bins per trade, two 16-bit counters per word
-    uint64_t thr_tb[kTileTrades];         // after the selection: threshold tie-break
-  };
-  uint64_t prefix[kTileTrades];           // radix-select prefix, then the threshold key
-  int32_t y[kTileSlots];
-  uint16_t owner[kTileSlots];
-  uint8_t meta[kTileSlots];
-  uint8_t far[kTileSlots];
-  int16_t kk[kTileTrades];                // rank still sought (1-based; |D| <= 128)
-  int8_t shift[kTileTrades];
-};
-
-static_assert(sizeof(TileShared) + sizeof(TileA) + 1024 <= 233472 / 4, "tile threshold kernel: 4 CTAs per SM");
-
-__device__ __forceinline__ uint64_t tile_hkey(int k, int64_t s) {
-  return ((static_cast<uint64_t>(k) << 31) | static_cast<uint64_t>(s)) + 1;
-}
-__device__ __forceinline__ uint32_t tile_hslot(uint64_t hk) {
-  const uint32_t x = static_cast<uint32_t>(hk) * 0x9E3779B1u ^ static_cast<uint32_t>(hk >> 32) * 0x85EBCA6Bu;
-  return x >> (32 - kTileHashLg);
-}
-__device__ void tile_hinsert(unsigned long long* h, uint64_t hk, uint32_t bit) {
-  uint32_t s = tile_hslot(hk);
-  const unsigned long long want = static_cast<unsigned long long>(hk) << 16;
-  for (;;) {
-    unsigned long long cur = h[s];
-    if (cur == 0ull) {
-      const unsigned long long prev = atomicCAS(&h[s], 0ull, want | bit);
-      if (prev == 0ull) return;
-      cur = prev;
-    }
-    if ((cur >> 16) == hk) {
-      atomicOr(reinterpret_cast<unsigned int*>(&h[s]), bit);
-      return;
-    }
-    s = (s + 1) & (kTileHash - 1);
-  }
-}
-__device__ __forceinline__ int tile_hfind(const unsigned long long* h, uint64_t hk) {
-  uint32_t s = tile_hslot(hk);
-  for (;;) {
-    const unsigned long long cur = h[s];
-    if (cur == 0ull) return -1;
-    if ((cur >> 16) == hk) return static_cast<int>(s);
-    s = (s + 1) & (kTileHash - 1);
-  }
-}
-
-// Tile order: round robin over the CTAs (`blocked` = 0), or each CTA a run of
-// consecutive tiles (`blocked` = 1).  A trade defers when a trade it depends
-// on has not published yet: in one large graph those are spread over all
-// earlier indices, and round robin finishes them first; in a batch of small
-// graphs they sit in the tiles just before, which a CTA running consecutive
-// tiles has already done.
-__global__ void __launch_bounds__(kTileThreads) k_phase_a_tile(StepCtx c, const int32_t* __restrict__ list,
-                                                               const int64_t* __restrict__ tile_off,
-                                                               const int32_t* __restrict__ tile_first,
-                                                               const int64_t* __restrict__ counts, int blocked) {
-  __shared__ TileShared sh;
-  extern __shared__ __align__(16) char dsm[];
-  TileA& ta = *reinterpret_cast<TileA*>(dsm);
-  const int64_t ntrades = counts[0], total_w = counts[3];
-  const int64_t ntiles = (total_w + kTileCap - 1) / kTileCap;
-  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;   // tiles per CTA when blocked
-  for (int64_t i = 0;; ++i) {
-    if (blocked && i >= per) break;
-    const int64_t tile = blocked ? blockIdx.x * per + i : blockIdx.x + i * gridDim.x;
-    if (tile >= ntiles) break;
-    for (int i = threadIdx.x; i < kTileHash; i += blockDim.x) ta.hash[i] = 0ull;
-    if (!tile_setup(c, sh, TileEntries{ta.y, ta.owner, ta.kc}, list, tile_off, tile_first, ntrades, total_w,
-                    tile))
-      continue;
-    const int E = sh.nslots;
-    // entries into the hash: presence bit (row, column) per (trade, far trade)
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = ta.owner[e];
-      if (k == kNoOwner) continue;
-      const int32_t yy = ta.y[e];
-      const int64_t s = yy >> 1;
-      if (s == sh.t[k]) continue;
-      const int r = (e - sh.lofs[k]) >= sh.du[k];
-      tile_hinsert(ta.hash, tile_hkey(k, s), 1u << (2 * r + (yy & 1)));
-    }
-    __syncthreads();
-    // block analysis, dependencies, keys
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = ta.owner[e];
-      if (k == kNoOwner) continue;
-      const int64_t t = sh.t[k], t2 = 2 * t;
-      const int r = (e - sh.lofs[k]) >= sh.du[k];
-      const int32_t yy = ta.y[e];
-      const int64_t s = yy >> 1;
-      const bool single = (t2 + 1 >= c.n);
-      ta.far[e] = 0;
-      if (s == t) {
-        ta.meta[e] = static_cast<uint8_t>(r | kUV);
-        continue;
-      }
-      const int slot = tile_hfind(ta.hash, tile_hkey(k, s));
-      const uint32_t bits = static_cast<uint32_t>(ta.hash[slot]) & 15u;
-      const int u0 = bits & 1, u1 = (bits >> 1) & 1, v0 = (bits >> 2) & 1, v1 = (bits >> 3) & 1;
-      const int cu = u0 + u1, cv = v0 + v1;
-      uint8_t m = static_cast<uint8_t>(r | (u0 << 4) | (u1 << 5) | (v0 << 6) | (v1 << 7));
-      const bool multi = (bits & (bits - 1u)) != 0;   // two or more block edges (rare)
-      if (multi && !single && s > t && s < c.T && (u0 + v0 == 1 || u1 + v1 == 1)) atomicOr(&sh.flags[k], 2);
-      int col_now = yy & 1;
-      int other = 0;   // a single edge leaves the other row without this neighbour
-      if (multi) other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
-      if (multi && !single && s < t && (cu == 1 || cv == 1)) {
-        if (ld_acquire(c.done + s) != c.stamp) {
-          atomicOr(&sh.flags[k], 1);
-          continue;
-        }
-        int m1[2][2] = {{0, 0}, {0, 0}};
-        const int bb[2][2] = {{u0, u1}, {v0, v1}};
-        const int cnt_row[2] = {cu, cv};
-#pragma unroll
-        for (int rho = 0; rho < 2; ++rho)
-#pragma unroll
-          for (int gam = 0; gam < 2; ++gam) {
-            if (!bb[rho][gam]) continue;
-            int g2 = gam;
-            if (cnt_row[rho] == 1) {
-              const uint32_t x = static_cast<uint32_t>(t2 + rho), y = static_cast<uint32_t>(2 * s + gam);
-              g2 = far_keeps_low(c, ta.kc[k], s, min(x, y), max(x, y)) ? 0 : 1;
-            }
-            m1[rho][g2] = 1;
-            if (rho == r && gam == (yy & 1)) col_now = g2;
-          }
-        other = m1[1 - r][col_now];
-      }
-      const uint32_t x = static_cast<uint32_t>(t2 + r), y = static_cast<uint32_t>(yy);
-      const uint32_t lo = min(x, y), hi = max(x, y);
-      const EdgeKeys ek = edge_keys(ta.kc[k], lo, hi);
-      const bool lo_mine = (lo >> 1) == static_cast<uint32_t>(t);
-      ta.key[e] = lo_mine ? ek.lo_side : ek.hi_side;
-      ta.far[e] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 58);
-      if (!other && !single) {
-        m |= kInD;
-        if (r == 0) atomicAdd(&sh.acnt[k], 1);
-      }
-      ta.meta[e] = m;
-    }
-    __syncthreads();
-    // deferred trades leave; the others start selecting their a-th smallest key
-    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
-      const int32_t t = sh.t[k];
-      if (sh.flags[k] & 1) {
-        c.done[t] = kDeferred;
-        atomicAdd(c.def_count, 1ull);
-      }
-      const bool skip = (sh.flags[k] & 1) || sh.acnt[k] == 0 || 2 * int64_t(t) + 1 >= c.n;
-      ta.kk[k] = static_cast<int16_t>(skip ? 0 : sh.acnt[k]);
-      ta.shift[k] = skip ? -1 : 60;
-      ta.prefix[k] = 0;
-    }
-    __syncthreads();
-    for (int round = 0; round < 16; ++round) {
-      for (int i = threadIdx.x; i < kTileTrades * 8; i += blockDim.x) ta.hist[i] = 0;
-      __syncthreads();
-      for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const int k = ta.owner[e];
-        if (k == kNoOwner || !(ta.meta[e] & kInD)) continue;
-        const int sft = ta.shift[k];
-        if (sft < 0) continue;
-        const uint64_t key = ta.key[e];
-        if (sft < 60 && (key >> (sft + 4)) != (ta.prefix[k] >> (sft + 4))) continue;
-        const uint32_t d = static_cast<uint32_t>(key >> sft) & 15u;
-        atomicAdd(&ta.hist[k * 8 + (d >> 1)], (d & 1) ? 0x10000u : 1u);
-      }
-      __syncthreads();
-      bool more = false;
-      for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
-        const int sft = ta.shift[k];
-        if (sft < 0) continue;
-        int below = 0;
-        const int kk = ta.kk[k];
-        for (int b = 0; b < 16; ++b) {
-          const uint32_t w = ta.hist[k * 8 + (b >> 1)];
-          const int cb = static_cast<int>((b & 1) ? (w >> 16) : (w & 0xffffu));
-          if (below < kk && kk <= below + cb) {
-            ta.kk[k] = static_cast<int16_t>(kk - below);
-            ta.prefix[k] |= static_cast<uint64_t>(b) << sft;
-            if (cb == 1 || sft == 0) {
-              ta.shift[k] = static_cast<int8_t>(-2 - sft);   // resolved; -2 - shift keeps the last shift
-            } else {
-              ta.shift[k] = static_cast<int8_t>(sft - 4);
-              more = true;
-            }
-            break;
-          }
-          below += cb;
-        }
-      }
-      if (!__syncthreads_or(more)) break;   // every thread takes the same exit
-    }
-    for (int k = threadIdx.x; k < kTileTrades; k += blockDim.x) ta.thr_tb[k] = 0;   // histogram no longer needed
-    __syncthreads();
-    // the threshold element of each trade: the one matching its prefix (ties on
-    // all 64 bits, which need the (lo, hi) order, are ranked explicitly)
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = ta.owner[e];
-      if (k == kNoOwner || !(ta.meta[e] & kInD)) continue;
-      const int code = ta.shift[k];
-      if (code > -2) continue;
-      const int sft = -2 - code;
-      const uint64_t key = ta.key[e];
-      if ((key >> sft) != (ta.prefix[k] >> sft)) continue;
-      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
-      const uint8_t m = ta.meta[e];
-      const uint64_t tb = tie_break(lo_of(t2, m, ta.y[e]), hi_of(t2, m, ta.y[e]));
-      if (sft > 0) {
-        ta.prefix[k] = key;
-        ta.thr_tb[k] = tb;
-      } else {   // every candidate has this exact key
-        const int lo0 = sh.lofs[k], L = sh.du[k] + sh.dv[k];
-        int r = 0;
-        for (int j = lo0; j < lo0 + L; ++j) {
-          if (j == e || !(ta.meta[j] & kInD) || ta.key[j] != key) continue;
-          r += tie_break(lo_of(t2, ta.meta[j], ta.y[j]), hi_of(t2, ta.meta[j], ta.y[j])) < tb;
-        }
-        if (r == ta.kk[k] - 1) ta.thr_tb[k] = tb;
-      }
-    }
-    __syncthreads();
-    // own decisions; flips go into the hash for the far-side test
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = ta.owner[e];
-      if (k == kNoOwner || (sh.flags[k] & 1)) continue;
-      const uint8_t m = ta.meta[e];
-      if (!(m & kInD)) continue;
-      const int64_t t2 = 2 * static_cast<int64_t>(sh.t[k]);
-      const int r = m & kR;
-      const bool has_thr = ta.shift[k] <= -2;
-      const bool low = has_thr && at_or_below(ta.key[e], tie_break(lo_of(t2, m, ta.y[e]), hi_of(t2, m, ta.y[e])),
-                                              ta.prefix[k], ta.thr_tb[k]);
-      if ((low ? 0 : 1) != r) {
-        ta.meta[e] = m | kFlip;
-        const int32_t yy = ta.y[e];
-        const int slot = tile_hfind(ta.hash, tile_hkey(k, yy >> 1));
-        atomicOr(reinterpret_cast<unsigned int*>(&ta.hash[slot]), 16u << (2 * r + (yy & 1)));
-      }
-    }
-    __syncthreads();
-    // will the far trade consider this edge?  Write the stash byte.
-    for (int e = threadIdx.x; e < E; e += blockDim.x) {
-      const int k = ta.owner[e];
-      if (k == kNoOwner || (sh.flags[k] & 1)) continue;
-      const uint8_t m = ta.meta[e];
-      const int f = (m & kFlip) ? 1 : 0;
-      int in_far = 0;
-      const int64_t t = sh.t[k];
-      if (!(m & kUV)) {
-        const int r = m & kR;
-        const int32_t yy = ta.y[e];
-        const int64_t s = yy >> 1;
-        const int u0 = (m >> 4) & 1, u1 = (m >> 5) & 1, v0 = (m >> 6) & 1, v1 = (m >> 7) & 1;
-        const int cr = r ? (v0 + v1) : (u0 + u1);
-        if (2 * t + 1 >= c.n || s < t) {
-          in_far = (cr == 1);
-        } else if (s < c.T) {
-          if (u0 + u1 + v0 + v1 == 1) {
-            in_far = 1;
-          } else {   // block after t's own decisions: presence bits 0..3, flips 4..7
-            const uint32_t fl = static_cast<uint32_t>(ta.hash[tile_hfind(ta.hash, tile_hkey(k, s))]);
-            const int myrow = r ^ f;
-            int same = 0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (!((fl >> q) & 1)) continue;
-              same += (((q >> 1) ^ ((fl >> (4 + q)) & 1)) == myrow);
-            }
-            in_far = (same == 1);
-          }
-        }
-      }
-      c.stash[sh.b0[k] + (e - sh.lofs[k])] =
-          static_cast<uint8_t>(f | (in_far << 1) | (in_far ? (ta.far[e] << 2) : 0));
-    }
-    // publish every completed trade's threshold (fenced when a later trade waits on it)
-    for (int k = threadIdx.x; k < sh.ntr; k += blockDim.x) {
-      const int32_t t = sh.t[k];
-      if ((sh.flags[k] & 1) || 2 * int64_t(t) + 1 >= c.n) continue;
-      const bool has_thr = ta.shift[k] <= -2;
-      const uint64_t tk = has_thr ? ta.prefix[k] : 0;
-      c.thr_key[t] = tk;
-      c.thr_tb[t] = has_thr ? ta.thr_tb[k] : 0;
-      c.thr_top[t] = static_cast<uint8_t>(tk >> 58);
-      if (sh.flags[k] & 2) {
-        __threadfence();
-        st_release(c.done + t, c.stamp);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// --------------------------------------------------------- flat rebuild
+// ------------------------------------------------------ rebuild: fix-up
 //
-// Phase B over the whole position-space adjacency at once: a CTA takes a
-// chunk of 2048 consecutive entries, each thread 8 consecutive entries.  Trade
-// t owns entries [rp[2t], rp[2t+2]); the trades a chunk touches go to a
-// shared table (start, u/v boundary, new row offsets), or are looked up in
-// global memory when a chunk spans more trades than the table holds (only
-// with many empty trades).  Entries of the same (trade, new side) in a warp
-// claim their slots together with one global atomic on the trade's counter
-// (rows are sets; a counter past the row's degree latches an error).
+// Phase A leaves every entry in its new row (step g+1 layout) as a
+// placeholder: the far end's step-g position y with bit 31 set when the far
+// trade decides the edge, and a side byte (bit 0 the own trade's flip, bits
+// 1..7 the top 7 bits of the far trade's key for the edge).  The fix-up
+// replaces each placeholder by the step-(g+1) position of the far end: y
+// itself, or the node of y's trade that the trade's threshold gives it.  One
+// 8-byte record per far trade holds both of its nodes' new positions and its
+// threshold's top 8 bits; the pass runs once per slice of far trades small
+// enough for the records to stay in L2, each pass reading every placeholder
+// and writing the entries of its slice.  A prefix tie (1 in 128) needs the
+// full key, hence the edge's own end at the start of the step: the node of
+// the entry's row (found by a search of the chunk's row offsets) before the
+// own flip.
 
-constexpr int kFlatThreads = 256;
-constexpr int kFlatPer = 8;                              // consecutive entries per thread
-constexpr int kFlatChunk = kFlatThreads * kFlatPer;      // entries per chunk
-constexpr int kFlatTrades = 512;                         // trades in the shared table
+constexpr int kFixThreads = 256;
+constexpr int kFixPer = 8;                             // consecutive entries per thread
+constexpr int kFixChunk = kFixThreads * kFixPer;       // entries per chunk
 
-struct FlatTrade {
-  int64_t start, b1;    // first entry, first entry of v's row
-  int64_t ou, ov;       // new row offsets of u and v
-  int32_t du, dv;
-};
-
-__device__ __forceinline__ FlatTrade flat_trade(const StepCtx& c, int64_t t) {
-  FlatTrade f;
-  f.start = c.rp[2 * t];
-  f.b1 = c.rp[2 * t + 1];
-  const bool single = 2 * t + 1 >= c.n;
-  const int64_t end = single ? f.b1 : c.rp[2 * t + 2];
-  f.du = static_cast<int32_t>(f.b1 - f.start);
-  f.dv = static_cast<int32_t>(end - f.b1);
-  const int32_t pu = c.M[2 * t];
-  f.ou = c.rp_next[pu];
-  bool bad = c.rp_next[pu + 1] - f.ou != f.du;
-  f.ov = 0;
-  if (!single) {
-    const int32_t pv = c.M[2 * t + 1];
-    f.ov = c.rp_next[pv];
-    bad |= c.rp_next[pv + 1] - f.ov != f.dv;
+// Rows whose entries contain each chunk's first entry (one thread per row:
+// every chunk start lies in exactly one non-empty row); the last entry holds
+// the last row.
+__global__ void k_chunk_rows(int64_t nrows, const int64_t* __restrict__ rp, int64_t nchunks,
+                             int32_t* __restrict__ chunk_row) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < nrows; p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t a = rp[p], b = rp[p + 1];
+    for (int64_t ch = (a + kFixChunk - 1) / kFixChunk; ch < nchunks && ch * kFixChunk < b; ++ch)
+      chunk_row[ch] = static_cast<int32_t>(p);
+    if (p == nrows - 1) chunk_row[nchunks] = static_cast<int32_t>(p);
   }
-  if (bad) latch(c.err, kErrRowLength);
-  return f;
 }
 
-// Last trade in [lo, hi] whose first entry is <= e (global row offsets).
-__device__ __forceinline__ int64_t flat_owner(const StepCtx& c, int64_t lo, int64_t hi, int64_t e) {
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (c.rp[2 * mid] <= e) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// What the rebuild needs of a far trade s, in one record: the new positions
-// of its two nodes and the top 6 bits of its threshold key.  Up to 2^29
-// positions it fits 8 bytes (29 + 29 + 6 bits), else 16.
-constexpr int64_t kNarrowPackMax = int64_t(1) << 29;
+// What the fix-up needs of a far trade s: the new positions of its two nodes
+// and the top 8 bits of its threshold key.  Up to 2^28 positions it fits 8
+// bytes (28 + 28 + 8 bits), else 16.
+constexpr int64_t kNarrowPackMax = int64_t(1) << 28;
 
 struct FarTrade {
   int32_t x, y;    // new positions of nodes 2s and 2s+1
-  uint32_t top;    // threshold prefix
+  uint32_t top;    // threshold prefix (8 bits)
 };
 
 template <bool kNarrow>
@@ -1214,9 +1284,9 @@ __global__ void k_far_pack(StepCtx c, int64_t ntasks, void* __restrict__ pack) {
   for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < ntasks; s += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t x = static_cast<uint32_t>(c.M[2 * s]);
     const uint32_t y = 2 * s + 1 < c.n ? static_cast<uint32_t>(c.M[2 * s + 1]) : 0u;
-    const uint32_t top = c.thr_top[s];
+    const uint32_t top = 2 * s + 1 < c.n ? c.thr_top[s] : 0u;
     if constexpr (kNarrow) {
-      static_cast<uint64_t*>(pack)[s] = uint64_t(x) | (uint64_t(y) << 29) | (uint64_t(top) << 58);
+      static_cast<uint64_t*>(pack)[s] = uint64_t(x) | (uint64_t(y) << 28) | (uint64_t(top) << 56);
     } else {
       static_cast<int4*>(pack)[s] = make_int4(static_cast<int32_t>(x), static_cast<int32_t>(y),
                                               static_cast<int32_t>(top), 0);
@@ -1225,173 +1295,81 @@ __global__ void k_far_pack(StepCtx c, int64_t ntasks, void* __restrict__ pack) {
 }
 
 template <bool kNarrow>
-__device__ __forceinline__ FarTrade far_trade(const void* pack, int32_t s) {
+__device__ __forceinline__ FarTrade far_trade(const void* pack, uint32_t s) {
   if constexpr (kNarrow) {
     const uint64_t v = __ldg(static_cast<const unsigned long long*>(pack) + s);
-    return {static_cast<int32_t>(v & 0x1FFFFFFFu), static_cast<int32_t>((v >> 29) & 0x1FFFFFFFu),
-            static_cast<uint32_t>(v >> 58)};
+    return {static_cast<int32_t>(v & 0x0FFFFFFFu), static_cast<int32_t>((v >> 28) & 0x0FFFFFFFu),
+            static_cast<uint32_t>(v >> 56)};
   } else {
     const int4 v = __ldg(static_cast<const int4*>(pack) + s);
     return {v.x, v.y, static_cast<uint32_t>(v.z)};
   }
 }
 
-// The first and last trade with entries in each chunk (one thread per trade:
-// every chunk boundary lies in exactly one non-empty trade).
-__global__ void k_flat_ranges(StepCtx c, int64_t nnz, int64_t ntasks, int32_t* __restrict__ cf,
-                              int32_t* __restrict__ cl) {
-  const int64_t nchunks = (nnz + kFlatChunk - 1) / kFlatChunk;
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t b = c.rp[2 * t];
-    const int64_t e = 2 * t + 1 >= c.n ? c.rp[2 * t + 1] : c.rp[2 * t + 2];
-    if (e <= b) continue;
-    // chunks whose first entry lies in [b, e)
-    for (int64_t ch = (b + kFlatChunk - 1) / kFlatChunk; ch < nchunks && ch * kFlatChunk < e; ++ch)
-      cf[ch] = static_cast<int32_t>(t);
-    // chunks whose last entry lies in [b, e)
-    for (int64_t ch = b / kFlatChunk; ch < nchunks; ++ch) {
-      const int64_t last = ((ch + 1) * kFlatChunk < nnz ? (ch + 1) * kFlatChunk : nnz) - 1;
-      if (last >= e) break;
-      if (last >= b) cl[ch] = static_cast<int32_t>(t);
-    }
+// Row (step g+1 position) holding entry e of chunk ch.
+__device__ __forceinline__ int64_t fix_row(const StepCtx& c, const int32_t* chunk_row, int64_t ch, int64_t e) {
+  int64_t lo = chunk_row[ch], hi = chunk_row[ch + 1];
+  while (lo < hi) {   // last row whose first entry is <= e
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (c.rp_next[mid] <= e) lo = mid; else hi = mid - 1;
   }
+  return lo;
 }
 
 template <bool kNarrow>
-__global__ void __launch_bounds__(kFlatThreads) k_phase_b_flat(StepCtx c, int64_t nnz, int64_t ntasks,
-                                                               int32_t* __restrict__ slots,
-                                                               const int32_t* __restrict__ cf,
-                                                               const int32_t* __restrict__ cl,
-                                                               const void* __restrict__ pack) {
-  __shared__ FlatTrade tab[kFlatTrades];
-  __shared__ int32_t cnt[2 * kFlatTrades];     // entries of this chunk per (local trade, new side)
-  __shared__ int32_t gbase[2 * kFlatTrades];   // their first slot in the new row
-  const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
-  const int64_t nchunks = (nnz + kFlatChunk - 1) / kFlatChunk;
+__global__ void __launch_bounds__(kFixThreads) k_fixup(StepCtx c, int64_t nnz, uint32_t s_lo, uint32_t s_hi,
+                                                       const int32_t* __restrict__ ph, const uint8_t* __restrict__ fb,
+                                                       int32_t* __restrict__ out, const void* __restrict__ pack,
+                                                       const int32_t* __restrict__ chunk_row) {
+  const int64_t nchunks = (nnz + kFixChunk - 1) / kFixChunk;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int64_t e0 = ch * kFlatChunk;
-    const int64_t e1 = e0 + kFlatChunk < nnz ? e0 + kFlatChunk : nnz;
-    const int64_t tf = cf[ch], tl = cl[ch];
-    const int ntr = static_cast<int>(tl - tf + 1 < kFlatTrades + 1 ? tl - tf + 1 : kFlatTrades + 1);
-    const bool in_table = ntr <= kFlatTrades;
-    if (in_table) {
-      for (int q = threadIdx.x; q < ntr; q += blockDim.x) tab[q] = flat_trade(c, tf + q);
-      for (int q = threadIdx.x; q < 2 * ntr; q += blockDim.x) cnt[q] = 0;
-    }
-    __syncthreads();
-    const int64_t base = e0 + static_cast<int64_t>(threadIdx.x) * kFlatPer;
-    // owner of this thread's first entry, then walk forward
-    int64_t q = 0;
-    if (base < e1) {
-      if (in_table) {
-        int lo = 0, hi = ntr - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (tab[mid].start <= base) lo = mid; else hi = mid - 1;
-        }
-        q = lo;
-      } else {
-        q = flat_owner(c, tf, tl, base) - tf;
-      }
-    }
-    FlatTrade ft = in_table ? tab[q] : flat_trade(c, tf + q);
-    int64_t next_start = (tf + q + 1 <= tl) ? (in_table ? tab[q + 1].start : c.rp[2 * (tf + q + 1)]) : INT64_MAX;
-    // the thread's 8 entries and stash bytes (32 B and 8 B, aligned: chunks
-    // start at multiples of 2048 entries); a partial run at the end loads singly
-    int32_t yv[kFlatPer];
-    uint8_t sv[kFlatPer];
-    if (base + kFlatPer <= e1) {
-      const int4 a0 = __ldcs(reinterpret_cast<const int4*>(c.col + base));
-      const int4 a1 = __ldcs(reinterpret_cast<const int4*>(c.col + base) + 1);
-      yv[0] = a0.x; yv[1] = a0.y; yv[2] = a0.z; yv[3] = a0.w;
-      yv[4] = a1.x; yv[5] = a1.y; yv[6] = a1.z; yv[7] = a1.w;
-      const uint2 b = __ldcs(reinterpret_cast<const uint2*>(c.stash + base));
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        sv[j] = static_cast<uint8_t>(b.x >> (8 * j));
-        sv[4 + j] = static_cast<uint8_t>(b.y >> (8 * j));
-      }
+    const int64_t base = ch * kFixChunk + static_cast<int64_t>(threadIdx.x) * kFixPer;
+    if (base >= nnz) continue;
+    uint32_t pv[kFixPer];
+    uint32_t bv[2];
+    if (base + kFixPer <= nnz) {   // 32 B and 8 B, aligned: chunks start at multiples of 2048 entries
+      const uint4 a0 = __ldcs(reinterpret_cast<const uint4*>(ph + base));
+      const uint4 a1 = __ldcs(reinterpret_cast<const uint4*>(ph + base) + 1);
+      pv[0] = a0.x; pv[1] = a0.y; pv[2] = a0.z; pv[3] = a0.w;
+      pv[4] = a1.x; pv[5] = a1.y; pv[6] = a1.z; pv[7] = a1.w;
+      const uint2 b = __ldcs(reinterpret_cast<const uint2*>(fb + base));
+      bv[0] = b.x;
+      bv[1] = b.y;
     } else {
+      bv[0] = bv[1] = 0;
 #pragma unroll
-      for (int j = 0; j < kFlatPer; ++j) {
-        yv[j] = base + j < e1 ? c.col[base + j] : 0;
-        sv[j] = base + j < e1 ? c.stash[base + j] : 0;
+      for (int j = 0; j < kFixPer; ++j) {
+        pv[j] = base + j < nnz ? static_cast<uint32_t>(ph[base + j]) : 0xFFFFFFFFu;
+        if (base + j < nnz) bv[j >> 2] |= static_cast<uint32_t>(fb[base + j]) << (8 * (j & 3));
       }
     }
-    int32_t outv[kFlatPer], keyv[kFlatPer], posv[kFlatPer];
 #pragma unroll
-    for (int j = 0; j < kFlatPer; ++j) {
-      const int64_t e = base + j;
-      const bool valid = e < e1;
-      if (valid) {
-        while (e >= next_start) {   // next non-empty trade (empty trades share its start)
-          ++q;
-          ft = in_table ? tab[q] : flat_trade(c, tf + q);
-          next_start = (tf + q + 1 <= tl) ? (in_table ? tab[q + 1].start : c.rp[2 * (tf + q + 1)]) : INT64_MAX;
+    for (int j = 0; j < kFixPer; ++j) {
+      const uint32_t p = pv[j];
+      const uint32_t y = p & 0x7FFFFFFFu;
+      const uint32_t s = y >> 1;
+      if (p == 0xFFFFFFFFu) continue;
+      if (y >= static_cast<uint32_t>(c.n)) {   // a slot phase A did not fill
+        latch(c.err, kErrRowLength);
+        continue;
+      }
+      if (s < s_lo || s >= s_hi) continue;
+      const FarTrade ft = far_trade<kNarrow>(pack, s);
+      int side = static_cast<int>(y & 1u);
+      if (p >> 31) {   // the far trade decides: prefixes first, the full key on a tie
+        const uint32_t b = (bv[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+        const uint32_t fp = b >> 1, tp = ft.top >> 1;
+        if (fp != tp) {
+          side = fp < tp ? 0 : 1;
+        } else {
+          const int64_t e = base + j;
+          const uint32_t xr = static_cast<uint32_t>(c.Minv[fix_row(c, chunk_row, ch, e)]) ^ (b & 1u);
+          const uint32_t lo = min(xr, y), hi = max(xr, y);
+          side = far_keeps_low(c, key_ctx(c, s), s, lo, hi) ? 0 : 1;
         }
       }
-      int key = -1;
-      int32_t out = 0;
-      if (valid) {
-        const int64_t t = tf + q;
-        const int r = e >= ft.b1;
-        const int32_t yy = yv[j];
-        const uint8_t st = sv[j];
-        const int r2 = r ^ (st & 1);
-        const int32_t s = yy >> 1;
-        const FarTrade fs = far_trade<kNarrow>(pack, s);   // one gather: new positions, threshold prefix
-        int hi_node = yy & 1;
-        if (st & 2) {
-          const uint32_t fp = st >> 2, tt = fs.top;
-          bool low;
-          if (fp != tt) {
-            low = fp < tt;
-          } else {
-            const uint32_t x = static_cast<uint32_t>(2 * t + r), y = static_cast<uint32_t>(yy);
-            low = far_keeps_low(c, key_ctx(c, t), s, min(x, y), max(x, y));   // prefix tie: 1 in 64
-          }
-          hi_node = low ? 0 : 1;
-        }
-        out = hi_node ? fs.y : fs.x;
-        key = static_cast<int>(2 * q + r2);
-      }
-      // the entries of one (trade, side) in the warp take consecutive slots
-      const unsigned grp = __match_any_sync(kFull, key);
-      const int leader = __ffs(grp) - 1;
-      int slot0 = 0;
-      if (lane == leader && key >= 0)
-        slot0 = in_table ? atomicAdd(&cnt[key], __popc(grp))
-                         : atomicAdd(&slots[2 * (tf + q) + (key & 1)], __popc(grp));
-      slot0 = __shfl_sync(kFull, slot0, leader);
-      outv[j] = out;
-      keyv[j] = key;
-      posv[j] = slot0 + __popc(grp & below);
-      if (!in_table && key >= 0) {   // global slot already final
-        const int p = posv[j];
-        const int r2 = key & 1;
-        if (p < (r2 ? ft.dv : ft.du)) c.col_next[(r2 ? ft.ov : ft.ou) + p] = out;
-        else latch(c.err, kErrRowSide);
-      }
+      out[base + j] = side ? ft.y : ft.x;
     }
-    if (in_table) {
-      // one global reservation per (trade, side) of the chunk, then the writes
-      __syncthreads();
-      for (int k = threadIdx.x; k < 2 * ntr; k += blockDim.x)
-        if (cnt[k]) gbase[k] = atomicAdd(&slots[2 * (tf + (k >> 1)) + (k & 1)], cnt[k]);
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < kFlatPer; ++j) {
-        const int key = keyv[j];
-        if (key < 0) continue;
-        const FlatTrade& f = tab[key >> 1];
-        const int r2 = key & 1;
-        const int p = gbase[key] + posv[j];
-        if (p < (r2 ? f.dv : f.du)) c.col_next[(r2 ? f.ov : f.ou) + p] = outv[j];
-        else latch(c.err, kErrRowSide);
-      }
-    }
-    __syncthreads();   // the table is reloaded for the next chunk
   }
 }
 
@@ -1452,7 +1430,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
     }
     const int32_t* ys = nullptr;
     if (staged(L)) {   // this trade's entries were staged by the previous one (or the prologue)
-      const bool late = !mbar_wait(&mbar, parity);
+      const bool late = !mbar_wait(&mbar, parity, c.wait_ns);
       parity ^= 1;
       if (__syncthreads_or(late)) {
         failed = true;
@@ -1464,7 +1442,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
   }
   if (failed) {   // a copy did not complete in time: report, let it land, leave
     if (threadIdx.x == 0) latch(c.err, kErrStage);
-    mbar_wait(&mbar, parity ^ 1);
+    mbar_wait(&mbar, parity ^ 1, c.wait_ns);
   }
 }
 
@@ -1544,11 +1522,9 @@ int init_trade_kernels(Graph* h) {
                                   static_cast<int>(ws_a_bytes(kBlockMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(sizeof(TileA))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_cta<kBigThreads, kCtaJ, kCta1024B>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kCta1024Ws)));
   // shared memory, not L1, limits how many CTAs of these kernels an SM holds
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_tile, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  cudaSharedmemCarveoutMaxShared));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
   return CB_OK;
@@ -1558,6 +1534,15 @@ size_t trade_ws_slice_bytes(int64_t max_trade) {
   return (ws_a_bytes(static_cast<int>(max_trade)) + 255) & ~size_t(255);
 }
 size_t trade_smem_bytes(int entries) { return ws_a_bytes(entries); }
+
+// Passes of the fix-up: enough that one pass's far-trade records (8 or 16
+// bytes per trade) stay below kFixSliceBytes, or the "fix_passes" option.
+constexpr int64_t kFixSliceBytes = int64_t(48) << 20;
+int fix_passes(const Graph* h) {
+  if (h->fix_passes > 0) return h->fix_passes;
+  const int64_t rec = (h->n <= kNarrowPackMax && !h->wide_pack) ? 8 : 16;
+  return static_cast<int>(std::max<int64_t>(1, (h->ntasks * rec + kFixSliceBytes - 1) / kFixSliceBytes));
+}
 
 int super_step(Graph* h) {
   if (h->g >= 0xfffffffeull) return fail(h, CB_ERANGE, "super-step counter exhausted");
@@ -1575,7 +1560,9 @@ int super_step(Graph* h) {
   c.seg_of = h->seg_of;
   c.rp = h->rp[h->cur];
   c.col = h->col[h->cur];
-  c.stash = h->stash;
+  c.fb = h->stash;
+  c.ph = h->col[nxt];
+  c.Minv = h->Minv;
   c.thr_key = h->thr_key;
   c.thr_tb = h->thr_tb;
   c.thr_top = h->thr_top;
@@ -1583,9 +1570,8 @@ int super_step(Graph* h) {
   c.err = h->err;
   c.M = h->M;
   c.rp_next = h->rp[nxt];
-  c.col_next = h->col[nxt];
-  // counters: [0..2] class list lengths, [3] tile weight total, [4..5] deferred
-  // lists, [8..] pass input counts, [kCounters-1] global-workspace trades
+  // counters: [0..2] class list lengths, [4] deferred trades, [5] chunks
+  // claimed by the in-order pass, [kCounters-1] global-workspace trades
   int64_t* cnt = h->counters;
   unsigned long long* ucnt = reinterpret_cast<unsigned long long*>(cnt);
   c.gws_count = ucnt + kCounters - 1;
@@ -1598,29 +1584,25 @@ int super_step(Graph* h) {
   auto grid_n = [&](int64_t work) {
     return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, h->num_sms * 8)));
   };
-  {  // classes in index order (stable compaction) and tile offsets
+  {  // classes in index order (stable compaction)
     k_class_flags<<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, tile_max, block_max, h->cls_flag);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
     const int64_t n1 = ntasks + 1;
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 3; ++q)
       CB_CUDA(h, exclusive_scan_i32(h->cls_flag + q * ntasks, h->cls_scan + q * n1, ntasks, h->scan_ws, s,
                                     &h->launches));
     k_class_scatter<<<grid_n(ntasks), 256, 0, s>>>(ntasks, h->cls_flag, h->cls_scan, h->list[0], h->list[1],
-                                                    h->list[2], h->tile_off);
+                                                    h->list[2]);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 3; ++q)
       CB_CUDA(h, cudaMemcpyAsync(cnt + q, h->cls_scan + q * n1 + ntasks, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    k_tile_first<<<grid_n(ntasks), 256, 0, s>>>(h->tile_off, cnt, h->tile_first);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
   }
   const size_t med_smem = ws_a_bytes(std::max(block_max, 1));      // in-order pass (no staging)
   const size_t big_smem = ws_a_bytes(std::max(h->smem_max, 1));
   const size_t med_smem_st = block_smem_bytes(std::max(block_max, 1));   // threshold kernels with staging
   const size_t big_smem_st = block_smem_bytes(std::max(h->smem_max, 1));
-  const unsigned tgrid = static_cast<unsigned>(h->num_sms * 8);
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
   char* gws = static_cast<char*>(h->ws_global);
@@ -1629,23 +1611,52 @@ int super_step(Graph* h) {
   // chunks claimed by the in-order pass.
   c.wait = 0;
   c.def_count = ucnt + 4;
-  if (h->tile_paths & 1) {
-    k_phase_a_tile<<<tgrid, kTileThreads, sizeof(TileA), s>>>(c, h->list[0], h->tile_off, h->tile_first, cnt,
-                                                              h->nseg > 1 ? 1 : 0);
+  c.cand_max = h->cand_max;
+  c.wait_ns = h->wait_ns;
+  c.hold_publish = h->hold_publish;
+  if (h->tile_paths) {
+    k_phase_a_warp<<<static_cast<unsigned>(h->num_sms * 8), 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(
+        c, h->list[0], cnt + 0);
   } else {
     k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[0], cnt + 0, block_max, gws,
                                                                         h->ws_slice, block_max);
   }
   CB_CUDA(h, cudaGetLastError());
   ++h->launches;
-  k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[1], cnt + 1, block_max, gws,
-                                                                      h->ws_slice, block_max);
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
-  k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, h->list[2], cnt + 2, h->smem_max, gws,
-                                                                      h->ws_slice, h->smem_max);
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
+  if (h->cta_paths) {
+    // registers: up to 1024 entries on 256 threads, up to min(4096, smem_max)
+    // on 1024; larger trades from a global-memory workspace
+    const int l256 = kCtaJ * kMedThreads, l1024 = kCtaJ * kBigThreads;
+    const int lreg = std::min(l1024, h->smem_max);
+    const unsigned big_grid = static_cast<unsigned>(h->num_sms);
+    k_phase_a_cta<kMedThreads, kCtaJ, kCta256B><<<mgrid, kMedThreads, kCta256Ws, s>>>(c, h->list[1], cnt + 1, 0, l256);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    if (block_max > l256) {   // the 256-thread class holds trades above the 256-thread registers
+      k_phase_a_cta<kBigThreads, kCtaJ, kCta1024B><<<big_grid, kBigThreads, kCta1024Ws, s>>>(c, h->list[1], cnt + 1,
+                                                                                            l256, l1024);
+      CB_CUDA(h, cudaGetLastError());
+      ++h->launches;
+    }
+    k_phase_a_cta<kBigThreads, kCtaJ, kCta1024B><<<big_grid, kBigThreads, kCta1024Ws, s>>>(c, h->list[2], cnt + 2, 0,
+                                                                                          lreg);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    if (gws) {
+      k_phase_a_huge<<<bgrid, kBigThreads, 0, s>>>(c, h->list[2], cnt + 2, lreg, gws, h->ws_slice);
+      CB_CUDA(h, cudaGetLastError());
+      ++h->launches;
+    }
+  } else {
+    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[1], cnt + 1, block_max, gws,
+                                                                        h->ws_slice, block_max);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, h->list[2], cnt + 2, h->smem_max, gws,
+                                                                        h->ws_slice, h->smem_max);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+  }
   // second pass: the deferred trades in index order, waiting on dependencies.
   // 1024-thread CTAs keep large trades in shared memory; 256-thread CTAs (four
   // per SM) run many small deferred trades at once, large ones from a global
@@ -1666,28 +1677,38 @@ int super_step(Graph* h) {
     ++h->launches;
   }
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
-  // phase B: one flat pass over every entry; per-trade slot counters start at zero
+  // rebuild: far-trade records, each chunk's first row, then the fix-up in
+  // passes over slices of the far trades; its output overwrites this step's
+  // adjacency, which phase A no longer needs, and becomes step g+1's
   {
-    int32_t* slots = h->cls_flag;   // 2 x ntasks, free after the classification
-    int32_t* cf = h->cls_flag + 2 * ntasks;   // chunk ranges (the scratch holds 2 x (nnz / 2048 + 1) more)
-    const int64_t nchunks = (h->nnz + kFlatChunk - 1) / kFlatChunk;
-    int32_t* cl = cf + nchunks;
-    CB_CUDA(h, cudaMemsetAsync(slots, 0, sizeof(int32_t) * 2 * ntasks, s));
+    const int64_t nnz = h->nnz;
+    const int64_t nchunks = (nnz + kFixChunk - 1) / kFixChunk;
+    int32_t* chunk_row = h->cls_flag;   // nchunks + 1 entries, free after the classification
     if (nchunks > 0) {
-      k_flat_ranges<<<grid_n(ntasks), 256, 0, s>>>(c, h->nnz, ntasks, cf, cl);
-      CB_CUDA(h, cudaGetLastError());
-      ++h->launches;
       const bool narrow = h->n <= kNarrowPackMax && !h->wide_pack;
       if (narrow) k_far_pack<true><<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, h->far_pack);
       else k_far_pack<false><<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, h->far_pack);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
-      const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 8));
-      if (narrow) k_phase_b_flat<true><<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl, h->far_pack);
-      else k_phase_b_flat<false><<<fgrid, kFlatThreads, 0, s>>>(c, h->nnz, ntasks, slots, cf, cl, h->far_pack);
+      k_chunk_rows<<<grid_n(h->n), 256, 0, s>>>(h->n, c.rp_next, nchunks, chunk_row);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
+      const int passes = fix_passes(h);
+      const int64_t per = (ntasks + passes - 1) / passes;
+      const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 8));
+      int32_t* out = h->col[h->cur];
+      for (int q = 0; q < passes; ++q) {
+        const uint32_t lo = static_cast<uint32_t>(std::min<int64_t>(ntasks, q * per));
+        const uint32_t hi = static_cast<uint32_t>(std::min<int64_t>(ntasks, (q + 1) * per));
+        if (narrow)
+          k_fixup<true><<<fgrid, kFixThreads, 0, s>>>(c, nnz, lo, hi, c.ph, c.fb, out, h->far_pack, chunk_row);
+        else
+          k_fixup<false><<<fgrid, kFixThreads, 0, s>>>(c, nnz, lo, hi, c.ph, c.fb, out, h->far_pack, chunk_row);
+        CB_CUDA(h, cudaGetLastError());
+        ++h->launches;
+      }
     }
+    std::swap(h->col[0], h->col[1]);   // the step's output is now the other side of the ping-pong
   }
   if (h->timing) {
     CB_CUDA(h, cudaEventRecord(h->ev[3], s));

@@ -63,7 +63,6 @@ namespace {
 constexpr int32_t kInf = 0x7fffffff;            // no further trade
 constexpr int kUniThreads = 256;
 constexpr int kUniSmemElems = 2048;             // trades up to this many entries work in shared memory
-constexpr uint64_t kUniWaitNs = 20000000000ull; // a single wait longer than 20 s is a failure
 constexpr int64_t kUniChunkMin = 65536;
 
 __device__ __forceinline__ void latch(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
@@ -202,6 +201,8 @@ struct UniCtx {
   char* gslice;
   int64_t slice_elems;
   unsigned long long* swaps;   // (performed, possible) swap counts, or null
+  uint64_t wait_ns;            // longest single wait (run queue, inbox entry)
+  int64_t hold_trade;          // test hook: messages to this trade of the chunk are dropped (-1: none)
 };
 
 // The run queue: a ticket (kHead) takes the next slot, a push (kTail)
@@ -230,7 +231,7 @@ __device__ int64_t take_ticket(const UniCtx& c) {
       t = ld_relaxed_i32(c.queue + q);
       if (t >= 0) break;
       if (ld_volatile_i32(c.err) != 0) return -1;
-      if (globaltimer() - t0 > kUniWaitNs) {
+      if (globaltimer() - t0 > c.wait_ns) {
         latch(c.err, kErrUniformWait);
         return -1;
       }
@@ -241,6 +242,7 @@ __device__ int64_t take_ticket(const UniCtx& c) {
 
 // Append (other, other_tau) to node x's inbox at trade d.
 __device__ void append(const UniCtx& c, int32_t d, int32_t x, int32_t other, int32_t other_tau) {
+  if (d == c.hold_trade) return;   // test hook: the trade never becomes runnable
   const int32_t a = c.tp[2 * int64_t(d)], b = c.tp[2 * int64_t(d) + 1];
   const int side = (x == a) ? 0 : 1;
   if (x != a && x != b) {
@@ -308,7 +310,7 @@ __global__ void k_uni_route(UniCtx c, int64_t n, const int32_t* __restrict__ col
 }
 
 // Bounded wait for an inbox entry still being written (the cold path).
-__device__ __noinline__ bool wait_entry(const int2* p, const int32_t* err, int2* out) {
+__device__ __noinline__ bool wait_entry(const int2* p, const int32_t* err, uint64_t wait_ns, int2* out) {
   int2 m = ld_relaxed_v2(p);
   if (m.x != -1) {
     *out = m;
@@ -322,7 +324,7 @@ __device__ __noinline__ bool wait_entry(const int2* p, const int32_t* err, int2*
       *out = m;
       return true;
     }
-    if (ld_volatile_i32(err) != 0 || globaltimer() - t0 > kUniWaitNs) return false;
+    if (ld_volatile_i32(err) != 0 || globaltimer() - t0 > wait_ns) return false;
   }
 }
 
@@ -456,7 +458,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
     const int side = e >= du;
     const int2* p = side ? inv + (e - du) : inu + e;
     int2 m = __ldcg(p);
-    if (m.x == -1 && !wait_entry(p, c.err, &m)) {
+    if (m.x == -1 && !wait_entry(p, c.err, c.wait_ns, &m)) {
       ok = false;
       m = make_int2(0, kInf);
     }
@@ -805,6 +807,8 @@ int uniform_trades(Graph* h, uint64_t count) {
     c.ctr = b->ctr;
     c.ocur = b->ocur;
     c.col_out = h->col[spare];
+    c.wait_ns = h->uni_wait_ns;
+    c.hold_trade = h->hold_trade;
     c.err = h->err;
     c.gslice = b->gslice;
     c.slice_elems = b->slice_elems;

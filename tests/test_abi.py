@@ -37,3 +37,14 @@ def test_binding_loads_and_rejects_bad_arguments(libpath):
 def test_binding_names_match_the_abi():
     for f in cb.declared_functions():
         assert hasattr(cb, f), f
+
+
+def test_return_codes_match_the_header():
+    import re
+    from pathlib import Path
+    text = (Path(build.INCLUDE) / "cb.h").read_text()
+    codes = {name: int(val) for name, val in re.findall(r"#define (CB_E[A-Z]+) \((-\d+)\)", text)}
+    assert codes["CB_ETIMEOUT"] == cb.CB_ETIMEOUT
+    for name, val in codes.items():
+        assert getattr(cb, name) == val, name
+    assert len(set(codes.values())) == len(codes)

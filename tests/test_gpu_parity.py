@@ -104,6 +104,15 @@ CASES = [
     (3001, 3, 300, 2.0, 18, {"wide_pack": 1}),        # 16-byte far-trade records (n > 2^29 layout)
     (3000, 4, 1500, 2.0, 13, {}),                     # heavy tail: block-path hubs
     (20000, 1, 3, 2.0, 23, {}),                       # degrees 1-2: rebuild chunks beyond the 512-trade table
+    (2500, 3, 60, 2.0, 19, {"cand_max": 1}),          # register paths: every shared prefix takes more radix digits
+    (3000, 4, 1500, 2.0, 20, {"cand_max": 1}),        # the same on the 256- and 1024-thread register kernels
+    (3000, 4, 1500, 2.0, 21, {"cta_paths": 0}),       # shared-memory kernels for the larger classes
+    (3000, 4, 1500, 2.0, 24, {"block_max": 2048}),    # 256-thread class above its registers: 1024-thread kernel
+    (3000, 4, 1500, 2.0, 25, {"smem_max": 512}),      # register kernels up to 512 entries, global workspace above
+    (2500, 3, 60, 2.0, 26, {"tile_paths": 0, "cta_paths": 0}),
+    (3001, 3, 300, 2.0, 27, {"fix_passes": 3}),       # rebuild in three slices of the far trades
+    (20000, 1, 3, 2.0, 28, {"fix_passes": 7}),
+    (3001, 3, 300, 2.0, 29, {"fix_passes": 2, "wide_pack": 1}),
 ]
 
 
@@ -126,6 +135,8 @@ def test_dense_graphs_resolve_dependencies(n, a, b, seed):
     _run_pair(g.row_ptr, g.col, seed + 300, 3, options={"tile_paths": 0})
     _run_pair(g.row_ptr, g.col, seed + 400, 3, options={"block_max": 0, "smem_max": 128})
     _run_pair(g.row_ptr, g.col, seed + 500, 3, options={"inorder_threads": 256, "block_max": 256})
+    _run_pair(g.row_ptr, g.col, seed + 600, 3, options={"cand_max": 1})
+    _run_pair(g.row_ptr, g.col, seed + 700, 3, options={"tile_paths": 1, "cta_paths": 0})
 
 
 def test_dependency_passes_happen():
