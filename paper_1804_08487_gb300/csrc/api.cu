@@ -66,7 +66,7 @@ void release(Graph* h) {
   free_uniform(h);
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
-                  h->list[0], h->list[1], h->list[2], h->Minv, h->cls_flag, h->cls_scan,
+                  h->lists, h->Minv, h->cls_flag, h->cls_scan,
                   h->counters, h->err,
                   h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs, h->far_pack,
                   h->lcg_ab, h->lcg_gaps, h->swaps};
@@ -218,12 +218,13 @@ void destroy_graph(Graph* h) {
   delete static_cast<cb_graph*>(h);
 }
 
-// Scratch of 3 int32 per trade (class flags), then (rebuild) the first row
-// of each 2048-entry chunk plus one.
+// Scratch int32: the trade classes' counts per 2048-trade chunk, then
+// (rebuild) the first row of each 2048-entry chunk plus one.
 int64_t cls_flag_count(int64_t ntasks, int64_t nnz) {
-  const int64_t chunks = nnz / 2048 + 1;
-  return std::max<int64_t>(3 * ntasks, chunks + 1);
+  return std::max<int64_t>(kClasses * (ntasks / 2048 + 1), nnz / 2048 + 2);
 }
+// Scratch int64: the exclusive scan of those counts.
+int64_t cls_scan_count(int64_t ntasks) { return kClasses * (ntasks / 2048 + 1) + 1; }
 
 // Common part of handle creation.  On entry: n, nnz, the segment table (host
 // and device, seg_of for batches) and the id-space CSR (rp_id, col[0],
@@ -259,9 +260,8 @@ int finish_create(Graph* h) {
       dalloc(h, &h->stash, nnz) ||
       dalloc(h, &h->thr_key, h->ntasks) || dalloc(h, &h->thr_tb, h->ntasks) || dalloc(h, &h->done, h->ntasks) ||
       dalloc(h, &h->far_pack, h->ntasks) ||
-      dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->list[0], h->ntasks) || dalloc(h, &h->list[1], h->ntasks) ||
-      dalloc(h, &h->list[2], h->ntasks) ||
-      dalloc(h, &h->cls_flag, cls_flag_count(h->ntasks, nnz)) || dalloc(h, &h->cls_scan, 3 * (h->ntasks + 1)) ||
+      dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->lists, h->ntasks) ||
+      dalloc(h, &h->cls_flag, cls_flag_count(h->ntasks, nnz)) || dalloc(h, &h->cls_scan, cls_scan_count(h->ntasks)) ||
       dmalloc(h, &h->sort_ws, h->sort_ws_bytes) || dmalloc(h, &h->scan_ws, h->scan_ws_bytes))
     return fail(h, CB_ENOMEM, "device allocation failed");
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
@@ -433,7 +433,7 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   int64_t b = 0;
   b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * (nnz + kColPad) + 32 + 8 * kCounters;   // cb_create
   b += 2 * 4 * n + 2 * 8 * (n + 1) + 4 * 4 * n + nnz;                                     // per node, side bytes
-  b += ntasks * (8 + 8 + 4 + 16 + 1 + 3 * 4 + 24) + 4 * cls_flag_count(ntasks, nnz) + 32;
+  b += ntasks * (8 + 8 + 4 + 16 + 1 + 4) + 4 * cls_flag_count(ntasks, nnz) + 8 * cls_scan_count(ntasks) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;
   if (max_trade > kBlockMaxDefault || maxdeg > 16384) {   // default block_max
@@ -783,11 +783,12 @@ int cb_stats(cb_handle h, int64_t* out, int count) {
                              h->stream));
   CB_CUDA(h, cudaStreamSynchronize(h->stream));
   const int64_t* hc = h->host_counters;
-  h->stats[0] = hc[4] ? 2 : 1;   // the in-order pass runs only what the first pass deferred
-  h->stats[1] = hc[4];
-  h->stats[2] = hc[0];
-  h->stats[3] = hc[1] + hc[2];
-  h->stats[4] = hc[kCounters - 1];
+  h->stats[0] = hc[kCtrDeferred] ? 2 : 1;   // the in-order pass runs only what the first pass deferred
+  h->stats[1] = hc[kCtrDeferred];
+  h->stats[2] = hc[kCtrClsLen];
+  h->stats[3] = 0;
+  for (int k = 1; k < kClasses; ++k) h->stats[3] += hc[kCtrClsLen + k];
+  h->stats[4] = hc[kCtrGws];
   const int k = std::min(count, 6);
   for (int i = 0; i < k; ++i) out[i] = h->stats[i];
   return k;

@@ -32,6 +32,14 @@ constexpr int kBlockMaxDefault = 1024;   // default of the "block_max" option
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
 constexpr int kCounters = 32;       // device counters per handle
+// Trade size classes of the threshold phase (one team size each) and the
+// device counters of a super step.
+constexpr int kClasses = 7;
+constexpr int kCtrClsLen = 0;       // [0, kClasses): trades per class
+constexpr int kCtrClsStart = 8;     // [8, 8 + kClasses): first entry of each class in the class lists
+constexpr int kCtrDeferred = 16;    // trades the first pass deferred
+constexpr int kCtrClaims = 17;      // chunks claimed by the in-order pass
+constexpr int kCtrGws = kCounters - 1;   // trades whose workspace is in global memory
 constexpr int kMaxLcgGaps = 1024;   // p - n for the relaxed permutation (prime gaps below 2^31 are far smaller)
 
 // One independent graph of a handle.  A plain handle holds one; a batch handle
@@ -91,9 +99,9 @@ struct Graph {
   uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)
   uint32_t* done = nullptr;                // per trade: 1 once the threshold is published (cleared per step)
   int4* far_pack = nullptr;                // per trade: new positions of its nodes, threshold prefix (rebuild)
-  int32_t* list[3] = {nullptr, nullptr, nullptr};   // trades per size class (warp, 256, 1024 threads), index order
-  int32_t* cls_flag = nullptr;             // scratch: 3 x ntasks class flags, then the rebuild's chunk rows
-  int64_t* cls_scan = nullptr;             // 3 x (ntasks+1) scratch: exclusive scans of the class flags
+  int32_t* lists = nullptr;                // trades of every size class, class after class, index order within
+  int32_t* cls_flag = nullptr;             // scratch: per-chunk class counts, then the rebuild's chunk rows
+  int64_t* cls_scan = nullptr;             // scratch: their exclusive scan
   int64_t* counters = nullptr;             // list lengths, deferred count, claims (kCounters)
   int32_t* err = nullptr;                  // latched device error
   // workspaces

@@ -118,3 +118,64 @@ __device__ __forceinline__ int next_pow2(int x) {
 }
 
 }  // namespace cb
+
+namespace cb {
+
+// A team of NT threads (a multiple of 32) inside a larger CTA: threads
+// [id NT, (id+1) NT) form team id and synchronise on named barrier id+1
+// (barrier 0 stays with the whole CTA), so several teams of one CTA work on
+// different trades independently.  `red` points at the team's kRedSlots
+// int64 slots of shared memory; reductions take one barrier, as BlockTeam's.
+template <int NT>
+struct SubTeam {
+  static constexpr int N = NT;
+  static constexpr int NW = NT / 32;
+  static constexpr int kRedSlots = 2 * NW;
+  int rank;
+  int bar;
+  int buf;
+  int64_t* red;
+  __device__ __forceinline__ SubTeam(int64_t* r, int id) : rank(threadIdx.x % NT), bar(id + 1), buf(0), red(r) {}
+  __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(NT) : "memory"); }
+  __device__ __forceinline__ bool any(bool p) const {
+    int r;
+    asm volatile(
+        "{\n .reg .pred q, o;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred o, %2, %3, q;\n selp.s32 %0, 1, 0, o;\n}"
+        : "=r"(r)
+        : "r"(p ? 1 : 0), "r"(bar), "n"(NT)
+        : "memory");
+    return r != 0;
+  }
+  __device__ int64_t sum(int64_t v) {
+    const int lane = rank & 31;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    int64_t* part = red + buf * NW;
+    if (lane == 0) part[rank >> 5] = v;
+    sync();
+    buf ^= 1;
+    int64_t x = lane < NW ? part[lane] : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+  }
+  __device__ int64_t exscan(int64_t v) {
+    const int lane = rank & 31, w = rank >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    int64_t* part = red + buf * NW;
+    if (lane == 31) part[w] = x;
+    sync();
+    buf ^= 1;
+    int64_t before = lane < w ? part[lane] : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) before += __shfl_xor_sync(kFull, before, o);
+    return x - v + before;
+  }
+};
+
+}  // namespace cb

@@ -86,6 +86,15 @@ struct SelOut {
   int32_t bin, below, cnt, pad;
 };
 
+// The trades of class k: (list, length).
+struct ClassList {
+  const int32_t* list;
+  int64_t len;
+};
+__device__ __forceinline__ ClassList class_list(const int32_t* lists, const int64_t* ctr, int k) {
+  return {lists + ctr[kCtrClsStart + k], ctr[kCtrClsLen + k]};
+}
+
 struct TradeRows {
   int64_t b0;
   int du, dv;
@@ -230,22 +239,19 @@ __device__ __forceinline__ void flag_or(uint8_t* fl, int p, uint32_t bits) {
   atomicOr(reinterpret_cast<unsigned int*>(fl + (p & ~3)), bits << (8 * (p & 3)));
 }
 
-// Sets `bit` in the slot of far trade s (creating it); returns the slot.
-__device__ __forceinline__ int h_insert(uint32_t* hk, uint8_t* fl, int lgH, uint32_t s, uint32_t bit) {
-  const uint32_t key = s + 1u;
-  const uint32_t mask = (1u << lgH) - 1u;
-  uint32_t p = hslot(s, lgH);
+// Slot of key (far trade + 1) starting the probe at p: the key's slot if an
+// entry of the same far trade placed it, else the first empty slot, claimed
+// with a compare-and-swap.  Used only for the few entries that lost the
+// plain-store round of an insert.
+__device__ __forceinline__ uint32_t h_claim(uint32_t* hk, uint32_t mask, uint32_t key, uint32_t p) {
   for (;;) {
     uint32_t cur = hk[p];
-    if (cur == 0) {
+    if (cur == 0u) {
       cur = atomicCAS(&hk[p], 0u, key);
-      if (cur == 0) cur = key;
+      if (cur == 0u) return p;
     }
-    if (cur == key) {
-      flag_or(fl, static_cast<int>(p), bit);
-      return static_cast<int>(p);
-    }
-    p = (p + 1) & mask;
+    if (cur == key) return p;
+    p = (p + 1u) & mask;
   }
 }
 
@@ -256,6 +262,7 @@ constexpr int kSelBins = 1 << kSelBits;
 
 // meta bits per entry (team paths add the neighbour's column bit)
 constexpr uint8_t kCol = 16;    // neighbour sits at the odd position 2s+1
+constexpr uint8_t kPend = 32;   // not placed in the hash yet
 
 constexpr int kCand = 32;       // candidates sharing the threshold's bin, ranked by full key
 
@@ -461,7 +468,11 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   for (int i = tm.rank; i < kSelBins; i += Team::N) w.hist[i] = 0;
   if (tm.rank == 0) *w.ncand = 0;
   tm.sync();
-  // entries into the hash: presence bit (row, column) in the far trade's slot
+  // entries into the hash: the far trade's slot (open addressing, far trade
+  // + 1 as key: a plain store into an empty home slot, read back after a
+  // barrier; an entry whose home slot another key won claims a further slot
+  // with a compare-and-swap), then the presence bit (row, column) in the
+  // slot's flags
   for (int i = tm.rank; i < L; i += Team::N) {
     const int r = i >= du;
     const int32_t yy = ystage ? ystage[i] : __ldcg(c.col + tr.b0 + i);
@@ -471,9 +482,36 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
       m |= kUV;
       w.slot[i] = -1;
     } else {
-      w.slot[i] = h_insert(w.hkey, w.hflag, w.lgH, static_cast<uint32_t>(s), 1u << (2 * r + (yy & 1)));
+      m |= kPend;
+      w.slot[i] = static_cast<int32_t>(hslot(static_cast<uint32_t>(s), w.lgH));
     }
     w.meta[i] = m;
+  }
+  {
+    const uint32_t hmask = (1u << w.lgH) - 1u;
+    for (int i = tm.rank; i < L; i += Team::N) {
+      if (!(w.meta[i] & kPend)) continue;
+      const int32_t yy = ystage ? ystage[i] : __ldcg(c.col + tr.b0 + i);
+      const int sl = w.slot[i];
+      if (w.hkey[sl] == 0u) w.hkey[sl] = (static_cast<uint32_t>(yy) >> 1) + 1u;
+    }
+    tm.sync();
+    for (int i = tm.rank; i < L; i += Team::N) {
+      const uint8_t m = w.meta[i];
+      if (!(m & kPend)) continue;
+      const int32_t yy = ystage ? ystage[i] : __ldcg(c.col + tr.b0 + i);
+      const uint32_t sl = static_cast<uint32_t>(w.slot[i]);
+      const uint32_t key = (static_cast<uint32_t>(yy) >> 1) + 1u;
+      if (w.hkey[sl] != key)   // lost the slot to another key: claim one further on
+        w.slot[i] = static_cast<int32_t>(h_claim(w.hkey, hmask, key, (sl + 1u) & hmask));
+      w.meta[i] = m & ~kPend;
+    }
+    tm.sync();
+    for (int i = tm.rank; i < L; i += Team::N) {
+      const uint8_t m = w.meta[i];
+      if (m & kUV) continue;
+      flag_or(w.hflag, w.slot[i], 1u << (2 * (m & kR) + ((m & kCol) ? 1 : 0)));
+    }
   }
   tm.sync();
   if (sn.issue && tm.rank == 0) stage_issue(c.col, sn.b0, sn.L, sn.buf, sn.mbar);
@@ -775,7 +813,7 @@ __host__ __device__ constexpr int hash_lg_c(int L) {
 // of at most LMAX entries and 2^B histogram bins.
 template <int LMAX, int B>
 struct RegWs {
-  static constexpr int kH = 1 << hash_lg_c(LMAX);
+  static constexpr int kH = 1 << hash_lg_c(2 * LMAX);   // at least 4 slots per entry
   static constexpr size_t kCk = 0;                              // candidate keys
   static constexpr size_t kCtb = kCk + kCand * 8;               // candidate tie-breaks
   static constexpr size_t kSel = kCtb + kCand * 8;              // selection results shared by the team
@@ -783,8 +821,8 @@ struct RegWs {
   static constexpr size_t kNc = kPw + 16;                       // candidate count
   static constexpr size_t kHk = kNc + 16;                       // hash slot keys (far trade + 1; 0 = empty)
   static constexpr size_t kHist = kHk + size_t(kH) * 4;         // radix histogram
-  static constexpr size_t kHf = kHist + (size_t(1) << B) * 4;   // slot flags: block matrix 0..3, flips 4..7
-  static constexpr size_t kBytes = (kHf + size_t(kH) + 15) & ~size_t(15);
+  static constexpr size_t kHb = kHist + (size_t(1) << B) * 4;   // slot block bytes (see block_flags)
+  static constexpr size_t kBytes = (kHb + size_t(kH) * 4 + 15) & ~size_t(15);
   char* base;
   __device__ __forceinline__ uint64_t* ck() const { return reinterpret_cast<uint64_t*>(base + kCk); }
   __device__ __forceinline__ uint64_t* ctb() const { return reinterpret_cast<uint64_t*>(base + kCtb); }
@@ -793,8 +831,24 @@ struct RegWs {
   __device__ __forceinline__ int32_t* ncand() const { return reinterpret_cast<int32_t*>(base + kNc); }
   __device__ __forceinline__ uint32_t* hk() const { return reinterpret_cast<uint32_t*>(base + kHk); }
   __device__ __forceinline__ uint32_t* hist() const { return reinterpret_cast<uint32_t*>(base + kHist); }
-  __device__ __forceinline__ uint8_t* hf() const { return reinterpret_cast<uint8_t*>(base + kHf); }
+  __device__ __forceinline__ uint32_t* hb() const { return reinterpret_cast<uint32_t*>(base + kHb); }
 };
+
+// A slot's block word holds one byte per edge of the 2x2 block matrix
+// (byte 2 rho + gamma: the trade's node rho adjacent to the far node
+// 2s + gamma): 0 absent, 1 present, 3 present and moved by the trade.
+// Plain byte stores fill it (the entries of one slot write different bytes,
+// or equal values), so it needs no atomics.  block_flags turns it into the
+// flag layout of the shared-memory path: presence bits 0..3, flips 4..7.
+__device__ __forceinline__ uint32_t compact_bytes(uint32_t x) {   // x: bytes 0 or 1
+  return (x | (x >> 7) | (x >> 14) | (x >> 21)) & 15u;
+}
+__device__ __forceinline__ uint32_t block_flags(uint32_t w) {
+  return compact_bytes(w & 0x01010101u) | (compact_bytes((w >> 1) & 0x01010101u) << 4);
+}
+__device__ __forceinline__ void block_mark(uint32_t* hb, uint32_t slot, int q, uint8_t v) {
+  reinterpret_cast<uint8_t*>(hb + slot)[q] = v;
+}
 
 // Word d of an element's 128-bit order (key, lo, hi): key high, key low, lo, hi.
 __device__ __forceinline__ uint32_t sel_word(int d, uint64_t key, uint32_t lo, uint32_t hi) {
@@ -831,13 +885,18 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const TradeRows tr = trade_rows(c, t);
   const KeyCtx kc = key_ctx(c, t);
   const int du = tr.du, L = tr.du + tr.dv;
-  const int lgH = hash_lg(L);
+  // at least 4 hash slots per entry, and about one first-digit bin per entry
+  const int lgH = max(5, 34 - __clz(max(L, 2) - 1));   // next power of two >= 4 L
   const int H = 1 << lgH;
+  const int B0 = min(B, max(5, 32 - __clz(max(L - 1, 1))));
+  const int NB0 = 1 << B0;
   const uint32_t t32 = static_cast<uint32_t>(t), T32 = static_cast<uint32_t>(c.T);
   const uint32_t t2u = 2u * t32;
-  for (int i = tm.rank; i < H; i += Team::N) w.hk()[i] = 0u;
-  for (int i = tm.rank; i < (H + 3) / 4; i += Team::N) reinterpret_cast<uint32_t*>(w.hf())[i] = 0u;
-  for (int i = tm.rank; i < NB; i += Team::N) w.hist()[i] = 0u;
+  for (int i = tm.rank; i < H; i += Team::N) {
+    w.hk()[i] = 0u;
+    w.hb()[i] = 0u;
+  }
+  for (int i = tm.rank; i < NB0; i += Team::N) w.hist()[i] = 0u;
   if (tm.rank == 0) *w.ncand() = 0;
   tm.sync();
   // entries into the hash: presence bit (row, column) in the far trade's slot
@@ -855,10 +914,54 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
       const uint32_t s = static_cast<uint32_t>(yy) >> 1;
       uint32_t m = kMValid | (r ? kMR : 0u) | ((yy & 1) ? kMCol : 0u);
       if (s == t32) m |= kMUV;
-      else m |= static_cast<uint32_t>(h_insert(w.hk(), w.hf(), lgH, s, 1u << (2 * r + (yy & 1))));
+      else m |= hslot(s, lgH);
       y[j] = static_cast<uint32_t>(yy);
       mt[j] = m;
     }
+  }
+  // the hash (open addressing, far trade + 1 as key): every entry writes its
+  // key into its home slot if that is empty (a plain store); after a barrier
+  // it reads the slot back: its key (written by itself or by an entry of the
+  // same far trade) places it; the few entries whose slot another key won
+  // claim a further slot with a compare-and-swap.
+  {
+    uint32_t pend = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if ((mt[j] & kMValid) && !(mt[j] & kMUV)) pend |= 1u << j;
+    // a warp repeats the plain round (its barriers are cheap) until every
+    // entry is placed; a larger team runs one round, then compare-and-swap
+    constexpr bool kRounds = Team::N == 32;
+    for (;;) {
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if ((pend >> j) & 1u) {
+          const uint32_t sl = mt[j] & kMSlot;
+          if (w.hk()[sl] == 0u) w.hk()[sl] = (y[j] >> 1) + 1u;
+        }
+      tm.sync();
+      bool more = false;
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if ((pend >> j) & 1u) {
+          const uint32_t sl = mt[j] & kMSlot;
+          const uint32_t key = (y[j] >> 1) + 1u;
+          if (w.hk()[sl] == key) {
+            pend &= ~(1u << j);
+          } else if (kRounds) {
+            mt[j] = (mt[j] & ~kMSlot) | ((sl + 1u) & static_cast<uint32_t>(H - 1));
+            more = true;
+          } else {   // lost the slot to another key: claim one further on
+            mt[j] = (mt[j] & ~kMSlot) | h_claim(w.hk(), static_cast<uint32_t>(H - 1), key, (sl + 1u) & (H - 1));
+          }
+        }
+      if (!kRounds || !tm.any(more)) break;
+    }
+    tm.sync();
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if ((mt[j] & kMValid) && !(mt[j] & kMUV))
+        block_mark(w.hb(), mt[j] & kMSlot, 2 * ((mt[j] & kMR) ? 1 : 0) + ((mt[j] & kMCol) ? 1 : 0), 1);
   }
   tm.sync();
   // block analysis, keys, histogram of the first radix digit
@@ -871,7 +974,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     const int r = (m & kMR) ? 1 : 0;
     const uint32_t colb = (m & kMCol) ? 1u : 0u;
     const uint32_t s = y[j] >> 1;
-    const uint32_t f = w.hf()[m & kMSlot] & 15u;
+    const uint32_t f = block_flags(w.hb()[m & kMSlot]) & 15u;
     int other = 0;   // the other row is adjacent to this neighbour when t acts
     if (f & (f - 1u)) {
       // a block of two or more edges: common neighbours and dependencies
@@ -921,7 +1024,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     if (!other && !tr.single) {
       m |= kMInD;
       cnt_a += (r == 0);
-      atomicAdd(&w.hist()[kt[j] >> (32 - B)], 1u);
+      atomicAdd(&w.hist()[kt[j] >> (32 - B0)], 1u);
     }
     mt[j] = m;
   }
@@ -944,19 +1047,20 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const bool no_thr = tr.single || a == 0;   // u keeps nothing of D
   uint64_t tk = 0, tt = 0;
   if (!no_thr) {
-    // the bin of the first digit (top B key bits) that holds the a-th smallest element
+    // the bin of the first digit (top B0 key bits) that holds the a-th smallest element
     constexpr int BPM = (NB + Team::N - 1) / Team::N;
     {
-      const int b0 = tm.rank * BPM;
+      const int bpm0 = (NB0 + Team::N - 1) / Team::N;
+      const int b0 = tm.rank * bpm0;
       int local = 0;
 #pragma unroll
       for (int q = 0; q < BPM; ++q)
-        if (b0 + q < NB) local += static_cast<int>(w.hist()[b0 + q]);
+        if (q < bpm0 && b0 + q < NB0) local += static_cast<int>(w.hist()[b0 + q]);
       int run = static_cast<int>(tm.exscan(local));
 #pragma unroll
       for (int q = 0; q < BPM; ++q) {
         const int b = b0 + q;
-        if (b < NB) {
+        if (q < bpm0 && b < NB0) {
           const int hc = static_cast<int>(w.hist()[b]);
           if (run < a && a <= run + hc) {
             w.sel()->bin = b;
@@ -968,11 +1072,11 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
       }
     }
     tm.sync();
-    int qbits = B;              // top bits of the order fixed so far
+    int qbits = B0;             // top bits of the order fixed so far
     int kk = a - w.sel()->below;  // rank sought among the elements sharing them
     int cnt = w.sel()->cnt;
     if (tm.rank == 0) {
-      w.pw()[0] = static_cast<uint32_t>(w.sel()->bin) << (32 - B);
+      w.pw()[0] = static_cast<uint32_t>(w.sel()->bin) << (32 - B0);
       w.pw()[1] = w.pw()[2] = w.pw()[3] = 0u;
     }
     tm.sync();
@@ -1029,11 +1133,11 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       if (!(mt[j] & kMInD)) continue;
-      if (qbits == B && (kt[j] >> (32 - B)) != (w.pw()[0] >> (32 - B))) continue;
+      if (qbits == B0 && (kt[j] >> (32 - B0)) != (w.pw()[0] >> (32 - B0))) continue;
       uint32_t lo, hi;
       entry_lo_hi(t2u, mt[j], y[j], &lo, &hi);
       const uint64_t key = kKeepKey ? ((static_cast<uint64_t>(kt[j]) << 32) | kl[j]) : own_key(kc, t, lo, hi);
-      if (qbits > B && !sel_match(qbits, w.pw(), key, lo, hi)) continue;
+      if (qbits > B0 && !sel_match(qbits, w.pw(), key, lo, hi)) continue;
       if (cnt == 1) {
         w.sel()->key = key;
         w.sel()->tb = tie_break(lo, hi);
@@ -1078,7 +1182,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     }
     if ((low ? 0 : 1) != r) {
       mt[j] = m | kMFlip;
-      if (m & kMMulti) flag_or(w.hf(), static_cast<int>(m & kMSlot), 16u << (2 * r + ((m & kMCol) ? 1 : 0)));
+      if (m & kMMulti) block_mark(w.hb(), m & kMSlot, 2 * r + ((m & kMCol) ? 1 : 0), 3);
     }
   }
   if (multi_any) tm.sync();
@@ -1109,13 +1213,13 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     if (!(m & kMUV)) {
       const uint32_t s = y[j] >> 1;
       if (tr.single || s < t32) {
-        const uint32_t fl = w.hf()[m & kMSlot];
+        const uint32_t fl = block_flags(w.hb()[m & kMSlot]);
         in_far = __popc(r ? (fl & 12u) : (fl & 3u)) == 1;   // trade s acted before t: initial block
       } else if (s < T32) {
         if (!(m & kMMulti)) {
           in_far = 1;
         } else {                           // block after t's own decisions: presence bits 0..3, flips 4..7
-          const uint32_t fl = w.hf()[m & kMSlot];
+          const uint32_t fl = block_flags(w.hb()[m & kMSlot]);
           const int myrow = r ^ f;
           int same = 0;
 #pragma unroll
@@ -1153,86 +1257,146 @@ constexpr int kWarpB = 7;                       // first radix digit: 128 bins
 constexpr int kWarpWarps = 8;                   // warps per CTA
 using WarpWs = RegWs<32 * kWarpJ, kWarpB>;
 
-__global__ void __launch_bounds__(32 * kWarpWarps) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ list,
-                                                                  const int64_t* __restrict__ count) {
+__global__ void __launch_bounds__(32 * kWarpWarps) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ lists,
+                                                                  const int64_t* __restrict__ ctr, int cls) {
   extern __shared__ __align__(16) char wsm[];
   const int wid = threadIdx.x >> 5;
   const WarpWs w{wsm + WarpWs::kBytes * wid};
   WarpTeam tm;
-  const int64_t len = *count;
+  const ClassList cl = class_list(lists, ctr, cls);
   const int64_t step = static_cast<int64_t>(gridDim.x) * kWarpWarps;
-  for (int64_t q = static_cast<int64_t>(blockIdx.x) * kWarpWarps + wid; q < len; q += step)
-    phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, list[q], w);
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * kWarpWarps + wid; q < cl.len; q += step)
+    phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, cl.list[q], w);
 }
 
-
-// Phase A of larger trades, one CTA of NT threads per trade (J entries per
-// thread in registers, so L <= NT J): trades of `list` with lmin < L <= lmax;
-// the others are left to another launch.
-template <int NT, int J, int B>
-__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_cta(StepCtx c, const int32_t* __restrict__ list,
-                                                                     const int64_t* __restrict__ count, int lmin,
-                                                                     int lmax) {
-  extern __shared__ __align__(16) char csm[];
-  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
-  BlockTeam<NT> tm(red);
-  const RegWs<NT * J, B> w{csm};
-  const int64_t len = *count;
-  for (int64_t q = blockIdx.x; q < len; q += gridDim.x) {
-    const int64_t t = list[q];
-    const TradeRows tr = trade_rows(c, t);
-    const int L = tr.du + tr.dv;
-    if (L <= lmin || L > lmax) continue;   // the same test in every thread
-    phase_a_reg<BlockTeam<NT>, J, B, false>(tm, c, t, w);
-  }
+// Phase A of larger trades: a CTA of CT threads holds CT / NT teams of NT
+// threads (named barriers), each running one trade at a time with kTeamJ
+// entries per thread in registers (L <= NT kTeamJ).
+constexpr int kTeamJ = 4;
+template <int NT>
+struct TeamCfg {
+  static constexpr int B = NT == 64 ? 8 : NT == 128 ? 9 : NT == 256 ? 10 : NT == 512 ? 11 : 12;   // ~1 bin per entry
+  using Ws = RegWs<NT * kTeamJ, B>;
+  static constexpr int kMax = NT * kTeamJ;
+};
+template <int CT, int NT>
+__global__ void __launch_bounds__(CT, CT == 256 ? 4 : 1) k_phase_a_team(StepCtx c, const int32_t* __restrict__ lists,
+                                                                      const int64_t* __restrict__ ctr, int cls) {
+  constexpr int kTeams = CT / NT;
+  using Ws = typename TeamCfg<NT>::Ws;
+  extern __shared__ __align__(16) char tsm[];
+  __shared__ int64_t red[kTeams * SubTeam<NT>::kRedSlots];
+  const int id = threadIdx.x / NT;
+  SubTeam<NT> tm(red + id * SubTeam<NT>::kRedSlots, id);
+  const Ws w{tsm + Ws::kBytes * id};
+  const ClassList cl = class_list(lists, ctr, cls);
+  const int64_t step = static_cast<int64_t>(gridDim.x) * kTeams;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * kTeams + id; q < cl.len; q += step)
+    phase_a_reg<SubTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, cl.list[q], w);
 }
-constexpr int kCtaJ = 4;         // entries per thread: up to 1024 on 256 threads, 4096 on 1024
-constexpr int kCta256B = 10;     // 1024 bins
-constexpr int kCta1024B = 12;    // 4096 bins
-constexpr size_t kCta256Ws = RegWs<256 * kCtaJ, kCta256B>::kBytes;
-constexpr size_t kCta1024Ws = RegWs<1024 * kCtaJ, kCta1024B>::kBytes;
-
-// Phase A of the largest trades (L > lmin) with the general procedure:
-// entries, keys and flags in a global-memory workspace slice per CTA.
-__global__ void __launch_bounds__(kBigThreads, 1) k_phase_a_huge(StepCtx c, const int32_t* __restrict__ list,
-                                                                const int64_t* __restrict__ count, int lmin,
-                                                                char* gws, size_t slice) {
-  __shared__ int64_t red[BlockTeam<kBigThreads>::kRedSlots];
-  __shared__ SelOut sel;
-  BlockTeam<kBigThreads> tm(red);
-  const int64_t len = *count;
-  for (int64_t q = blockIdx.x; q < len; q += gridDim.x) {
-    const int64_t t = list[q];
-    const TradeRows tr = trade_rows(c, t);
-    const int L = tr.du + tr.dv;
-    if (L <= lmin) continue;
-    if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
-    phase_a(tm, c, t, carve_a(gws + slice * blockIdx.x, L), &sel);
-  }
+template <int CT, int NT>
+constexpr size_t team_smem() {
+  return TeamCfg<NT>::Ws::kBytes * (CT / NT);
 }
 
 // ---------------------------------------------------------- classification
+//
+// Every trade falls into one of kClasses size classes (by L = deg u + deg v
+// against ascending thresholds), each run by its own team size.  The class
+// lists are one stable counting sort: counts per class and 2048-trade chunk,
+// one exclusive scan of those counts in class-major order (so each class's
+// list follows the previous class's), then every chunk places its trades,
+// in index order within each class.
 
-// Class of each trade: small (one warp), medium (256 threads), large (1024).
-__global__ void k_class_flags(StepCtx c, int64_t ntasks, int tile_max, int block_max, int32_t* __restrict__ f) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
-    const TradeRows tr = trade_rows(c, t);
-    const int L = tr.du + tr.dv;
-    const int cls = L <= tile_max ? 0 : (L <= block_max ? 1 : 2);
-    f[t] = cls == 0;
-    f[ntasks + t] = cls == 1;
-    f[2 * ntasks + t] = cls == 2;
+constexpr int kClassThreads = 256;
+constexpr int kClassPer = 8;
+constexpr int kClassChunk = kClassThreads * kClassPer;   // trades per chunk
+
+struct ClassTh {
+  int th[kClasses - 1];   // class k holds th[k-1] < L <= th[k] (th[-1] = -1, th[kClasses-1] = inf)
+};
+__device__ __forceinline__ int trade_class(const ClassTh& th, int L) {
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < kClasses - 1; ++i) k += L > th.th[i];
+  return k;
+}
+
+__global__ void __launch_bounds__(kClassThreads) k_class_count(StepCtx c, int64_t ntasks, ClassTh th,
+                                                               int64_t nchunks, int32_t* __restrict__ counts) {
+  __shared__ int wc[kClassThreads / 32][kClasses];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    int mine[kClasses] = {0, 0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < kClassPer; ++j) {
+      const int64_t t = ch * kClassChunk + j * kClassThreads + threadIdx.x;
+      int k = -1;
+      if (t < ntasks) {
+        const TradeRows tr = trade_rows(c, t);
+        k = trade_class(th, tr.du + tr.dv);
+      }
+#pragma unroll
+      for (int q = 0; q < kClasses; ++q) mine[q] += __popc(__ballot_sync(kFull, k == q));
+    }
+    if (lane == 0)
+      for (int q = 0; q < kClasses; ++q) wc[warp][q] = mine[q];
+    __syncthreads();
+    if (threadIdx.x < kClasses) {
+      int tot = 0;
+      for (int w = 0; w < kClassThreads / 32; ++w) tot += wc[w][threadIdx.x];
+      counts[threadIdx.x * nchunks + ch] = tot;
+    }
+    __syncthreads();
   }
 }
 
-// Stable compaction of each class into index order.
-__global__ void k_class_scatter(int64_t ntasks, const int32_t* __restrict__ f, const int64_t* __restrict__ sc,
-                                int32_t* __restrict__ l0, int32_t* __restrict__ l1, int32_t* __restrict__ l2) {
-  const int64_t n1 = ntasks + 1;
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < ntasks; t += int64_t(gridDim.x) * blockDim.x) {
-    if (f[t]) l0[sc[t]] = static_cast<int32_t>(t);
-    else if (f[ntasks + t]) l1[sc[n1 + t]] = static_cast<int32_t>(t);
-    else l2[sc[2 * n1 + t]] = static_cast<int32_t>(t);
+__global__ void __launch_bounds__(kClassThreads) k_class_place(StepCtx c, int64_t ntasks, ClassTh th,
+                                                               int64_t nchunks, const int64_t* __restrict__ off,
+                                                               int32_t* __restrict__ lists) {
+  __shared__ int wc[kClassThreads / 32][kClasses];
+  __shared__ int64_t base[kClasses];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    if (threadIdx.x < kClasses) base[threadIdx.x] = off[threadIdx.x * nchunks + ch];
+    __syncthreads();
+    for (int j = 0; j < kClassPer; ++j) {
+      const int64_t t = ch * kClassChunk + j * kClassThreads + threadIdx.x;
+      int k = -1;
+      if (t < ntasks) {
+        const TradeRows tr = trade_rows(c, t);
+        k = trade_class(th, tr.du + tr.dv);
+      }
+      unsigned same = 0;
+#pragma unroll
+      for (int q = 0; q < kClasses; ++q) {
+        const unsigned b = __ballot_sync(kFull, k == q);
+        if (k == q) same = b;
+        if (lane == 0) wc[warp][q] = __popc(b);
+      }
+      __syncthreads();
+      if (k >= 0) {
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += wc[w][k];
+        lists[base[k] + before + __popc(same & below)] = static_cast<int32_t>(t);
+      }
+      __syncthreads();
+      if (threadIdx.x < kClasses) {
+        int tot = 0;
+        for (int w = 0; w < kClassThreads / 32; ++w) tot += wc[w][threadIdx.x];
+        base[threadIdx.x] += tot;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Each class's first list entry and length into the counters.
+__global__ void k_class_bounds(const int64_t* __restrict__ off, int64_t nchunks, int64_t* __restrict__ ctr) {
+  const int k = threadIdx.x;
+  if (k < kClasses) {
+    ctr[kCtrClsStart + k] = off[k * nchunks];
+    ctr[kCtrClsLen + k] = off[(k + 1) * nchunks] - off[k * nchunks];
   }
 }
 
@@ -1376,9 +1540,9 @@ __global__ void __launch_bounds__(kFixThreads) k_fixup(StepCtx c, int64_t nnz, u
 // ---------------------------------------------------------------- team paths
 
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx c, const int32_t* __restrict__ list,
-                                                      const int64_t* __restrict__ count, int smem_max, char* gws,
-                                                      size_t slice, int stage_cap) {
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx c, const int32_t* __restrict__ lists,
+                                                      const int64_t* __restrict__ ctr, int cls, int smem_max,
+                                                      char* gws, size_t slice, int stage_cap) {
   // dynamic shared memory: the workspace, then the staging buffer of a
   // trade's entries (stage_cap + 8 int32, 16-byte aligned)
   extern __shared__ __align__(16) char sbuf[];
@@ -1386,7 +1550,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
   __shared__ SelOut sel;
   __shared__ uint64_t mbar;
   BlockTeam<NT> tm(red);
-  const int64_t len = *count;
+  const ClassList cl = class_list(lists, ctr, cls);
+  const int32_t* list = cl.list;
+  const int64_t len = cl.len;
   int32_t* stage = reinterpret_cast<int32_t*>(sbuf + ((ws_a_bytes(smem_max) + 127) & ~size_t(127)));
   if (threadIdx.x == 0) {
     mbar_init(&mbar, 1);
@@ -1522,8 +1688,11 @@ int init_trade_kernels(Graph* h) {
                                   static_cast<int>(ws_a_bytes(kBlockMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_cta<kBigThreads, kCtaJ, kCta1024B>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kCta1024Ws)));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(team_smem<kBigThreads, 512>())));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, kBigThreads>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(team_smem<kBigThreads, kBigThreads>())));
   // shared memory, not L1, limits how many CTAs of these kernels an SM holds
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
@@ -1574,30 +1743,47 @@ int super_step(Graph* h) {
   // claimed by the in-order pass, [kCounters-1] global-workspace trades
   int64_t* cnt = h->counters;
   unsigned long long* ucnt = reinterpret_cast<unsigned long long*>(cnt);
-  c.gws_count = ucnt + kCounters - 1;
+  c.gws_count = ucnt + kCtrGws;
   CB_CUDA(h, cudaMemsetAsync(cnt, 0, kCounters * sizeof(int64_t), s));
   const int64_t ntasks = h->ntasks;
   if (ntasks == 0) return finish_step(h);
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * ntasks, s));
-  const int tile_max = std::min(h->tile_max, kTileMaxCap);
+  const int tile_max = h->tile_paths ? std::min(h->tile_max, kTileMaxCap) : 0;
   const int block_max = std::max(h->block_max, tile_max);
+  // size classes: warp (L <= tile_max), teams of 64 / 128 / 256 threads (up
+  // to 256 / 512 / block_max <= 1024 entries), of 512 / 1024 threads in a
+  // 1024-thread CTA (up to 2048 / min(4096, smem_max)), and the largest
+  // trades on the shared-memory kernel; "cta_paths" 0 sends everything above
+  // the warp class to the shared-memory kernels (256 threads up to
+  // block_max, 1024 above)
+  ClassTh th;
+  {
+    const int lreg = std::min(TeamCfg<kBigThreads>::kMax, h->smem_max);
+    const int t3 = h->cta_paths ? std::max(tile_max, std::min(block_max, TeamCfg<256>::kMax)) : block_max;
+    const int t5 = h->cta_paths ? std::max(t3, lreg) : t3;
+    th.th[0] = tile_max;
+    th.th[1] = h->cta_paths ? std::min(std::max(TeamCfg<64>::kMax, tile_max), t3) : tile_max;
+    th.th[2] = h->cta_paths ? std::min(std::max(TeamCfg<128>::kMax, th.th[1]), t3) : tile_max;
+    th.th[3] = t3;
+    th.th[4] = h->cta_paths ? std::min(std::max(TeamCfg<512>::kMax, t3), t5) : t3;
+    th.th[5] = t5;
+  }
   auto grid_n = [&](int64_t work) {
     return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, h->num_sms * 8)));
   };
-  {  // classes in index order (stable compaction)
-    k_class_flags<<<grid_n(ntasks), 256, 0, s>>>(c, ntasks, tile_max, block_max, h->cls_flag);
+  {  // class lists: a stable counting sort of the trades by class
+    const int64_t nch = (ntasks + kClassChunk - 1) / kClassChunk;
+    const unsigned cgrid = static_cast<unsigned>(std::min<int64_t>(nch, int64_t(h->num_sms) * 8));
+    k_class_count<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, h->cls_flag);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
-    const int64_t n1 = ntasks + 1;
-    for (int q = 0; q < 3; ++q)
-      CB_CUDA(h, exclusive_scan_i32(h->cls_flag + q * ntasks, h->cls_scan + q * n1, ntasks, h->scan_ws, s,
-                                    &h->launches));
-    k_class_scatter<<<grid_n(ntasks), 256, 0, s>>>(ntasks, h->cls_flag, h->cls_scan, h->list[0], h->list[1],
-                                                    h->list[2]);
+    CB_CUDA(h, exclusive_scan_i32(h->cls_flag, h->cls_scan, kClasses * nch, h->scan_ws, s, &h->launches));
+    k_class_place<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, h->cls_scan, h->lists);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
-    for (int q = 0; q < 3; ++q)
-      CB_CUDA(h, cudaMemcpyAsync(cnt + q, h->cls_scan + q * n1 + ntasks, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_class_bounds<<<1, 32, 0, s>>>(h->cls_scan, nch, cnt);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
   }
   const size_t med_smem = ws_a_bytes(std::max(block_max, 1));      // in-order pass (no staging)
   const size_t big_smem = ws_a_bytes(std::max(h->smem_max, 1));
@@ -1605,58 +1791,46 @@ int super_step(Graph* h) {
   const size_t big_smem_st = block_smem_bytes(std::max(h->smem_max, 1));
   const unsigned mgrid = static_cast<unsigned>(h->num_sms * 4);
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
+  const unsigned sgrid = static_cast<unsigned>(h->num_sms);
   char* gws = static_cast<char*>(h->ws_global);
   // phase A, first pass: every class; a trade whose dependency has not
-  // published yet is marked deferred.  Counters: [4] deferred trades, [5]
-  // chunks claimed by the in-order pass.
+  // published yet is marked deferred.
   c.wait = 0;
-  c.def_count = ucnt + 4;
+  c.def_count = ucnt + kCtrDeferred;
   c.cand_max = h->cand_max;
   c.wait_ns = h->wait_ns;
   c.hold_publish = h->hold_publish;
-  if (h->tile_paths) {
-    k_phase_a_warp<<<static_cast<unsigned>(h->num_sms * 8), 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(
-        c, h->list[0], cnt + 0);
-  } else {
-    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[0], cnt + 0, block_max, gws,
-                                                                        h->ws_slice, block_max);
-  }
-  CB_CUDA(h, cudaGetLastError());
-  ++h->launches;
+  const int32_t* L = h->lists;
+  auto launched = [&]() -> int {
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    return CB_OK;
+  };
+  k_phase_a_warp<<<static_cast<unsigned>(h->num_sms * 8), 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(
+      c, L, cnt, 0);
+  if ((rc = launched())) return rc;
   if (h->cta_paths) {
-    // registers: up to 1024 entries on 256 threads, up to min(4096, smem_max)
-    // on 1024; larger trades from a global-memory workspace
-    const int l256 = kCtaJ * kMedThreads, l1024 = kCtaJ * kBigThreads;
-    const int lreg = std::min(l1024, h->smem_max);
-    const unsigned big_grid = static_cast<unsigned>(h->num_sms);
-    k_phase_a_cta<kMedThreads, kCtaJ, kCta256B><<<mgrid, kMedThreads, kCta256Ws, s>>>(c, h->list[1], cnt + 1, 0, l256);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-    if (block_max > l256) {   // the 256-thread class holds trades above the 256-thread registers
-      k_phase_a_cta<kBigThreads, kCtaJ, kCta1024B><<<big_grid, kBigThreads, kCta1024Ws, s>>>(c, h->list[1], cnt + 1,
-                                                                                            l256, l1024);
-      CB_CUDA(h, cudaGetLastError());
-      ++h->launches;
-    }
-    k_phase_a_cta<kBigThreads, kCtaJ, kCta1024B><<<big_grid, kBigThreads, kCta1024Ws, s>>>(c, h->list[2], cnt + 2, 0,
-                                                                                          lreg);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-    if (gws) {
-      k_phase_a_huge<<<bgrid, kBigThreads, 0, s>>>(c, h->list[2], cnt + 2, lreg, gws, h->ws_slice);
-      CB_CUDA(h, cudaGetLastError());
-      ++h->launches;
-    }
+    k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 1);
+    if ((rc = launched())) return rc;
+    k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 2);
+    if ((rc = launched())) return rc;
+    k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 3);
+    if ((rc = launched())) return rc;
+    k_phase_a_team<kBigThreads, 512><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt, 4);
+    if ((rc = launched())) return rc;
+    k_phase_a_team<kBigThreads, kBigThreads><<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(
+        c, L, cnt, 5);
+    if ((rc = launched())) return rc;
   } else {
-    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, h->list[1], cnt + 1, block_max, gws,
-                                                                        h->ws_slice, block_max);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, h->list[2], cnt + 2, h->smem_max, gws,
-                                                                        h->ws_slice, h->smem_max);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
+    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 3, block_max, gws, h->ws_slice,
+                                                                        block_max);
+    if ((rc = launched())) return rc;
   }
+  // the largest trades: 1024 threads, up to smem_max entries in shared memory
+  // (staged by a bulk copy), a global-memory slice above
+  k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 6, h->smem_max, gws, h->ws_slice,
+                                                                      h->smem_max);
+  if ((rc = launched())) return rc;
   // second pass: the deferred trades in index order, waiting on dependencies.
   // 1024-thread CTAs keep large trades in shared memory; 256-thread CTAs (four
   // per SM) run many small deferred trades at once, large ones from a global
@@ -1664,14 +1838,14 @@ int super_step(Graph* h) {
   c.wait = 1;
   if (h->inorder_threads == kBigThreads) {
     const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
-    k_phase_a_inorder<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + 5, h->smem_max, gws,
+    k_phase_a_inorder<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims, h->smem_max, gws,
                                                                        h->ws_slice);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
   } else {
     const unsigned igrid = static_cast<unsigned>(gws ? std::min(h->num_sms * 4, h->ws_ctas) : h->num_sms * 4);
     const int64_t chunk = std::max<int64_t>(512, (ntasks + int64_t(igrid) * 4 - 1) / (int64_t(igrid) * 4));
-    k_phase_a_inorder<kMedThreads><<<igrid, kMedThreads, med_smem, s>>>(c, ntasks, chunk, ucnt + 5, block_max, gws,
+    k_phase_a_inorder<kMedThreads><<<igrid, kMedThreads, med_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims, block_max, gws,
                                                                        h->ws_slice);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
