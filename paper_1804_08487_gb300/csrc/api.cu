@@ -265,9 +265,9 @@ int finish_create(Graph* h) {
       dmalloc(h, &h->sort_ws, h->sort_ws_bytes) || dmalloc(h, &h->scan_ws, h->scan_ws_bytes))
     return fail(h, CB_ENOMEM, "device allocation failed");
   CB_CUDA(h, cudaMemsetAsync(h->done, 0, sizeof(uint32_t) * std::max<int64_t>(h->ntasks, 1), s));
-  // the rebuild reads 8 placeholders (32 B) and 8 side bytes per vector load
+  // the rebuild reads 8 placeholders (32 B) and 8 side words (16 B) per vector load
   if ((reinterpret_cast<uintptr_t>(h->col[0]) | reinterpret_cast<uintptr_t>(h->col[1])) % 16 ||
-      reinterpret_cast<uintptr_t>(h->stash) % 8)
+      reinterpret_cast<uintptr_t>(h->stash) % 16)
     return fail(h, CB_ECUDA, "device allocation not aligned for vector loads");
   if ((rc = size_trade_workspace(h))) return rc;
   // rows in id space, sorted (sorted input is used as it is), then validated:
@@ -432,7 +432,7 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   const int64_t nb = int64_t(1) << bucket_bits(n);
   int64_t b = 0;
   b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * (nnz + kColPad) + 32 + 8 * kCounters;   // cb_create
-  b += 2 * 4 * n + 2 * 8 * (n + 1) + 4 * 4 * n + nnz;                                     // per node, side bytes
+  b += 2 * 4 * n + 2 * 8 * (n + 1) + 4 * 4 * n + 2 * nnz;                                 // per node, side words
   b += ntasks * (8 + 8 + 4 + 16 + 1 + 4) + 4 * cls_flag_count(ntasks, nnz) + 8 * cls_scan_count(ntasks) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;

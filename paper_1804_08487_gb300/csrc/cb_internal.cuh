@@ -93,7 +93,7 @@ struct Graph {
   int32_t* M = nullptr;                    // step-g position -> step-(g+1) position
   int32_t* Minv = nullptr;                 // step-(g+1) position -> step-g position
   int32_t* deg_next = nullptr;             // degree by step-(g+1) position
-  uint8_t* stash = nullptr;                // per placed entry (step g+1 layout): bit0 own flip, bits 1..7 far key prefix
+  uint16_t* stash = nullptr;               // per placed entry (step g+1 layout): bit0 own flip, bits 1.. far key prefix
   uint64_t* thr_key = nullptr;             // per trade: threshold key
   uint8_t* thr_top = nullptr;              // per trade: top 6 bits of the threshold key
   uint64_t* thr_tb = nullptr;              // per trade: threshold tie-break (lo<<32|hi)

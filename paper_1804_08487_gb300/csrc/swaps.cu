@@ -11,18 +11,18 @@
 namespace cb {
 namespace {
 
-// out[0] += moved entries among all nnz, out[1] += rp[two_t] (the entries of
+// out[0] += moved entries among all nnz (bit 0 of each side word), out[1] += rp[two_t] (the entries of
 // the traded positions' rows in the step just done).
-__global__ void k_count_flips(const uint8_t* __restrict__ stash, int64_t nnz, const int64_t* __restrict__ rp,
+__global__ void k_count_flips(const uint16_t* __restrict__ stash, int64_t nnz, const int64_t* __restrict__ rp,
                               int64_t two_t, unsigned long long* out) {
   const int64_t end = nnz;
-  const int64_t words = end >> 2;
+  const int64_t words = end >> 1;
   const int64_t tid = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   unsigned long long local = 0;
   const uint32_t* w = reinterpret_cast<const uint32_t*>(stash);
-  for (int64_t i = tid; i < words; i += stride) local += __popc(__ldg(w + i) & 0x01010101u);
-  for (int64_t e = (words << 2) + tid; e < end; e += stride) local += stash[e] & 1u;
+  for (int64_t i = tid; i < words; i += stride) local += __popc(__ldg(w + i) & 0x00010001u);
+  for (int64_t e = (words << 1) + tid; e < end; e += stride) local += stash[e] & 1u;
 #pragma unroll
   for (int o = 16; o; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(&out[0], local);

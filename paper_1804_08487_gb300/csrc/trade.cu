@@ -63,7 +63,7 @@ struct StepCtx {
   const int32_t* seg_of;    // graph of each position (null: one graph)
   const int64_t* rp;
   const int32_t* col;
-  uint8_t* fb;              // side byte of every placed entry (step g+1 layout)
+  uint16_t* fb;             // side word of every placed entry (step g+1 layout)
   int32_t* ph;              // placeholders of every entry in its new row (step g+1 layout)
   const int32_t* Minv;      // step-(g+1) position -> step-g position
   uint64_t* thr_key;
@@ -263,6 +263,12 @@ constexpr int kSelBins = 1 << kSelBits;
 // meta bits per entry (team paths add the neighbour's column bit)
 constexpr uint8_t kCol = 16;    // neighbour sits at the odd position 2s+1
 constexpr uint8_t kPend = 32;   // not placed in the hash yet
+// Bits of the far trade's key an entry's side word keeps (the rebuild decides
+// with them unless they equal the far threshold's, 1 in 2^kFarBits).
+constexpr int kFarBits = 11;
+// Placeholder and side-word bits (see the rebuild's fix-up).
+constexpr uint32_t kPhDone = 0x80000000u;   // placeholder resolved by an earlier pass (new position in bits 0..30)
+constexpr uint32_t kFbInFar = 1u << 12;     // side word: the far trade decides the edge
 
 constexpr int kCand = 32;       // candidates sharing the threshold's bin, ranked by full key
 
@@ -274,7 +280,7 @@ struct WsA {
   int32_t* slot;              // hash slot of the entry's far trade (-1: the edge {u,v})
   uint16_t* top;              // top 16 bits of the own key
   uint8_t* meta;
-  uint8_t* far;               // top 6 bits of the far trade's key
+  uint16_t* far;              // top kFarBits bits of the far trade's key
   uint32_t* hkey;             // 2^lgH slot keys
   uint8_t* hflag;             // 2^lgH slot flag bytes
   uint32_t* hist;             // kSelBins bins
@@ -290,7 +296,7 @@ __host__ __device__ inline int hash_lg(int L) {
 __host__ __device__ inline size_t ws_a_bytes(int L) {
   const size_t L16 = (static_cast<size_t>(L) + 15) & ~size_t(15);
   const size_t H = size_t(1) << hash_lg(L);
-  return H * 4 + ((H + 15) & ~size_t(15)) + kSelBins * 4 + kCand * 20 + 16 + L16 * 4 + L16 * 2 + L16 + L16 + 64;
+  return H * 4 + ((H + 15) & ~size_t(15)) + kSelBins * 4 + kCand * 20 + 16 + L16 * 4 + L16 * 2 + L16 + L16 * 2 + 64;
 }
 // Dynamic shared memory of k_phase_a_block: workspace for `cap` entries, then
 // the staging buffer of a trade's entries.
@@ -314,7 +320,7 @@ __device__ inline WsA carve_a(void* base, int L) {
   w.slot = reinterpret_cast<int32_t*>(p); p += L16 * 4;
   w.top = reinterpret_cast<uint16_t*>(p); p += L16 * 2;
   w.meta = reinterpret_cast<uint8_t*>(p); p += L16;
-  w.far = reinterpret_cast<uint8_t*>(p);
+  w.far = reinterpret_cast<uint16_t*>(p);
   return w;
 }
 
@@ -587,7 +593,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     const bool lo_mine = (lo >> 1) == t32;
     const uint32_t top = static_cast<uint32_t>((lo_mine ? ek.lo_side : ek.hi_side) >> 48);
     w.top[i] = static_cast<uint16_t>(top);
-    w.far[i] = static_cast<uint8_t>((lo_mine ? ek.hi_side : ek.lo_side) >> 57);
+    w.far[i] = static_cast<uint16_t>((lo_mine ? ek.hi_side : ek.lo_side) >> (64 - kFarBits));
     if (!other && !tr.single) {
       m |= kInD;
       cnt_a += (r == 0);
@@ -767,8 +773,8 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     const int k = side ? s1++ : s0++;
     if (k >= (side ? dv : du)) continue;   // counts checked above: never write outside the row
     const int64_t slot = (side ? ov : ou) + k;
-    c.ph[slot] = entry_y(w, t2, i) | (in_far ? static_cast<int32_t>(0x80000000u) : 0);
-    c.fb[slot] = static_cast<uint8_t>(f | (in_far ? (w.far[i] << 1) : 0));
+    c.ph[slot] = entry_y(w, t2, i);
+    c.fb[slot] = static_cast<uint16_t>(f | (in_far ? ((w.far[i] << 1) | kFbInFar) : 0u));
   }
   if (tm.rank == 0 && !tr.single) {
     c.thr_key[t] = tk;
@@ -793,15 +799,15 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
 // published yet is deferred to the in-order pass.
 
 // per-entry meta word
-constexpr uint32_t kMSlot = 0xFFFFu;        // hash slot of the far trade
-constexpr uint32_t kMR = 1u << 16;          // entry sits in v's row
-constexpr uint32_t kMCol = 1u << 17;        // neighbour at the odd position 2s+1
-constexpr uint32_t kMUV = 1u << 18;         // the edge {u, v}
-constexpr uint32_t kMInD = 1u << 19;        // element of D
-constexpr uint32_t kMFlip = 1u << 20;       // the trade moves the edge to its other node
-constexpr uint32_t kMValid = 1u << 21;      // an entry of the trade
-constexpr uint32_t kMMulti = 1u << 22;      // block of two or more edges
-constexpr int kMFarShift = 24;              // bits 24..30: top 7 bits of the far trade's key
+constexpr uint32_t kMSlot = 0x3FFFu;        // hash slot of the far trade (tables of at most 2^14 slots)
+constexpr uint32_t kMR = 1u << 14;          // entry sits in v's row
+constexpr uint32_t kMCol = 1u << 15;        // neighbour at the odd position 2s+1
+constexpr uint32_t kMUV = 1u << 16;         // the edge {u, v}
+constexpr uint32_t kMInD = 1u << 17;        // element of D
+constexpr uint32_t kMFlip = 1u << 18;       // the trade moves the edge to its other node
+constexpr uint32_t kMValid = 1u << 19;      // an entry of the trade
+constexpr uint32_t kMMulti = 1u << 20;      // block of two or more edges
+constexpr int kMFarShift = 21;              // bits 21..31: top kFarBits bits of the far trade's key
 
 __host__ __device__ constexpr int hash_lg_c(int L) {
   int lg = 1;
@@ -1020,7 +1026,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     const uint64_t far = lo_mine ? ek.hi_side : ek.lo_side;
     kt[j] = static_cast<uint32_t>(own >> 32);
     if (kKeepKey) kl[j] = static_cast<uint32_t>(own);
-    m |= static_cast<uint32_t>(far >> 57) << kMFarShift;
+    m |= static_cast<uint32_t>(far >> (64 - kFarBits)) << kMFarShift;
     if (!other && !tr.single) {
       m |= kMInD;
       cnt_a += (r == 0);
@@ -1235,8 +1241,8 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     const int k = side ? s1++ : s0++;
     if (k >= (side ? tr.dv : du)) continue;   // counts checked above: never write outside the row
     const int64_t slot = (side ? ov : ou) + k;
-    c.ph[slot] = static_cast<int32_t>(y[j] | (static_cast<uint32_t>(in_far) << 31));
-    c.fb[slot] = static_cast<uint8_t>(f | (in_far ? (((m >> kMFarShift) & 127u) << 1) : 0u));
+    c.ph[slot] = static_cast<int32_t>(y[j]);
+    c.fb[slot] = static_cast<uint16_t>(f | (in_far ? (((m >> kMFarShift) << 1) | kFbInFar) : 0u));
   }
   if (tm.rank == 0 && !tr.single) {
     c.thr_key[t] = tk;
@@ -1403,18 +1409,19 @@ __global__ void k_class_bounds(const int64_t* __restrict__ off, int64_t nchunks,
 // ------------------------------------------------------ rebuild: fix-up
 //
 // Phase A leaves every entry in its new row (step g+1 layout) as a
-// placeholder: the far end's step-g position y with bit 31 set when the far
-// trade decides the edge, and a side byte (bit 0 the own trade's flip, bits
-// 1..7 the top 7 bits of the far trade's key for the edge).  The fix-up
+// placeholder: the far end's step-g position y, and a side word (bit 0 the
+// own trade's flip, bits 1..kFarBits the top bits of the far trade's key for
+// the edge, bit 12 set when the far trade decides the edge).  The fix-up
 // replaces each placeholder by the step-(g+1) position of the far end: y
 // itself, or the node of y's trade that the trade's threshold gives it.  One
 // 8-byte record per far trade holds both of its nodes' new positions and its
 // threshold's top 8 bits; the pass runs once per slice of far trades small
 // enough for the records to stay in L2, each pass reading every placeholder
-// and writing the entries of its slice.  A prefix tie (1 in 128) needs the
-// full key, hence the edge's own end at the start of the step: the node of
-// the entry's row (found by a search of the chunk's row offsets) before the
-// own flip.
+// and writing the entries of its slice.  Equal 8-bit prefixes (1 in 256)
+// fetch the far threshold's longer prefix; a tie there too (1 in 2^kFarBits)
+// needs the full key, hence the edge's own end at the start of the step: the
+// node of the entry's row (found by a search of the chunk's row offsets)
+// before the own flip.
 
 constexpr int kFixThreads = 256;
 constexpr int kFixPer = 8;                             // consecutive entries per thread
@@ -1480,61 +1487,142 @@ __device__ __forceinline__ int64_t fix_row(const StepCtx& c, const int32_t* chun
   return lo;
 }
 
+constexpr int kFixQueue = 2 * kFixChunk;    // prefix ties a CTA defers before resolving them together
+
+// The kFixPer placeholders and side words of a thread starting at entry base
+// (entries at or past nnz read as 0xFFFFFFFF).
+template <bool kStream>
+__device__ __forceinline__ void fix_load(const int32_t* ph, const uint16_t* fb, int64_t base, int64_t nnz,
+                                         uint32_t* pv, uint32_t* bv) {
+  if (base + kFixPer <= nnz) {   // 32 B and 16 B, aligned: chunks start at multiples of 2048 entries
+    const uint4* p4 = reinterpret_cast<const uint4*>(ph + base);
+    const uint4 a0 = kStream ? __ldcs(p4) : __ldcg(p4);
+    const uint4 a1 = kStream ? __ldcs(p4 + 1) : __ldcg(p4 + 1);
+    pv[0] = a0.x; pv[1] = a0.y; pv[2] = a0.z; pv[3] = a0.w;
+    pv[4] = a1.x; pv[5] = a1.y; pv[6] = a1.z; pv[7] = a1.w;
+    const uint4 b = __ldcs(reinterpret_cast<const uint4*>(fb + base));
+    bv[0] = b.x; bv[1] = b.y; bv[2] = b.z; bv[3] = b.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kFixPer / 2; ++j) bv[j] = 0;
+#pragma unroll
+    for (int j = 0; j < kFixPer; ++j) {
+      const bool in = base + j < nnz;
+      pv[j] = in ? static_cast<uint32_t>(ph[base + j]) : 0xFFFFFFFFu;
+      if (in) bv[j >> 1] |= static_cast<uint32_t>(fb[base + j]) << (16 * (j & 1));
+    }
+  }
+}
+
+// The new position of entry e's far end when its 8-bit key prefix equals
+// the far threshold's: the threshold's longer prefix, and on a tie there too
+// the full key of the edge (its own end at the start of the step is the
+// node of the entry's row before the own flip).
 template <bool kNarrow>
-__global__ void __launch_bounds__(kFixThreads) k_fixup(StepCtx c, int64_t nnz, uint32_t s_lo, uint32_t s_hi,
-                                                       const int32_t* __restrict__ ph, const uint8_t* __restrict__ fb,
+__device__ uint32_t fix_tie(const StepCtx& c, const void* pack, const int32_t* chunk_row, int64_t e, uint32_t y,
+                            uint32_t b) {
+  const uint32_t s = y >> 1;
+  const FarTrade ft = far_trade<kNarrow>(pack, s);
+  const uint32_t fp = (b >> 1) & ((1u << kFarBits) - 1u);
+  const uint32_t tp = static_cast<uint32_t>(__ldcg(c.thr_key + s) >> (64 - kFarBits));
+  bool low;
+  if (fp != tp) {
+    low = fp < tp;
+  } else {
+    const uint32_t xr = static_cast<uint32_t>(c.Minv[fix_row(c, chunk_row, e / kFixChunk, e)]) ^ (b & 1u);
+    low = far_keeps_low(c, key_ctx(c, s), s, min(xr, y), max(xr, y));
+  }
+  return static_cast<uint32_t>(low ? ft.x : ft.y);
+}
+
+// One pass over far trades [s_lo, s_hi).  A pass other than the last writes
+// the new positions of its entries into the placeholders (marked kPhDone);
+// the last one writes every entry's new position to `out` in full vectors.
+// Entries whose 8-bit prefix ties wait in a per-CTA queue and are resolved
+// together, so that their extra loads hold up no warp.
+template <bool kNarrow, bool kLast>
+__global__ void __launch_bounds__(kFixThreads, 5) k_fixup(StepCtx c, int64_t nnz, uint32_t s_lo, uint32_t s_hi,
+                                                       int32_t* __restrict__ ph, const uint16_t* __restrict__ fb,
                                                        int32_t* __restrict__ out, const void* __restrict__ pack,
                                                        const int32_t* __restrict__ chunk_row) {
-  const int64_t nchunks = (nnz + kFixChunk - 1) / kFixChunk;
-  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int64_t base = ch * kFixChunk + static_cast<int64_t>(threadIdx.x) * kFixPer;
-    if (base >= nnz) continue;
-    uint32_t pv[kFixPer];
-    uint32_t bv[2];
-    if (base + kFixPer <= nnz) {   // 32 B and 8 B, aligned: chunks start at multiples of 2048 entries
-      const uint4 a0 = __ldcs(reinterpret_cast<const uint4*>(ph + base));
-      const uint4 a1 = __ldcs(reinterpret_cast<const uint4*>(ph + base) + 1);
-      pv[0] = a0.x; pv[1] = a0.y; pv[2] = a0.z; pv[3] = a0.w;
-      pv[4] = a1.x; pv[5] = a1.y; pv[6] = a1.z; pv[7] = a1.w;
-      const uint2 b = __ldcs(reinterpret_cast<const uint2*>(fb + base));
-      bv[0] = b.x;
-      bv[1] = b.y;
-    } else {
-      bv[0] = bv[1] = 0;
-#pragma unroll
-      for (int j = 0; j < kFixPer; ++j) {
-        pv[j] = base + j < nnz ? static_cast<uint32_t>(ph[base + j]) : 0xFFFFFFFFu;
-        if (base + j < nnz) bv[j >> 2] |= static_cast<uint32_t>(fb[base + j]) << (8 * (j & 3));
-      }
+  __shared__ int64_t qe[kFixQueue];
+  __shared__ int qn;
+  if (threadIdx.x == 0) qn = 0;
+  __syncthreads();
+  auto flush = [&]() {
+    const int k = qn;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+      const int64_t e = qe[i];
+      const uint32_t y = static_cast<uint32_t>(ph[e]);
+      const uint32_t v = fix_tie<kNarrow>(c, pack, chunk_row, e, y, fb[e]);
+      if (kLast) out[e] = static_cast<int32_t>(v);
+      else ph[e] = static_cast<int32_t>(v | kPhDone);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+  };
+  const int64_t nchunks = (nnz + kFixChunk - 1) / kFixChunk;
+  const int64_t tofs = static_cast<int64_t>(threadIdx.x) * kFixPer;
+  uint32_t pv[kFixPer], bv[kFixPer / 2];
+  int64_t ch = blockIdx.x;
+  if (ch < nchunks) fix_load<kLast>(ph, fb, ch * kFixChunk + tofs, nnz, pv, bv);
+  for (; ch < nchunks; ch += gridDim.x) {
+    const int64_t base = ch * kFixChunk + tofs;
+    // the next chunk's loads go out before this chunk's gathers
+    uint32_t pn[kFixPer], bn[kFixPer / 2];
+    const int64_t nxt = ch + gridDim.x;
+    if (nxt < nchunks) fix_load<kLast>(ph, fb, nxt * kFixChunk + tofs, nnz, pn, bn);
+    uint32_t res[kFixPer];
 #pragma unroll
     for (int j = 0; j < kFixPer; ++j) {
       const uint32_t p = pv[j];
-      const uint32_t y = p & 0x7FFFFFFFu;
-      const uint32_t s = y >> 1;
+      res[j] = 0u;
       if (p == 0xFFFFFFFFu) continue;
+      if (p & kPhDone) {   // an earlier pass resolved it
+        res[j] = p & ~kPhDone;
+        continue;
+      }
+      const uint32_t y = p, s = y >> 1;
       if (y >= static_cast<uint32_t>(c.n)) {   // a slot phase A did not fill
         latch(c.err, kErrRowLength);
         continue;
       }
-      if (s < s_lo || s >= s_hi) continue;
+      if (s < s_lo || s >= s_hi) continue;   // another pass's (never the last pass's)
       const FarTrade ft = far_trade<kNarrow>(pack, s);
+      const uint32_t b = (bv[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
       int side = static_cast<int>(y & 1u);
-      if (p >> 31) {   // the far trade decides: prefixes first, the full key on a tie
-        const uint32_t b = (bv[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-        const uint32_t fp = b >> 1, tp = ft.top >> 1;
-        if (fp != tp) {
-          side = fp < tp ? 0 : 1;
-        } else {
-          const int64_t e = base + j;
-          const uint32_t xr = static_cast<uint32_t>(c.Minv[fix_row(c, chunk_row, ch, e)]) ^ (b & 1u);
-          const uint32_t lo = min(xr, y), hi = max(xr, y);
-          side = far_keeps_low(c, key_ctx(c, s), s, lo, hi) ? 0 : 1;
+      if (b & kFbInFar) {   // the far trade decides: key prefixes first
+        const uint32_t f8 = ((b >> 1) & ((1u << kFarBits) - 1u)) >> (kFarBits - 8);
+        if (f8 == ft.top) {   // 1 in 256: resolved with the queue
+          qe[atomicAdd(&qn, 1)] = base + j;
+          continue;
         }
+        side = f8 < ft.top ? 0 : 1;
       }
-      out[base + j] = side ? ft.y : ft.x;
+      res[j] = static_cast<uint32_t>(side ? ft.y : ft.x);
+      if (!kLast) ph[base + j] = static_cast<int32_t>(res[j] | kPhDone);
     }
+    if (kLast) {
+      if (base + kFixPer <= nnz) {
+        uint4* o4 = reinterpret_cast<uint4*>(out + base);
+        __stcs(o4, make_uint4(res[0], res[1], res[2], res[3]));
+        __stcs(o4 + 1, make_uint4(res[4], res[5], res[6], res[7]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < kFixPer; ++j)
+          if (base + j < nnz) out[base + j] = static_cast<int32_t>(res[j]);
+      }
+    }
+    __syncthreads();   // queued entries (and, on the last pass, their vector stores) are in place
+    if (qn > kFixQueue - kFixChunk) flush();   // room for a whole chunk more
+#pragma unroll
+    for (int j = 0; j < kFixPer; ++j) pv[j] = pn[j];
+#pragma unroll
+    for (int j = 0; j < kFixPer / 2; ++j) bv[j] = bn[j];
   }
+  __syncthreads();
+  flush();
 }
 
 // ---------------------------------------------------------------- team paths
@@ -1706,7 +1794,7 @@ size_t trade_smem_bytes(int entries) { return ws_a_bytes(entries); }
 
 // Passes of the fix-up: enough that one pass's far-trade records (8 or 16
 // bytes per trade) stay below kFixSliceBytes, or the "fix_passes" option.
-constexpr int64_t kFixSliceBytes = int64_t(48) << 20;
+constexpr int64_t kFixSliceBytes = int64_t(72) << 20;
 int fix_passes(const Graph* h) {
   if (h->fix_passes > 0) return h->fix_passes;
   const int64_t rec = (h->n <= kNarrowPackMax && !h->wide_pack) ? 8 : 16;
@@ -1869,15 +1957,15 @@ int super_step(Graph* h) {
       ++h->launches;
       const int passes = fix_passes(h);
       const int64_t per = (ntasks + passes - 1) / passes;
-      const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 8));
+      const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 5));
       int32_t* out = h->col[h->cur];
       for (int q = 0; q < passes; ++q) {
         const uint32_t lo = static_cast<uint32_t>(std::min<int64_t>(ntasks, q * per));
         const uint32_t hi = static_cast<uint32_t>(std::min<int64_t>(ntasks, (q + 1) * per));
-        if (narrow)
-          k_fixup<true><<<fgrid, kFixThreads, 0, s>>>(c, nnz, lo, hi, c.ph, c.fb, out, h->far_pack, chunk_row);
-        else
-          k_fixup<false><<<fgrid, kFixThreads, 0, s>>>(c, nnz, lo, hi, c.ph, c.fb, out, h->far_pack, chunk_row);
+        const bool last = q == passes - 1;
+        auto fk = narrow ? (last ? k_fixup<true, true> : k_fixup<true, false>)
+                         : (last ? k_fixup<false, true> : k_fixup<false, false>);
+        fk<<<fgrid, kFixThreads, 0, s>>>(c, nnz, lo, hi, c.ph, c.fb, out, h->far_pack, chunk_row);
         CB_CUDA(h, cudaGetLastError());
         ++h->launches;
       }
