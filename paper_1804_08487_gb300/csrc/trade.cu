@@ -856,6 +856,37 @@ __device__ __forceinline__ void block_mark(uint32_t* hb, uint32_t slot, int q, u
   reinterpret_cast<uint8_t*>(hb + slot)[q] = v;
 }
 
+// Trade t (nodes at t2u, t2u+1) depends on the earlier trade s through a
+// block of two or more edges (flags f: bit 2 rho + gamma, t's node rho
+// adjacent to s's node 2s + gamma): replay s's decisions on the block from
+// its published threshold and return whether t's other node is adjacent to
+// the s-node that the row-r entry of column colb ends on when t acts (a
+// common neighbour).  Kept out of line: the path is rare, and inlined into
+// every unrolled entry it would copy Philox many times over.
+__device__ __noinline__ int replay_other(const uint64_t* thr_key, const uint64_t* thr_tb, KeyCtx kc, uint32_t t2u,
+                                         uint32_t s, uint32_t f, int r, int colb) {
+  const int u0 = f & 1, u1 = (f >> 1) & 1, v0 = (f >> 2) & 1, v1 = (f >> 3) & 1;
+  const int bits[2][2] = {{u0, u1}, {v0, v1}};
+  const int cnt_row[2] = {u0 + u1, v0 + v1};
+  int m1[2][2] = {{0, 0}, {0, 0}};
+  int col_now = colb;
+  const uint64_t tk = __ldcg(thr_key + s), tt = __ldcg(thr_tb + s);
+  for (int rho = 0; rho < 2; ++rho)
+    for (int gam = 0; gam < 2; ++gam) {
+      if (!bits[rho][gam]) continue;
+      int g2 = gam;
+      if (cnt_row[rho] == 1) {
+        const uint32_t x = t2u + rho, yb = 2u * s + gam;
+        const uint32_t lo = min(x, yb), hi = max(x, yb);
+        const uint64_t k = side_key(kc, lo, hi, (lo >> 1) == s);
+        g2 = at_or_below(k, tie_break(lo, hi), tk, tt) ? 0 : 1;
+      }
+      m1[rho][g2] = 1;
+      if (rho == r && gam == colb) col_now = g2;
+    }
+  return m1[1 - r][col_now];
+}
+
 // Word d of an element's 128-bit order (key, lo, hi): key high, key low, lo, hi.
 __device__ __forceinline__ uint32_t sel_word(int d, uint64_t key, uint32_t lo, uint32_t hi) {
   return d == 0 ? static_cast<uint32_t>(key >> 32) : d == 1 ? static_cast<uint32_t>(key) : d == 2 ? lo : hi;
@@ -997,24 +1028,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
           mt[j] = m;
           continue;
         }
-        // replay trade s's decisions on this block
-        int m1[2][2] = {{0, 0}, {0, 0}};
-        const int bits[2][2] = {{u0, u1}, {v0, v1}};
-        const int cnt_row[2] = {cu, cv};
-#pragma unroll
-        for (int rho = 0; rho < 2; ++rho)
-#pragma unroll
-          for (int gam = 0; gam < 2; ++gam) {
-            if (!bits[rho][gam]) continue;
-            int g2 = gam;
-            if (cnt_row[rho] == 1) {
-              const uint32_t x = t2u + rho, yb = 2u * s + gam;
-              g2 = far_keeps_low(c, kc, s, min(x, yb), max(x, yb)) ? 0 : 1;
-            }
-            m1[rho][g2] = 1;
-            if (rho == r && gam == static_cast<int>(colb)) col_now = g2;
-          }
-        other = m1[1 - r][col_now];
+        other = replay_other(c.thr_key, c.thr_tb, kc, t2u, s, f, r, static_cast<int>(colb));
       }
     }
     // both trades' keys of this edge (step-start positions)
@@ -1263,7 +1277,7 @@ constexpr int kWarpB = 7;                       // first radix digit: 128 bins
 constexpr int kWarpWarps = 8;                   // warps per CTA
 using WarpWs = RegWs<32 * kWarpJ, kWarpB>;
 
-__global__ void __launch_bounds__(32 * kWarpWarps) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ lists,
+__global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ lists,
                                                                   const int64_t* __restrict__ ctr, int cls) {
   extern __shared__ __align__(16) char wsm[];
   const int wid = threadIdx.x >> 5;
@@ -1465,6 +1479,30 @@ __global__ void k_far_pack(StepCtx c, int64_t ntasks, void* __restrict__ pack) {
   }
 }
 
+// The record as loaded: 8 bytes, or 16 for the wide layout.
+template <bool kNarrow>
+struct FarRaw {
+  uint64_t v;
+};
+template <>
+struct FarRaw<false> {
+  int4 v;
+};
+template <bool kNarrow>
+__device__ __forceinline__ FarRaw<kNarrow> far_raw(const void* pack, uint32_t s) {
+  if constexpr (kNarrow) return {__ldg(static_cast<const unsigned long long*>(pack) + s)};
+  else return {__ldg(static_cast<const int4*>(pack) + s)};
+}
+template <bool kNarrow>
+__device__ __forceinline__ FarTrade far_decode(const FarRaw<kNarrow>& r) {
+  if constexpr (kNarrow) {
+    return {static_cast<int32_t>(r.v & 0x0FFFFFFFu), static_cast<int32_t>((r.v >> 28) & 0x0FFFFFFFu),
+            static_cast<uint32_t>(r.v >> 56)};
+  } else {
+    return {r.v.x, r.v.y, static_cast<uint32_t>(r.v.z)};
+  }
+}
+
 template <bool kNarrow>
 __device__ __forceinline__ FarTrade far_trade(const void* pack, uint32_t s) {
   if constexpr (kNarrow) {
@@ -1541,7 +1579,7 @@ __device__ uint32_t fix_tie(const StepCtx& c, const void* pack, const int32_t* c
 // Entries whose 8-bit prefix ties wait in a per-CTA queue and are resolved
 // together, so that their extra loads hold up no warp.
 template <bool kNarrow, bool kLast>
-__global__ void __launch_bounds__(kFixThreads, 5) k_fixup(StepCtx c, int64_t nnz, uint32_t s_lo, uint32_t s_hi,
+__global__ void __launch_bounds__(kFixThreads, 4) k_fixup(StepCtx c, int64_t nnz, uint32_t s_lo, uint32_t s_hi,
                                                        int32_t* __restrict__ ph, const uint16_t* __restrict__ fb,
                                                        int32_t* __restrict__ out, const void* __restrict__ pack,
                                                        const int32_t* __restrict__ chunk_row) {
@@ -1573,23 +1611,25 @@ __global__ void __launch_bounds__(kFixThreads, 5) k_fixup(StepCtx c, int64_t nnz
     uint32_t pn[kFixPer], bn[kFixPer / 2];
     const int64_t nxt = ch + gridDim.x;
     if (nxt < nchunks) fix_load<kLast>(ph, fb, nxt * kFixChunk + tofs, nnz, pn, bn);
+    // first every gather of the thread's entries in this slice, then the decisions
     uint32_t res[kFixPer];
+    FarRaw<kNarrow> ftv[kFixPer];
+    uint32_t todo = 0;   // bit j: entry j is this pass's
 #pragma unroll
     for (int j = 0; j < kFixPer; ++j) {
       const uint32_t p = pv[j];
-      res[j] = 0u;
-      if (p == 0xFFFFFFFFu) continue;
-      if (p & kPhDone) {   // an earlier pass resolved it
-        res[j] = p & ~kPhDone;
-        continue;
-      }
-      const uint32_t y = p, s = y >> 1;
-      if (y >= static_cast<uint32_t>(c.n)) {   // a slot phase A did not fill
-        latch(c.err, kErrRowLength);
-        continue;
-      }
-      if (s < s_lo || s >= s_hi) continue;   // another pass's (never the last pass's)
-      const FarTrade ft = far_trade<kNarrow>(pack, s);
+      res[j] = (p & kPhDone) && p != 0xFFFFFFFFu ? (p & ~kPhDone) : 0u;   // an earlier pass resolved it
+      const uint32_t s = p >> 1;
+      const bool mine = !(p & kPhDone) && s >= s_lo && s < s_hi && p < static_cast<uint32_t>(c.n);
+      if (!(p & kPhDone) && p >= static_cast<uint32_t>(c.n)) latch(c.err, kErrRowLength);   // a slot phase A did not fill
+      if (mine) ftv[j] = far_raw<kNarrow>(pack, s);
+      todo |= static_cast<uint32_t>(mine) << j;
+    }
+#pragma unroll
+    for (int j = 0; j < kFixPer; ++j) {
+      if (!((todo >> j) & 1u)) continue;
+      const uint32_t y = pv[j];
+      const FarTrade ft = far_decode<kNarrow>(ftv[j]);
       const uint32_t b = (bv[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
       int side = static_cast<int>(y & 1u);
       if (b & kFbInFar) {   // the far trade decides: key prefixes first
@@ -1957,7 +1997,7 @@ int super_step(Graph* h) {
       ++h->launches;
       const int passes = fix_passes(h);
       const int64_t per = (ntasks + passes - 1) / passes;
-      const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 5));
+      const unsigned fgrid = static_cast<unsigned>(std::min<int64_t>(nchunks, int64_t(h->num_sms) * 4));
       int32_t* out = h->col[h->cur];
       for (int q = 0; q < passes; ++q) {
         const uint32_t lo = static_cast<uint32_t>(std::min<int64_t>(ntasks, q * per));
