@@ -2,7 +2,7 @@
 """Throughput of the global Curveball super step on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload n2^25|n2^20|n2^21|n4096|ensemble|serving|uniform|swaps]
+                    [--workload n2^25|n2^20|n2^21|n4096|ensemble|serving|uniform|swaps|autocorr]
 
 One "step" is one global super step (Def. "Undirected Global Trade",
 Section 3.3) over the whole graph.  The metric is edge-trades/s = m * steps /
@@ -23,7 +23,9 @@ the headline of the line.
 
 --workload uniform times uniform single trades instead (Simple Undirected
 Curveball, Section 3.2): one step is n/2 trades on the --uniform-graph graph,
-run as the successor-list dataflow.  --workload swaps prints the appendix's
+run as the successor-list dataflow.  --workload autocorr runs Section 5.1's
+mixing experiment (fraction of edges still correlated against the thinning
+k, n = 2000).  --workload swaps prints the appendix's
 swap-fraction series (uniform trades against global trades as n grows).
 """
 import argparse
@@ -671,6 +673,81 @@ def run_swaps(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ edge autocorrelation
+
+AUTOCORR_N = 2000            # Section 5.1: n = 2 10^3, PLD(a = 5, b, gamma = 2)
+AUTOCORR_BS = (25, 750)
+AUTOCORR_CHAINS = 8          # independent chains per b
+AUTOCORR_STEPS = 6000        # super steps of each (not thinned) chain
+AUTOCORR_KMAX = 64
+
+
+def autocorr_graphs():
+    """The chains of the autocorrelation workload: for each b, AUTOCORR_CHAINS
+    PLD([5, b), 2) graphs on 2000 nodes (Havel-Hakimi), seeds 5000 + 100 b + i."""
+    from paper_1804_08487_gb300 import synth
+    graphs, seeds, groups = [], [], []
+    for b in AUTOCORR_BS:
+        for i in range(AUTOCORR_CHAINS):
+            s = 5000 + 100 * b + i
+            g = synth.powerlaw_graph(AUTOCORR_N, 5, b, 2.0, s)
+            graphs.append((g.row_ptr, g.col))
+            seeds.append(s)
+            groups.append(b)
+    return graphs, seeds, groups
+
+
+def run_autocorr(args):
+    """Section 5.1's mixing experiment with global trades: the fraction of
+    edges still correlated with the start (BIC on the k-thinned presence
+    series) as a function of the thinning k, for PLD([5, b), 2) graphs with
+    n = 2000 and b in {25, 750}, 6000 super steps per chain; all chains of
+    both b in one batch handle."""
+    import numpy as np
+    import torch
+    from paper_1804_08487_gb300 import cb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    graphs, seeds, groups = autocorr_graphs()
+    stream = torch.cuda.Stream()
+    e = cb.Ensemble(graphs, seeds, stream=stream)
+    e.set_option("presence", AUTOCORR_STEPS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e.global_trades(AUTOCORR_STEPS)
+    e.sync()
+    t_chain = time.perf_counter() - t0
+    series = {}
+    t1 = time.perf_counter()
+    for b in AUTOCORR_BS:
+        corr = np.zeros(AUTOCORR_KMAX, dtype=np.int64)
+        occ = 0
+        for i, gb in enumerate(groups):
+            if gb != b:
+                continue
+            c_i, _, o_i, _ = e.autocorr(AUTOCORR_KMAX, graph=i)
+            corr += np.asarray(c_i, dtype=np.int64)
+            occ += o_i
+        series[f"b={b}"] = [round(float(x) / occ, 5) for x in corr]
+    t_class = time.perf_counter() - t1
+    e.close()
+    frac25 = series["b=25"]
+    k1 = next((k + 1 for k, f in enumerate(frac25) if f <= 0.01), None)
+    line = {
+        "metric": "fraction of edges still correlated (k-thinned presence series, BIC)", "value": k1,
+        "unit": "smallest k with at most 1 % of edges correlated (b=25)", "n_gpus": 1, "steps": AUTOCORR_STEPS,
+        "warmup": 0, "ms_per_step": t_chain / AUTOCORR_STEPS * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"edge autocorrelation: n={AUTOCORR_N}, PLD([5,b),2), b in {list(AUTOCORR_BS)}, "
+                               f"{AUTOCORR_CHAINS} chains per b, {AUTOCORR_STEPS} global super steps, k = 1.."
+                               f"{AUTOCORR_KMAX}", "parallelism": "batch handle"},
+        "series": series, "seconds": {"chains_with_record": t_chain, "classification": t_class},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ ours
 
 def run_ours(args):
@@ -819,6 +896,33 @@ def run_reference(args):
         }
         print(json.dumps(line), flush=True)
         return
+    if args.workload == "autocorr":
+        from oracle import Oracle
+        from oracle import autocorr as ac
+        from paper_1804_08487_gb300 import synth
+        steps, kmax = 400, 16
+        g = synth.powerlaw_graph(AUTOCORR_N, 5, 25, 2.0, 5000 + 100 * 25)
+        t0 = time.perf_counter()
+        o = Oracle(g.row_ptr, g.col, 5000 + 100 * 25)
+        lists = [o.edges()]
+        for _ in range(steps):
+            o.superstep(1)
+            lists.append(o.edges())
+        corr, occ, _ = ac.fraction_correlated(lists, AUTOCORR_N, kmax)
+        dt = time.perf_counter() - t0
+        sample = f"oracle: one chain, n={AUTOCORR_N} PLD([5,25),2), {steps} super steps, k = 1..{kmax}"
+        line = {
+            "impl": "reference", "metric": "fraction of edges still correlated (k-thinned presence series, BIC)",
+            "value": None, "unit": "fraction", "n_gpus": world, "steps": steps, "warmup": 0,
+            "ms_per_step": dt / steps * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "edge autocorrelation (oracle sample)", "parallelism": "single"},
+            "series": {"b=25": [round(float(x) / occ, 5) for x in corr]},
+            "cpu_baseline": {"value": dt, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": dt, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "swaps":
         from oracle import Oracle
         from paper_1804_08487_gb300 import synth
@@ -937,6 +1041,8 @@ def main():
         run_uniform(args)
     elif args.workload == "swaps":
         run_swaps(args)
+    elif args.workload == "autocorr":
+        run_autocorr(args)
     else:
         run_ours(args)
 

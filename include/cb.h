@@ -251,6 +251,12 @@ int cb_timings(cb_handle h, double* ms, int count);
  *   "hold_trade" uniform trades: messages to this trade (index within the
  *               call) are dropped, so it never runs and the executor's
  *               waits run out (a test of the timeout path); -1: none [-1].
+ *   "presence"  T > 0: record the edge presence of every node pair of every
+ *               graph now and after each of the next T super steps (for
+ *               cb_autocorr; one bit per pair and state, T <= 10^6, at most
+ *               64 GB); super steps then run without the recorded CUDA
+ *               graphs, plus one recording kernel each.  Setting it again
+ *               starts a new record; 0 stops and frees it [0].
  *   "fix_passes" passes of the rebuild over slices of the far trades (0:
  *               as many as keep one slice's records in L2) [0]; 0..64.
  *   "swap_stats" 1: count neighbourhood swaps (see cb_swap_counts) from zero
@@ -273,6 +279,31 @@ int cb_set_option(cb_handle h, const char* key, int64_t value);
  * when counting was never on.  Synchronises the handle's stream.
  */
 int cb_swap_counts(cb_handle h, int64_t* performed, int64_t* possible);
+
+/*
+ * Edge autocorrelation of the recorded chain (Section 5.1, "Mixing of
+ * Edge-Switching, Curveball and Global Curveball").  For every node pair
+ * that is an edge in at least one recorded state (option "presence"), the
+ * series Z_t (edge present in state t) is thinned to every k-th entry, and
+ * the transitions of the thinned series are fitted to an independent and to
+ * a first-order Markov model; the edge counts as correlated when the Markov
+ * model fits better by the Bayesian information criterion:
+ * G^2 = 2 (L_Markov - L_independent) > ln N, N the number of thinned
+ * transitions.  (The paper cites the criterion without printing it; this is
+ * the reading used here.)  A constant series, or one with N < 2, counts as
+ * independent.
+ *   graph       graph index of a batch handle, or -1 for all graphs.
+ *   kmax        thinnings k = 1..kmax, 1 <= kmax <= 64.
+ *   correlated  kmax host int64: edges classified as correlated for each k.
+ *   near_ties   kmax host int64 (may be NULL): decisions with
+ *               |G^2 - ln N| < 1e-9, which rounding could flip.
+ *   occurring   (may be NULL) edges that occur in some recorded state.
+ *   states      (may be NULL) recorded states (1 + super steps recorded).
+ * The fraction of correlated edges is correlated[k-1] / *occurring.
+ * Synchronises the handle's stream.
+ */
+int cb_autocorr(cb_handle h, int32_t graph, int32_t kmax, int64_t* correlated, int64_t* near_ties,
+                int64_t* occurring, int64_t* states);
 
 /*
  * The permutation of super step g for n nodes and `seed` (the same order as

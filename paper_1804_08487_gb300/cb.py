@@ -113,6 +113,8 @@ def load():
     lib.cb_uniform_next.argtypes = [vp, C.POINTER(u64)]
     lib.cb_uniform_pairs.restype = i32
     lib.cb_uniform_pairs.argtypes = [u64, i64, u64, i64, vp, vp]
+    lib.cb_autocorr.restype = i32
+    lib.cb_autocorr.argtypes = [vp, i32, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.cb_successors.restype = i32
     lib.cb_successors.argtypes = [i64, vp, i64, vp, vp, vp]
     _lib = lib
@@ -321,6 +323,16 @@ def cb_successors(n: int, pairs, suc_begin_out, suc_out, stream=None):
     return _check(load().cb_successors(n, pp, count, pb, ps, _stream(stream)))
 
 
+def cb_autocorr(h, graph: int, kmax: int):
+    """Edge autocorrelation of the presence record: (correlated counts for
+    k = 1..kmax, near-tie counts, occurring edges, recorded states)."""
+    corr = (C.c_int64 * kmax)()
+    near = (C.c_int64 * kmax)()
+    occ, st = C.c_int64(0), C.c_int64(0)
+    _check(load().cb_autocorr(h, graph, kmax, corr, near, C.byref(occ), C.byref(st)), h)
+    return list(corr), list(near), occ.value, st.value
+
+
 def cb_stats(h):
     out = (C.c_int64 * 8)()
     k = _check(load().cb_stats(h, out, 8), h)
@@ -383,6 +395,9 @@ class Curveball:
 
     def sync(self):
         cb_sync(self.h)
+
+    def autocorr(self, kmax: int, graph: int = -1):
+        return cb_autocorr(self.h, graph, kmax)
 
     def close(self):
         if getattr(self, "h", None):

@@ -64,6 +64,7 @@ void release(Graph* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_uniform(h);
+  free_presence(h);
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
                   h->lists, h->Minv, h->cls_flag, h->cls_scan,
@@ -646,7 +647,7 @@ int cb_global_trades(cb_handle h, uint32_t supersteps) {
   if (h->g + supersteps >= 0xfffffffeull) return fail(h, CB_ERANGE, "super-step counter would pass 2^32-2");
   const int64_t launches0 = h->launches;
   for (double& v : h->phase_ms) v = 0;
-  if (h->use_graph && !h->timing && !h->swap_stats && supersteps > 0) {
+  if (h->use_graph && !h->timing && !h->swap_stats && !h->pres && supersteps > 0) {
     if (!h->step_exec[0]) {
       const int rc = capture_step_graphs(h);
       if (rc) return rc;
@@ -662,6 +663,7 @@ int cb_global_trades(cb_handle h, uint32_t supersteps) {
     for (uint32_t i = 0; i < supersteps; ++i) {
       int rc = super_step(h);
       if (!rc && h->swap_stats) rc = count_swaps(h);
+      if (!rc && h->pres) rc = record_presence(h);
       if (rc) return rc;
     }
   }
@@ -818,6 +820,10 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     if (value < 0 || value > 1) return fail(h, CB_EINVAL, "tile_paths is 0 or 1");
     h->tile_paths = static_cast<int>(value);
     return CB_OK;
+  }
+  if (!std::strcmp(key, "presence")) {
+    if (value < 0 || value > 1000000) return fail(h, CB_EINVAL, "presence out of range [0, 10^6]");
+    return set_presence(h, value);
   }
   if (!std::strcmp(key, "wait_ms")) {
     if (value < 1 || value > 600000) return fail(h, CB_EINVAL, "wait_ms out of range [1, 600000]");

@@ -24,7 +24,8 @@ enum DevErr : int32_t {
 // The codes that report a bounded wait running out (CB_ETIMEOUT).
 inline bool is_timeout(int32_t e) { return e == kErrResolve || e == kErrStage || e == kErrUniformWait; }
 
-struct UniBufs;   // uniform-trade buffers (uniform.cu)
+struct UniBufs;        // uniform-trade buffers (uniform.cu)
+struct PresenceBufs;   // edge presence record (autocorr.cu)
 
 constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
 constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
@@ -139,6 +140,8 @@ struct Graph {
   // uniform single trades (uniform.cu)
   UniBufs* uni = nullptr;
   uint64_t uni_next = 0;        // index of the next uniform trade
+  // edge presence record for the autocorrelation of Section 5.1 (autocorr.cu)
+  PresenceBufs* pres = nullptr;
   // swap counts (swaps.cu): device pair (performed, possible), when on
   bool swap_stats = false;
   int64_t* swaps = nullptr;
@@ -224,6 +227,11 @@ int set_swap_stats(Graph* h, bool on);     // on: counts from zero
 // uniform.cu
 int uniform_trades(Graph* h, uint64_t count);
 void free_uniform(Graph* h);
+
+// autocorr.cu
+int set_presence(Graph* h, int64_t T);   // T > 0: record the next T super steps (and now); 0: stop
+int record_presence(Graph* h);           // the current state, while recording
+void free_presence(Graph* h);
 
 // device bytes a plain handle of n nodes / nnz entries / largest degree takes (upper estimate)
 int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sms);
