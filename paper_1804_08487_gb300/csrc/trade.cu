@@ -42,7 +42,9 @@
 namespace cb {
 namespace {
 
-constexpr uint32_t kDeferred = 2;              // done[t]: deferred by the first pass
+constexpr uint32_t kDeferred = 2;              // done[t]: deferred (a dependency had not published)
+constexpr uint32_t kComplete = 3;              // done[t]: complete, no later trade waits for it
+constexpr int kRetryPasses = 2;                // parallel passes over the deferred trades before the in-order one
 
 // meta bits per entry (phase A)
 constexpr uint8_t kR = 1;       // entry sits in v's row
@@ -783,6 +785,8 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     if (publish_fence && !c.hold_publish) {
       __threadfence();
       st_release(c.done + t, c.stamp);
+    } else if (!publish_fence) {
+      c.done[t] = kComplete;   // a deferred trade done in a retry pass leaves the deferred list
     }
   }
   tm.sync();
@@ -1265,6 +1269,8 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     if (publish_fence && !c.hold_publish) {
       __threadfence();
       st_release(c.done + t, c.stamp);
+    } else if (!publish_fence) {
+      c.done[t] = kComplete;   // a deferred trade done in a retry pass leaves the deferred list
     }
   }
   tm.sync();
@@ -1343,7 +1349,8 @@ __device__ __forceinline__ int trade_class(const ClassTh& th, int L) {
 }
 
 __global__ void __launch_bounds__(kClassThreads) k_class_count(StepCtx c, int64_t ntasks, ClassTh th,
-                                                               int64_t nchunks, int32_t* __restrict__ counts) {
+                                                               int64_t nchunks, int only_deferred,
+                                                               int32_t* __restrict__ counts) {
   __shared__ int wc[kClassThreads / 32][kClasses];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -1351,7 +1358,7 @@ __global__ void __launch_bounds__(kClassThreads) k_class_count(StepCtx c, int64_
     for (int j = 0; j < kClassPer; ++j) {
       const int64_t t = ch * kClassChunk + j * kClassThreads + threadIdx.x;
       int k = -1;
-      if (t < ntasks) {
+      if (t < ntasks && (!only_deferred || __ldcg(c.done + t) == kDeferred)) {
         const TradeRows tr = trade_rows(c, t);
         k = trade_class(th, tr.du + tr.dv);
       }
@@ -1371,7 +1378,8 @@ __global__ void __launch_bounds__(kClassThreads) k_class_count(StepCtx c, int64_
 }
 
 __global__ void __launch_bounds__(kClassThreads) k_class_place(StepCtx c, int64_t ntasks, ClassTh th,
-                                                               int64_t nchunks, const int64_t* __restrict__ off,
+                                                               int64_t nchunks, int only_deferred,
+                                                               const int64_t* __restrict__ off,
                                                                int32_t* __restrict__ lists) {
   __shared__ int wc[kClassThreads / 32][kClasses];
   __shared__ int64_t base[kClasses];
@@ -1383,7 +1391,7 @@ __global__ void __launch_bounds__(kClassThreads) k_class_place(StepCtx c, int64_
     for (int j = 0; j < kClassPer; ++j) {
       const int64_t t = ch * kClassChunk + j * kClassThreads + threadIdx.x;
       int k = -1;
-      if (t < ntasks) {
+      if (t < ntasks && (!only_deferred || __ldcg(c.done + t) == kDeferred)) {
         const TradeRows tr = trade_rows(c, t);
         k = trade_class(th, tr.du + tr.dv);
       }
@@ -1899,20 +1907,6 @@ int super_step(Graph* h) {
   auto grid_n = [&](int64_t work) {
     return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, h->num_sms * 8)));
   };
-  {  // class lists: a stable counting sort of the trades by class
-    const int64_t nch = (ntasks + kClassChunk - 1) / kClassChunk;
-    const unsigned cgrid = static_cast<unsigned>(std::min<int64_t>(nch, int64_t(h->num_sms) * 8));
-    k_class_count<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, h->cls_flag);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-    CB_CUDA(h, exclusive_scan_i32(h->cls_flag, h->cls_scan, kClasses * nch, h->scan_ws, s, &h->launches));
-    k_class_place<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, h->cls_scan, h->lists);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-    k_class_bounds<<<1, 32, 0, s>>>(h->cls_scan, nch, cnt);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
-  }
   const size_t med_smem = ws_a_bytes(std::max(block_max, 1));      // in-order pass (no staging)
   const size_t big_smem = ws_a_bytes(std::max(h->smem_max, 1));
   const size_t med_smem_st = block_smem_bytes(std::max(block_max, 1));   // threshold kernels with staging
@@ -1921,8 +1915,6 @@ int super_step(Graph* h) {
   const unsigned bgrid = static_cast<unsigned>(std::max(1, std::min(h->num_sms, h->ws_ctas)));
   const unsigned sgrid = static_cast<unsigned>(h->num_sms);
   char* gws = static_cast<char*>(h->ws_global);
-  // phase A, first pass: every class; a trade whose dependency has not
-  // published yet is marked deferred.
   c.wait = 0;
   c.def_count = ucnt + kCtrDeferred;
   c.cand_max = h->cand_max;
@@ -1934,35 +1926,61 @@ int super_step(Graph* h) {
     ++h->launches;
     return CB_OK;
   };
-  k_phase_a_warp<<<static_cast<unsigned>(h->num_sms * 8), 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(
-      c, L, cnt, 0);
-  if ((rc = launched())) return rc;
-  if (h->cta_paths) {
-    k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 1);
-    if ((rc = launched())) return rc;
-    k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 2);
-    if ((rc = launched())) return rc;
-    k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 3);
-    if ((rc = launched())) return rc;
-    k_phase_a_team<kBigThreads, 512><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt, 4);
-    if ((rc = launched())) return rc;
-    k_phase_a_team<kBigThreads, kBigThreads><<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(
-        c, L, cnt, 5);
-    if ((rc = launched())) return rc;
-  } else {
-    k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 3, block_max, gws, h->ws_slice,
-                                                                        block_max);
-    if ((rc = launched())) return rc;
-  }
-  // the largest trades: 1024 threads, up to smem_max entries in shared memory
-  // (staged by a bulk copy), a global-memory slice above
-  k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 6, h->smem_max, gws, h->ws_slice,
-                                                                      h->smem_max);
-  if ((rc = launched())) return rc;
-  // second pass: the deferred trades in index order, waiting on dependencies.
-  // 1024-thread CTAs keep large trades in shared memory; 256-thread CTAs (four
-  // per SM) run many small deferred trades at once, large ones from a global
-  // slice.
+  // class lists (every trade, or only the deferred ones): a stable counting
+  // sort of the trades by class
+  auto classify = [&](int only_deferred) -> int {
+    const int64_t nch = (ntasks + kClassChunk - 1) / kClassChunk;
+    const unsigned cgrid = static_cast<unsigned>(std::min<int64_t>(nch, int64_t(h->num_sms) * 8));
+    k_class_count<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, only_deferred, h->cls_flag);
+    int r = launched();
+    if (r) return r;
+    CB_CUDA(h, exclusive_scan_i32(h->cls_flag, h->cls_scan, kClasses * nch, h->scan_ws, s, &h->launches));
+    k_class_place<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, only_deferred, h->cls_scan, h->lists);
+    if ((r = launched())) return r;
+    k_class_bounds<<<1, 32, 0, s>>>(h->cls_scan, nch, cnt);
+    return launched();
+  };
+  // one pass of every class's kernel; a trade whose dependency has not
+  // published yet is (again) marked deferred
+  auto run_classes = [&]() -> int {
+    int r;
+    k_phase_a_warp<<<static_cast<unsigned>(h->num_sms * 8), 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(
+        c, L, cnt, 0);
+    if ((r = launched())) return r;
+    if (h->cta_paths) {
+      k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 1);
+      if ((r = launched())) return r;
+      k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 2);
+      if ((r = launched())) return r;
+      k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 3);
+      if ((r = launched())) return r;
+      k_phase_a_team<kBigThreads, 512><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt, 4);
+      if ((r = launched())) return r;
+      k_phase_a_team<kBigThreads, kBigThreads><<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(
+          c, L, cnt, 5);
+      if ((r = launched())) return r;
+    } else {
+      k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 3, block_max, gws, h->ws_slice,
+                                                                          block_max);
+      if ((r = launched())) return r;
+    }
+    // the largest trades: 1024 threads, up to smem_max entries in shared
+    // memory (staged by a bulk copy), a global-memory slice above
+    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 6, h->smem_max, gws, h->ws_slice,
+                                                                        h->smem_max);
+    return launched();
+  };
+  // the first pass over every trade, then kRetryPasses parallel passes over
+  // the deferred ones: each runs every deferred trade whose dependencies
+  // have published by then (a trade the previous pass completed leaves the
+  // list), so chains of dependent trades shrink by a level per pass
+  if ((rc = classify(0)) || (rc = run_classes())) return rc;
+  for (int r = 0; r < kRetryPasses; ++r)
+    if ((rc = classify(1)) || (rc = run_classes())) return rc;
+  // last pass: the trades still deferred, in index order, waiting on
+  // dependencies.  1024-thread CTAs keep large trades in shared memory;
+  // 256-thread CTAs (four per SM) run many small deferred trades at once,
+  // large ones from a global slice.
   c.wait = 1;
   if (h->inorder_threads == kBigThreads) {
     const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
