@@ -321,8 +321,10 @@ int cb_autocorr(cb_handle h, int32_t graph, int32_t kmax, int64_t* correlated, i
  * Scratch: one static 13 MiB device array, held by every device that loads
  * the library until the process exits, and shared by every call on that
  * device.  The first call on a device looks up that array's device address
- * (once per device, with the device current); make the first call before any
- * stream capture.  Each call clears the counters it needs, but calls that
+ * (once per device, with the device current) and keeps it for the life of
+ * the process; make the first call before any stream capture.  Resetting a
+ * device (cudaDeviceReset) after that call is not supported: the kept
+ * address would no longer name the array.  Each call clears the counters it needs, but calls that
  * overlap on the GPU (different streams, or host threads) race on the shared
  * scratch and must be serialised by the caller.  No cudaMalloc, cudaFree or
  * other allocating routine is called.  Errors are reported through
