@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n2^25")
     ap.add_argument("--batched", type=int, default=1, help="1: add the batched-ensemble comparison to the line")
+    ap.add_argument("--generate", type=int, default=0,
+                    help="1: time the workload's input graph generated on the device against the host generator")
     ap.add_argument("--requests", type=int, default=200, help="serving workload: number of requests replayed")
     ap.add_argument("--uniform-graph", default="n2^25",
                     help="uniform workload: the plain graph the uniform single trades run on")
@@ -673,6 +675,48 @@ def run_swaps(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ input generation
+
+def run_generate(args):
+    """The workload's input graph generated on the device (include/cb_gen.h)
+    against the host generator: wall time of each, and the device graph's
+    sha256 against the stored digest of the host graph."""
+    import hashlib
+    import numpy as np
+    import torch
+    from paper_1804_08487_gb300 import cb
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    w = workload(args.workload if args.workload in ("n2^25", "n2^20", "n2^21", "n4096") else "n2^25")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rp, col, dseed = cb.generate_powerlaw(w.n, w.a, w.b, w.gamma, w.degree_seed)
+    torch.cuda.synchronize()
+    t_dev = time.perf_counter() - t0
+    h = hashlib.sha256()
+    h.update(memoryview(np.ascontiguousarray(rp.cpu().numpy(), dtype="<i8")).cast("B"))
+    h.update(memoryview(np.ascontiguousarray(col.cpu().numpy(), dtype="<i4")).cast("B"))
+    m = col.numel() // 2
+    del rp, col
+    torch.cuda.empty_cache()
+    t1 = time.perf_counter()
+    g = w.graph()
+    t_host = time.perf_counter() - t1
+    path = os.path.join(ROOT, "tests", "golden", f"plain_{args.workload.replace('^', 'p')}.json")
+    want = json.load(open(path)).get("graph_sha256") if os.path.exists(path) else None
+    line = {
+        "metric": "input generation time (PLD degrees + Havel-Hakimi)", "value": t_dev, "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": t_dev * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "m": m, "degree_seed": dseed, "parallelism": "single"},
+        "host_seconds": t_host, "host_cores": os.cpu_count(), "same_degree_seed": dseed == g.degree_seed,
+        "graph_sha256_matches_stored": (h.hexdigest() == want) if want else None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------ edge autocorrelation
 
 AUTOCORR_N = 2000            # Section 5.1: n = 2 10^3, PLD(a = 5, b, gamma = 2)
@@ -1043,6 +1087,8 @@ def main():
         run_swaps(args)
     elif args.workload == "autocorr":
         run_autocorr(args)
+    elif args.generate:
+        run_generate(args)
     else:
         run_ours(args)
 

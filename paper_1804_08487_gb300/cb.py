@@ -113,6 +113,10 @@ def load():
     lib.cb_uniform_next.argtypes = [vp, C.POINTER(u64)]
     lib.cb_uniform_pairs.restype = i32
     lib.cb_uniform_pairs.argtypes = [u64, i64, u64, i64, vp, vp]
+    lib.cb_generate_pld.restype = i32
+    lib.cb_generate_pld.argtypes = [i64, i32, i32, C.c_double, u64, vp, C.POINTER(i64), vp]
+    lib.cb_generate_hh.restype = i32
+    lib.cb_generate_hh.argtypes = [i64, vp, vp, vp, C.POINTER(i64), vp]
     lib.cb_autocorr.restype = i32
     lib.cb_autocorr.argtypes = [vp, i32, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.cb_successors.restype = i32
@@ -321,6 +325,49 @@ def cb_successors(n: int, pairs, suc_begin_out, suc_out, stream=None):
         raise ValueError("cb_successors takes device memory")
     count = pairs.numel() // 2
     return _check(load().cb_successors(n, pp, count, pb, ps, _stream(stream)))
+
+
+def cb_generate_pld(n: int, a: int, b: int, gamma: float, seed: int, deg_out, stream=None) -> int:
+    """PLD([a,b), gamma) degrees into `deg_out` (an int32 CUDA tensor of n
+    entries); returns their sum."""
+    p, kind, _ = _ptr(deg_out)
+    if n and kind != CB_DEVICE:
+        raise ValueError("deg_out must be device memory")
+    total = C.c_int64(0)
+    _check(load().cb_generate_pld(n, a, b, float(gamma), C.c_uint64(seed & (2**64 - 1)), p, C.byref(total),
+                                  _stream(stream)))
+    return total.value
+
+
+def cb_generate_hh(n: int, deg, row_ptr_out, col_out, stream=None) -> int:
+    """Havel-Hakimi realisation of `deg` (int32 CUDA tensor) into row_ptr_out
+    (int64, n+1) and col_out (int32, sum of degrees), CUDA tensors; returns m."""
+    ptrs = [_ptr(x) for x in (deg, row_ptr_out, col_out)]
+    if n and any(k != CB_DEVICE for p, k, _ in ptrs if p is not None):
+        raise ValueError("cb_generate_hh takes device memory")
+    m = C.c_int64(0)
+    _check(load().cb_generate_hh(n, ptrs[0][0], ptrs[1][0], ptrs[2][0], C.byref(m), _stream(stream)))
+    return m.value
+
+
+def generate_powerlaw(n: int, a: int, b: int, gamma: float, seed: int, max_redraws: int = 64, stream=None):
+    """(row_ptr, col, degree_seed) as CUDA tensors: PLD([a,b), gamma) degrees
+    realised by Havel-Hakimi on the device, a non-graphical draw redrawn with
+    seed+1 (the host generator's policy)."""
+    import torch
+    deg = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    for k in range(max_redraws):
+        total = cb_generate_pld(n, a, b, gamma, seed + k, deg, stream)
+        col = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+        try:
+            cb_generate_hh(n, deg, rp, col, stream)
+        except CbError as e:
+            if e.code == CB_EINVAL:
+                continue
+            raise
+        return rp, col[:total], seed + k
+    raise CbError(CB_EINVAL, f"no graphical draw in {max_redraws} tries")
 
 
 def cb_autocorr(h, graph: int, kmax: int):
