@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--generate", type=int, default=0,
                     help="1: time the workload's input graph generated on the device against the host generator")
     ap.add_argument("--requests", type=int, default=200, help="serving workload: number of requests replayed")
+    ap.add_argument("--plain-compare", type=int, default=1,
+                    help="ensemble workload: 0 skips the 256 sequential plain runs it is compared with")
     ap.add_argument("--uniform-graph", default="n2^25",
                     help="uniform workload: the plain graph the uniform single trades run on")
     ap.add_argument("--perm", default="sort", choices=["sort", "relaxed"],
@@ -159,21 +161,60 @@ def workload(name):
     return synth.PLAIN[name]
 
 
-def measured_traffic():
-    """DRAM bytes per super step of the threshold phase at n=2^25 from the
-    committed ncu summary, or None if the trade kernels changed since."""
+# DRAM bytes per directed entry of each kernel that can be the dominant one,
+# from ncu `dram__bytes_read.sum + dram__bytes_write.sum` of one launch on the
+# n=2^21 graph of the same degree law (profiles/), and the sha256 of
+# csrc/trade.cu those counters were taken on: traffic grows with the entries a
+# launch processes, so the full-size figure is that per-entry value times the
+# launch's entries.  A kernel changed since then reports no traffic.
+SMALL_CASE_TRAFFIC = {}
+
+
+def measured_traffic(kernel, entries):
+    """DRAM bytes of one launch of `kernel` processing `entries` directed
+    entries, scaled from the small-case ncu capture, or None."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_traffic_plain_n2p25.md")
-    src = os.path.join(ROOT, "paper_1804_08487_gb300", "csrc", "trade.cu")
-    try:
-        text = open(path).read()
-        vals = dict(line.split(": ", 1) for line in text.splitlines()
-                    if line.startswith(("traffic_threshold_bytes_per_step", "source_sha256_trade_cu")))
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != vals["source_sha256_trade_cu"].strip():
-            return None
-        return float(vals["traffic_threshold_bytes_per_step"])
-    except (OSError, KeyError, ValueError):
+    rec = SMALL_CASE_TRAFFIC.get(kernel)
+    if rec is None:
         return None
+    src = os.path.join(ROOT, "paper_1804_08487_gb300", "csrc", "trade.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["trade_cu_sha256"]:
+        return None
+    return rec["bytes_per_entry"] * entries
+
+
+# the threshold phase's kernel of each size class (cb_timings ms[4 + k])
+CLASS_KERNELS = ["k_phase_a_warp", "k_phase_a_team<256,64>", "k_phase_a_team<256,128>", "k_phase_a_team<256,256>",
+                 "k_phase_a_team<1024,512>", "k_phase_a_team<1024,1024>", "k_phase_a_block<1024>"]
+# algorithmic bytes: a threshold kernel reads each directed entry of its
+# trades (4 B) and writes it into the new row with its side word (4 + 2 B),
+# plus per trade its two rows' offsets, positions, threshold and done flag
+# (48 B); the fix-up reads each placeholder and side word (4 + 2 B) and
+# writes the final entry (4 B), plus the 8-byte far-trade record written and
+# read once per trade
+THRESHOLD_BYTES_PER_ENTRY = 10
+THRESHOLD_BYTES_PER_TRADE = 48
+FIXUP_BYTES_PER_ENTRY = 10
+FIXUP_BYTES_PER_TRADE = 16
+
+
+def dominant_kernel(stats, phases, m, ntasks, K):
+    """The kernel (or, for the rebuild, the fix-up launches of one step) with
+    the largest event-timed device time per super step, its algorithmic bytes
+    per launch and average launch duration.  The first threshold pass's class
+    kernels are bracketed by events; the retry passes and the in-order pass
+    run only the few deferred trades."""
+    cands = []
+    for k, name in enumerate(CLASS_KERNELS):
+        ms = phases.get(f"class{k}_ms", 0.0) / K
+        if ms > 0:
+            b = (THRESHOLD_BYTES_PER_ENTRY * stats.get(f"class{k}_entries", 0)
+                 + THRESHOLD_BYTES_PER_TRADE * stats.get(f"class{k}_trades", 0))
+            cands.append((ms, name, b, stats.get(f"class{k}_entries", 0)))
+    cands.append((phases["rebuild_ms"] / K, "k_fixup (rebuild phase)",
+                  FIXUP_BYTES_PER_ENTRY * 2 * m + FIXUP_BYTES_PER_TRADE * ntasks, 2 * m))
+    ms, name, b, entries = max(cands)
+    return name, b, ms, entries
 
 
 def verify_step1(name, c, m):
@@ -246,11 +287,12 @@ def ensemble_graphs(count=ENSEMBLE_GRAPHS):
     return graphs, [w.chain_seed for w in members]
 
 
-def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=25, clocks=None):
+def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=25, clocks=None, plain_compare=True):
     """Batched: one handle, autotuned (its tuning steps are untimed warm-up),
-    CUDA-graph replay, `steps` timed super steps.  Plain: each graph in its
-    own handle, `steps` super steps each, timed one after another (device
-    time summed), with direct launches and with CUDA-graph replay."""
+    CUDA-graph replay, `steps` timed super steps.  Plain (unless
+    plain_compare is off): each graph in its own handle, `steps` super steps
+    each, timed one after another (device time summed), with direct launches
+    and with CUDA-graph replay."""
     import torch
     from paper_1804_08487_gb300 import cb
 
@@ -291,17 +333,18 @@ def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=25,
             c.close()
         return total
 
-    plain_ms = plain(0)
-    plain_graph_ms = plain(1)
     et = total_m * steps
-    return {
-        "workload": ENSEMBLE_NAME, "graphs": len(graphs), "n_total": total_n, "m_total": total_m,
-        "steps": steps, "batched_ms": batched_ms, "batched_edge_trades_s": et / (batched_ms / 1e3),
-        "plain_ms": plain_ms, "plain_edge_trades_s": et / (plain_ms / 1e3),
-        "plain_cuda_graph_ms": plain_graph_ms, "plain_cuda_graph_edge_trades_s": et / (plain_graph_ms / 1e3),
-        "speedup_vs_plain": plain_ms / batched_ms, "speedup_vs_plain_cuda_graph": plain_graph_ms / batched_ms,
-        "autotuned": tuned, "batched_launches": launches, "clocks": clk,
-    }
+    r = {"workload": ENSEMBLE_NAME, "graphs": len(graphs), "n_total": total_n, "m_total": total_m,
+         "steps": steps, "batched_ms": batched_ms, "batched_edge_trades_s": et / (batched_ms / 1e3),
+         "autotuned": tuned, "batched_launches": launches, "clocks": clk}
+    if plain_compare:
+        plain_ms = plain(0)
+        plain_graph_ms = plain(1)
+        r.update({"plain_ms": plain_ms, "plain_edge_trades_s": et / (plain_ms / 1e3),
+                  "plain_cuda_graph_ms": plain_graph_ms,
+                  "plain_cuda_graph_edge_trades_s": et / (plain_graph_ms / 1e3),
+                  "speedup_vs_plain": plain_ms / batched_ms, "speedup_vs_plain_cuda_graph": plain_graph_ms / batched_ms})
+    return r
 
 
 def _oracle_member_rate(args):
@@ -345,7 +388,8 @@ def run_ensemble(args):
     graphs, seeds = ensemble_graphs()
     seeds = ensemble_replica_seeds(seeds, rank)   # each replica its own chains
     stream = torch.cuda.Stream()
-    r = measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, clocks=ClockSampler(local))
+    r = measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, clocks=ClockSampler(local),
+                         plain_compare=bool(args.plain_compare))
     t_ms = max_over_ranks(r["batched_ms"], world)
     # end to end: create from pinned host buffers, the super steps, every
     # graph's edge list back to pinned host memory
@@ -381,7 +425,7 @@ def run_ensemble(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": "whole super step", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"},
-        "batched_vs_plain": r["speedup_vs_plain"],
+        "batched_vs_plain": r.get("speedup_vs_plain"),
         "batched": r,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_desc},
         "e2e": {"value": job_rate(world, r["m_total"] * K, e2e_s), "unit": UNIT,
@@ -873,7 +917,7 @@ def run_ours(args):
     batched = None
     if args.batched:
         graphs, seeds = ensemble_graphs()
-        batched = measure_ensemble(graphs, seeds, stream)
+        batched = measure_ensemble(graphs, seeds, stream, clocks=ClockSampler(local))
 
     if rank != 0:
         if world > 1:
@@ -882,13 +926,14 @@ def run_ours(args):
         return
     peak, peak_kind = peaks()
     K = args.steps
-    # algorithmic bytes: threshold phase reads every adjacency entry (4 B);
-    # rebuild reads and writes every entry (8 B); the whole step moves
-    # 16m + 24n bytes at minimum.
-    phase_bytes = {"threshold": 2 * g.m * 4, "rebuild": 2 * g.m * 8}
+    # roofline of the dominant kernel (algorithmic bytes per launch over its
+    # event-timed launch duration); the whole step moves 16m + 24n bytes at
+    # minimum (every directed entry read and written once, per node its key,
+    # position and order)
+    ntasks = (g.n + 1) // 2
+    dom, dom_bytes, dom_ms, dom_entries = dominant_kernel(stats, phases, g.m, ntasks, K)
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     phase_ms = {"threshold": phases["threshold_ms"] / K, "rebuild": phases["rebuild_ms"] / K}
-    dom = max(phase_ms, key=phase_ms.get)
-    achieved = phase_bytes[dom] / (phase_ms[dom] / 1e3) / 1e9
     b_min = 16 * g.m + 24 * g.n
     step_gbs = b_min / (t_max / K / 1e3) / 1e9
     cpu_v, cpu_desc, _, _ = cpu_sample(w, perm=args.perm)
@@ -896,10 +941,12 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic", "config": config_of(w, g, world, args.perm),
-        "roofline": {"bound": "hbm", "kernel": f"{dom} phase", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": measured_traffic() if (dom == "threshold" and args.workload == "n2^25") else None,
-                     "traffic_unit": "bytes per super step", "peak_source": f"{peak_kind} hbm_gbs"},
+                     "traffic": measured_traffic(dom, dom_entries),
+                     "traffic_unit": "DRAM bytes per launch (ncu on the n=2^21 graph, scaled by entries)",
+                     "algorithmic_bytes": dom_bytes, "launch_ms": dom_ms,
+                     "peak_source": f"{peak_kind} hbm_gbs (burst copy)"},
         "roofline_step": {"bytes_min": b_min, "achieved": step_gbs, "peak": peak, "unit": "GB/s",
                           "frac": step_gbs / peak},
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cpu_desc},
@@ -909,7 +956,9 @@ def run_ours(args):
         "clocks": clk,
         "phase_ms_per_step": {"permutation": phases["permutation_ms"] / K, "threshold": phase_ms["threshold"],
                               "rebuild": phase_ms["rebuild"], "step": phases["step_ms"] / K},
+        "class_ms_per_step": {CLASS_KERNELS[k]: phases.get(f"class{k}_ms", 0.0) / K for k in range(7)},
         "dependency_passes_last_step": stats.get("passes"),
+        "deferred_last_step": {"first_pass": stats.get("deferred"), "in_order": stats.get("inorder_trades")},
         "parity": parity,
         "swap_fraction": {"performed": sw_done, "possible": sw_all,
                           "fraction": sw_done / sw_all if sw_all else None, "of": "one global trade"},

@@ -174,14 +174,21 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
  * Counters of the last cb_global_trades call, for tests and tuning
  * (synchronises the handle's stream; out[5] counts the kernels inside the
  * CUDA graphs replayed when "cuda_graph" is on):
- * out[0] = threshold passes of the last super step: 1, or 2 when the first
- *          pass deferred trades to the in-order pass,
+ * out[0] = threshold passes of the last super step that ran trades: the
+ *          first pass, each retry pass with deferred trades left, and the
+ *          in-order pass when trades were still deferred,
  * out[1] = trades the first pass deferred,
- * out[2] = trades on the tile path, out[3] = on the 256- and 1024-thread paths,
+ * out[2] = trades of the first pass on the warp path (size class 0),
+ *          out[3] = on the larger teams (classes 1..6),
  * out[4] = trades whose workspace did not fit in shared memory,
  * out[5] = kernel launches issued by the last cb_global_trades or
- *          cb_uniform_trades call.
- * `count` = capacity of out; returns the number of counters written.
+ *          cb_uniform_trades call,
+ * out[6] = trades still deferred after the retry passes (run by the in-order
+ *          pass),
+ * out[7 + k], k < 7 = trades of size class k in the first pass,
+ * out[14 + k] = their directed entries (deg u + deg v summed).
+ * `count` = capacity of out (at most 21 are written); returns the number of
+ * counters written.
  */
 int cb_stats(cb_handle h, int64_t* out, int count);
 
@@ -192,8 +199,10 @@ int cb_stats(cb_handle h, int64_t* out, int count);
  * ms[0] = permutation of the next step and its row offsets, ms[1] = the
  * threshold phase (every trade's |A_{u-v}|-th smallest key, including the
  * passes that resolve dependent trades), ms[2] = the rebuild phase (new rows
- * for the next step), ms[3] = whole super steps.  Returns the number of
- * values written (<= count).
+ * for the next step), ms[3] = whole super steps, ms[4 + k], k < 7 = the
+ * first threshold pass's kernel of size class k (0 where the class shares
+ * another class's kernel).  Returns the number of values written
+ * (<= count, at most 11).
  */
 int cb_timings(cb_handle h, double* ms, int count);
 
@@ -227,6 +236,9 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               index order: 1024 (large trades in shared memory) or 256
  *               (four CTAs per SM; trades above block_max from global
  *               memory) [1024; 256 for cb_create_batch].
+ *   "retry_passes" parallel passes over the deferred trades between the
+ *               first pass and the in-order pass, each running every deferred
+ *               trade whose dependencies have published by then [2]; 0..4.
  *   "relaxed"   1: relaxed global trades (Def. "Relaxed global trade",
  *               Appendix EM-GCB): super step g orders the nodes by
  *               h(x) = (a x + b) mod p, p the smallest prime >= n, with
@@ -337,10 +349,10 @@ int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_o
  * super steps (they advance the chain; the result does not depend on the
  * options): one to load the kernels, then the rest shared evenly by the
  * candidate settings, one knob at a time, of "tile_max", "block_max",
- * "smem_max" and "inorder_threads", timed with CUDA events, and keeps the
- * fastest.  chosen (may be NULL) receives up to `count` values: tile_max,
- * block_max, smem_max, inorder_threads, super steps used.  Returns the
- * number of values written.
+ * "smem_max", "inorder_threads" and "retry_passes", timed with CUDA
+ * events, and keeps the fastest.  chosen (may be NULL) receives up to
+ * `count` values: tile_max, block_max, smem_max, inorder_threads, super
+ * steps used, retry_passes.  Returns the number of values written.
  */
 int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count);
 

@@ -214,9 +214,9 @@ def cb_export_graph(h, index: int, out=None):
 
 
 def cb_autotune(h, max_steps: int):
-    out = (C.c_int64 * 5)()
-    k = _check(load().cb_autotune(h, max_steps, out, 5), h)
-    names = ["tile_max", "block_max", "smem_max", "inorder_threads", "steps"]
+    out = (C.c_int64 * 6)()
+    k = _check(load().cb_autotune(h, max_steps, out, 6), h)
+    names = ["tile_max", "block_max", "smem_max", "inorder_threads", "steps", "retry_passes"]
     return {names[i]: out[i] for i in range(k)}
 
 
@@ -380,18 +380,27 @@ def cb_autocorr(h, graph: int, kmax: int):
     return list(corr), list(near), occ.value, st.value
 
 
+TRADE_CLASSES = 7   # size classes of the threshold phase
+
+# cb_stats: out[0..7), then trades and directed entries per size class of the
+# first threshold pass
+_STAT_NAMES = (["passes", "deferred", "tile_trades", "block_trades", "global_ws_trades", "launches",
+                "inorder_trades"] + [f"class{k}_trades" for k in range(TRADE_CLASSES)]
+               + [f"class{k}_entries" for k in range(TRADE_CLASSES)])
+_TIMING_NAMES = (["permutation_ms", "threshold_ms", "rebuild_ms", "step_ms"]
+                 + [f"class{k}_ms" for k in range(TRADE_CLASSES)])
+
+
 def cb_stats(h):
-    out = (C.c_int64 * 8)()
-    k = _check(load().cb_stats(h, out, 8), h)
-    names = ["passes", "deferred", "tile_trades", "block_trades", "global_ws_trades", "launches"]
-    return {names[i]: out[i] for i in range(k)}
+    out = (C.c_int64 * len(_STAT_NAMES))()
+    k = _check(load().cb_stats(h, out, len(_STAT_NAMES)), h)
+    return {_STAT_NAMES[i]: out[i] for i in range(k)}
 
 
 def cb_timings(h):
-    out = (C.c_double * 4)()
-    k = _check(load().cb_timings(h, out, 4), h)
-    names = ["permutation_ms", "threshold_ms", "rebuild_ms", "step_ms"]
-    return {names[i]: out[i] for i in range(k)}
+    out = (C.c_double * len(_TIMING_NAMES))()
+    k = _check(load().cb_timings(h, out, len(_TIMING_NAMES)), h)
+    return {_TIMING_NAMES[i]: out[i] for i in range(k)}
 
 
 def cb_set_option(h, key: str, value: int):

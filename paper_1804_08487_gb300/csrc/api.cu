@@ -785,20 +785,28 @@ int cb_stats(cb_handle h, int64_t* out, int count) {
                              h->stream));
   CB_CUDA(h, cudaStreamSynchronize(h->stream));
   const int64_t* hc = h->host_counters;
-  h->stats[0] = hc[kCtrDeferred] ? 2 : 1;   // the in-order pass runs only what the first pass deferred
-  h->stats[1] = hc[kCtrDeferred];
-  h->stats[2] = hc[kCtrClsLen];
+  // pass r + 1 runs what pass r left deferred (the last: the in-order pass)
+  int64_t passes = 1;
+  for (int r = 0; r <= h->retry_passes; ++r) passes += hc[kCtrPassLeft + r] > 0;
+  h->stats[0] = passes;
+  h->stats[1] = hc[kCtrPassLeft];
+  h->stats[2] = hc[kCtrFirstLen];
   h->stats[3] = 0;
-  for (int k = 1; k < kClasses; ++k) h->stats[3] += hc[kCtrClsLen + k];
+  for (int k = 1; k < kClasses; ++k) h->stats[3] += hc[kCtrFirstLen + k];
   h->stats[4] = hc[kCtrGws];
-  const int k = std::min(count, 6);
+  h->stats[6] = hc[kCtrPassLeft + h->retry_passes];
+  for (int k = 0; k < kClasses; ++k) {
+    h->stats[7 + k] = hc[kCtrFirstLen + k];
+    h->stats[7 + kClasses + k] = hc[kCtrFirstEnt + k];
+  }
+  const int k = std::min(count, kStats);
   for (int i = 0; i < k; ++i) out[i] = h->stats[i];
   return k;
 }
 
 int cb_timings(cb_handle h, double* ms, int count) {
   if (!h || !ms || count < 0) return fail(h, CB_EINVAL, "bad argument");
-  const int k = std::min(count, 4);
+  const int k = std::min(count, 4 + kClasses);
   for (int i = 0; i < k; ++i) ms[i] = h->phase_ms[i];
   return k;
 }
@@ -872,6 +880,11 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     h->timing = value != 0;
     return CB_OK;
   }
+  if (!std::strcmp(key, "retry_passes")) {
+    if (value < 0 || value > kRetryPassesMax) return fail(h, CB_EINVAL, "retry_passes out of range [0, 4]");
+    h->retry_passes = static_cast<int>(value);
+    return CB_OK;
+  }
   if (!std::strcmp(key, "inorder_threads")) {
     if (value != 256 && value != 1024) return fail(h, CB_EINVAL, "inorder_threads is 256 or 1024");
     h->inorder_threads = static_cast<int>(value);
@@ -934,10 +947,12 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
     int cand[4];
     int ncand;
   };
-  Knob knobs[4] = {{&h->tile_max, {32, 64, 96, 128}, 4},
-                   {&h->block_max, {512, 1024, 2048, 0}, 3},
-                   {&h->smem_max, {2048, 4096, 8192, 0}, 3},
-                   {&h->inorder_threads, {256, 1024, 0, 0}, 2}};
+  constexpr int kKnobs = 5;
+  Knob knobs[kKnobs] = {{&h->tile_max, {32, 64, 96, 128}, 4},
+                        {&h->block_max, {512, 1024, 2048, 0}, 3},
+                        {&h->smem_max, {2048, 4096, 8192, 0}, 3},
+                        {&h->inorder_threads, {256, 1024, 0, 0}, 2},
+                        {&h->retry_passes, {0, 1, 2, 4}, 4}};
   float ms = 0;
   if (used < max_steps) rc = trial(&ms);   // first launches load the kernels: not timed as a candidate
   {
@@ -945,7 +960,7 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
     for (const Knob& kn : knobs) total += kn.ncand;
     if (max_steps > used) per = std::max<uint32_t>(1, (max_steps - used) / static_cast<uint32_t>(total));
   }
-  for (int k = 0; k < 4 && rc == CB_OK; ++k) {
+  for (int k = 0; k < kKnobs && rc == CB_OK; ++k) {
     int best = *knobs[k].field;
     float best_ms = 3.4e38f;
     for (int j = 0; j < knobs[k].ncand && used < max_steps && rc == CB_OK; ++j) {
@@ -964,8 +979,9 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  const int64_t vals[5] = {h->tile_max, h->block_max, h->smem_max, h->inorder_threads, static_cast<int64_t>(used)};
-  const int k = chosen ? std::min(count, 5) : 0;
+  const int64_t vals[6] = {h->tile_max,        h->block_max, h->smem_max, h->inorder_threads,
+                           static_cast<int64_t>(used), h->retry_passes};
+  const int k = chosen ? std::min(count, 6) : 0;
   for (int i = 0; i < k; ++i) chosen[i] = vals[i];
   return k;
 }

@@ -32,14 +32,18 @@ constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kBlockMaxDefault = 1024;   // default of the "block_max" option
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
-constexpr int kCounters = 32;       // device counters per handle
+constexpr int kCounters = 48;       // device counters per handle
 // Trade size classes of the threshold phase (one team size each) and the
 // device counters of a super step.
 constexpr int kClasses = 7;
 constexpr int kCtrClsLen = 0;       // [0, kClasses): trades per class
 constexpr int kCtrClsStart = 8;     // [8, 8 + kClasses): first entry of each class in the class lists
-constexpr int kCtrDeferred = 16;    // trades the first pass deferred
 constexpr int kCtrClaims = 17;      // chunks claimed by the in-order pass
+constexpr int kCtrFirstLen = 18;    // [18, 18 + kClasses): trades per class in the first pass
+constexpr int kCtrFirstEnt = 25;    // [25, 25 + kClasses): directed entries per class in the first pass
+constexpr int kCtrPassLeft = 32;    // [32, 32 + kRetryPassesMax + 1): trades left deferred after pass r
+constexpr int kRetryPassesMax = 4;
+constexpr int kStats = 7 + 2 * kClasses;   // counters cb_stats reports
 constexpr int kCtrGws = kCounters - 1;   // trades whose workspace is in global memory
 constexpr int kMaxLcgGaps = 1024;   // p - n for the relaxed permutation (prime gaps below 2^31 are far smaller)
 
@@ -130,6 +134,7 @@ struct Graph {
   int smem_max = kSmemMaxCap;
   int bucket_cap = 2048;
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
+  int retry_passes = 2;         // parallel passes over the deferred trades before the in-order pass
   bool wide_pack = false;       // 16-byte far-trade records even when 8 bytes would do (tests)
   // relaxed global trade: permutations from h(x) = (a x + b) mod p
   bool relaxed = false;
@@ -147,11 +152,15 @@ struct Graph {
   int64_t* swaps = nullptr;
 
   // stats of the last cb_global_trades
-  int64_t stats[8] = {0};
+  int64_t stats[kStats] = {0};
   int64_t launches = 0;                    // kernel launches issued by this handle
   bool timing = false;                     // record CUDA events around the phases
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double phase_ms[4] = {0, 0, 0, 0};       // permutation+prep, thresholds, rebuild, whole step
+  // events: [0..4) phase bounds, [4, 4 + kClasses + 1) bounds of the first
+  // pass's class kernels
+  cudaEvent_t ev[4 + kClasses + 1] = {};
+  // permutation+prep, thresholds, rebuild, whole step, then the first pass's
+  // kernel of each size class
+  double phase_ms[4 + kClasses] = {};
   int latched = CB_OK;
   std::string last_error;
 };

@@ -44,7 +44,6 @@ namespace {
 
 constexpr uint32_t kDeferred = 2;              // done[t]: deferred (a dependency had not published)
 constexpr uint32_t kComplete = 3;              // done[t]: complete, no later trade waits for it
-constexpr int kRetryPasses = 2;                // parallel passes over the deferred trades before the in-order one
 
 // meta bits per entry (phase A)
 constexpr uint8_t kR = 1;       // entry sits in v's row
@@ -75,7 +74,7 @@ struct StepCtx {
   int32_t* err;
   const int32_t* M;
   const int64_t* rp_next;
-  unsigned long long* def_count;   // trades deferred by the first pass
+  unsigned long long* def_count;   // trades this pass deferred
   uint32_t wait;                   // 0: defer a trade whose dependency is unpublished; 1: wait for it
   unsigned long long* gws_count;
   int cand_max;                    // register paths: most candidates ranked directly (else more radix digits)
@@ -1348,25 +1347,42 @@ __device__ __forceinline__ int trade_class(const ClassTh& th, int L) {
   return k;
 }
 
+// The first classification of a step also adds up every class's directed
+// entries (L summed) into ctr[kCtrFirstEnt + k], for the stats.
 __global__ void __launch_bounds__(kClassThreads) k_class_count(StepCtx c, int64_t ntasks, ClassTh th,
                                                                int64_t nchunks, int only_deferred,
-                                                               int32_t* __restrict__ counts) {
+                                                               int32_t* __restrict__ counts,
+                                                               int64_t* __restrict__ ctr) {
   __shared__ int wc[kClassThreads / 32][kClasses];
+  __shared__ unsigned long long we[kClasses];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < kClasses) we[threadIdx.x] = 0;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     int mine[kClasses] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned ent[kClasses] = {0, 0, 0, 0, 0, 0, 0};
     for (int j = 0; j < kClassPer; ++j) {
       const int64_t t = ch * kClassChunk + j * kClassThreads + threadIdx.x;
-      int k = -1;
+      int k = -1, L = 0;
       if (t < ntasks && (!only_deferred || __ldcg(c.done + t) == kDeferred)) {
         const TradeRows tr = trade_rows(c, t);
-        k = trade_class(th, tr.du + tr.dv);
+        L = tr.du + tr.dv;
+        k = trade_class(th, L);
       }
 #pragma unroll
-      for (int q = 0; q < kClasses; ++q) mine[q] += __popc(__ballot_sync(kFull, k == q));
+      for (int q = 0; q < kClasses; ++q) {
+        mine[q] += __popc(__ballot_sync(kFull, k == q));
+        ent[q] += k == q ? static_cast<unsigned>(L) : 0u;
+      }
     }
     if (lane == 0)
       for (int q = 0; q < kClasses; ++q) wc[warp][q] = mine[q];
+    if (!only_deferred) {
+#pragma unroll
+      for (int q = 0; q < kClasses; ++q) {
+        const unsigned e = __reduce_add_sync(kFull, ent[q]);
+        if (lane == 0 && e) atomicAdd(&we[q], static_cast<unsigned long long>(e));
+      }
+    }
     __syncthreads();
     if (threadIdx.x < kClasses) {
       int tot = 0;
@@ -1375,6 +1391,8 @@ __global__ void __launch_bounds__(kClassThreads) k_class_count(StepCtx c, int64_
     }
     __syncthreads();
   }
+  if (!only_deferred && threadIdx.x < kClasses && we[threadIdx.x])
+    atomicAdd(reinterpret_cast<unsigned long long*>(ctr + kCtrFirstEnt + threadIdx.x), we[threadIdx.x]);
 }
 
 __global__ void __launch_bounds__(kClassThreads) k_class_place(StepCtx c, int64_t ntasks, ClassTh th,
@@ -1419,12 +1437,16 @@ __global__ void __launch_bounds__(kClassThreads) k_class_place(StepCtx c, int64_
   }
 }
 
-// Each class's first list entry and length into the counters.
-__global__ void k_class_bounds(const int64_t* __restrict__ off, int64_t nchunks, int64_t* __restrict__ ctr) {
+// Each class's first list entry and length into the counters (for the
+// first classification of a step also into the stats' copy).
+__global__ void k_class_bounds(const int64_t* __restrict__ off, int64_t nchunks, int first,
+                               int64_t* __restrict__ ctr) {
   const int k = threadIdx.x;
   if (k < kClasses) {
+    const int64_t len = off[(k + 1) * nchunks] - off[k * nchunks];
     ctr[kCtrClsStart + k] = off[k * nchunks];
-    ctr[kCtrClsLen + k] = off[(k + 1) * nchunks] - off[k * nchunks];
+    ctr[kCtrClsLen + k] = len;
+    if (first) ctr[kCtrFirstLen + k] = len;
   }
 }
 
@@ -1875,8 +1897,9 @@ int super_step(Graph* h) {
   c.err = h->err;
   c.M = h->M;
   c.rp_next = h->rp[nxt];
-  // counters: [0..2] class list lengths, [4] deferred trades, [5] chunks
-  // claimed by the in-order pass, [kCounters-1] global-workspace trades
+  // counters (kCtr* in cb_internal.cuh): class lists, the first pass's class
+  // sizes, deferrals per pass, chunks claimed by the in-order pass,
+  // global-workspace trades
   int64_t* cnt = h->counters;
   unsigned long long* ucnt = reinterpret_cast<unsigned long long*>(cnt);
   c.gws_count = ucnt + kCtrGws;
@@ -1916,7 +1939,6 @@ int super_step(Graph* h) {
   const unsigned sgrid = static_cast<unsigned>(h->num_sms);
   char* gws = static_cast<char*>(h->ws_global);
   c.wait = 0;
-  c.def_count = ucnt + kCtrDeferred;
   c.cand_max = h->cand_max;
   c.wait_ns = h->wait_ns;
   c.hold_publish = h->hold_publish;
@@ -1931,52 +1953,69 @@ int super_step(Graph* h) {
   auto classify = [&](int only_deferred) -> int {
     const int64_t nch = (ntasks + kClassChunk - 1) / kClassChunk;
     const unsigned cgrid = static_cast<unsigned>(std::min<int64_t>(nch, int64_t(h->num_sms) * 8));
-    k_class_count<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, only_deferred, h->cls_flag);
+    k_class_count<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, only_deferred, h->cls_flag, cnt);
     int r = launched();
     if (r) return r;
     CB_CUDA(h, exclusive_scan_i32(h->cls_flag, h->cls_scan, kClasses * nch, h->scan_ws, s, &h->launches));
     k_class_place<<<cgrid, kClassThreads, 0, s>>>(c, ntasks, th, nch, only_deferred, h->cls_scan, h->lists);
     if ((r = launched())) return r;
-    k_class_bounds<<<1, 32, 0, s>>>(h->cls_scan, nch, cnt);
+    k_class_bounds<<<1, 32, 0, s>>>(h->cls_scan, nch, !only_deferred, cnt);
     return launched();
   };
   // one pass of every class's kernel; a trade whose dependency has not
   // published yet is (again) marked deferred
+  // with "timing" on, the first pass brackets each class's kernel with
+  // events ev[4 + k] .. ev[5 + k] (a class without its own kernel takes none)
+  bool time_classes = false;
+  auto mark = [&](int k) -> int {
+    if (time_classes) CB_CUDA(h, cudaEventRecord(h->ev[4 + k], s));
+    return CB_OK;
+  };
   auto run_classes = [&]() -> int {
     int r;
+    if ((r = mark(0))) return r;
     k_phase_a_warp<<<static_cast<unsigned>(h->num_sms * 8), 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(
         c, L, cnt, 0);
-    if ((r = launched())) return r;
+    if ((r = launched()) || (r = mark(1))) return r;
     if (h->cta_paths) {
       k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 1);
-      if ((r = launched())) return r;
+      if ((r = launched()) || (r = mark(2))) return r;
       k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 2);
-      if ((r = launched())) return r;
+      if ((r = launched()) || (r = mark(3))) return r;
       k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 3);
-      if ((r = launched())) return r;
+      if ((r = launched()) || (r = mark(4))) return r;
       k_phase_a_team<kBigThreads, 512><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt, 4);
-      if ((r = launched())) return r;
+      if ((r = launched()) || (r = mark(5))) return r;
       k_phase_a_team<kBigThreads, kBigThreads><<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(
           c, L, cnt, 5);
-      if ((r = launched())) return r;
+      if ((r = launched()) || (r = mark(6))) return r;
     } else {
       k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 3, block_max, gws, h->ws_slice,
                                                                           block_max);
       if ((r = launched())) return r;
+      for (int k = 2; k <= 6; ++k)
+        if ((r = mark(k))) return r;
     }
     // the largest trades: 1024 threads, up to smem_max entries in shared
     // memory (staged by a bulk copy), a global-memory slice above
     k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 6, h->smem_max, gws, h->ws_slice,
                                                                         h->smem_max);
-    return launched();
+    if ((r = launched())) return r;
+    return mark(7);
   };
-  // the first pass over every trade, then kRetryPasses parallel passes over
+  // the first pass over every trade, then retry_passes parallel passes over
   // the deferred ones: each runs every deferred trade whose dependencies
   // have published by then (a trade the previous pass completed leaves the
-  // list), so chains of dependent trades shrink by a level per pass
+  // list), so chains of dependent trades shrink by a level per pass.  Pass
+  // r counts its deferrals in ctr[kCtrPassLeft + r].
+  time_classes = h->timing;
+  c.def_count = ucnt + kCtrPassLeft;
   if ((rc = classify(0)) || (rc = run_classes())) return rc;
-  for (int r = 0; r < kRetryPasses; ++r)
+  time_classes = false;
+  for (int r = 0; r < h->retry_passes; ++r) {
+    c.def_count = ucnt + kCtrPassLeft + 1 + r;
     if ((rc = classify(1)) || (rc = run_classes())) return rc;
+  }
   // last pass: the trades still deferred, in index order, waiting on
   // dependencies.  1024-thread CTAs keep large trades in shared memory;
   // 256-thread CTAs (four per SM) run many small deferred trades at once,
@@ -2042,6 +2081,11 @@ int super_step(Graph* h) {
     h->phase_ms[1] += b;
     h->phase_ms[2] += d;
     h->phase_ms[3] += tot;
+    for (int k = 0; k < kClasses; ++k) {
+      float e = 0;
+      CB_CUDA(h, cudaEventElapsedTime(&e, h->ev[4 + k], h->ev[5 + k]));
+      h->phase_ms[4 + k] += e;
+    }
   }
   return finish_step(h);
 }

@@ -137,6 +137,35 @@ def test_dense_graphs_resolve_dependencies(n, a, b, seed):
     _run_pair(g.row_ptr, g.col, seed + 500, 3, options={"inorder_threads": 256, "block_max": 256})
     _run_pair(g.row_ptr, g.col, seed + 600, 3, options={"cand_max": 1})
     _run_pair(g.row_ptr, g.col, seed + 700, 3, options={"tile_paths": 1, "cta_paths": 0})
+    _run_pair(g.row_ptr, g.col, seed + 800, 3, options={"retry_passes": 0})   # deferred trades straight to the in-order pass
+    _run_pair(g.row_ptr, g.col, seed + 900, 3, options={"retry_passes": 4})
+
+
+def test_stats_count_every_trade_and_entry():
+    """The first pass's size classes hold every trade and every directed
+    entry once; the retry passes never leave more deferred than they got."""
+    g = synth.powerlaw_graph(3000, 4, 1500, 2.0, 13)
+    c = Curveball(g.row_ptr, g.col, 3)
+    c.set_option("timing", 1)
+    for retry in (0, 2, 4):
+        c.set_option("retry_passes", retry)
+        c.global_trades(1)
+        st = c.stats()
+        assert sum(st[f"class{k}_trades"] for k in range(7)) == (g.n + 1) // 2
+        assert sum(st[f"class{k}_entries"] for k in range(7)) == 2 * g.m
+        assert st["tile_trades"] == st["class0_trades"]
+        assert st["tile_trades"] + st["block_trades"] == (g.n + 1) // 2
+        assert 0 <= st["inorder_trades"] <= st["deferred"]
+        assert 1 <= st["passes"] <= 2 + retry
+        tm = c.timings()
+        assert tm["class0_ms"] > 0 and tm["class0_ms"] <= tm["threshold_ms"]
+    big = synth.powerlaw_graph(400, 60, 300, 2.0, 5)
+    c = Curveball(big.row_ptr, big.col, 9)
+    c.set_option("retry_passes", 0)
+    for _ in range(3):
+        c.global_trades(1)
+        st = c.stats()
+        assert st["inorder_trades"] == st["deferred"]
 
 
 def test_dependency_passes_happen():
