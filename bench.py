@@ -184,8 +184,9 @@ def measured_traffic(kernel, entries):
 
 
 # the threshold phase's kernel of each size class (cb_timings ms[4 + k])
-CLASS_KERNELS = ["k_phase_a_warp", "k_phase_a_team<256,64>", "k_phase_a_team<256,128>", "k_phase_a_team<256,256>",
-                 "k_phase_a_team<1024,512>", "k_phase_a_team<1024,1024>", "k_phase_a_block<1024>"]
+CLASS_KERNELS = ["k_phase_a_lanes<8>", "k_phase_a_lanes<16>", "k_phase_a_warp", "k_phase_a_team<256,64>",
+                 "k_phase_a_team<256,128>", "k_phase_a_team<256,256>", "k_phase_a_team<1024,512>",
+                 "k_phase_a_team<1024,1024>", "k_phase_a_block<1024>"]
 # algorithmic bytes: a threshold kernel reads each directed entry of its
 # trades (4 B) and writes it into the new row with its side word (4 + 2 B),
 # plus per trade its two rows' offsets, positions, threshold and done flag
@@ -956,7 +957,7 @@ def run_ours(args):
         "clocks": clk,
         "phase_ms_per_step": {"permutation": phases["permutation_ms"] / K, "threshold": phase_ms["threshold"],
                               "rebuild": phase_ms["rebuild"], "step": phases["step_ms"] / K},
-        "class_ms_per_step": {CLASS_KERNELS[k]: phases.get(f"class{k}_ms", 0.0) / K for k in range(7)},
+        "class_ms_per_step": {CLASS_KERNELS[k]: phases.get(f"class{k}_ms", 0.0) / K for k in range(len(CLASS_KERNELS))},
         "dependency_passes_last_step": stats.get("passes"),
         "deferred_last_step": {"first_pass": stats.get("deferred"), "in_order": stats.get("inorder_trades")},
         "parity": parity,

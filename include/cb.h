@@ -51,6 +51,7 @@ extern "C" {
 #define CB_ESIZE (-6)    /* caller buffer too small (size reported) */
 #define CB_ERANGE (-7)   /* super-step counter would exceed 2^32 - 2 */
 #define CB_ETIMEOUT (-8) /* a bounded device wait ran out (the handle stays destroyable) */
+#define CB_EIO (-9)      /* a file could not be read or written, or is not in the expected format */
 
 #define CB_HOST 0
 #define CB_DEVICE 1
@@ -178,16 +179,16 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
  *          first pass, each retry pass with deferred trades left, and the
  *          in-order pass when trades were still deferred,
  * out[1] = trades the first pass deferred,
- * out[2] = trades of the first pass on the warp path (size class 0),
- *          out[3] = on the larger teams (classes 1..6),
+ * out[2] = trades of the first pass on warps or parts of a warp (size
+ *          classes 0..2), out[3] = on the larger teams (classes 3..8),
  * out[4] = trades whose workspace did not fit in shared memory,
  * out[5] = kernel launches issued by the last cb_global_trades or
  *          cb_uniform_trades call,
  * out[6] = trades still deferred after the retry passes (run by the in-order
  *          pass),
- * out[7 + k], k < 7 = trades of size class k in the first pass,
- * out[14 + k] = their directed entries (deg u + deg v summed).
- * `count` = capacity of out (at most 21 are written); returns the number of
+ * out[7 + k], k < 9 = trades of size class k in the first pass,
+ * out[16 + k] = their directed entries (deg u + deg v summed).
+ * `count` = capacity of out (at most 25 are written); returns the number of
  * counters written.
  */
 int cb_stats(cb_handle h, int64_t* out, int count);
@@ -199,10 +200,10 @@ int cb_stats(cb_handle h, int64_t* out, int count);
  * ms[0] = permutation of the next step and its row offsets, ms[1] = the
  * threshold phase (every trade's |A_{u-v}|-th smallest key, including the
  * passes that resolve dependent trades), ms[2] = the rebuild phase (new rows
- * for the next step), ms[3] = whole super steps, ms[4 + k], k < 7 = the
+ * for the next step), ms[3] = whole super steps, ms[4 + k], k < 9 = the
  * first threshold pass's kernel of size class k (0 where the class shares
  * another class's kernel).  Returns the number of values written
- * (<= count, at most 11).
+ * (<= count, at most 13).
  */
 int cb_timings(cb_handle h, double* ms, int count);
 
@@ -236,6 +237,8 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               index order: 1024 (large trades in shared memory) or 256
  *               (four CTAs per SM; trades above block_max from global
  *               memory) [1024; 256 for cb_create_batch].
+ *   "lane_teams" 1: trades of at most 32 / 64 entries run on teams of 8 /
+ *               16 lanes, several per warp; 0: on whole warps [1].
  *   "retry_passes" parallel passes over the deferred trades between the
  *               first pass and the in-order pass, each running every deferred
  *               trade whose dependencies have published by then [2]; 0..4.
@@ -355,6 +358,42 @@ int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_o
  * steps used, retry_passes.  Returns the number of values written.
  */
 int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count);
+
+/*
+ * cb_autotune with a file cache.  The key (cb_tune_key) names the GPU (device
+ * name, SM count), floor(log2 n), floor(log2 graphs) and the handle's degree
+ * distribution: for each degree bit length b = 0..32, the share of directed
+ * entries of the nodes whose degree has b bits, in 64ths.  When cache_path
+ * holds the key, its settings are applied (no super step runs; chosen[4] =
+ * 0); otherwise cb_autotune runs and its choice is stored under the key.  The
+ * cache is a JSON file, {"version": 1, "entries": [{"key": ..., "tile_max":
+ * ..., "block_max": ..., "smem_max": ..., "inorder_threads": ...,
+ * "retry_passes": ...}, ...]}, written whole to cache_path + ".tmp" and
+ * renamed over cache_path.  chosen / count and the return value as for
+ * cb_autotune; CB_EIO when the file cannot be read or written or is not such
+ * a cache (it is then left unchanged).
+ */
+int cb_autotune_cached(cb_handle h, uint32_t max_steps, const char* cache_path, int64_t* chosen, int count);
+
+/*
+ * The cache key of a handle (see cb_autotune_cached) into key[0..cap), NUL
+ * terminated.  Runs one histogram kernel over the degrees and synchronises the
+ * handle's stream.  Returns the key's length, CB_ESIZE if cap is too small.
+ */
+int cb_tune_key(cb_handle h, char* key, int cap);
+
+/*
+ * Host-only access to a tuning cache file (no device work).  lookup: the
+ * settings stored under key into vals (tile_max, block_max, smem_max,
+ * inorder_threads, retry_passes; up to count of them); returns how many were
+ * written, 0 when the file or the key does not exist.  store: vals (exactly 5,
+ * in that order) under key, replacing an entry with the same key and keeping
+ * the others.  A key may not contain '"', '\', '{', '}' or control
+ * characters (CB_EINVAL).  Both return CB_EIO for a file that cannot be read
+ * or written or is not a tuning cache.
+ */
+int cb_tune_cache_lookup(const char* path, const char* key, int64_t* vals, int count);
+int cb_tune_cache_store(const char* path, const char* key, const int64_t* vals, int count);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@ CUDA library; there is no CPU fallback: if the library is missing this module
 raises instead of computing anything.
 """
 import ctypes as C
+import os
 import re
 from pathlib import Path
 
@@ -22,6 +23,7 @@ CB_ECHECK = -5
 CB_ESIZE = -6
 CB_ERANGE = -7
 CB_ETIMEOUT = -8
+CB_EIO = -9
 CB_HOST = 0
 CB_DEVICE = 1
 
@@ -89,6 +91,12 @@ def load():
     lib.cb_export_graph.argtypes = [vp, i32, vp, i64, C.POINTER(i64), i32]
     lib.cb_autotune.restype = i32
     lib.cb_autotune.argtypes = [vp, u32, C.POINTER(i64), i32]
+    for f in ("cb_autotune_cached", "cb_tune_key", "cb_tune_cache_lookup", "cb_tune_cache_store"):
+        getattr(lib, f).restype = i32
+    lib.cb_autotune_cached.argtypes = [vp, u32, C.c_char_p, C.POINTER(i64), i32]
+    lib.cb_tune_key.argtypes = [vp, C.c_char_p, i32]
+    lib.cb_tune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(i64), i32]
+    lib.cb_tune_cache_store.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(i64), i32]
     lib.cb_device_bytes.restype = i32
     lib.cb_device_bytes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     lib.cb_estimate_bytes.restype = i64
@@ -218,6 +226,34 @@ def cb_autotune(h, max_steps: int):
     k = _check(load().cb_autotune(h, max_steps, out, 6), h)
     names = ["tile_max", "block_max", "smem_max", "inorder_threads", "steps", "retry_passes"]
     return {names[i]: out[i] for i in range(k)}
+
+
+_TUNE_NAMES = ["tile_max", "block_max", "smem_max", "inorder_threads", "retry_passes"]
+
+
+def cb_autotune_cached(h, max_steps: int, cache_path: str):
+    out = (C.c_int64 * 6)()
+    k = _check(load().cb_autotune_cached(h, max_steps, os.fsencode(cache_path), out, 6), h)
+    names = ["tile_max", "block_max", "smem_max", "inorder_threads", "steps", "retry_passes"]
+    return {names[i]: out[i] for i in range(k)}
+
+
+def cb_tune_key(h) -> str:
+    buf = C.create_string_buffer(512)
+    _check(load().cb_tune_key(h, buf, len(buf)), h)
+    return buf.value.decode()
+
+
+def cb_tune_cache_lookup(path: str, key: str):
+    """The settings stored under key (a dict), or None."""
+    out = (C.c_int64 * 5)()
+    k = _check(load().cb_tune_cache_lookup(os.fsencode(path), key.encode(), out, 5))
+    return {_TUNE_NAMES[i]: out[i] for i in range(k)} if k else None
+
+
+def cb_tune_cache_store(path: str, key: str, settings: dict):
+    vals = (C.c_int64 * 5)(*[int(settings[nm]) for nm in _TUNE_NAMES])
+    return _check(load().cb_tune_cache_store(os.fsencode(path), key.encode(), vals, 5))
 
 
 def cb_global_trades(h, supersteps: int):
@@ -380,7 +416,7 @@ def cb_autocorr(h, graph: int, kmax: int):
     return list(corr), list(near), occ.value, st.value
 
 
-TRADE_CLASSES = 7   # size classes of the threshold phase
+TRADE_CLASSES = 9   # size classes of the threshold phase
 
 # cb_stats: out[0..7), then trades and directed entries per size class of the
 # first threshold pass
@@ -436,8 +472,13 @@ class Curveball:
     def set_option(self, key, value):
         cb_set_option(self.h, key, value)
 
-    def autotune(self, max_steps: int):
+    def autotune(self, max_steps: int, cache_path=None):
+        if cache_path is not None:
+            return cb_autotune_cached(self.h, max_steps, cache_path)
         return cb_autotune(self.h, max_steps)
+
+    def tune_key(self) -> str:
+        return cb_tune_key(self.h)
 
     def uniform_trades(self, count: int = 1):
         cb_uniform_trades(self.h, count)

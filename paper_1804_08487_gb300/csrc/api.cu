@@ -790,9 +790,8 @@ int cb_stats(cb_handle h, int64_t* out, int count) {
   for (int r = 0; r <= h->retry_passes; ++r) passes += hc[kCtrPassLeft + r] > 0;
   h->stats[0] = passes;
   h->stats[1] = hc[kCtrPassLeft];
-  h->stats[2] = hc[kCtrFirstLen];
-  h->stats[3] = 0;
-  for (int k = 1; k < kClasses; ++k) h->stats[3] += hc[kCtrFirstLen + k];
+  h->stats[2] = h->stats[3] = 0;
+  for (int k = 0; k < kClasses; ++k) h->stats[k < kWarpClasses ? 2 : 3] += hc[kCtrFirstLen + k];
   h->stats[4] = hc[kCtrGws];
   h->stats[6] = hc[kCtrPassLeft + h->retry_passes];
   for (int k = 0; k < kClasses; ++k) {
@@ -878,6 +877,11 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
       for (auto& e : h->ev) CB_CUDA(h, cudaEventCreate(&e));
     }
     h->timing = value != 0;
+    return CB_OK;
+  }
+  if (!std::strcmp(key, "lane_teams")) {
+    if (value < 0 || value > 1) return fail(h, CB_EINVAL, "lane_teams is 0 or 1");
+    h->lane_teams = static_cast<int>(value);
     return CB_OK;
   }
   if (!std::strcmp(key, "retry_passes")) {

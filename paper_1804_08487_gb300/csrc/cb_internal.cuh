@@ -35,13 +35,14 @@ constexpr int kBlockThreads = 256;  // CTA size of the block path
 constexpr int kCounters = 48;       // device counters per handle
 // Trade size classes of the threshold phase (one team size each) and the
 // device counters of a super step.
-constexpr int kClasses = 7;
+constexpr int kClasses = 9;
+constexpr int kWarpClasses = 3;     // classes 0..2 run on warps or parts of a warp
 constexpr int kCtrClsLen = 0;       // [0, kClasses): trades per class
-constexpr int kCtrClsStart = 8;     // [8, 8 + kClasses): first entry of each class in the class lists
-constexpr int kCtrClaims = 17;      // chunks claimed by the in-order pass
-constexpr int kCtrFirstLen = 18;    // [18, 18 + kClasses): trades per class in the first pass
-constexpr int kCtrFirstEnt = 25;    // [25, 25 + kClasses): directed entries per class in the first pass
-constexpr int kCtrPassLeft = 32;    // [32, 32 + kRetryPassesMax + 1): trades left deferred after pass r
+constexpr int kCtrClsStart = 10;    // [10, 10 + kClasses): first entry of each class in the class lists
+constexpr int kCtrClaims = 19;      // chunks claimed by the in-order pass
+constexpr int kCtrFirstLen = 20;    // [20, 20 + kClasses): trades per class in the first pass
+constexpr int kCtrFirstEnt = 29;    // [29, 29 + kClasses): directed entries per class in the first pass
+constexpr int kCtrPassLeft = 40;    // [40, 40 + kRetryPassesMax + 1): trades left deferred after pass r
 constexpr int kRetryPassesMax = 4;
 constexpr int kStats = 7 + 2 * kClasses;   // counters cb_stats reports
 constexpr int kCtrGws = kCounters - 1;   // trades whose workspace is in global memory
@@ -135,6 +136,7 @@ struct Graph {
   int bucket_cap = 2048;
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
   int retry_passes = 2;         // parallel passes over the deferred trades before the in-order pass
+  int lane_teams = 1;           // trades up to 32 / 64 entries on teams of 8 / 16 lanes
   bool wide_pack = false;       // 16-byte far-trade records even when 8 bytes would do (tests)
   // relaxed global trade: permutations from h(x) = (a x + b) mod p
   bool relaxed = false;

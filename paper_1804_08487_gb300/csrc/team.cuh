@@ -33,6 +33,38 @@ struct WarpTeam {
   __device__ __forceinline__ uint64_t bcast(uint64_t v, int src) const { return __shfl_sync(kFull, v, src); }
 };
 
+// W consecutive lanes of a warp (W = 8 or 16): a warp holds 32 / W such
+// teams, each on its own trade.  Synchronisation and shuffles name only the
+// team's lanes, so teams that diverge (different trip counts, an early
+// return) never wait for each other; while they run the same instructions,
+// one warp instruction serves all of them.
+template <int W>
+struct LaneTeam {
+  static_assert(W == 8 || W == 16, "lane teams of 8 or 16 lanes");
+  static constexpr int N = W;
+  int rank;
+  unsigned mask;
+  __device__ __forceinline__ LaneTeam()
+      : rank(threadIdx.x & (W - 1)), mask(((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1))) {}
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+  __device__ __forceinline__ bool any(bool p) const { return __any_sync(mask, p); }
+  __device__ __forceinline__ int64_t sum(int64_t v) const {
+#pragma unroll
+    for (int o = W / 2; o; o >>= 1) v += __shfl_xor_sync(mask, v, o, W);
+    return v;
+  }
+  __device__ __forceinline__ int64_t exscan(int64_t v) const {
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+      const int64_t y = __shfl_up_sync(mask, x, o, W);
+      if (rank >= o) x += y;
+    }
+    return x - v;
+  }
+  __device__ __forceinline__ uint64_t bcast(uint64_t v, int src) const { return __shfl_sync(mask, v, src, W); }
+};
+
 // A CTA of NT threads; `red` points at kRedSlots int64 slots of shared memory.
 // Reductions take one barrier: warp partials go to one of two buffers in
 // turn, and every warp combines them itself.  A buffer is written again only

@@ -822,6 +822,8 @@ __host__ __device__ constexpr int hash_lg_c(int L) {
 // of at most LMAX entries and 2^B histogram bins.
 template <int LMAX, int B>
 struct RegWs {
+  static_assert(B >= 5, "tables are cleared in 16-byte stores");
+  static constexpr int kLmax = LMAX;
   static constexpr int kH = 1 << hash_lg_c(2 * LMAX);   // at least 4 slots per entry
   static constexpr size_t kCk = 0;                              // candidate keys
   static constexpr size_t kCtb = kCk + kCand * 8;               // candidate tie-breaks
@@ -832,6 +834,7 @@ struct RegWs {
   static constexpr size_t kHist = kHk + size_t(kH) * 4;         // radix histogram
   static constexpr size_t kHb = kHist + (size_t(1) << B) * 4;   // slot block bytes (see block_flags)
   static constexpr size_t kBytes = (kHb + size_t(kH) * 4 + 15) & ~size_t(15);
+  static_assert(kHk % 16 == 0 && kHist % 16 == 0 && kHb % 16 == 0, "16-byte aligned tables");
   char* base;
   __device__ __forceinline__ uint64_t* ck() const { return reinterpret_cast<uint64_t*>(base + kCk); }
   __device__ __forceinline__ uint64_t* ctb() const { return reinterpret_cast<uint64_t*>(base + kCtb); }
@@ -925,6 +928,10 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const TradeRows tr = trade_rows(c, t);
   const KeyCtx kc = key_ctx(c, t);
   const int du = tr.du, L = tr.du + tr.dv;
+  // the new rows' offsets, loaded now so their two dependent loads overlap
+  // the trade's work
+  const int64_t ou = c.rp_next[__ldg(c.M + 2 * t)];
+  const int64_t ov = tr.single ? 0 : c.rp_next[__ldg(c.M + 2 * t + 1)];
   // at least 4 hash slots per entry, and about one first-digit bin per entry
   const int lgH = max(5, 34 - __clz(max(L, 2) - 1));   // next power of two >= 4 L
   const int H = 1 << lgH;
@@ -932,11 +939,19 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const int NB0 = 1 << B0;
   const uint32_t t32 = static_cast<uint32_t>(t), T32 = static_cast<uint32_t>(c.T);
   const uint32_t t2u = 2u * t32;
-  for (int i = tm.rank; i < H; i += Team::N) {
-    w.hk()[i] = 0u;
-    w.hb()[i] = 0u;
+  {
+    // clear the tables in 16-byte stores (H and NB0 are powers of two >= 32;
+    // the layout keeps every table 16-byte aligned)
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    uint4* hk4 = reinterpret_cast<uint4*>(w.hk());
+    uint4* hb4 = reinterpret_cast<uint4*>(w.hb());
+    uint4* hs4 = reinterpret_cast<uint4*>(w.hist());
+    for (int i = tm.rank; i < (H >> 2); i += Team::N) {
+      hk4[i] = z;
+      hb4[i] = z;
+    }
+    for (int i = tm.rank; i < (NB0 >> 2); i += Team::N) hs4[i] = z;
   }
-  for (int i = tm.rank; i < NB0; i += Team::N) w.hist()[i] = 0u;
   if (tm.rank == 0) *w.ncand() = 0;
   tm.sync();
   // entries into the hash: presence bit (row, column) in the far trade's slot
@@ -969,9 +984,10 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
 #pragma unroll
     for (int j = 0; j < J; ++j)
       if ((mt[j] & kMValid) && !(mt[j] & kMUV)) pend |= 1u << j;
-    // a warp repeats the plain round (its barriers are cheap) until every
-    // entry is placed; a larger team runs one round, then compare-and-swap
-    constexpr bool kRounds = Team::N == 32;
+    // a warp or part of one repeats the plain round (its barriers are
+    // cheap) until every entry is placed; a larger team runs one round, then
+    // compare-and-swap
+    constexpr bool kRounds = Team::N <= 32;
     for (;;) {
 #pragma unroll
       for (int j = 0; j < J; ++j)
@@ -1223,8 +1239,6 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const int64_t pre = tm.exscan(static_cast<int64_t>(n0) | (static_cast<int64_t>(n1) << 32));
   int s0 = static_cast<int>(pre & 0xffffffff), s1 = static_cast<int>(pre >> 32);
   if (tm.rank == Team::N - 1 && (s0 + n0 != du || s1 + n1 != tr.dv)) latch(c.err, kErrRowLength);
-  const int64_t ou = c.rp_next[c.M[2 * t]];
-  const int64_t ov = tr.single ? 0 : c.rp_next[c.M[2 * t + 1]];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const uint32_t m = mt[j];
@@ -1281,6 +1295,31 @@ constexpr int kWarpJ = 4;                       // entries per lane: trades up t
 constexpr int kWarpB = 7;                       // first radix digit: 128 bins
 constexpr int kWarpWarps = 8;                   // warps per CTA
 using WarpWs = RegWs<32 * kWarpJ, kWarpB>;
+
+// The smallest trades (L <= W J, W = 8 or 16) on teams of W lanes: 32 / W
+// trades per warp, so the per-trade work (clearing the tables, scans,
+// reductions, the threshold search) takes one warp instruction for all of
+// them.
+template <int W>
+struct LaneCfg {
+  static constexpr int B = W == 8 ? 5 : 6;   // ~1 first-digit bin per entry
+  using Ws = RegWs<W * kWarpJ, B>;
+  static constexpr int kTeams = 32 * kWarpWarps / W;   // teams per CTA
+  static constexpr size_t kSmem = Ws::kBytes * kTeams;
+};
+template <int W>
+__global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_lanes(StepCtx c, const int32_t* __restrict__ lists,
+                                                                   const int64_t* __restrict__ ctr, int cls) {
+  using Cfg = LaneCfg<W>;
+  extern __shared__ __align__(16) char lsm[];
+  const int id = threadIdx.x / W;
+  const typename Cfg::Ws w{lsm + Cfg::Ws::kBytes * id};
+  LaneTeam<W> tm;
+  const ClassList cl = class_list(lists, ctr, cls);
+  const int64_t step = static_cast<int64_t>(gridDim.x) * Cfg::kTeams;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * Cfg::kTeams + id; q < cl.len; q += step)
+    phase_a_reg<LaneTeam<W>, kWarpJ, Cfg::B, true>(tm, c, cl.list[q], w);
+}
 
 __global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ lists,
                                                                   const int64_t* __restrict__ ctr, int cls) {
@@ -1358,8 +1397,8 @@ __global__ void __launch_bounds__(kClassThreads) k_class_count(StepCtx c, int64_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x < kClasses) we[threadIdx.x] = 0;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    int mine[kClasses] = {0, 0, 0, 0, 0, 0, 0};
-    unsigned ent[kClasses] = {0, 0, 0, 0, 0, 0, 0};
+    int mine[kClasses] = {};
+    unsigned ent[kClasses] = {};
     for (int j = 0; j < kClassPer; ++j) {
       const int64_t t = ch * kClassChunk + j * kClassThreads + threadIdx.x;
       int k = -1, L = 0;
@@ -1851,8 +1890,16 @@ int init_trade_kernels(Graph* h) {
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, kBigThreads>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(team_smem<kBigThreads, kBigThreads>())));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(LaneCfg<8>::kSmem)));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(LaneCfg<16>::kSmem)));
   // shared memory, not L1, limits how many CTAs of these kernels an SM holds
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
   return CB_OK;
 }
@@ -1920,12 +1967,16 @@ int super_step(Graph* h) {
     const int lreg = std::min(TeamCfg<kBigThreads>::kMax, h->smem_max);
     const int t3 = h->cta_paths ? std::max(tile_max, std::min(block_max, TeamCfg<256>::kMax)) : block_max;
     const int t5 = h->cta_paths ? std::max(t3, lreg) : t3;
-    th.th[0] = tile_max;
-    th.th[1] = h->cta_paths ? std::min(std::max(TeamCfg<64>::kMax, tile_max), t3) : tile_max;
-    th.th[2] = h->cta_paths ? std::min(std::max(TeamCfg<128>::kMax, th.th[1]), t3) : tile_max;
-    th.th[3] = t3;
-    th.th[4] = h->cta_paths ? std::min(std::max(TeamCfg<512>::kMax, t3), t5) : t3;
-    th.th[5] = t5;
+    // lane teams of 8 / 16 (L <= 32 / 64), a warp (L <= tile_max), teams of
+    // 64 .. 1024 threads, the 1024-thread shared-memory kernel
+    th.th[0] = h->lane_teams ? std::min(LaneCfg<8>::Ws::kLmax, tile_max) : 0;
+    th.th[1] = h->lane_teams ? std::min(LaneCfg<16>::Ws::kLmax, tile_max) : 0;
+    th.th[2] = tile_max;
+    th.th[3] = h->cta_paths ? std::min(std::max(TeamCfg<64>::kMax, tile_max), t3) : tile_max;
+    th.th[4] = h->cta_paths ? std::min(std::max(TeamCfg<128>::kMax, th.th[3]), t3) : tile_max;
+    th.th[5] = t3;
+    th.th[6] = h->cta_paths ? std::min(std::max(TeamCfg<512>::kMax, t3), t5) : t3;
+    th.th[7] = t5;
   }
   auto grid_n = [&](int64_t work) {
     return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, h->num_sms * 8)));
@@ -1971,37 +2022,45 @@ int super_step(Graph* h) {
     if (time_classes) CB_CUDA(h, cudaEventRecord(h->ev[4 + k], s));
     return CB_OK;
   };
+  const unsigned wgrid = static_cast<unsigned>(h->num_sms * 8);
   auto run_classes = [&]() -> int {
     int r;
     if ((r = mark(0))) return r;
-    k_phase_a_warp<<<static_cast<unsigned>(h->num_sms * 8), 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(
-        c, L, cnt, 0);
-    if ((r = launched()) || (r = mark(1))) return r;
-    if (h->cta_paths) {
-      k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 1);
+    if (h->lane_teams) {
+      k_phase_a_lanes<8><<<wgrid, 32 * kWarpWarps, LaneCfg<8>::kSmem, s>>>(c, L, cnt, 0);
+      if ((r = launched()) || (r = mark(1))) return r;
+      k_phase_a_lanes<16><<<wgrid, 32 * kWarpWarps, LaneCfg<16>::kSmem, s>>>(c, L, cnt, 1);
       if ((r = launched()) || (r = mark(2))) return r;
-      k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 2);
-      if ((r = launched()) || (r = mark(3))) return r;
-      k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 3);
+    } else if ((r = mark(1)) || (r = mark(2))) {
+      return r;
+    }
+    k_phase_a_warp<<<wgrid, 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(c, L, cnt, 2);
+    if ((r = launched()) || (r = mark(3))) return r;
+    if (h->cta_paths) {
+      k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 3);
       if ((r = launched()) || (r = mark(4))) return r;
-      k_phase_a_team<kBigThreads, 512><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt, 4);
+      k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 4);
       if ((r = launched()) || (r = mark(5))) return r;
-      k_phase_a_team<kBigThreads, kBigThreads><<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(
-          c, L, cnt, 5);
+      k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 5);
       if ((r = launched()) || (r = mark(6))) return r;
+      k_phase_a_team<kBigThreads, 512><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt, 6);
+      if ((r = launched()) || (r = mark(7))) return r;
+      k_phase_a_team<kBigThreads, kBigThreads><<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(
+          c, L, cnt, 7);
+      if ((r = launched()) || (r = mark(8))) return r;
     } else {
-      k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 3, block_max, gws, h->ws_slice,
+      k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 5, block_max, gws, h->ws_slice,
                                                                           block_max);
       if ((r = launched())) return r;
-      for (int k = 2; k <= 6; ++k)
+      for (int k = 4; k <= 8; ++k)
         if ((r = mark(k))) return r;
     }
     // the largest trades: 1024 threads, up to smem_max entries in shared
     // memory (staged by a bulk copy), a global-memory slice above
-    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 6, h->smem_max, gws, h->ws_slice,
+    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 8, h->smem_max, gws, h->ws_slice,
                                                                         h->smem_max);
     if ((r = launched())) return r;
-    return mark(7);
+    return mark(9);
   };
   // the first pass over every trade, then retry_passes parallel passes over
   // the deferred ones: each runs every deferred trade whose dependencies

@@ -140,6 +140,7 @@ def test_autotune_does_not_change_the_chain():
     assert got["block_max"] in (512, 1024, 2048, 128) or got["block_max"] >= got["tile_max"]
     assert got["smem_max"] in (2048, 4096, 8192)
     assert got["inorder_threads"] in (256, 1024)
+    assert got["retry_passes"] in (0, 1, 2, 4)
     assert tuned.step == 9
     tuned.set_option("cuda_graph", 1)
     tuned.global_trades(3)
@@ -148,6 +149,35 @@ def test_autotune_does_not_change_the_chain():
     o = Oracle(g.row_ptr, g.col, 5)
     o.superstep(12)
     assert np.array_equal(plain.edges(), o.edges())
+
+
+def test_autotune_cache_reuses_settings(tmp_path):
+    """The first handle tunes and stores its choice under its key; a second
+    handle of the same graph takes it from the file without running a super
+    step, and its chain still equals the oracle's."""
+    g = synth.powerlaw_graph(20000, 3, 2000, 2.0, 21)
+    path = str(tmp_path / "tune.json")
+    first = Curveball(g.row_ptr, g.col, 5)
+    key = first.tune_key()
+    assert key.split("|")[1].startswith("sm") and len(key.split("|")[-1].split(",")) == 33
+    got = first.autotune(20, cache_path=path)
+    assert got["steps"] == 20 and first.step == 20
+    with open(path) as f:
+        doc = json.load(f)
+    assert [e["key"] for e in doc["entries"]] == [key]
+    second = Curveball(g.row_ptr, g.col, 7)
+    assert second.tune_key() == key
+    again = second.autotune(20, cache_path=path)
+    assert again["steps"] == 0 and second.step == 0
+    for name in ("tile_max", "block_max", "smem_max", "inorder_threads", "retry_passes"):
+        assert again[name] == got[name], name
+    o = Oracle(g.row_ptr, g.col, 7)
+    second.global_trades(3)
+    o.superstep(3)
+    assert np.array_equal(second.edges(), o.edges())
+    # a batch of the same graphs has its own key (graph count)
+    ens = Ensemble([(g.row_ptr, g.col)] * 4, [1, 2, 3, 4])
+    assert ens.tune_key() != key
 
 
 def test_batch_rejects_out_of_range_local_ids():

@@ -14,7 +14,7 @@ import pytest
 
 from oracle import Oracle
 from paper_1804_08487_gb300 import synth
-from paper_1804_08487_gb300.cb import CB_EINVAL, CB_ESIZE, CbError, Curveball
+from paper_1804_08487_gb300.cb import CB_EINVAL, CB_ESIZE, TRADE_CLASSES, CbError, Curveball
 from tests import exact
 from tests.helpers import (canonical_from_csr, check_simple_canonical, csr_from_edges, degrees,
                            edge_hash)
@@ -113,6 +113,9 @@ CASES = [
     (3001, 3, 300, 2.0, 27, {"fix_passes": 3}),       # rebuild in three slices of the far trades
     (20000, 1, 3, 2.0, 28, {"fix_passes": 7}),
     (3001, 3, 300, 2.0, 29, {"fix_passes": 2, "wide_pack": 1}),
+    (3001, 2, 40, 2.0, 30, {"lane_teams": 0}),         # small trades on whole warps
+    (3001, 2, 40, 2.0, 31, {"tile_max": 48}),          # lane teams of 16 up to 48 entries, warps above
+    (3001, 2, 40, 2.0, 32, {"cand_max": 1}),           # lane teams: further radix digits
 ]
 
 
@@ -151,14 +154,15 @@ def test_stats_count_every_trade_and_entry():
         c.set_option("retry_passes", retry)
         c.global_trades(1)
         st = c.stats()
-        assert sum(st[f"class{k}_trades"] for k in range(7)) == (g.n + 1) // 2
-        assert sum(st[f"class{k}_entries"] for k in range(7)) == 2 * g.m
-        assert st["tile_trades"] == st["class0_trades"]
+        assert sum(st[f"class{k}_trades"] for k in range(TRADE_CLASSES)) == (g.n + 1) // 2
+        assert sum(st[f"class{k}_entries"] for k in range(TRADE_CLASSES)) == 2 * g.m
+        assert st["tile_trades"] == sum(st[f"class{k}_trades"] for k in range(3))
         assert st["tile_trades"] + st["block_trades"] == (g.n + 1) // 2
         assert 0 <= st["inorder_trades"] <= st["deferred"]
         assert 1 <= st["passes"] <= 2 + retry
         tm = c.timings()
-        assert tm["class0_ms"] > 0 and tm["class0_ms"] <= tm["threshold_ms"]
+        assert all(0 <= tm[f"class{k}_ms"] <= tm["threshold_ms"] for k in range(TRADE_CLASSES))
+        assert tm["class0_ms"] > 0
     big = synth.powerlaw_graph(400, 60, 300, 2.0, 5)
     c = Curveball(big.row_ptr, big.col, 9)
     c.set_option("retry_passes", 0)
