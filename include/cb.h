@@ -202,8 +202,9 @@ int cb_stats(cb_handle h, int64_t* out, int count);
  * passes that resolve dependent trades), ms[2] = the rebuild phase (new rows
  * for the next step), ms[3] = whole super steps, ms[4 + k], k < 9 = the
  * first threshold pass's kernel of size class k (0 where the class shares
- * another class's kernel).  Returns the number of values written
- * (<= count, at most 13).
+ * another class's kernel), ms[13] = the retry passes over deferred trades,
+ * ms[14] = the in-order pass.  Returns the number of values written
+ * (<= count, at most 15).
  */
 int cb_timings(cb_handle h, double* ms, int count);
 

@@ -424,7 +424,7 @@ _STAT_NAMES = (["passes", "deferred", "tile_trades", "block_trades", "global_ws_
                 "inorder_trades"] + [f"class{k}_trades" for k in range(TRADE_CLASSES)]
                + [f"class{k}_entries" for k in range(TRADE_CLASSES)])
 _TIMING_NAMES = (["permutation_ms", "threshold_ms", "rebuild_ms", "step_ms"]
-                 + [f"class{k}_ms" for k in range(TRADE_CLASSES)])
+                 + [f"class{k}_ms" for k in range(TRADE_CLASSES)] + ["retry_ms", "inorder_ms"])
 
 
 def cb_stats(h):

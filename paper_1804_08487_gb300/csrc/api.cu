@@ -805,7 +805,7 @@ int cb_stats(cb_handle h, int64_t* out, int count) {
 
 int cb_timings(cb_handle h, double* ms, int count) {
   if (!h || !ms || count < 0) return fail(h, CB_EINVAL, "bad argument");
-  const int k = std::min(count, 4 + kClasses);
+  const int k = std::min(count, kTimings);
   for (int i = 0; i < k; ++i) ms[i] = h->phase_ms[i];
   return k;
 }

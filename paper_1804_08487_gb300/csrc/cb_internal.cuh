@@ -45,6 +45,7 @@ constexpr int kCtrFirstEnt = 29;    // [29, 29 + kClasses): directed entries per
 constexpr int kCtrPassLeft = 40;    // [40, 40 + kRetryPassesMax + 1): trades left deferred after pass r
 constexpr int kRetryPassesMax = 4;
 constexpr int kStats = 7 + 2 * kClasses;   // counters cb_stats reports
+constexpr int kTimings = 6 + kClasses;     // values cb_timings reports
 constexpr int kCtrGws = kCounters - 1;   // trades whose workspace is in global memory
 constexpr int kMaxLcgGaps = 1024;   // p - n for the relaxed permutation (prime gaps below 2^31 are far smaller)
 
@@ -158,11 +159,11 @@ struct Graph {
   int64_t launches = 0;                    // kernel launches issued by this handle
   bool timing = false;                     // record CUDA events around the phases
   // events: [0..4) phase bounds, [4, 4 + kClasses + 1) bounds of the first
-  // pass's class kernels
-  cudaEvent_t ev[4 + kClasses + 1] = {};
-  // permutation+prep, thresholds, rebuild, whole step, then the first pass's
-  // kernel of each size class
-  double phase_ms[4 + kClasses] = {};
+  // pass's class kernels, then the end of the retry passes
+  cudaEvent_t ev[4 + kClasses + 2] = {};
+  // permutation+prep, thresholds, rebuild, whole step, the first pass's
+  // kernel of each size class, the retry passes, the in-order pass
+  double phase_ms[kTimings] = {};
   int latched = CB_OK;
   std::string last_error;
 };

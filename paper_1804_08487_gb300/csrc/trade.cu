@@ -2075,6 +2075,7 @@ int super_step(Graph* h) {
     c.def_count = ucnt + kCtrPassLeft + 1 + r;
     if ((rc = classify(1)) || (rc = run_classes())) return rc;
   }
+  if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[5 + kClasses], s));
   // last pass: the trades still deferred, in index order, waiting on
   // dependencies.  1024-thread CTAs keep large trades in shared memory;
   // 256-thread CTAs (four per SM) run many small deferred trades at once,
@@ -2145,6 +2146,11 @@ int super_step(Graph* h) {
       CB_CUDA(h, cudaEventElapsedTime(&e, h->ev[4 + k], h->ev[5 + k]));
       h->phase_ms[4 + k] += e;
     }
+    float re = 0, io = 0;
+    CB_CUDA(h, cudaEventElapsedTime(&re, h->ev[4 + kClasses], h->ev[5 + kClasses]));
+    CB_CUDA(h, cudaEventElapsedTime(&io, h->ev[5 + kClasses], h->ev[2]));
+    h->phase_ms[4 + kClasses] += re;
+    h->phase_ms[5 + kClasses] += io;
   }
   return finish_step(h);
 }

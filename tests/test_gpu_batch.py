@@ -161,7 +161,7 @@ def test_autotune_cache_reuses_settings(tmp_path):
     key = first.tune_key()
     assert key.split("|")[1].startswith("sm") and len(key.split("|")[-1].split(",")) == 33
     got = first.autotune(20, cache_path=path)
-    assert got["steps"] == 20 and first.step == 20
+    assert 0 < got["steps"] <= 20 and first.step == got["steps"]
     with open(path) as f:
         doc = json.load(f)
     assert [e["key"] for e in doc["entries"]] == [key]
