@@ -67,7 +67,7 @@ void release(Graph* h) {
   free_presence(h);
   void* bufs[] = {h->deg_id, h->rp_id, h->order[0], h->order[1], h->rp[0], h->rp[1], h->col[0], h->col[1],
                   h->pos_next, h->M, h->deg_next, h->stash, h->thr_key, h->thr_tb, h->thr_top, h->done,
-                  h->lists, h->Minv, h->cls_flag, h->cls_scan,
+                  h->lists, h->dlist, h->Minv, h->cls_flag, h->cls_scan,
                   h->counters, h->err,
                   h->ws_global, h->sort_ws, h->scan_ws, h->segs, h->seg_of, h->pairs, h->far_pack,
                   h->lcg_ab, h->lcg_gaps, h->swaps};
@@ -261,7 +261,7 @@ int finish_create(Graph* h) {
       dalloc(h, &h->stash, nnz) ||
       dalloc(h, &h->thr_key, h->ntasks) || dalloc(h, &h->thr_tb, h->ntasks) || dalloc(h, &h->done, h->ntasks) ||
       dalloc(h, &h->far_pack, h->ntasks) ||
-      dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->lists, h->ntasks) ||
+      dalloc(h, &h->thr_top, h->ntasks) || dalloc(h, &h->lists, h->ntasks) || dalloc(h, &h->dlist, 2 * h->ntasks) ||
       dalloc(h, &h->cls_flag, cls_flag_count(h->ntasks, nnz)) || dalloc(h, &h->cls_scan, cls_scan_count(h->ntasks)) ||
       dmalloc(h, &h->sort_ws, h->sort_ws_bytes) || dmalloc(h, &h->scan_ws, h->scan_ws_bytes))
     return fail(h, CB_ENOMEM, "device allocation failed");
@@ -434,7 +434,7 @@ int64_t estimate_handle_bytes(int64_t n, int64_t nnz, int64_t maxdeg, int num_sm
   int64_t b = 0;
   b += sizeof(Seg) + 8 * (n + 1) + 4 * n + 2 * 4 * (nnz + kColPad) + 32 + 8 * kCounters;   // cb_create
   b += 2 * 4 * n + 2 * 8 * (n + 1) + 4 * 4 * n + 2 * nnz;                                 // per node, side words
-  b += ntasks * (8 + 8 + 4 + 16 + 1 + 4) + 4 * cls_flag_count(ntasks, nnz) + 8 * cls_scan_count(ntasks) + 32;
+  b += ntasks * (8 + 8 + 4 + 16 + 1 + 4 + 8) + 4 * cls_flag_count(ntasks, nnz) + 8 * cls_scan_count(ntasks) + 32;
   b += static_cast<int64_t>(perm_ws_bytes(std::max<int64_t>(n, 1), nb) + scan_ws_bytes(std::max(n + 1, nb + 1)));
   const int64_t max_trade = 2 * maxdeg;
   if (max_trade > kBlockMaxDefault || maxdeg > 16384) {   // default block_max

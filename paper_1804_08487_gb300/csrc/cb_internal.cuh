@@ -32,7 +32,7 @@ constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kBlockMaxDefault = 1024;   // default of the "block_max" option
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
-constexpr int kCounters = 48;       // device counters per handle
+constexpr int kCounters = 64;       // device counters per handle
 // Trade size classes of the threshold phase (one team size each) and the
 // device counters of a super step.
 constexpr int kClasses = 9;
@@ -44,6 +44,8 @@ constexpr int kCtrFirstLen = 20;    // [20, 20 + kClasses): trades per class in 
 constexpr int kCtrFirstEnt = 29;    // [29, 29 + kClasses): directed entries per class in the first pass
 constexpr int kCtrPassLeft = 40;    // [40, 40 + kRetryPassesMax + 1): trades left deferred after pass r
 constexpr int kRetryPassesMax = 4;
+constexpr int kCtrListClaim = 48;   // [48, 48 + kRetryPassesMax + 1): list positions claimed by pass r + 1
+constexpr int kCtrListOk = 56;      // 1: the in-order pass runs on the sorted list of the last pass
 constexpr int kStats = 7 + 2 * kClasses;   // counters cb_stats reports
 constexpr int kTimings = 6 + kClasses;     // values cb_timings reports
 constexpr int kCtrGws = kCounters - 1;   // trades whose workspace is in global memory
@@ -107,6 +109,7 @@ struct Graph {
   uint32_t* done = nullptr;                // per trade: 1 once the threshold is published (cleared per step)
   int4* far_pack = nullptr;                // per trade: new positions of its nodes, threshold prefix (rebuild)
   int32_t* lists = nullptr;                // trades of every size class, class after class, index order within
+  int32_t* dlist = nullptr;                // 2 ntasks: the trades each pass deferred, for the next one
   int32_t* cls_flag = nullptr;             // scratch: per-chunk class counts, then the rebuild's chunk rows
   int64_t* cls_scan = nullptr;             // scratch: their exclusive scan
   int64_t* counters = nullptr;             // list lengths, deferred count, claims (kCounters)

@@ -75,6 +75,7 @@ struct StepCtx {
   const int32_t* M;
   const int64_t* rp_next;
   unsigned long long* def_count;   // trades this pass deferred
+  int32_t* def_list;               // where they go, at positions 0, 1, ... (null: not listed)
   uint32_t wait;                   // 0: defer a trade whose dependency is unpublished; 1: wait for it
   unsigned long long* gws_count;
   int cand_max;                    // register paths: most candidates ranked directly (else more radix digits)
@@ -129,6 +130,30 @@ __device__ __forceinline__ uint64_t globaltimer() {
 }
 __device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {
   return *reinterpret_cast<const volatile int32_t*>(p);
+}
+
+// A trade whose dependency has not published: marked, counted, and listed
+// for the next pass.
+__device__ __forceinline__ void defer_trade(const StepCtx& c, int64_t t) {
+  c.done[t] = kDeferred;
+  const unsigned long long i = atomicAdd(c.def_count, 1ull);
+  if (c.def_list) c.def_list[i] = static_cast<int32_t>(t);
+}
+
+// In-order passes: wait until trade s has published (true), at most wait_ns;
+// a wait that runs out latches kErrResolve, and after any error every wait
+// gives up at once (false).
+__device__ __noinline__ bool wait_published(const uint32_t* done_s, int32_t* err, uint32_t stamp, uint64_t wait_ns) {
+  const uint64_t t0 = globaltimer();
+  while (ld_acquire(done_s) != stamp) {
+    if (ld_volatile_i32(err) != 0) return false;
+    if (globaltimer() - t0 > wait_ns) {
+      latch(err, kErrResolve);
+      return false;
+    }
+    __nanosleep(128);
+  }
+  return true;
 }
 
 // ------------------------------------------------- bulk copies (TMA engine)
@@ -606,10 +631,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   const int64_t tot = tm.sum(static_cast<int64_t>(cnt_a) | (static_cast<int64_t>(defer) << 32) |
                              (static_cast<int64_t>(has_dependents) << 48));
   if ((tot >> 32) & 0xffff) {
-    if (tm.rank == 0) {
-      c.done[t] = kDeferred;
-      atomicAdd(c.def_count, 1ull);
-    }
+    if (tm.rank == 0) defer_trade(c, t);
     return;
   }
   const int a = static_cast<int>(tot & 0xffffffff);
@@ -987,14 +1009,19 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     // a warp or part of one repeats the plain round (its barriers are
     // cheap) until every entry is placed; a larger team runs one round, then
     // compare-and-swap
+    // (the first round's slots are all empty or written in this round, so
+    // its stores need no check).  An entry marks its edge in the slot's
+    // block word as soon as its slot is final.
     constexpr bool kRounds = Team::N <= 32;
+    bool first = true;
     for (;;) {
 #pragma unroll
       for (int j = 0; j < J; ++j)
         if ((pend >> j) & 1u) {
           const uint32_t sl = mt[j] & kMSlot;
-          if (w.hk()[sl] == 0u) w.hk()[sl] = (y[j] >> 1) + 1u;
+          if (first || w.hk()[sl] == 0u) w.hk()[sl] = (y[j] >> 1) + 1u;
         }
+      first = false;
       tm.sync();
       bool more = false;
 #pragma unroll
@@ -1002,22 +1029,21 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
         if ((pend >> j) & 1u) {
           const uint32_t sl = mt[j] & kMSlot;
           const uint32_t key = (y[j] >> 1) + 1u;
+          const int q = 2 * ((mt[j] & kMR) ? 1 : 0) + ((mt[j] & kMCol) ? 1 : 0);
           if (w.hk()[sl] == key) {
             pend &= ~(1u << j);
+            block_mark(w.hb(), sl, q, 1);
           } else if (kRounds) {
             mt[j] = (mt[j] & ~kMSlot) | ((sl + 1u) & static_cast<uint32_t>(H - 1));
             more = true;
           } else {   // lost the slot to another key: claim one further on
-            mt[j] = (mt[j] & ~kMSlot) | h_claim(w.hk(), static_cast<uint32_t>(H - 1), key, (sl + 1u) & (H - 1));
+            const uint32_t sl2 = h_claim(w.hk(), static_cast<uint32_t>(H - 1), key, (sl + 1u) & (H - 1));
+            mt[j] = (mt[j] & ~kMSlot) | sl2;
+            block_mark(w.hb(), sl2, q, 1);
           }
         }
       if (!kRounds || !tm.any(more)) break;
     }
-    tm.sync();
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-      if ((mt[j] & kMValid) && !(mt[j] & kMUV))
-        block_mark(w.hb(), mt[j] & kMSlot, 2 * ((mt[j] & kMR) ? 1 : 0) + ((mt[j] & kMCol) ? 1 : 0), 1);
   }
   tm.sync();
   // block analysis, keys, histogram of the first radix digit
@@ -1042,7 +1068,10 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
       int col_now = static_cast<int>(colb);
       other = r ? (col_now ? u1 : u0) : (col_now ? v1 : v0);
       if (!tr.single && s < t32 && (cu == 1 || cv == 1)) {
-        if (ld_acquire(c.done + s) != c.stamp) {   // first pass: leave it to the in-order pass
+        // unpublished: a parallel pass leaves the trade to a later pass,
+        // an in-order pass waits
+        if (ld_acquire(c.done + s) != c.stamp &&
+            !(c.wait && wait_published(c.done + s, c.err, c.stamp, c.wait_ns))) {
           defer = true;
           mt[j] = m;
           continue;
@@ -1073,10 +1102,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const int64_t tot = tm.sum(static_cast<int64_t>(cnt_a) | (static_cast<int64_t>(defer) << 20) |
                              (static_cast<int64_t>(has_dependents) << 32) | (static_cast<int64_t>(any_multi) << 44));
   if ((tot >> 20) & 0xfff) {
-    if (tm.rank == 0) {
-      c.done[t] = kDeferred;
-      atomicAdd(c.def_count, 1ull);
-    }
+    if (tm.rank == 0) defer_trade(c, t);
     tm.sync();
     return;
   }
@@ -1809,7 +1835,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
   }
 }
 
-// The trades the first pass deferred, in index order.  CTAs claim chunks of
+// The trades still deferred after the retry passes, in index order, found
+// by scanning every trade's done flag.  CTAs claim chunks of
 // trade indices in increasing order and run the deferred trades of a chunk one
 // after another; a trade waits for an unpublished dependency instead of
 // deferring.  A dependency s < t is either complete (first pass) or deferred
@@ -1817,16 +1844,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
 // claimed before t by a CTA that is already running.  By induction on the
 // index, the smallest unfinished claimed trade waits for nothing, so every
 // wait ends whatever the residency of the grid.
+// It runs when the deferred trades did not fit the sorted list (skip = the
+// list's flag, nonzero when k_phase_a_list runs them instead).
 template <int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_inorder(StepCtx c, int64_t ntasks, int64_t chunk,
                                                         unsigned long long* claim, int smem_max, char* gws,
-                                                        size_t slice) {
+                                                        size_t slice, const int64_t* skip) {
   extern __shared__ __align__(16) char sbuf[];
   __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ SelOut sel;
   __shared__ int64_t first;
   __shared__ int32_t found[NT];
   __shared__ int nfound;
+  if (*reinterpret_cast<const volatile int64_t*>(skip)) return;
   BlockTeam<NT> tm(red);
   for (;;) {
     if (threadIdx.x == 0) first = static_cast<int64_t>(atomicAdd(claim, 1ull)) * chunk;
@@ -1857,6 +1887,73 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_inorder(StepC
       __syncthreads();
     }
   }
+}
+
+// The retry passes and, when the list could be sorted, the in-order pass,
+// over an explicit list of deferred trades: list[0 .. *count).  CTAs claim
+// positions one at a time.  A retry pass (c.wait = 0) defers a trade again
+// whose dependency has not published, into the next pass's list.  The
+// in-order pass (c.wait = 1, list sorted by trade index, launched only when
+// *ok) waits instead: a dependency s < t is complete or deferred, and then
+// it sits earlier in the list, claimed before t by a running CTA, so by
+// induction every wait ends.  Trades of at most 4 NT entries run on the
+// register path, larger ones on the shared-memory path (a global slice
+// above gen_max entries).
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_list(StepCtx c, const int32_t* __restrict__ list,
+                                                                     const unsigned long long* count, const int64_t* ok,
+                                                                     unsigned long long* claim, int gen_max, char* gws,
+                                                                     size_t slice) {
+  using Ws = typename TeamCfg<NT>::Ws;
+  extern __shared__ __align__(16) char sbuf[];
+  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
+  __shared__ SelOut sel;
+  __shared__ int64_t pick;
+  if (ok && *reinterpret_cast<const volatile int64_t*>(ok) == 0) return;
+  const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
+  BlockTeam<NT> tm(red);
+  for (;;) {
+    if (threadIdx.x == 0) pick = static_cast<int64_t>(atomicAdd(claim, 1ull));
+    __syncthreads();
+    const int64_t p = pick;
+    __syncthreads();
+    if (p >= nl) return;
+    const int64_t t = __ldcg(list + p);
+    const TradeRows tr = trade_rows(c, t);
+    const int L = tr.du + tr.dv;
+    if (L <= Ws::kLmax) {
+      phase_a_reg<BlockTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, t, Ws{sbuf});
+    } else {
+      char* wsb = sbuf;
+      if (L > gen_max) {
+        wsb = gws + slice * blockIdx.x;
+        if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
+      }
+      phase_a(tm, c, t, carve_a(wsb, L), &sel);
+    }
+    __syncthreads();
+  }
+}
+
+// The last pass's list of deferred trades sorted by index in one CTA, when
+// it holds at most kSortListMax trades (*ok = 1); otherwise *ok = 0 and the
+// in-order pass scans the done flags instead.
+constexpr int kSortListMax = 4096;
+__global__ void __launch_bounds__(1024) k_sort_list(int32_t* list, const unsigned long long* count, int64_t* ok) {
+  __shared__ int32_t a[kSortListMax];
+  __shared__ int64_t red[BlockTeam<1024>::kRedSlots];
+  const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
+  if (nl > kSortListMax) {
+    if (threadIdx.x == 0) *ok = 0;
+    return;
+  }
+  const int P = nl > 1 ? next_pow2(static_cast<int>(nl)) : 1;
+  for (int i = threadIdx.x; i < P; i += 1024) a[i] = i < nl ? list[i] : 0x7fffffff;
+  __syncthreads();
+  BlockTeam<1024> tm(red);
+  team_bitonic_sort(tm, a, P);
+  for (int i = threadIdx.x; i < nl; i += 1024) list[i] = a[i];
+  if (threadIdx.x == 0) *ok = 1;
 }
 
 // End of a super step: every graph's step counter moves on.
@@ -1890,6 +1987,12 @@ int init_trade_kernels(Graph* h) {
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, kBigThreads>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(team_smem<kBigThreads, kBigThreads>())));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_list<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(std::max(TeamCfg<kMedThreads>::Ws::kBytes,
+                                                            ws_a_bytes(kBlockMaxCap)))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_list<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(std::max(TeamCfg<kBigThreads>::Ws::kBytes,
+                                                            ws_a_bytes(kSmemMaxCap)))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(LaneCfg<8>::kSmem)));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2064,36 +2167,63 @@ int super_step(Graph* h) {
   };
   // the first pass over every trade, then retry_passes parallel passes over
   // the deferred ones: each runs every deferred trade whose dependencies
-  // have published by then (a trade the previous pass completed leaves the
-  // list), so chains of dependent trades shrink by a level per pass.  Pass
-  // r counts its deferrals in ctr[kCtrPassLeft + r].
+  // have published by then, so chains of dependent trades shrink by a level
+  // per pass.  Pass r counts its deferrals in ctr[kCtrPassLeft + r] and lists
+  // them in dlist[r & 1] for pass r + 1.
   time_classes = h->timing;
   c.def_count = ucnt + kCtrPassLeft;
+  c.def_list = h->dlist;
   if ((rc = classify(0)) || (rc = run_classes())) return rc;
   time_classes = false;
+  const unsigned lgrid = static_cast<unsigned>(gws ? std::min(h->num_sms * 4, h->ws_ctas) : h->num_sms * 4);
+  const size_t list_smem = std::max(TeamCfg<kMedThreads>::Ws::kBytes, ws_a_bytes(std::max(block_max, 1)));
+  const size_t list_smem_big = std::max(TeamCfg<kBigThreads>::Ws::kBytes, ws_a_bytes(std::max(h->smem_max, 1)));
   for (int r = 0; r < h->retry_passes; ++r) {
+    const int32_t* in = h->dlist + (r & 1) * ntasks;
     c.def_count = ucnt + kCtrPassLeft + 1 + r;
-    if ((rc = classify(1)) || (rc = run_classes())) return rc;
+    c.def_list = h->dlist + ((r + 1) & 1) * ntasks;
+    k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, in, ucnt + kCtrPassLeft + r, nullptr,
+                                                                     ucnt + kCtrListClaim + r, block_max, gws,
+                                                                     h->ws_slice);
+    CB_CUDA(h, cudaGetLastError());
+    ++h->launches;
   }
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[5 + kClasses], s));
   // last pass: the trades still deferred, in index order, waiting on
-  // dependencies.  1024-thread CTAs keep large trades in shared memory;
-  // 256-thread CTAs (four per SM) run many small deferred trades at once,
-  // large ones from a global slice.
-  c.wait = 1;
-  if (h->inorder_threads == kBigThreads) {
-    const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
-    k_phase_a_inorder<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims, h->smem_max, gws,
-                                                                       h->ws_slice);
+  // dependencies: over the last list sorted by index when it is short,
+  // else by scanning every trade's done flag.  1024-thread CTAs keep large
+  // trades in shared memory; 256-thread CTAs (four per SM) run many small
+  // deferred trades at once, large ones from a global slice.
+  {
+    const int R = h->retry_passes;
+    int32_t* last = h->dlist + (R & 1) * ntasks;
+    const unsigned long long* nlast = ucnt + kCtrPassLeft + R;
+    int64_t* ok = cnt + kCtrListOk;
+    k_sort_list<<<1, 1024, 0, s>>>(last, nlast, ok);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
-  } else {
-    const unsigned igrid = static_cast<unsigned>(gws ? std::min(h->num_sms * 4, h->ws_ctas) : h->num_sms * 4);
-    const int64_t chunk = std::max<int64_t>(512, (ntasks + int64_t(igrid) * 4 - 1) / (int64_t(igrid) * 4));
-    k_phase_a_inorder<kMedThreads><<<igrid, kMedThreads, med_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims, block_max, gws,
+    c.wait = 1;
+    c.def_count = ucnt + kCtrPassLeft + R + 1;   // a wait that ran out leaves its trade deferred
+    c.def_list = nullptr;
+    unsigned long long* lclaim = ucnt + kCtrListClaim + R;
+    if (h->inorder_threads == kBigThreads) {
+      k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(c, last, nlast, ok, lclaim, h->smem_max,
+                                                                           gws, h->ws_slice);
+      CB_CUDA(h, cudaGetLastError());
+      const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
+      k_phase_a_inorder<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims,
+                                                                         h->smem_max, gws, h->ws_slice, ok);
+      CB_CUDA(h, cudaGetLastError());
+    } else {
+      k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, last, nlast, ok, lclaim, block_max, gws,
                                                                        h->ws_slice);
-    CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
+      CB_CUDA(h, cudaGetLastError());
+      const int64_t chunk = std::max<int64_t>(512, (ntasks + int64_t(lgrid) * 4 - 1) / (int64_t(lgrid) * 4));
+      k_phase_a_inorder<kMedThreads><<<lgrid, kMedThreads, med_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims,
+                                                                         block_max, gws, h->ws_slice, ok);
+      CB_CUDA(h, cudaGetLastError());
+    }
+    h->launches += 2;
   }
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
   // rebuild: far-trade records, each chunk's first row, then the fix-up in
