@@ -42,10 +42,11 @@ constexpr int kCtrClsStart = 10;    // [10, 10 + kClasses): first entry of each 
 constexpr int kCtrClaims = 19;      // chunks claimed by the in-order pass
 constexpr int kCtrFirstLen = 20;    // [20, 20 + kClasses): trades per class in the first pass
 constexpr int kCtrFirstEnt = 29;    // [29, 29 + kClasses): directed entries per class in the first pass
-constexpr int kCtrPassLeft = 40;    // [40, 40 + kRetryPassesMax + 1): trades left deferred after pass r
+constexpr int kCtrPassLeft = 40;    // [40, 40 + kRetryPassesMax + 2): trades left deferred after pass r
 constexpr int kRetryPassesMax = 4;
-constexpr int kCtrListClaim = 48;   // [48, 48 + kRetryPassesMax + 1): list positions claimed by pass r + 1
-constexpr int kCtrListOk = 56;      // 1: the in-order pass runs on the sorted list of the last pass
+static_assert(40 + kRetryPassesMax + 2 <= 46 && 46 + 3 * kRetryPassesMax < 59, "counter layout");
+constexpr int kCtrListClaim = 46;   // [46, 46 + 3 kRetryPassesMax]: list positions claimed by the passes' kernels
+constexpr int kCtrListOk = 59;      // 1: the in-order pass runs on the sorted list of the last pass
 constexpr int kStats = 7 + 2 * kClasses;   // counters cb_stats reports
 constexpr int kTimings = 6 + kClasses;     // values cb_timings reports
 constexpr int kCtrGws = kCounters - 1;   // trades whose workspace is in global memory

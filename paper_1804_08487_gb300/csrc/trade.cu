@@ -1891,19 +1891,21 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_inorder(StepC
 
 // The retry passes and, when the list could be sorted, the in-order pass,
 // over an explicit list of deferred trades: list[0 .. *count).  CTAs claim
-// positions one at a time.  A retry pass (c.wait = 0) defers a trade again
-// whose dependency has not published, into the next pass's list.  The
-// in-order pass (c.wait = 1, list sorted by trade index, launched only when
-// *ok) waits instead: a dependency s < t is complete or deferred, and then
-// it sits earlier in the list, claimed before t by a running CTA, so by
-// induction every wait ends.  Trades of at most 4 NT entries run on the
-// register path, larger ones on the shared-memory path (a global slice
-// above gen_max entries).
+// positions one at a time and run the trades of L = deg u + deg v in
+// [lmin, lmax], skipping the others.  A retry pass (c.wait = 0) defers a
+// trade again whose dependency has not published, into the next pass's list.
+// The in-order pass (c.wait = 1, list sorted by trade index, launched only
+// when *ok, all sizes) waits instead: a dependency s < t is complete or
+// deferred, and then it sits earlier in the list, claimed before t by a
+// running CTA, so by induction every wait ends.  Trades of at most 32 kWarpJ
+// entries run on the CTA's first warp, up to 4 NT on the register path of
+// the whole CTA, larger ones on the shared-memory path (a global slice above
+// gen_max entries).
 template <int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_list(StepCtx c, const int32_t* __restrict__ list,
                                                                      const unsigned long long* count, const int64_t* ok,
-                                                                     unsigned long long* claim, int gen_max, char* gws,
-                                                                     size_t slice) {
+                                                                     unsigned long long* claim, int lmin, int lmax,
+                                                                     int gen_max, char* gws, size_t slice) {
   using Ws = typename TeamCfg<NT>::Ws;
   extern __shared__ __align__(16) char sbuf[];
   __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
@@ -1921,7 +1923,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_list(StepCtx 
     const int64_t t = __ldcg(list + p);
     const TradeRows tr = trade_rows(c, t);
     const int L = tr.du + tr.dv;
-    if (L <= Ws::kLmax) {
+    if (L < lmin || L > lmax) continue;
+    if (L <= WarpWs::kLmax) {
+      if (threadIdx.x < 32) {
+        WarpTeam wt;
+        phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(wt, c, t, WarpWs{sbuf});
+      }
+    } else if (L <= Ws::kLmax) {
       phase_a_reg<BlockTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, t, Ws{sbuf});
     } else {
       char* wsb = sbuf;
@@ -1932,6 +1940,28 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_list(StepCtx 
       phase_a(tm, c, t, carve_a(wsb, L), &sel);
     }
     __syncthreads();
+  }
+}
+
+// A retry pass's small trades (L <= 32 kWarpJ): every warp claims list
+// positions on its own.
+__global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_list_warp(StepCtx c, const int32_t* __restrict__ list,
+                                                                       const unsigned long long* count,
+                                                                       unsigned long long* claim) {
+  extern __shared__ __align__(16) char wsm[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WarpWs w{wsm + WarpWs::kBytes * wid};
+  WarpTeam tm;
+  const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
+  for (;;) {
+    int64_t p = 0;
+    if (lane == 0) p = static_cast<int64_t>(atomicAdd(claim, 1ull));
+    p = static_cast<int64_t>(tm.bcast(static_cast<uint64_t>(p), 0));
+    if (p >= nl) return;
+    const int64_t t = __ldcg(list + p);
+    const TradeRows tr = trade_rows(c, t);
+    if (tr.du + tr.dv > WarpWs::kLmax) continue;
+    phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, t, w);
   }
 }
 
@@ -2179,14 +2209,26 @@ int super_step(Graph* h) {
   const size_t list_smem = std::max(TeamCfg<kMedThreads>::Ws::kBytes, ws_a_bytes(std::max(block_max, 1)));
   const size_t list_smem_big = std::max(TeamCfg<kBigThreads>::Ws::kBytes, ws_a_bytes(std::max(h->smem_max, 1)));
   for (int r = 0; r < h->retry_passes; ++r) {
+    // small trades on warps, medium on 256-thread CTAs, the largest on
+    // 1024-thread CTAs (shared memory up to smem_max entries)
     const int32_t* in = h->dlist + (r & 1) * ntasks;
+    const unsigned long long* nin = ucnt + kCtrPassLeft + r;
     c.def_count = ucnt + kCtrPassLeft + 1 + r;
     c.def_list = h->dlist + ((r + 1) & 1) * ntasks;
-    k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, in, ucnt + kCtrPassLeft + r, nullptr,
-                                                                     ucnt + kCtrListClaim + r, block_max, gws,
-                                                                     h->ws_slice);
+    k_phase_a_list_warp<<<wgrid, 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(c, in, nin,
+                                                                                  ucnt + kCtrListClaim + 3 * r);
     CB_CUDA(h, cudaGetLastError());
-    ++h->launches;
+    k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, in, nin, nullptr,
+                                                                     ucnt + kCtrListClaim + 3 * r + 1,
+                                                                     WarpWs::kLmax + 1, TeamCfg<kMedThreads>::kMax,
+                                                                     block_max, gws, h->ws_slice);
+    CB_CUDA(h, cudaGetLastError());
+    k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(c, in, nin, nullptr,
+                                                                         ucnt + kCtrListClaim + 3 * r + 2,
+                                                                         TeamCfg<kMedThreads>::kMax + 1, 0x7fffffff,
+                                                                         h->smem_max, gws, h->ws_slice);
+    CB_CUDA(h, cudaGetLastError());
+    h->launches += 3;
   }
   if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[5 + kClasses], s));
   // last pass: the trades still deferred, in index order, waiting on
@@ -2205,18 +2247,18 @@ int super_step(Graph* h) {
     c.wait = 1;
     c.def_count = ucnt + kCtrPassLeft + R + 1;   // a wait that ran out leaves its trade deferred
     c.def_list = nullptr;
-    unsigned long long* lclaim = ucnt + kCtrListClaim + R;
+    unsigned long long* lclaim = ucnt + kCtrListClaim + 3 * kRetryPassesMax;
     if (h->inorder_threads == kBigThreads) {
-      k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(c, last, nlast, ok, lclaim, h->smem_max,
-                                                                           gws, h->ws_slice);
+      k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(c, last, nlast, ok, lclaim, 0, 0x7fffffff,
+                                                                           h->smem_max, gws, h->ws_slice);
       CB_CUDA(h, cudaGetLastError());
       const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
       k_phase_a_inorder<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims,
                                                                          h->smem_max, gws, h->ws_slice, ok);
       CB_CUDA(h, cudaGetLastError());
     } else {
-      k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, last, nlast, ok, lclaim, block_max, gws,
-                                                                       h->ws_slice);
+      k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, last, nlast, ok, lclaim, 0, 0x7fffffff,
+                                                                       block_max, gws, h->ws_slice);
       CB_CUDA(h, cudaGetLastError());
       const int64_t chunk = std::max<int64_t>(512, (ntasks + int64_t(lgrid) * 4 - 1) / (int64_t(lgrid) * 4));
       k_phase_a_inorder<kMedThreads><<<lgrid, kMedThreads, med_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims,
