@@ -1911,35 +1911,59 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_list(StepCtx 
   __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ SelOut sel;
   __shared__ int64_t pick;
+  __shared__ int32_t found[NT];
+  __shared__ int nfound;
   if (ok && *reinterpret_cast<const volatile int64_t*>(ok) == 0) return;
   const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
   BlockTeam<NT> tm(red);
+  // the in-order pass claims one position at a time (the order of the
+  // claims is what makes its waits end); a retry pass claims NT at once and
+  // keeps the trades of its size range
+  const bool ordered = ok != nullptr;
   for (;;) {
-    if (threadIdx.x == 0) pick = static_cast<int64_t>(atomicAdd(claim, 1ull));
+    if (threadIdx.x == 0) pick = static_cast<int64_t>(atomicAdd(claim, ordered ? 1ull : static_cast<unsigned long long>(NT)));
     __syncthreads();
-    const int64_t p = pick;
+    const int64_t base = pick;
     __syncthreads();
-    if (p >= nl) return;
-    const int64_t t = __ldcg(list + p);
-    const TradeRows tr = trade_rows(c, t);
-    const int L = tr.du + tr.dv;
-    if (L < lmin || L > lmax) continue;
-    if (L <= WarpWs::kLmax) {
-      if (threadIdx.x < 32) {
-        WarpTeam wt;
-        phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(wt, c, t, WarpWs{sbuf});
+    if (base >= nl) return;
+    int nf = 1;
+    if (!ordered) {
+      const int64_t p = base + threadIdx.x;
+      int32_t t = -1;
+      if (p < nl) {
+        t = __ldcg(list + p);
+        const TradeRows tr = trade_rows(c, t);
+        const int L = tr.du + tr.dv;
+        if (L < lmin || L > lmax) t = -1;
       }
-    } else if (L <= Ws::kLmax) {
-      phase_a_reg<BlockTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, t, Ws{sbuf});
-    } else {
-      char* wsb = sbuf;
-      if (L > gen_max) {
-        wsb = gws + slice * blockIdx.x;
-        if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
-      }
-      phase_a(tm, c, t, carve_a(wsb, L), &sel);
+      const int mine = t >= 0 ? 1 : 0;
+      const int before = static_cast<int>(tm.exscan(mine));
+      if (mine) found[before] = t;
+      if (threadIdx.x == NT - 1) nfound = before + mine;
+      __syncthreads();
+      nf = nfound;
     }
-    __syncthreads();
+    for (int q = 0; q < nf; ++q) {
+      const int64_t t = ordered ? __ldcg(list + base) : found[q];
+      const TradeRows tr = trade_rows(c, t);
+      const int L = tr.du + tr.dv;
+      if (L <= WarpWs::kLmax) {
+        if (threadIdx.x < 32) {
+          WarpTeam wt;
+          phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(wt, c, t, WarpWs{sbuf});
+        }
+      } else if (L <= Ws::kLmax) {
+        phase_a_reg<BlockTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, t, Ws{sbuf});
+      } else {
+        char* wsb = sbuf;
+        if (L > gen_max) {
+          wsb = gws + slice * blockIdx.x;
+          if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
+        }
+        phase_a(tm, c, t, carve_a(wsb, L), &sel);
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -1954,14 +1978,23 @@ __global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_list_warp(StepCt
   WarpTeam tm;
   const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
   for (;;) {
-    int64_t p = 0;
-    if (lane == 0) p = static_cast<int64_t>(atomicAdd(claim, 1ull));
-    p = static_cast<int64_t>(tm.bcast(static_cast<uint64_t>(p), 0));
-    if (p >= nl) return;
-    const int64_t t = __ldcg(list + p);
-    const TradeRows tr = trade_rows(c, t);
-    if (tr.du + tr.dv > WarpWs::kLmax) continue;
-    phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, t, w);
+    // 32 positions per claim; the small trades among them run one by one
+    int64_t base = 0;
+    if (lane == 0) base = static_cast<int64_t>(atomicAdd(claim, 32ull));
+    base = static_cast<int64_t>(tm.bcast(static_cast<uint64_t>(base), 0));
+    if (base >= nl) return;
+    int32_t t = -1;
+    if (base + lane < nl) {
+      t = __ldcg(list + base + lane);
+      const TradeRows tr = trade_rows(c, t);
+      if (tr.du + tr.dv > WarpWs::kLmax) t = -1;
+    }
+    unsigned todo = __ballot_sync(kFull, t >= 0);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, __shfl_sync(kFull, t, src), w);
+    }
   }
 }
 
