@@ -238,6 +238,9 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               index order: 1024 (large trades in shared memory) or 256
  *               (four CTAs per SM; trades above block_max from global
  *               memory) [1024; 256 for cb_create_batch].
+ *   "uniform_threads" CTA size of the executor of cb_uniform_trades: 256
+ *               (two CTAs per SM), 512 or 1024 (more threads per hub trade,
+ *               fewer trades at once) [256].
  *   "lane_teams" 1: trades of at most 32 / 64 entries run on teams of 8 /
  *               16 lanes, several per warp; 0: on whole warps [1].
  *   "retry_passes" parallel passes over the deferred trades between the

@@ -879,6 +879,11 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     h->timing = value != 0;
     return CB_OK;
   }
+  if (!std::strcmp(key, "uniform_threads")) {
+    if (value != 256 && value != 512 && value != 1024) return fail(h, CB_EINVAL, "uniform_threads is 256, 512 or 1024");
+    h->uni_threads = static_cast<int>(value);
+    return CB_OK;
+  }
   if (!std::strcmp(key, "lane_teams")) {
     if (value < 0 || value > 1) return fail(h, CB_EINVAL, "lane_teams is 0 or 1");
     h->lane_teams = static_cast<int>(value);

@@ -32,7 +32,7 @@ constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kBlockMaxDefault = 1024;   // default of the "block_max" option
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
 constexpr int kBlockThreads = 256;  // CTA size of the block path
-constexpr int kCounters = 64;       // device counters per handle
+constexpr int kCounters = 96;       // device counters per handle
 // Trade size classes of the threshold phase (one team size each) and the
 // device counters of a super step.
 constexpr int kClasses = 9;
@@ -44,9 +44,12 @@ constexpr int kCtrFirstLen = 20;    // [20, 20 + kClasses): trades per class in 
 constexpr int kCtrFirstEnt = 29;    // [29, 29 + kClasses): directed entries per class in the first pass
 constexpr int kCtrPassLeft = 40;    // [40, 40 + kRetryPassesMax + 2): trades left deferred after pass r
 constexpr int kRetryPassesMax = 4;
-static_assert(40 + kRetryPassesMax + 2 <= 46 && 46 + 3 * kRetryPassesMax < 59, "counter layout");
-constexpr int kCtrListClaim = 46;   // [46, 46 + 3 kRetryPassesMax]: list positions claimed by the passes' kernels
-constexpr int kCtrListOk = 59;      // 1: the in-order pass runs on the sorted list of the last pass
+constexpr int kCtrPassSmall = 48;   // [48, 54): of those, the small ones (listed from the front of the list)
+constexpr int kCtrPassBig = 56;     // [56, 62): the others (listed from the back)
+constexpr int kCtrListClaim = 64;   // [64, 64 + 3 kRetryPassesMax]: list positions claimed by the passes' kernels
+constexpr int kCtrListOk = 80;      // 1: the in-order pass runs on the sorted list of the last pass
+constexpr int kCtrListN = 81;       // the sorted list's length
+static_assert(40 + kRetryPassesMax + 2 <= 48 && 64 + 3 * kRetryPassesMax < 80, "counter layout");
 constexpr int kStats = 7 + 2 * kClasses;   // counters cb_stats reports
 constexpr int kTimings = 6 + kClasses;     // values cb_timings reports
 constexpr int kCtrGws = kCounters - 1;   // trades whose workspace is in global memory
@@ -142,6 +145,7 @@ struct Graph {
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
   int retry_passes = 2;         // parallel passes over the deferred trades before the in-order pass
   int lane_teams = 1;           // trades up to 32 / 64 entries on teams of 8 / 16 lanes
+  int uni_threads = 256;        // CTA size of the uniform-trade executor (256, 512 or 1024)
   bool wide_pack = false;       // 16-byte far-trade records even when 8 bytes would do (tests)
   // relaxed global trade: permutations from h(x) = (a x + b) mod p
   bool relaxed = false;

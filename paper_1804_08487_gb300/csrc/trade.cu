@@ -75,7 +75,10 @@ struct StepCtx {
   const int32_t* M;
   const int64_t* rp_next;
   unsigned long long* def_count;   // trades this pass deferred
-  int32_t* def_list;               // where they go, at positions 0, 1, ... (null: not listed)
+  int32_t* def_list;               // where they go (null: not listed): trades of at most kListSmall
+  unsigned long long* def_small;   // entries from position 0 up, the others from def_cap - 1 down,
+  unsigned long long* def_big;     // counted here
+  int64_t def_cap;
   uint32_t wait;                   // 0: defer a trade whose dependency is unpublished; 1: wait for it
   unsigned long long* gws_count;
   int cand_max;                    // register paths: most candidates ranked directly (else more radix digits)
@@ -133,11 +136,18 @@ __device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {
 }
 
 // A trade whose dependency has not published: marked, counted, and listed
-// for the next pass.
-__device__ __forceinline__ void defer_trade(const StepCtx& c, int64_t t) {
+// for the next pass, small trades (L <= kListSmall, run on warps) apart from
+// the others.
+constexpr int kListSmall = 128;
+__device__ __forceinline__ void defer_trade(const StepCtx& c, int64_t t, int L) {
   c.done[t] = kDeferred;
-  const unsigned long long i = atomicAdd(c.def_count, 1ull);
-  if (c.def_list) c.def_list[i] = static_cast<int32_t>(t);
+  atomicAdd(c.def_count, 1ull);
+  if (!c.def_list) return;
+  if (L <= kListSmall) {
+    c.def_list[atomicAdd(c.def_small, 1ull)] = static_cast<int32_t>(t);
+  } else {
+    c.def_list[c.def_cap - 1 - static_cast<int64_t>(atomicAdd(c.def_big, 1ull))] = static_cast<int32_t>(t);
+  }
 }
 
 // In-order passes: wait until trade s has published (true), at most wait_ns;
@@ -631,7 +641,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
   const int64_t tot = tm.sum(static_cast<int64_t>(cnt_a) | (static_cast<int64_t>(defer) << 32) |
                              (static_cast<int64_t>(has_dependents) << 48));
   if ((tot >> 32) & 0xffff) {
-    if (tm.rank == 0) defer_trade(c, t);
+    if (tm.rank == 0) defer_trade(c, t, L);
     return;
   }
   const int a = static_cast<int>(tot & 0xffffffff);
@@ -1102,7 +1112,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const int64_t tot = tm.sum(static_cast<int64_t>(cnt_a) | (static_cast<int64_t>(defer) << 20) |
                              (static_cast<int64_t>(has_dependents) << 32) | (static_cast<int64_t>(any_multi) << 44));
   if ((tot >> 20) & 0xfff) {
-    if (tm.rank == 0) defer_trade(c, t);
+    if (tm.rank == 0) defer_trade(c, t, L);
     tm.sync();
     return;
   }
@@ -1890,85 +1900,62 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_inorder(StepC
 }
 
 // The retry passes and, when the list could be sorted, the in-order pass,
-// over an explicit list of deferred trades: list[0 .. *count).  CTAs claim
-// positions one at a time and run the trades of L = deg u + deg v in
-// [lmin, lmax], skipping the others.  A retry pass (c.wait = 0) defers a
-// trade again whose dependency has not published, into the next pass's list.
-// The in-order pass (c.wait = 1, list sorted by trade index, launched only
-// when *ok, all sizes) waits instead: a dependency s < t is complete or
-// deferred, and then it sits earlier in the list, claimed before t by a
-// running CTA, so by induction every wait ends.  Trades of at most 32 kWarpJ
-// entries run on the CTA's first warp, up to 4 NT on the register path of
-// the whole CTA, larger ones on the shared-memory path (a global slice above
-// gen_max entries).
+// over explicit lists of deferred trades.  CTAs claim positions one at a
+// time (list[p], or list[-1 - p] when from_back, for p < *count) and run the
+// trades of L = deg u + deg v in [lmin, lmax], skipping the others.  A retry
+// pass (c.wait = 0) defers a trade again whose dependency has not published,
+// into the next pass's list.  The in-order pass (c.wait = 1, one list sorted
+// by trade index, launched only when *ok, all sizes) waits instead: a
+// dependency s < t is complete or deferred, and then it sits earlier in the
+// list, claimed before t by a running CTA, so by induction every wait ends.
+// Trades of at most 32 kWarpJ entries run on the CTA's first warp, up to
+// 4 NT on the register path of the whole CTA, larger ones on the
+// shared-memory path (a global slice above gen_max entries).
 template <int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_list(StepCtx c, const int32_t* __restrict__ list,
-                                                                     const unsigned long long* count, const int64_t* ok,
-                                                                     unsigned long long* claim, int lmin, int lmax,
-                                                                     int gen_max, char* gws, size_t slice) {
+                                                                     int from_back, const unsigned long long* count,
+                                                                     const int64_t* ok, unsigned long long* claim,
+                                                                     int lmin, int lmax, int gen_max, char* gws,
+                                                                     size_t slice) {
   using Ws = typename TeamCfg<NT>::Ws;
   extern __shared__ __align__(16) char sbuf[];
   __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ SelOut sel;
   __shared__ int64_t pick;
-  __shared__ int32_t found[NT];
-  __shared__ int nfound;
   if (ok && *reinterpret_cast<const volatile int64_t*>(ok) == 0) return;
   const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
   BlockTeam<NT> tm(red);
-  // the in-order pass claims one position at a time (the order of the
-  // claims is what makes its waits end); a retry pass claims NT at once and
-  // keeps the trades of its size range
-  const bool ordered = ok != nullptr;
   for (;;) {
-    if (threadIdx.x == 0) pick = static_cast<int64_t>(atomicAdd(claim, ordered ? 1ull : static_cast<unsigned long long>(NT)));
+    if (threadIdx.x == 0) pick = static_cast<int64_t>(atomicAdd(claim, 1ull));
     __syncthreads();
-    const int64_t base = pick;
+    const int64_t p = pick;
     __syncthreads();
-    if (base >= nl) return;
-    int nf = 1;
-    if (!ordered) {
-      const int64_t p = base + threadIdx.x;
-      int32_t t = -1;
-      if (p < nl) {
-        t = __ldcg(list + p);
-        const TradeRows tr = trade_rows(c, t);
-        const int L = tr.du + tr.dv;
-        if (L < lmin || L > lmax) t = -1;
+    if (p >= nl) return;
+    const int64_t t = __ldcg(list + (from_back ? -1 - p : p));
+    const TradeRows tr = trade_rows(c, t);
+    const int L = tr.du + tr.dv;
+    if (L < lmin || L > lmax) continue;
+    if (L <= WarpWs::kLmax) {
+      if (threadIdx.x < 32) {
+        WarpTeam wt;
+        phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(wt, c, t, WarpWs{sbuf});
       }
-      const int mine = t >= 0 ? 1 : 0;
-      const int before = static_cast<int>(tm.exscan(mine));
-      if (mine) found[before] = t;
-      if (threadIdx.x == NT - 1) nfound = before + mine;
-      __syncthreads();
-      nf = nfound;
-    }
-    for (int q = 0; q < nf; ++q) {
-      const int64_t t = ordered ? __ldcg(list + base) : found[q];
-      const TradeRows tr = trade_rows(c, t);
-      const int L = tr.du + tr.dv;
-      if (L <= WarpWs::kLmax) {
-        if (threadIdx.x < 32) {
-          WarpTeam wt;
-          phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(wt, c, t, WarpWs{sbuf});
-        }
-      } else if (L <= Ws::kLmax) {
-        phase_a_reg<BlockTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, t, Ws{sbuf});
-      } else {
-        char* wsb = sbuf;
-        if (L > gen_max) {
-          wsb = gws + slice * blockIdx.x;
-          if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
-        }
-        phase_a(tm, c, t, carve_a(wsb, L), &sel);
+    } else if (L <= Ws::kLmax) {
+      phase_a_reg<BlockTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, t, Ws{sbuf});
+    } else {
+      char* wsb = sbuf;
+      if (L > gen_max) {
+        wsb = gws + slice * blockIdx.x;
+        if (threadIdx.x == 0) atomicAdd(c.gws_count, 1ull);
       }
-      __syncthreads();
+      phase_a(tm, c, t, carve_a(wsb, L), &sel);
     }
+    __syncthreads();
   }
 }
 
-// A retry pass's small trades (L <= 32 kWarpJ): every warp claims list
-// positions on its own.
+// A retry pass's small trades (list[0 .. *count)): every warp claims one at
+// a time.
 __global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_list_warp(StepCtx c, const int32_t* __restrict__ list,
                                                                        const unsigned long long* count,
                                                                        unsigned long long* claim) {
@@ -1978,45 +1965,41 @@ __global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_list_warp(StepCt
   WarpTeam tm;
   const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
   for (;;) {
-    // 32 positions per claim; the small trades among them run one by one
-    int64_t base = 0;
-    if (lane == 0) base = static_cast<int64_t>(atomicAdd(claim, 32ull));
-    base = static_cast<int64_t>(tm.bcast(static_cast<uint64_t>(base), 0));
-    if (base >= nl) return;
-    int32_t t = -1;
-    if (base + lane < nl) {
-      t = __ldcg(list + base + lane);
-      const TradeRows tr = trade_rows(c, t);
-      if (tr.du + tr.dv > WarpWs::kLmax) t = -1;
-    }
-    unsigned todo = __ballot_sync(kFull, t >= 0);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, __shfl_sync(kFull, t, src), w);
-    }
+    int64_t p = 0;
+    if (lane == 0) p = static_cast<int64_t>(atomicAdd(claim, 1ull));
+    p = static_cast<int64_t>(tm.bcast(static_cast<uint64_t>(p), 0));
+    if (p >= nl) return;
+    phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, __ldcg(list + p), w);
   }
 }
 
-// The last pass's list of deferred trades sorted by index in one CTA, when
-// it holds at most kSortListMax trades (*ok = 1); otherwise *ok = 0 and the
-// in-order pass scans the done flags instead.
+// The last pass's list of deferred trades (nsmall from the front, nbig
+// from the back of list[0 .. cap)) gathered and sorted by index in one CTA
+// into list[0 .. n), when n <= kSortListMax (*ok = 1, *n_out = n);
+// otherwise *ok = 0 and the in-order pass scans the done flags instead.
 constexpr int kSortListMax = 4096;
-__global__ void __launch_bounds__(1024) k_sort_list(int32_t* list, const unsigned long long* count, int64_t* ok) {
+__global__ void __launch_bounds__(1024) k_sort_list(int32_t* list, int64_t cap, const unsigned long long* nsmall,
+                                                    const unsigned long long* nbig, int64_t* ok, int64_t* n_out) {
   __shared__ int32_t a[kSortListMax];
   __shared__ int64_t red[BlockTeam<1024>::kRedSlots];
-  const int64_t nl = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(count));
+  const int64_t ns = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(nsmall));
+  const int64_t nb = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(nbig));
+  const int64_t nl = ns + nb;
   if (nl > kSortListMax) {
     if (threadIdx.x == 0) *ok = 0;
     return;
   }
   const int P = nl > 1 ? next_pow2(static_cast<int>(nl)) : 1;
-  for (int i = threadIdx.x; i < P; i += 1024) a[i] = i < nl ? list[i] : 0x7fffffff;
+  for (int i = threadIdx.x; i < P; i += 1024)
+    a[i] = i < ns ? list[i] : i < nl ? list[cap - 1 - (i - ns)] : 0x7fffffff;
   __syncthreads();
   BlockTeam<1024> tm(red);
   team_bitonic_sort(tm, a, P);
   for (int i = threadIdx.x; i < nl; i += 1024) list[i] = a[i];
-  if (threadIdx.x == 0) *ok = 1;
+  if (threadIdx.x == 0) {
+    *ok = 1;
+    *n_out = nl;
+  }
 }
 
 // End of a super step: every graph's step counter moves on.
@@ -2232,10 +2215,18 @@ int super_step(Graph* h) {
   // the deferred ones: each runs every deferred trade whose dependencies
   // have published by then, so chains of dependent trades shrink by a level
   // per pass.  Pass r counts its deferrals in ctr[kCtrPassLeft + r] and lists
-  // them in dlist[r & 1] for pass r + 1.
+  // them in dlist[r & 1] for pass r + 1: the small ones from the front
+  // (ctr[kCtrPassSmall + r] of them), the others from the back
+  // (ctr[kCtrPassBig + r]).
+  auto list_for = [&](int r) {
+    c.def_count = ucnt + kCtrPassLeft + r;
+    c.def_list = h->dlist + (r & 1) * ntasks;
+    c.def_small = ucnt + kCtrPassSmall + r;
+    c.def_big = ucnt + kCtrPassBig + r;
+    c.def_cap = ntasks;
+  };
   time_classes = h->timing;
-  c.def_count = ucnt + kCtrPassLeft;
-  c.def_list = h->dlist;
+  list_for(0);
   if ((rc = classify(0)) || (rc = run_classes())) return rc;
   time_classes = false;
   const unsigned lgrid = static_cast<unsigned>(gws ? std::min(h->num_sms * 4, h->ws_ctas) : h->num_sms * 4);
@@ -2245,21 +2236,17 @@ int super_step(Graph* h) {
     // small trades on warps, medium on 256-thread CTAs, the largest on
     // 1024-thread CTAs (shared memory up to smem_max entries)
     const int32_t* in = h->dlist + (r & 1) * ntasks;
-    const unsigned long long* nin = ucnt + kCtrPassLeft + r;
-    c.def_count = ucnt + kCtrPassLeft + 1 + r;
-    c.def_list = h->dlist + ((r + 1) & 1) * ntasks;
-    k_phase_a_list_warp<<<wgrid, 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(c, in, nin,
+    list_for(r + 1);
+    k_phase_a_list_warp<<<wgrid, 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(c, in, ucnt + kCtrPassSmall + r,
                                                                                   ucnt + kCtrListClaim + 3 * r);
     CB_CUDA(h, cudaGetLastError());
-    k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, in, nin, nullptr,
-                                                                     ucnt + kCtrListClaim + 3 * r + 1,
-                                                                     WarpWs::kLmax + 1, TeamCfg<kMedThreads>::kMax,
-                                                                     block_max, gws, h->ws_slice);
+    k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(
+        c, in + ntasks, 1, ucnt + kCtrPassBig + r, nullptr, ucnt + kCtrListClaim + 3 * r + 1, kListSmall + 1,
+        TeamCfg<kMedThreads>::kMax, block_max, gws, h->ws_slice);
     CB_CUDA(h, cudaGetLastError());
-    k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(c, in, nin, nullptr,
-                                                                         ucnt + kCtrListClaim + 3 * r + 2,
-                                                                         TeamCfg<kMedThreads>::kMax + 1, 0x7fffffff,
-                                                                         h->smem_max, gws, h->ws_slice);
+    k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(
+        c, in + ntasks, 1, ucnt + kCtrPassBig + r, nullptr, ucnt + kCtrListClaim + 3 * r + 2,
+        TeamCfg<kMedThreads>::kMax + 1, 0x7fffffff, h->smem_max, gws, h->ws_slice);
     CB_CUDA(h, cudaGetLastError());
     h->launches += 3;
   }
@@ -2272,9 +2259,10 @@ int super_step(Graph* h) {
   {
     const int R = h->retry_passes;
     int32_t* last = h->dlist + (R & 1) * ntasks;
-    const unsigned long long* nlast = ucnt + kCtrPassLeft + R;
     int64_t* ok = cnt + kCtrListOk;
-    k_sort_list<<<1, 1024, 0, s>>>(last, nlast, ok);
+    const unsigned long long* nlast = ucnt + kCtrListN;
+    k_sort_list<<<1, 1024, 0, s>>>(last, ntasks, ucnt + kCtrPassSmall + R, ucnt + kCtrPassBig + R, ok,
+                                   cnt + kCtrListN);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
     c.wait = 1;
@@ -2282,15 +2270,15 @@ int super_step(Graph* h) {
     c.def_list = nullptr;
     unsigned long long* lclaim = ucnt + kCtrListClaim + 3 * kRetryPassesMax;
     if (h->inorder_threads == kBigThreads) {
-      k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(c, last, nlast, ok, lclaim, 0, 0x7fffffff,
-                                                                           h->smem_max, gws, h->ws_slice);
+      k_phase_a_list<kBigThreads><<<bgrid, kBigThreads, list_smem_big, s>>>(c, last, 0, nlast, ok, lclaim, 0,
+                                                                           0x7fffffff, h->smem_max, gws, h->ws_slice);
       CB_CUDA(h, cudaGetLastError());
       const int64_t chunk = std::max<int64_t>(1024, (ntasks + int64_t(bgrid) * 8 - 1) / (int64_t(bgrid) * 8));
       k_phase_a_inorder<kBigThreads><<<bgrid, kBigThreads, big_smem, s>>>(c, ntasks, chunk, ucnt + kCtrClaims,
                                                                          h->smem_max, gws, h->ws_slice, ok);
       CB_CUDA(h, cudaGetLastError());
     } else {
-      k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, last, nlast, ok, lclaim, 0, 0x7fffffff,
+      k_phase_a_list<kMedThreads><<<lgrid, kMedThreads, list_smem, s>>>(c, last, 0, nlast, ok, lclaim, 0, 0x7fffffff,
                                                                        block_max, gws, h->ws_slice);
       CB_CUDA(h, cudaGetLastError());
       const int64_t chunk = std::max<int64_t>(512, (ntasks + int64_t(lgrid) * 4 - 1) / (int64_t(lgrid) * 4));

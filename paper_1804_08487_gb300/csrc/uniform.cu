@@ -61,8 +61,11 @@ struct UniBufs {
 namespace {
 
 constexpr int32_t kInf = 0x7fffffff;            // no further trade
-constexpr int kUniThreads = 256;
-constexpr int kUniSmemElems = 2048;             // trades up to this many entries work in shared memory
+// Executor CTAs of NT = 256 (two per SM), 512 or 1024 threads (option
+// "uniform_threads"): larger CTAs give a hub trade more threads but keep
+// fewer trades running at once.
+template <int NT>
+constexpr int uni_smem_elems() { return NT == 1024 ? 4096 : 2048; }   // trades up to this many entries in shared memory
 constexpr int64_t kUniChunkMin = 65536;
 
 __device__ __forceinline__ void latch(int32_t* err, int32_t code) { atomicCAS(err, 0, code); }
@@ -437,11 +440,14 @@ __device__ __noinline__ int tied_before(const UniCtx& c, const int2* ent, const 
   return before;
 }
 
-constexpr int kMsgBatch = 2;   // messages per thread with their atomics in flight together
+// messages per thread with their atomics in flight together (one in the
+// 1024-thread executor, whose threads have 64 registers)
+template <int NT>
+constexpr int msg_batch() { return NT == 1024 ? 1 : 2; }
 
 // One trade by the whole CTA.  Returns false when a wait gave up.
-template <class HT>
-__device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k, const TradeWs<HT>& w, int hbits,
+template <int NT, class HT>
+__device__ bool uni_trade(BlockTeam<NT>& tm, const UniCtx& c, int64_t k, const TradeWs<HT>& w, int hbits,
                           int32_t* hist, int64_t* s_sel, int* s_abort) {
   const int32_t u = c.tp[2 * k], v = c.tp[2 * k + 1];
   const int du = static_cast<int>(c.rp[u + 1] - c.rp[u]), dv = static_cast<int>(c.rp[v + 1] - c.rp[v]);
@@ -454,7 +460,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   //    entry still in flight; clear the hash
   bool ok = true;
 #pragma unroll 4
-  for (int e = tm.rank; e < E; e += kUniThreads) {
+  for (int e = tm.rank; e < E; e += NT) {
     const int side = e >= du;
     const int2* p = side ? inv + (e - du) : inu + e;
     int2 m = __ldcg(p);
@@ -465,18 +471,18 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
     w.ent[e] = m;
     w.flag[e] = static_cast<uint8_t>(side);
   }
-  for (int s = tm.rank; s < H; s += kUniThreads) w.hash[s] = 0;
+  for (int s = tm.rank; s < H; s += NT) w.hash[s] = 0;
   if (!ok) atomicExch(s_abort, 1);
   tm.sync();
   if (*s_abort) return false;
   // 2. u's neighbours into the hash (entry index + 1)
-  for (int e = tm.rank; e < du; e += kUniThreads) {
+  for (int e = tm.rank; e < du; e += NT) {
     uint32_t s = hash_slot(w.ent[e].x, hbits);
     while (atomicCAS(&w.hash[s], HT(0), static_cast<HT>(e + 1)) != HT(0)) s = (s + 1) & (H - 1);
   }
   tm.sync();
   // 3. v's neighbours look themselves up: common neighbours and the edge {u, v}
-  for (int e = du + tm.rank; e < E; e += kUniThreads) {
+  for (int e = du + tm.rank; e < E; e += NT) {
     const int32_t x = w.ent[e].x;
     uint8_t f = 1;
     if (x == u) f |= 4;
@@ -498,7 +504,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   const uint64_t gi = c.first + static_cast<uint64_t>(k);
   int64_t cnt = 0;
 #pragma unroll 4
-  for (int e = tm.rank; e < E; e += kUniThreads) {
+  for (int e = tm.rank; e < E; e += NT) {
     uint8_t f = w.flag[e];
     if (f == 0 && w.ent[e].x == v) w.flag[e] = f = 4;
     if ((f & 6) == 0) {
@@ -517,10 +523,10 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   bool tie = false;
   if (na > 0 && na < nd) {
     for (int shift = 56;; shift -= 8) {
-      for (int b = tm.rank; b < 256; b += kUniThreads) hist[b] = 0;
+      for (int b = tm.rank; b < 256; b += NT) hist[b] = 0;
       tm.sync();
 #pragma unroll 4
-      for (int e = tm.rank; e < E; e += kUniThreads)
+      for (int e = tm.rank; e < E; e += NT)
         if ((w.flag[e] & 6) == 0 && (w.key[e] & mask) == prefix) atomicAdd(&hist[(w.key[e] >> shift) & 255], 1);
       tm.sync();
       const int hb = tm.rank < 256 ? hist[tm.rank] : 0;
@@ -545,7 +551,7 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   // decision: below the threshold's bucket to u, above to v, within it by rank
   int moved = 0;
 #pragma unroll 2
-  for (int e = tm.rank; e < E; e += kUniThreads) {
+  for (int e = tm.rank; e < E; e += NT) {
     const uint8_t f = w.flag[e];
     if (f & 6) continue;
     bool to_u;
@@ -569,12 +575,12 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
   tm.sync();
   // 6. every resulting edge goes on: common neighbours and the edge {u, v}
   //    stay, D as decided; atomics of a thread's messages overlap in batches
-  for (int e0 = 0; e0 < E; e0 += kUniThreads * kMsgBatch) {
-    Msg m[kMsgBatch];
-    bool has[kMsgBatch];
+  for (int e0 = 0; e0 < E; e0 += NT * msg_batch<NT>()) {
+    Msg m[msg_batch<NT>()];
+    bool has[msg_batch<NT>()];
 #pragma unroll
-    for (int j = 0; j < kMsgBatch; ++j) {
-      const int e = e0 + j * kUniThreads + tm.rank;
+    for (int j = 0; j < msg_batch<NT>(); ++j) {
+      const int e = e0 + j * NT + tm.rank;
       has[j] = false;
       if (e < E) {
         const uint8_t f = w.flag[e];
@@ -593,23 +599,24 @@ __device__ bool uni_trade(BlockTeam<kUniThreads>& tm, const UniCtx& c, int64_t k
       }
     }
 #pragma unroll
-    for (int j = 0; j < kMsgBatch; ++j)
+    for (int j = 0; j < msg_batch<NT>(); ++j)
       if (has[j]) deliver(c, m[j]);
   }
   tm.sync();   // the work space is reused by the next trade
   return true;
 }
 
-__global__ void __launch_bounds__(kUniThreads, 2) k_uni_exec(UniCtx c) {
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) k_uni_exec(UniCtx c) {
   extern __shared__ __align__(16) char usm[];
-  __shared__ int64_t red[BlockTeam<kUniThreads>::kRedSlots];
+  __shared__ int64_t red[BlockTeam<NT>::kRedSlots];
   __shared__ int32_t hist[256];
   __shared__ int64_t s_sel[3];
   __shared__ int64_t s_k;
   __shared__ int s_abort;
-  BlockTeam<kUniThreads> tm(red);
+  BlockTeam<NT> tm(red);
   if (threadIdx.x == 0) s_abort = 0;
-  const TradeWs ws_smem = carve_ws(usm, kUniSmemElems);
+  const TradeWs ws_smem = carve_ws(usm, uni_smem_elems<NT>());
   const TradeWs ws_glob =
       c.gslice ? carve_ws(c.gslice + static_cast<size_t>(blockIdx.x) * c.slice_elems * kWsBytesPerElem, c.slice_elems)
                : ws_smem;
@@ -622,7 +629,7 @@ __global__ void __launch_bounds__(kUniThreads, 2) k_uni_exec(UniCtx c) {
     const int64_t du = c.rp[u + 1] - c.rp[u];
     const int64_t E = du + (c.rp[v + 1] - c.rp[v]);
     bool ok;
-    if (E <= kUniSmemElems) {
+    if (E <= uni_smem_elems<NT>()) {
       ok = uni_trade(tm, c, k, ws_smem, hash_bits(2 * du), hist, s_sel, &s_abort);
     } else if (du <= kHash16MaxDu) {
       TradeWs<uint16_t> w16{ws_glob.ent, ws_glob.key, reinterpret_cast<uint16_t*>(usm), ws_glob.flag};
@@ -722,13 +729,18 @@ int uniform_trades(Graph* h, uint64_t count) {
     return rc;
   UniBufs* b = h->uni;
   // kernel resources: occupancy of the persistent executor, its sort space
-  const size_t smem = kWsBytesPerElem * kUniSmemElems;
-  CB_CUDA(h, cudaFuncSetAttribute(k_uni_exec, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  const int NT = h->uni_threads;
+  const void* exec = NT == 1024 ? reinterpret_cast<const void*>(k_uni_exec<1024>)
+                     : NT == 512 ? reinterpret_cast<const void*>(k_uni_exec<512>)
+                                 : reinterpret_cast<const void*>(k_uni_exec<256>);
+  const int smem_elems = NT == 1024 ? uni_smem_elems<1024>() : uni_smem_elems<256>();
+  const size_t smem = kWsBytesPerElem * smem_elems;
+  CB_CUDA(h, cudaFuncSetAttribute(exec, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   int per_sm = 0;
-  CB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uni_exec, kUniThreads, smem));
+  CB_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, exec, NT, smem));
   const int ctas = std::max(1, per_sm) * h->num_sms;
   const int64_t big = next_pow2_host(std::max<int64_t>(2 * h->maxdeg, 1));
-  if (2 * h->maxdeg > kUniSmemElems && (!b->gslice || b->slice_elems < big || b->ctas < ctas)) {
+  if (2 * h->maxdeg > smem_elems && (!b->gslice || b->slice_elems < big || b->ctas < ctas)) {
     if (b->gslice) {
       cudaFreeAsync(b->gslice, s);
       h->dev_bytes -= static_cast<int64_t>(b->slice_bytes);
@@ -815,7 +827,9 @@ int uniform_trades(Graph* h, uint64_t count) {
     c.swaps = h->swap_stats ? reinterpret_cast<unsigned long long*>(h->swaps) : nullptr;
     k_uni_route<<<grid_for_work(n * 32, h->num_sms), 256, 0, s>>>(c, n, h->col[h->cur]);
     CB_CUDA(h, cudaGetLastError());
-    k_uni_exec<<<ctas, kUniThreads, smem, s>>>(c);
+    if (NT == 1024) k_uni_exec<1024><<<ctas, 1024, smem, s>>>(c);
+    else if (NT == 512) k_uni_exec<512><<<ctas, 512, smem, s>>>(c);
+    else k_uni_exec<256><<<ctas, 256, smem, s>>>(c);
     CB_CUDA(h, cudaGetLastError());
     k_uni_check<<<g1, 256, 0, s>>>(n, c.rp, b->ocur, b->ctr, L, h->err);
     CB_CUDA(h, cudaGetLastError());

@@ -129,6 +129,16 @@ def test_uniform_trades_with_hubs_above_the_shared_hash():
     _run_pair(rp, col, 1, [n // 2, n // 2])
 
 
+@pytest.mark.parametrize("threads", [512, 1024])
+def test_uniform_trades_on_larger_executor_ctas(threads):
+    """The executor with 512 or 1024 threads per CTA: the same sequence,
+    hubs above every shared-memory size included."""
+    g = synth.powerlaw_graph(5001, 2, 2500, 2.0, 2)
+    _run_pair(g.row_ptr, g.col, 15, [2500, 2500], options={"uniform_threads": threads})
+    g = synth.powerlaw_graph(40, 10, 30, 2.0, 3)
+    _run_pair(g.row_ptr, g.col, 22, [20, 500, 3000], options={"uniform_threads": threads})
+
+
 def test_uniform_and_global_steps_alternate():
     g = synth.powerlaw_graph(3000, 3, 300, 2.0, 8)
     _run_pair(g.row_ptr, g.col, 21, [500, 1500, 1], steps_between=2)
