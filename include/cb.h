@@ -240,7 +240,7 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               memory) [1024; 256 for cb_create_batch].
  *   "uniform_threads" CTA size of the executor of cb_uniform_trades: 256
  *               (two CTAs per SM), 512 or 1024 (more threads per hub trade,
- *               fewer trades at once) [256].
+ *               fewer trades at once) [1024].
  *   "lane_teams" 1: trades of at most 32 / 64 entries run on teams of 8 /
  *               16 lanes, several per warp; 0: on whole warps [1].
  *   "retry_passes" parallel passes over the deferred trades between the

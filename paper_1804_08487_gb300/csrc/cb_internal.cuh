@@ -145,7 +145,7 @@ struct Graph {
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
   int retry_passes = 2;         // parallel passes over the deferred trades before the in-order pass
   int lane_teams = 1;           // trades up to 32 / 64 entries on teams of 8 / 16 lanes
-  int uni_threads = 256;        // CTA size of the uniform-trade executor (256, 512 or 1024)
+  int uni_threads = 1024;       // CTA size of the uniform-trade executor (256, 512 or 1024)
   bool wide_pack = false;       // 16-byte far-trade records even when 8 bytes would do (tests)
   // relaxed global trade: permutations from h(x) = (a x + b) mod p
   bool relaxed = false;

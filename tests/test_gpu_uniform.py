@@ -129,9 +129,9 @@ def test_uniform_trades_with_hubs_above_the_shared_hash():
     _run_pair(rp, col, 1, [n // 2, n // 2])
 
 
-@pytest.mark.parametrize("threads", [512, 1024])
-def test_uniform_trades_on_larger_executor_ctas(threads):
-    """The executor with 512 or 1024 threads per CTA: the same sequence,
+@pytest.mark.parametrize("threads", [256, 512])
+def test_uniform_trades_on_other_executor_ctas(threads):
+    """The executor with 256 or 512 threads per CTA (1024 by default): the same sequence,
     hubs above every shared-memory size included."""
     g = synth.powerlaw_graph(5001, 2, 2500, 2.0, 2)
     _run_pair(g.row_ptr, g.col, 15, [2500, 2500], options={"uniform_threads": threads})
