@@ -161,26 +161,24 @@ def workload(name):
     return synth.PLAIN[name]
 
 
-# DRAM bytes per directed entry of each kernel that can be the dominant one,
-# from ncu `dram__bytes_read.sum + dram__bytes_write.sum` of one launch on the
-# n=2^21 graph of the same degree law (profiles/), and the sha256 of
-# csrc/trade.cu those counters were taken on: traffic grows with the entries a
-# launch processes, so the full-size figure is that per-entry value times the
-# launch's entries.  A kernel changed since then reports no traffic.
-SMALL_CASE_TRAFFIC = {}
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass,
+# every launch of the unit in one super step) of the dominant unit of a
+# workload, and the sha256 of csrc/trade.cu the capture ran on; a unit whose
+# code changed since reports no traffic.  profiles/ holds the captures.
+MEASURED_TRAFFIC = {}
 
 
-def measured_traffic(kernel, entries):
-    """DRAM bytes of one launch of `kernel` processing `entries` directed
-    entries, scaled from the small-case ncu capture, or None."""
+def measured_traffic(unit, workload):
+    """DRAM bytes per launch of `unit` on `workload` from the committed ncu
+    capture, or None."""
     import hashlib
-    rec = SMALL_CASE_TRAFFIC.get(kernel)
+    rec = MEASURED_TRAFFIC.get((unit, workload))
     if rec is None:
         return None
     src = os.path.join(ROOT, "paper_1804_08487_gb300", "csrc", "trade.cu")
     if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["trade_cu_sha256"]:
         return None
-    return rec["bytes_per_entry"] * entries
+    return rec["bytes"]
 
 
 # the threshold phase's kernel of each size class (cb_timings ms[4 + k])
@@ -199,12 +197,18 @@ FIXUP_BYTES_PER_ENTRY = 10
 FIXUP_BYTES_PER_TRADE = 16
 
 
+# the rebuild is timed as one unit per super step: the far-trade records,
+# each chunk's first row, and the fix-up passes over slices of the far trades
+REBUILD_UNIT = "rebuild phase (k_far_pack, k_chunk_rows, k_fixup passes)"
+
+
 def dominant_kernel(stats, phases, m, ntasks, K):
     """The kernel (or, for the rebuild, the fix-up launches of one step) with
     the largest event-timed device time per super step, its algorithmic bytes
     per launch and average launch duration.  The first threshold pass's class
     kernels are bracketed by events; the retry passes and the in-order pass
-    run only the few deferred trades."""
+    run only the few deferred trades; the rebuild counts as one launch per
+    super step."""
     cands = []
     for k, name in enumerate(CLASS_KERNELS):
         ms = phases.get(f"class{k}_ms", 0.0) / K
@@ -212,7 +216,7 @@ def dominant_kernel(stats, phases, m, ntasks, K):
             b = (THRESHOLD_BYTES_PER_ENTRY * stats.get(f"class{k}_entries", 0)
                  + THRESHOLD_BYTES_PER_TRADE * stats.get(f"class{k}_trades", 0))
             cands.append((ms, name, b, stats.get(f"class{k}_entries", 0)))
-    cands.append((phases["rebuild_ms"] / K, "k_fixup (rebuild phase)",
+    cands.append((phases["rebuild_ms"] / K, REBUILD_UNIT,
                   FIXUP_BYTES_PER_ENTRY * 2 * m + FIXUP_BYTES_PER_TRADE * ntasks, 2 * m))
     ms, name, b, entries = max(cands)
     return name, b, ms, entries
@@ -274,6 +278,7 @@ def config_of(w, g, world, perm="sort"):
 
 ENSEMBLE_GRAPHS = 256
 ENSEMBLE_STEPS = 50
+ENSEMBLE_TUNE_STEPS = 60     # autotuning super steps before the timed ones (untimed warm-up)
 ENSEMBLE_NAME = ("ensemble of 256 graphs: n log-uniform in [2^10, 2^16], PLD([4, n/16), gamma in [2, 3]), "
                  "Havel-Hakimi, seed 1000+i, 50 super steps each")
 
@@ -288,7 +293,8 @@ def ensemble_graphs(count=ENSEMBLE_GRAPHS):
     return graphs, [w.chain_seed for w in members]
 
 
-def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=25, clocks=None, plain_compare=True):
+def measure_ensemble(graphs, seeds, stream, steps=ENSEMBLE_STEPS, tune_steps=ENSEMBLE_TUNE_STEPS, clocks=None,
+                     plain_compare=True):
     """Batched: one handle, autotuned (its tuning steps are untimed warm-up),
     CUDA-graph replay, `steps` timed super steps.  Plain (unless
     plain_compare is off): each graph in its own handle, `steps` super steps
@@ -419,7 +425,7 @@ def run_ensemble(args):
     value = job_rate(world, r["m_total"] * K, t_ms / 1e3)
     line = {
         "metric": METRIC + " (batched ensemble)", "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": 27, "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "warmup": ENSEMBLE_TUNE_STEPS + 2, "ms_per_step": t_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": ENSEMBLE_NAME, "graphs": r["graphs"], "n_total": r["n_total"],
                    "m_total": r["m_total"], "l2": "inputs smaller than L2 are re-read every step (no flush)",
@@ -944,8 +950,8 @@ def run_ours(args):
         "dtype": "int32", "data": "synthetic", "config": config_of(w, g, world, args.perm),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": measured_traffic(dom, dom_entries),
-                     "traffic_unit": "DRAM bytes per launch (ncu on the n=2^21 graph, scaled by entries)",
+                     "traffic": measured_traffic(dom, args.workload),
+                     "traffic_unit": "DRAM bytes per launch (ncu, one pass, same workload)",
                      "algorithmic_bytes": dom_bytes, "launch_ms": dom_ms,
                      "peak_source": f"{peak_kind} hbm_gbs (burst copy)"},
         "roofline_step": {"bytes_min": b_min, "achieved": step_gbs, "peak": peak, "unit": "GB/s",

@@ -131,7 +131,8 @@ int cb_export_graph(cb_handle h, int32_t index, int32_t* edges, int64_t capacity
  *     ordered by (key, lo, hi) and u receives the first |A_{u-v}| elements.
  * philox64(...) = r0<<32 | r1 of Philox4x32-10 (Salmon et al., SC'11) with
  * key words (low, high) 32 bits of the seed.  Asynchronous on the handle's
- * stream (with the "timing" option on, it waits once per super step).
+ * stream (with the "timing" option on, a super step waits for the events of
+ * the step two before it, so the host stays at most two steps ahead).
  * Returns CB_ERANGE if the step counter would pass 2^32 - 2.
  */
 int cb_global_trades(cb_handle h, uint32_t supersteps);
@@ -204,7 +205,7 @@ int cb_stats(cb_handle h, int64_t* out, int count);
  * first threshold pass's kernel of size class k (0 where the class shares
  * another class's kernel), ms[13] = the retry passes over deferred trades,
  * ms[14] = the in-order pass.  Returns the number of values written
- * (<= count, at most 15).
+ * (<= count, at most 15).  Waits for the events still outstanding.
  */
 int cb_timings(cb_handle h, double* ms, int count);
 
@@ -258,8 +259,9 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               n <= 2^29 would allow 8-byte ones (a test knob) [0].
  *   "bucket_cap" largest permutation bucket sorted in shared memory [2048];
  *               larger buckets take the global-memory fallback; 2..4096.
- *   "timing"    1: record CUDA events around the phases of each super step
- *               (adds one stream synchronisation per super step) [0].
+ *   "timing"    1: record CUDA events around the phases and the first
+ *               pass's kernels of each super step, in two sets used in turn
+ *               (the host waits for a set two steps after recording it) [0].
  *   "wait_ms"   longest single device wait, in milliseconds [1000 for a
  *               super step, 20000 for uniform trades]; 1..600000.  A wait
  *               that runs out makes the call (or the next cb_sync) return
@@ -355,9 +357,10 @@ int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32_t* order_o
  * Pick the fastest work split for this handle: runs up to max_steps real
  * super steps (they advance the chain; the result does not depend on the
  * options): one to load the kernels, then the rest shared evenly by the
- * candidate settings, one knob at a time, of "tile_max", "block_max",
- * "smem_max", "inorder_threads" and "retry_passes", timed with CUDA
- * events, and keeps the fastest.  chosen (may be NULL) receives up to
+ * current settings and the candidate settings, one knob at a time, of
+ * "tile_max", "block_max", "smem_max", "inorder_threads" and
+ * "retry_passes", timed with CUDA events; a candidate replaces the best
+ * setting so far only when it is at least 2 % faster.  chosen (may be NULL) receives up to
  * `count` values: tile_max, block_max, smem_max, inorder_threads, super
  * steps used, retry_passes.  Returns the number of values written.
  */

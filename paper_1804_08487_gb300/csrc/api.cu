@@ -77,8 +77,9 @@ void release(Graph* h) {
     if (x) cudaGraphExecDestroy(x);
   delete[] h->hsegs;
   delete[] h->host_counters;
-  for (auto& e : h->ev)
-    if (e) cudaEventDestroy(e);
+  for (auto& set : h->ev)
+    for (auto& e : set)
+      if (e) cudaEventDestroy(e);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -646,6 +647,11 @@ int cb_global_trades(cb_handle h, uint32_t supersteps) {
   if (h->latched) return fail(h, h->latched, "handle has a latched error: " + h->last_error);
   if (h->g + supersteps >= 0xfffffffeull) return fail(h, CB_ERANGE, "super-step counter would pass 2^32-2");
   const int64_t launches0 = h->launches;
+  // event sets still pending belong to the previous call
+  for (int set = 0; set < 2; ++set) {
+    const int rc = flush_timing(h, set, false);
+    if (rc) return rc;
+  }
   for (double& v : h->phase_ms) v = 0;
   if (h->use_graph && !h->timing && !h->swap_stats && !h->pres && supersteps > 0) {
     if (!h->step_exec[0]) {
@@ -805,6 +811,10 @@ int cb_stats(cb_handle h, int64_t* out, int count) {
 
 int cb_timings(cb_handle h, double* ms, int count) {
   if (!h || !ms || count < 0) return fail(h, CB_EINVAL, "bad argument");
+  for (int set = 0; set < 2; ++set) {
+    const int rc = flush_timing(h, set, true);
+    if (rc) return rc;
+  }
   const int k = std::min(count, kTimings);
   for (int i = 0; i < k; ++i) ms[i] = h->phase_ms[i];
   return k;
@@ -873,8 +883,9 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     return size_trade_workspace(h);
   }
   if (!std::strcmp(key, "timing")) {
-    if (value && !h->ev[0]) {
-      for (auto& e : h->ev) CB_CUDA(h, cudaEventCreate(&e));
+    if (value && !h->ev[0][0]) {
+      for (auto& set : h->ev)
+        for (auto& e : set) CB_CUDA(h, cudaEventCreate(&e));
     }
     h->timing = value != 0;
     return CB_OK;
@@ -957,26 +968,36 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
     int ncand;
   };
   constexpr int kKnobs = 5;
-  Knob knobs[kKnobs] = {{&h->tile_max, {32, 64, 96, 128}, 4},
+  Knob knobs[kKnobs] = {{&h->tile_max, {32, 64, 128, 0}, 3},
                         {&h->block_max, {512, 1024, 2048, 0}, 3},
-                        {&h->smem_max, {2048, 4096, 8192, 0}, 3},
+                        {&h->smem_max, {4096, 8192, 0, 0}, 2},
                         {&h->inorder_threads, {256, 1024, 0, 0}, 2},
-                        {&h->retry_passes, {0, 1, 2, 4}, 4}};
+                        {&h->retry_passes, {1, 2, 3, 0}, 3}};
   float ms = 0;
   if (used < max_steps) rc = trial(&ms);   // first launches load the kernels: not timed as a candidate
   {
-    int total = 0;   // candidate settings over all knobs
+    // the current settings, then every other candidate: super steps shared
+    // evenly, at least one each
+    int total = 1;
     for (const Knob& kn : knobs) total += kn.ncand;
     if (max_steps > used) per = std::max<uint32_t>(1, (max_steps - used) / static_cast<uint32_t>(total));
   }
+  float best_ms = 3.4e38f;
+  if (rc == CB_OK && used < max_steps) {
+    rc = trial(&ms);
+    if (rc == CB_OK) best_ms = ms;
+  }
+  // one knob at a time; a setting replaces the best one so far only when it
+  // is at least 2 % faster (a step's time varies with its deferred trades)
   for (int k = 0; k < kKnobs && rc == CB_OK; ++k) {
-    int best = *knobs[k].field;
-    float best_ms = 3.4e38f;
+    const int cur = *knobs[k].field;
+    int best = cur;
     for (int j = 0; j < knobs[k].ncand && used < max_steps && rc == CB_OK; ++j) {
+      if (knobs[k].cand[j] == cur) continue;
       *knobs[k].field = knobs[k].cand[j];
       rc = size_trade_workspace(h);   // the global workspace follows block_max and smem_max
       if (rc == CB_OK) rc = trial(&ms);
-      if (rc == CB_OK && ms < best_ms) {
+      if (rc == CB_OK && ms < 0.98f * best_ms) {
         best_ms = ms;
         best = knobs[k].cand[j];
       }

@@ -166,9 +166,13 @@ struct Graph {
   int64_t stats[kStats] = {0};
   int64_t launches = 0;                    // kernel launches issued by this handle
   bool timing = false;                     // record CUDA events around the phases
-  // events: [0..4) phase bounds, [4, 4 + kClasses + 1) bounds of the first
-  // pass's class kernels, then the end of the retry passes
-  cudaEvent_t ev[4 + kClasses + 2] = {};
+  // events, in two sets that super steps use in turn (the host waits for a
+  // step's events only when the set comes round again, two steps later):
+  // [0..4) phase bounds, [4, 4 + kClasses + 1) bounds of the first pass's
+  // class kernels, then the end of the retry passes
+  cudaEvent_t ev[2][4 + kClasses + 2] = {};
+  int ev_set = 0;                          // the set the next super step records
+  bool ev_pending[2] = {false, false};     // recorded, not yet added to phase_ms
   // permutation+prep, thresholds, rebuild, whole step, the first pass's
   // kernel of each size class, the retry passes, the in-order pass
   double phase_ms[kTimings] = {};
@@ -229,6 +233,7 @@ int export_sorted_pairs(Graph* h, int32_t* pairs);
 
 // trade.cu
 int super_step(Graph* h);
+int flush_timing(Graph* h, int set, bool add);   // wait for a recorded event set; add it to phase_ms
 int init_trade_kernels(Graph* h);   // one-time kernel attributes (outside stream capture)
 size_t trade_ws_slice_bytes(int64_t max_trade);
 

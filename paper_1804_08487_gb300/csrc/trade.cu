@@ -2071,10 +2071,16 @@ int super_step(Graph* h) {
   if (h->g >= 0xfffffffeull) return fail(h, CB_ERANGE, "super-step counter exhausted");
   cudaStream_t s = h->stream;
   const int nxt = 1 - h->cur;
-  if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[0], s));
+  const int eset = h->ev_set;
+  cudaEvent_t* ev = h->ev[eset];
+  if (h->timing && h->ev_pending[eset]) {
+    const int frc = flush_timing(h, eset, true);
+    if (frc) return frc;
+  }
+  if (h->timing) CB_CUDA(h, cudaEventRecord(ev[0], s));
   int rc = prepare_next(h);
   if (rc) return rc;
-  if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[1], s));
+  if (h->timing) CB_CUDA(h, cudaEventRecord(ev[1], s));
   StepCtx c;
   c.n = h->n;
   c.T = h->T;
@@ -2168,7 +2174,7 @@ int super_step(Graph* h) {
   // events ev[4 + k] .. ev[5 + k] (a class without its own kernel takes none)
   bool time_classes = false;
   auto mark = [&](int k) -> int {
-    if (time_classes) CB_CUDA(h, cudaEventRecord(h->ev[4 + k], s));
+    if (time_classes) CB_CUDA(h, cudaEventRecord(ev[4 + k], s));
     return CB_OK;
   };
   const unsigned wgrid = static_cast<unsigned>(h->num_sms * 8);
@@ -2250,7 +2256,7 @@ int super_step(Graph* h) {
     CB_CUDA(h, cudaGetLastError());
     h->launches += 3;
   }
-  if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[5 + kClasses], s));
+  if (h->timing) CB_CUDA(h, cudaEventRecord(ev[5 + kClasses], s));
   // last pass: the trades still deferred, in index order, waiting on
   // dependencies: over the last list sorted by index when it is short,
   // else by scanning every trade's done flag.  1024-thread CTAs keep large
@@ -2288,7 +2294,7 @@ int super_step(Graph* h) {
     }
     h->launches += 2;
   }
-  if (h->timing) CB_CUDA(h, cudaEventRecord(h->ev[2], s));
+  if (h->timing) CB_CUDA(h, cudaEventRecord(ev[2], s));
   // rebuild: far-trade records, each chunk's first row, then the fix-up in
   // passes over slices of the far trades; its output overwrites this step's
   // adjacency, which phase A no longer needs, and becomes step g+1's
@@ -2323,29 +2329,39 @@ int super_step(Graph* h) {
     std::swap(h->col[0], h->col[1]);   // the step's output is now the other side of the ping-pong
   }
   if (h->timing) {
-    CB_CUDA(h, cudaEventRecord(h->ev[3], s));
-    CB_CUDA(h, cudaEventSynchronize(h->ev[3]));
-    float a = 0, b = 0, d = 0, tot = 0;
-    CB_CUDA(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
-    CB_CUDA(h, cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
-    CB_CUDA(h, cudaEventElapsedTime(&d, h->ev[2], h->ev[3]));
-    CB_CUDA(h, cudaEventElapsedTime(&tot, h->ev[0], h->ev[3]));
-    h->phase_ms[0] += a;
-    h->phase_ms[1] += b;
-    h->phase_ms[2] += d;
-    h->phase_ms[3] += tot;
-    for (int k = 0; k < kClasses; ++k) {
-      float e = 0;
-      CB_CUDA(h, cudaEventElapsedTime(&e, h->ev[4 + k], h->ev[5 + k]));
-      h->phase_ms[4 + k] += e;
-    }
-    float re = 0, io = 0;
-    CB_CUDA(h, cudaEventElapsedTime(&re, h->ev[4 + kClasses], h->ev[5 + kClasses]));
-    CB_CUDA(h, cudaEventElapsedTime(&io, h->ev[5 + kClasses], h->ev[2]));
-    h->phase_ms[4 + kClasses] += re;
-    h->phase_ms[5 + kClasses] += io;
+    CB_CUDA(h, cudaEventRecord(ev[3], s));
+    h->ev_pending[eset] = true;
+    h->ev_set = 1 - eset;
   }
   return finish_step(h);
+}
+
+int flush_timing(Graph* h, int set, bool add) {
+  if (!h->ev_pending[set]) return CB_OK;
+  h->ev_pending[set] = false;
+  cudaEvent_t* ev = h->ev[set];
+  CB_CUDA(h, cudaEventSynchronize(ev[3]));
+  if (!add) return CB_OK;
+  float a = 0, b = 0, d = 0, tot = 0;
+  CB_CUDA(h, cudaEventElapsedTime(&a, ev[0], ev[1]));
+  CB_CUDA(h, cudaEventElapsedTime(&b, ev[1], ev[2]));
+  CB_CUDA(h, cudaEventElapsedTime(&d, ev[2], ev[3]));
+  CB_CUDA(h, cudaEventElapsedTime(&tot, ev[0], ev[3]));
+  h->phase_ms[0] += a;
+  h->phase_ms[1] += b;
+  h->phase_ms[2] += d;
+  h->phase_ms[3] += tot;
+  for (int k = 0; k < kClasses; ++k) {
+    float e = 0;
+    CB_CUDA(h, cudaEventElapsedTime(&e, ev[4 + k], ev[5 + k]));
+    h->phase_ms[4 + k] += e;
+  }
+  float re = 0, io = 0;
+  CB_CUDA(h, cudaEventElapsedTime(&re, ev[4 + kClasses], ev[5 + kClasses]));
+  CB_CUDA(h, cudaEventElapsedTime(&io, ev[5 + kClasses], ev[2]));
+  h->phase_ms[4 + kClasses] += re;
+  h->phase_ms[5 + kClasses] += io;
+  return CB_OK;
 }
 
 }  // namespace cb

@@ -136,11 +136,11 @@ def test_autotune_does_not_change_the_chain():
     plain = Curveball(g.row_ptr, g.col, 5)
     got = tuned.autotune(9)
     assert got["steps"] == 9
-    assert got["tile_max"] in (32, 64, 96, 128)
+    assert got["tile_max"] in (32, 64, 128)
     assert got["block_max"] in (512, 1024, 2048, 128) or got["block_max"] >= got["tile_max"]
-    assert got["smem_max"] in (2048, 4096, 8192)
+    assert got["smem_max"] in (4096, 8192)
     assert got["inorder_threads"] in (256, 1024)
-    assert got["retry_passes"] in (0, 1, 2, 4)
+    assert got["retry_passes"] in (1, 2, 3)
     assert tuned.step == 9
     tuned.set_option("cuda_graph", 1)
     tuned.global_trades(3)
