@@ -182,7 +182,7 @@ def measured_traffic(unit, workload):
 
 
 # the threshold phase's kernel of each size class (cb_timings ms[4 + k])
-CLASS_KERNELS = ["k_phase_a_lanes<8,4>", "k_phase_a_lanes<8,8>", "k_phase_a_lanes<16,8>", "k_phase_a_lanes<32,8>",
+CLASS_KERNELS = ["k_phase_a_lanes<8>", "k_phase_a_lanes<16>", "k_phase_a_warp", "k_phase_a_team<256,64>",
                  "k_phase_a_team<256,128>", "k_phase_a_team<256,256>", "k_phase_a_team<1024,512>",
                  "k_phase_a_team<1024,1024>", "k_phase_a_block<1024>"]
 # algorithmic bytes: a threshold kernel reads each directed entry of its

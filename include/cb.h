@@ -181,7 +181,7 @@ int cb_permutation(cb_handle h, uint64_t g, int32_t* order_out, int mem_kind);
  *          in-order pass when trades were still deferred,
  * out[1] = trades the first pass deferred,
  * out[2] = trades of the first pass on warps or parts of a warp (size
- *          classes 0..3), out[3] = on the larger teams (classes 4..8),
+ *          classes 0..2), out[3] = on the larger teams (classes 3..8),
  * out[4] = trades whose workspace did not fit in shared memory,
  * out[5] = kernel launches issued by the last cb_global_trades or
  *          cb_uniform_trades call,
@@ -217,8 +217,7 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               graph launch per super step [0].  Not while "timing" is on.
  *               The handle's stream must support capture (not the legacy
  *               default stream).  Changing any other option re-records.
- *   "tile_max"  trades up to this size run on warps or parts of a warp
- *               [256]; 0..256.
+ *   "tile_max"  trades up to this size are "small" [128]; 0..128.
  *   "tile_paths" threshold phase of small trades: 2 one warp per trade
  *               with its entries in registers; 1 the flat tile kernel (one
  *               thread per entry, many trades per CTA); 0 the 256-thread
@@ -243,8 +242,8 @@ int cb_timings(cb_handle h, double* ms, int count);
  *   "uniform_threads" CTA size of the executor of cb_uniform_trades: 256
  *               (two CTAs per SM), 512 or 1024 (more threads per hub trade,
  *               fewer trades at once) [1024].
- *   "lane_teams" 1: trades of at most 32 / 64 / 128 entries run on teams
- *               of 8 / 8 / 16 lanes, several per warp; 0: on whole warps [1].
+ *   "lane_teams" 1: trades of at most 32 / 64 entries run on teams of 8 /
+ *               16 lanes, several per warp; 0: on whole warps [1].
  *   "retry_passes" parallel passes over the deferred trades between the
  *               first pass and the in-order pass, each running every deferred
  *               trade whose dependencies have published by then [2]; 0..4.

@@ -829,7 +829,7 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
   }
   drop_step_graphs(h);   // every other option changes what a super step launches
   if (!std::strcmp(key, "tile_max")) {
-    if (value < 0 || value > kTileMaxCap) return fail(h, CB_EINVAL, "tile_max out of range [0, 256]");
+    if (value < 0 || value > kTileMaxCap) return fail(h, CB_EINVAL, "tile_max out of range [0, 128]");
     h->tile_max = static_cast<int>(value);
     return size_trade_workspace(h);
   }
@@ -968,7 +968,7 @@ int cb_autotune(cb_handle h, uint32_t max_steps, int64_t* chosen, int count) {
     int ncand;
   };
   constexpr int kKnobs = 5;
-  Knob knobs[kKnobs] = {{&h->tile_max, {64, 128, 256, 0}, 3},
+  Knob knobs[kKnobs] = {{&h->tile_max, {32, 64, 128, 0}, 3},
                         {&h->block_max, {512, 1024, 2048, 0}, 3},
                         {&h->smem_max, {4096, 8192, 0, 0}, 2},
                         {&h->inorder_threads, {256, 1024, 0, 0}, 2},

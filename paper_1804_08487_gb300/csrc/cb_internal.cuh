@@ -27,7 +27,7 @@ inline bool is_timeout(int32_t e) { return e == kErrResolve || e == kErrStage ||
 struct UniBufs;        // uniform-trade buffers (uniform.cu)
 struct PresenceBufs;   // edge presence record (autocorr.cu)
 
-constexpr int kTileMaxCap = 256;    // largest trade (deg u + deg v) on the warp-level paths
+constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
 constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kBlockMaxDefault = 1024;   // default of the "block_max" option
 constexpr int kSmemMaxCap = 8192;   // largest trade kept in shared memory on the 1024-thread path
@@ -36,7 +36,7 @@ constexpr int kCounters = 96;       // device counters per handle
 // Trade size classes of the threshold phase (one team size each) and the
 // device counters of a super step.
 constexpr int kClasses = 9;
-constexpr int kWarpClasses = 4;     // classes 0..3 run on warps or parts of a warp
+constexpr int kWarpClasses = 3;     // classes 0..2 run on warps or parts of a warp
 constexpr int kCtrClsLen = 0;       // [0, kClasses): trades per class
 constexpr int kCtrClsStart = 10;    // [10, 10 + kClasses): first entry of each class in the class lists
 constexpr int kCtrClaims = 19;      // chunks claimed by the in-order pass
@@ -144,7 +144,7 @@ struct Graph {
   int bucket_cap = 2048;
   int inorder_threads = 1024;   // CTA size of the in-order threshold pass (256 or 1024)
   int retry_passes = 2;         // parallel passes over the deferred trades before the in-order pass
-  int lane_teams = 1;           // trades up to 32 / 64 / 128 entries on teams of 8 / 8 / 16 lanes
+  int lane_teams = 1;           // trades up to 32 / 64 entries on teams of 8 / 16 lanes
   int uni_threads = 1024;       // CTA size of the uniform-trade executor (256, 512 or 1024)
   bool wide_pack = false;       // 16-byte far-trade records even when 8 bytes would do (tests)
   // relaxed global trade: permutations from h(x) = (a x + b) mod p

@@ -852,13 +852,11 @@ __host__ __device__ constexpr int hash_lg_c(int L) {
 
 // One team's workspace: a base address and a compile-time layout for trades
 // of at most LMAX entries and 2^B histogram bins.
-template <int LMAX, int B, int SLOTS = 4>
+template <int LMAX, int B>
 struct RegWs {
   static_assert(B >= 5, "tables are cleared in 16-byte stores");
-  static_assert(SLOTS == 2 || SLOTS == 4, "hash slots per entry");
   static constexpr int kLmax = LMAX;
-  static constexpr int kSlotsLg = SLOTS == 4 ? 2 : 1;         // log2 of the hash slots per entry
-  static constexpr int kH = 1 << hash_lg_c(SLOTS / 2 * LMAX);   // at least SLOTS slots per entry
+  static constexpr int kH = 1 << hash_lg_c(2 * LMAX);   // at least 4 slots per entry
   static constexpr size_t kCk = 0;                              // candidate keys
   static constexpr size_t kCtb = kCk + kCand * 8;               // candidate tie-breaks
   static constexpr size_t kSel = kCtb + kCand * 8;              // selection results shared by the team
@@ -967,7 +965,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
   const int64_t ou = c.rp_next[__ldg(c.M + 2 * t)];
   const int64_t ov = tr.single ? 0 : c.rp_next[__ldg(c.M + 2 * t + 1)];
   // at least 4 hash slots per entry, and about one first-digit bin per entry
-  const int lgH = max(5, 32 + Ws::kSlotsLg - __clz(max(L, 2) - 1));   // next power of two >= SLOTS L
+  const int lgH = max(5, 34 - __clz(max(L, 2) - 1));   // next power of two >= 4 L
   const int H = 1 << lgH;
   const int B0 = min(B, max(5, 32 - __clz(max(L - 1, 1))));
   const int NB0 = 1 << B0;
@@ -1327,49 +1325,47 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
 }
 
 // Phase A of small trades, one warp per trade (L <= 32 J): eight independent
-// warps per CTA, each with its own workspace; no CTA barriers.  The list
-// kernels of the retry and in-order passes use the J = 4 warp.
+// warps per CTA, each with its own workspace; no CTA barriers.
 constexpr int kWarpJ = 4;                       // entries per lane: trades up to 128 entries
 constexpr int kWarpB = 7;                       // first radix digit: 128 bins
 constexpr int kWarpWarps = 8;                   // warps per CTA
 using WarpWs = RegWs<32 * kWarpJ, kWarpB>;
 
-// Small trades on teams of W = 8, 16 or 32 lanes holding J = 4 or 8 entries
-// each (L <= W J): 32 / W trades per warp, so the per-trade work (clearing
-// the tables, scans, reductions, the threshold search) takes one warp
-// instruction for all of them, and with J = 8 it is shared by twice the
-// entries.  J = 8 uses 2 hash slots per entry (the warp's insert rounds
-// absorb the extra collisions) so that three CTAs fit an SM.
-template <int W, int J>
+// The smallest trades (L <= W J, W = 8 or 16) on teams of W lanes: 32 / W
+// trades per warp, so the per-trade work (clearing the tables, scans,
+// reductions, the threshold search) takes one warp instruction for all of
+// them.
+template <int W>
 struct LaneCfg {
-  static constexpr int kLmax = W * J;
-  static constexpr int B = kLmax <= 32 ? 5 : kLmax <= 64 ? 6 : kLmax <= 128 ? 7 : 8;   // ~1 bin per entry
-  using Ws = RegWs<kLmax, B, J == 8 ? 2 : 4>;
+  static constexpr int B = W == 8 ? 5 : 6;   // ~1 first-digit bin per entry
+  using Ws = RegWs<W * kWarpJ, B>;
   static constexpr int kTeams = 32 * kWarpWarps / W;   // teams per CTA
   static constexpr size_t kSmem = Ws::kBytes * kTeams;
-  static constexpr int kMinBlocks = J == 8 ? 3 : 4;
 };
 template <int W>
-struct LaneTeamOf {
-  using T = LaneTeam<W>;
-};
-template <>
-struct LaneTeamOf<32> {
-  using T = WarpTeam;
-};
-template <int W, int J>
-__global__ void __launch_bounds__(32 * kWarpWarps, LaneCfg<W, J>::kMinBlocks)
-    k_phase_a_lanes(StepCtx c, const int32_t* __restrict__ lists, const int64_t* __restrict__ ctr, int cls) {
-  using Cfg = LaneCfg<W, J>;
-  using Team = typename LaneTeamOf<W>::T;
+__global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_lanes(StepCtx c, const int32_t* __restrict__ lists,
+                                                                   const int64_t* __restrict__ ctr, int cls) {
+  using Cfg = LaneCfg<W>;
   extern __shared__ __align__(16) char lsm[];
   const int id = threadIdx.x / W;
   const typename Cfg::Ws w{lsm + Cfg::Ws::kBytes * id};
-  Team tm;
+  LaneTeam<W> tm;
   const ClassList cl = class_list(lists, ctr, cls);
   const int64_t step = static_cast<int64_t>(gridDim.x) * Cfg::kTeams;
   for (int64_t q = static_cast<int64_t>(blockIdx.x) * Cfg::kTeams + id; q < cl.len; q += step)
-    phase_a_reg<Team, J, Cfg::B, true>(tm, c, cl.list[q], w);
+    phase_a_reg<LaneTeam<W>, kWarpJ, Cfg::B, true>(tm, c, cl.list[q], w);
+}
+
+__global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_warp(StepCtx c, const int32_t* __restrict__ lists,
+                                                                  const int64_t* __restrict__ ctr, int cls) {
+  extern __shared__ __align__(16) char wsm[];
+  const int wid = threadIdx.x >> 5;
+  const WarpWs w{wsm + WarpWs::kBytes * wid};
+  WarpTeam tm;
+  const ClassList cl = class_list(lists, ctr, cls);
+  const int64_t step = static_cast<int64_t>(gridDim.x) * kWarpWarps;
+  for (int64_t q = static_cast<int64_t>(blockIdx.x) * kWarpWarps + wid; q < cl.len; q += step)
+    phase_a_reg<WarpTeam, kWarpJ, kWarpB, true>(tm, c, cl.list[q], w);
 }
 
 // Phase A of larger trades: a CTA of CT threads holds CT / NT teams of NT
@@ -1980,10 +1976,10 @@ __global__ void __launch_bounds__(32 * kWarpWarps, 4) k_phase_a_list_warp(StepCt
 // from the back of list[0 .. cap)) gathered and sorted by index in one CTA
 // into list[0 .. n), when n <= kSortListMax (*ok = 1, *n_out = n);
 // otherwise *ok = 0 and the in-order pass scans the done flags instead.
-constexpr int kSortListMax = 4096;
+constexpr int kSortListMax = 16384;   // 64 KB of dynamic shared memory
 __global__ void __launch_bounds__(1024) k_sort_list(int32_t* list, int64_t cap, const unsigned long long* nsmall,
                                                     const unsigned long long* nbig, int64_t* ok, int64_t* n_out) {
-  __shared__ int32_t a[kSortListMax];
+  extern __shared__ __align__(16) int32_t a[];
   __shared__ int64_t red[BlockTeam<1024>::kRedSlots];
   const int64_t ns = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(nsmall));
   const int64_t nb = static_cast<int64_t>(*reinterpret_cast<const volatile unsigned long long*>(nbig));
@@ -2036,30 +2032,24 @@ int init_trade_kernels(Graph* h) {
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, kBigThreads>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(team_smem<kBigThreads, kBigThreads>())));
+  CB_CUDA(h, cudaFuncSetAttribute(k_sort_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(kSortListMax * sizeof(int32_t))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_list<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(std::max(TeamCfg<kMedThreads>::Ws::kBytes,
                                                             ws_a_bytes(kBlockMaxCap)))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_list<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(std::max(TeamCfg<kBigThreads>::Ws::kBytes,
                                                             ws_a_bytes(kSmemMaxCap)))));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(LaneCfg<8, 4>::kSmem)));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(LaneCfg<8, 8>::kSmem)));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(LaneCfg<16, 8>::kSmem)));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(LaneCfg<32, 8>::kSmem)));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(LaneCfg<8>::kSmem)));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(LaneCfg<16>::kSmem)));
   // shared memory, not L1, limits how many CTAs of these kernels an SM holds
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8, 4>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  cudaSharedmemCarveoutMaxShared));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  cudaSharedmemCarveoutMaxShared));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<32, 8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
   return CB_OK;
 }
@@ -2133,14 +2123,13 @@ int super_step(Graph* h) {
     const int lreg = std::min(TeamCfg<kBigThreads>::kMax, h->smem_max);
     const int t3 = h->cta_paths ? std::max(tile_max, std::min(block_max, TeamCfg<256>::kMax)) : block_max;
     const int t5 = h->cta_paths ? std::max(t3, lreg) : t3;
-    // lane teams of 8 lanes (L <= 32 with 4 entries per lane, <= 64 with 8)
-    // and 16 lanes (<= 128), a warp of 8 entries per lane (<= tile_max),
-    // teams of 128 .. 1024 threads, the 1024-thread shared-memory kernel
-    th.th[0] = h->lane_teams ? std::min(LaneCfg<8, 4>::kLmax, tile_max) : 0;
-    th.th[1] = h->lane_teams ? std::min(LaneCfg<8, 8>::kLmax, tile_max) : 0;
-    th.th[2] = h->lane_teams ? std::min(LaneCfg<16, 8>::kLmax, tile_max) : 0;
-    th.th[3] = tile_max;
-    th.th[4] = h->cta_paths ? std::min(std::max(TeamCfg<128>::kMax, tile_max), t3) : tile_max;
+    // lane teams of 8 / 16 (L <= 32 / 64), a warp (L <= tile_max), teams of
+    // 64 .. 1024 threads, the 1024-thread shared-memory kernel
+    th.th[0] = h->lane_teams ? std::min(LaneCfg<8>::Ws::kLmax, tile_max) : 0;
+    th.th[1] = h->lane_teams ? std::min(LaneCfg<16>::Ws::kLmax, tile_max) : 0;
+    th.th[2] = tile_max;
+    th.th[3] = h->cta_paths ? std::min(std::max(TeamCfg<64>::kMax, tile_max), t3) : tile_max;
+    th.th[4] = h->cta_paths ? std::min(std::max(TeamCfg<128>::kMax, th.th[3]), t3) : tile_max;
     th.th[5] = t3;
     th.th[6] = h->cta_paths ? std::min(std::max(TeamCfg<512>::kMax, t3), t5) : t3;
     th.th[7] = t5;
@@ -2194,18 +2183,18 @@ int super_step(Graph* h) {
     int r;
     if ((r = mark(0))) return r;
     if (h->lane_teams) {
-      k_phase_a_lanes<8, 4><<<wgrid, 32 * kWarpWarps, LaneCfg<8, 4>::kSmem, s>>>(c, L, cnt, 0);
+      k_phase_a_lanes<8><<<wgrid, 32 * kWarpWarps, LaneCfg<8>::kSmem, s>>>(c, L, cnt, 0);
       if ((r = launched()) || (r = mark(1))) return r;
-      k_phase_a_lanes<8, 8><<<wgrid, 32 * kWarpWarps, LaneCfg<8, 8>::kSmem, s>>>(c, L, cnt, 1);
+      k_phase_a_lanes<16><<<wgrid, 32 * kWarpWarps, LaneCfg<16>::kSmem, s>>>(c, L, cnt, 1);
       if ((r = launched()) || (r = mark(2))) return r;
-      k_phase_a_lanes<16, 8><<<wgrid, 32 * kWarpWarps, LaneCfg<16, 8>::kSmem, s>>>(c, L, cnt, 2);
-      if ((r = launched()) || (r = mark(3))) return r;
-    } else if ((r = mark(1)) || (r = mark(2)) || (r = mark(3))) {
+    } else if ((r = mark(1)) || (r = mark(2))) {
       return r;
     }
-    k_phase_a_lanes<32, 8><<<wgrid, 32 * kWarpWarps, LaneCfg<32, 8>::kSmem, s>>>(c, L, cnt, 3);
-    if ((r = launched()) || (r = mark(4))) return r;
+    k_phase_a_warp<<<wgrid, 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(c, L, cnt, 2);
+    if ((r = launched()) || (r = mark(3))) return r;
     if (h->cta_paths) {
+      k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 3);
+      if ((r = launched()) || (r = mark(4))) return r;
       k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 4);
       if ((r = launched()) || (r = mark(5))) return r;
       k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 5);
@@ -2270,17 +2259,18 @@ int super_step(Graph* h) {
   }
   if (h->timing) CB_CUDA(h, cudaEventRecord(ev[5 + kClasses], s));
   // last pass: the trades still deferred, in index order, waiting on
-  // dependencies: over the last list sorted by index when it is short,
-  // else by scanning every trade's done flag.  1024-thread CTAs keep large
-  // trades in shared memory; 256-thread CTAs (four per SM) run many small
-  // deferred trades at once, large ones from a global slice.
+  // dependencies: over the last list sorted by index when it holds at most
+  // kSortListMax trades, else by scanning every trade's done flag.
+  // 1024-thread CTAs keep large trades in shared memory; 256-thread CTAs
+  // (four per SM) run many small deferred trades at once, large ones from a
+  // global slice.
   {
     const int R = h->retry_passes;
     int32_t* last = h->dlist + (R & 1) * ntasks;
     int64_t* ok = cnt + kCtrListOk;
     const unsigned long long* nlast = ucnt + kCtrListN;
-    k_sort_list<<<1, 1024, 0, s>>>(last, ntasks, ucnt + kCtrPassSmall + R, ucnt + kCtrPassBig + R, ok,
-                                   cnt + kCtrListN);
+    k_sort_list<<<1, 1024, kSortListMax * sizeof(int32_t), s>>>(last, ntasks, ucnt + kCtrPassSmall + R,
+                                                               ucnt + kCtrPassBig + R, ok, cnt + kCtrListN);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
     c.wait = 1;
