@@ -239,7 +239,7 @@ int finish_create(Graph* h) {
   h->m = nnz / 2;
   h->T = n / 2;
   h->ntasks = h->T + (n & 1);
-  if ((rc = init_trade_kernels(h))) return rc;
+  if ((rc = init_trade_kernels(h)) || (rc = init_perm_kernels(h))) return rc;
   if ((rc = check_row_offsets(h, h->rp_id, n))) return rc;
   {
     unsigned long long* dmax = reinterpret_cast<unsigned long long*>(h->counters);
@@ -924,7 +924,7 @@ int cb_set_option(cb_handle h, const char* key, int64_t value) {
     return CB_OK;
   }
   if (!std::strcmp(key, "bucket_cap")) {
-    if (value < 2 || value > 4096) return fail(h, CB_EINVAL, "bucket_cap out of range [2, 4096]");
+    if (value < 2 || value > kBucketCapMax) return fail(h, CB_EINVAL, "bucket_cap out of range [2, 4096]");
     h->bucket_cap = static_cast<int>(value);
     return CB_OK;
   }

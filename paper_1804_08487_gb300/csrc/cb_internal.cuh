@@ -27,6 +27,7 @@ inline bool is_timeout(int32_t e) { return e == kErrResolve || e == kErrStage ||
 struct UniBufs;        // uniform-trade buffers (uniform.cu)
 struct PresenceBufs;   // edge presence record (autocorr.cu)
 
+constexpr int kBucketCapMax = 4096;  // largest "bucket_cap"
 constexpr int kTileMaxCap = 128;    // largest trade (deg u + deg v) on the flat tile path
 constexpr int kBlockMaxCap = 2048;  // largest trade on the 256-thread path
 constexpr int kBlockMaxDefault = 1024;   // default of the "block_max" option
@@ -235,6 +236,7 @@ int export_sorted_pairs(Graph* h, int32_t* pairs);
 int super_step(Graph* h);
 int flush_timing(Graph* h, int set, bool add);   // wait for a recorded event set; add it to phase_ms
 int init_trade_kernels(Graph* h);   // one-time kernel attributes (outside stream capture)
+int init_perm_kernels(Graph* h);
 size_t trade_ws_slice_bytes(int64_t max_trade);
 
 // api.cu

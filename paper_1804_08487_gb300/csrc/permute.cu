@@ -169,13 +169,32 @@ __device__ __forceinline__ bool pair_less(uint64_t ka, int32_t ia, uint64_t kb, 
   return ka < kb || (ka == kb && ia < ib);
 }
 
-// One CTA per bucket: bitonic sort of (key, id) pairs in shared memory.
+// One CTA per bucket.  A bucket's keys agree on their leading bits and are
+// uniform below them, so a counting sort on the kSubBits bits below the
+// highest bit where they differ leaves about one key per bin for buckets of
+// up to ~kSubBins keys (keys agree above that bit, so the digit orders them);
+// keys sharing a bin are ranked by comparing (key, id) with each other.
+constexpr int kSubBits = 10;
+constexpr int kSubBins = 1 << kSubBits;
+// dynamic shared memory: keys, ids, bin starts (+1), bin cursors, and each
+// bin slot's element
+size_t bucket_smem_bytes(int cap_pow2) {
+  return static_cast<size_t>(cap_pow2) * (sizeof(uint64_t) + sizeof(int32_t) + sizeof(uint16_t)) +
+         (2 * kSubBins + 1) * sizeof(int32_t);
+}
 __global__ void __launch_bounds__(kPermThreads) k_bucket_sort(
     int nb, const int64_t* __restrict__ boff, const uint64_t* __restrict__ bkey,
     const int32_t* __restrict__ bid, int cap, int32_t* __restrict__ order,
     int32_t* __restrict__ pos, int32_t* __restrict__ overflow, int cap_pow2) {
   extern __shared__ uint64_t shk[];
-  int32_t* shi = reinterpret_cast<int32_t*>(shk + cap_pow2);   // padding up to cap_pow2 fits
+  int32_t* shi = reinterpret_cast<int32_t*>(shk + cap_pow2);
+  int32_t* bstart = shi + cap_pow2;        // kSubBins + 1
+  int32_t* bcur = bstart + kSubBins + 1;   // kSubBins
+  uint16_t* slot = reinterpret_cast<uint16_t*>(bcur + kSubBins);   // cap_pow2
+  __shared__ unsigned long long s_or, s_and;
+  __shared__ int wsum[kPermThreads / 32];
+  constexpr int kPer = kSubBins / kPermThreads;   // bins per thread in the scan
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     const int64_t o = boff[b];
     const int64_t bs = boff[b + 1] - o;
@@ -185,32 +204,76 @@ __global__ void __launch_bounds__(kPermThreads) k_bucket_sort(
       continue;
     }
     if (s == 0) continue;
-    int P = 1;
-    while (P < s) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-      shk[i] = i < s ? bkey[o + i] : ~0ull;
-      shi[i] = i < s ? bid[o + i] : 0x7fffffff;
+    if (threadIdx.x == 0) {
+      s_or = 0ull;
+      s_and = ~0ull;
+    }
+    for (int i = threadIdx.x; i < kSubBins; i += kPermThreads) bcur[i] = 0;
+    __syncthreads();
+    unsigned long long lor = 0ull, land = ~0ull;
+    for (int i = threadIdx.x; i < s; i += kPermThreads) {
+      const uint64_t k = bkey[o + i];
+      shk[i] = k;
+      shi[i] = bid[o + i];
+      lor |= k;
+      land &= k;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      lor |= __shfl_xor_sync(0xffffffffu, lor, off);
+      land &= __shfl_xor_sync(0xffffffffu, land, off);
+    }
+    if (lane == 0) {
+      atomicOr(&s_or, lor);
+      atomicAnd(&s_and, land);
     }
     __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-          const int l = i ^ j;
-          if (l > i) {
-            const uint64_t ka = shk[i], kb = shk[l];
-            const int32_t ia = shi[i], ib = shi[l];
-            const bool up = (i & k) == 0;
-            if (pair_less(kb, ib, ka, ia) == up) {
-              shk[i] = kb; shk[l] = ka; shi[i] = ib; shi[l] = ia;
-            }
-          }
-        }
-        __syncthreads();
-      }
+    const uint64_t diff = s_or ^ s_and;            // the bits where the bucket's keys differ
+    const int top = diff ? 63 - __clzll(static_cast<long long>(diff)) : 0;
+    const int sh = top + 1 > kSubBits ? top + 1 - kSubBits : 0;
+    for (int i = threadIdx.x; i < s; i += kPermThreads)
+      atomicAdd(&bcur[static_cast<int>(shk[i] >> sh) & (kSubBins - 1)], 1);
+    __syncthreads();
+    // exclusive scan of the bin counts: kPer consecutive bins per thread
+    int local = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) local += bcur[threadIdx.x * kPer + q];
+    int incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
     }
-    for (int i = threadIdx.x; i < s; i += blockDim.x) {
-      order[o + i] = shi[i];
-      if (pos) pos[shi[i]] = static_cast<int32_t>(o + i);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int run = incl - local;
+    for (int w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int bi = threadIdx.x * kPer + q;
+      const int c = bcur[bi];
+      bstart[bi] = run;
+      bcur[bi] = run;   // now the bin's cursor
+      run += c;
+    }
+    if (threadIdx.x == 0) bstart[kSubBins] = s;
+    __syncthreads();
+    for (int i = threadIdx.x; i < s; i += kPermThreads)
+      slot[atomicAdd(&bcur[static_cast<int>(shk[i] >> sh) & (kSubBins - 1)], 1)] = static_cast<uint16_t>(i);
+    __syncthreads();
+    // rank within the bin: the bin's start plus the smaller (key, id) in it
+    for (int i = threadIdx.x; i < s; i += kPermThreads) {
+      const uint64_t ki = shk[i];
+      const int32_t ii = shi[i];
+      const int d = static_cast<int>(ki >> sh) & (kSubBins - 1);
+      const int st = bstart[d], en = bstart[d + 1];
+      int r = st;
+      for (int q = st; q < en; ++q) {
+        const int j = slot[q];
+        r += (j != i && pair_less(shk[j], shi[j], ki, ii)) ? 1 : 0;
+      }
+      order[o + r] = ii;
+      if (pos) pos[ii] = static_cast<int32_t>(o + r);
     }
     __syncthreads();
   }
@@ -285,6 +348,14 @@ size_t perm_ws_bytes(int64_t n, int64_t nb) {
          align_up(sizeof(int32_t) * n) + scan_ws_bytes(nb + 1) + 256;
 }
 
+// The bucket sort's shared memory for the largest "bucket_cap" (set once,
+// outside any stream capture).
+int init_perm_kernels(Graph* h) {
+  CB_CUDA(h, cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(bucket_smem_bytes(kBucketCapMax))));
+  return CB_OK;
+}
+
 int compute_permutation(Graph* h, uint32_t dg, int64_t g_abs, int32_t* order_out, int32_t* pos_out) {
   const int64_t n = h->n;
   if (n == 0) return CB_OK;
@@ -327,7 +398,7 @@ int compute_permutation(Graph* h, uint32_t dg, int64_t g_abs, int32_t* order_out
   const int cap = h->bucket_cap;
   int cap_pow2 = 1;
   while (cap_pow2 < cap) cap_pow2 <<= 1;
-  const size_t ssm = static_cast<size_t>(cap_pow2) * (sizeof(uint64_t) + sizeof(int32_t));
+  const size_t ssm = bucket_smem_bytes(cap_pow2);
   const unsigned sgrid = static_cast<unsigned>(nb < h->num_sms * 8 ? nb : h->num_sms * 8);
   k_bucket_sort<<<sgrid, kPermThreads, ssm, s>>>(static_cast<int>(nb), w.boff, w.bkey, w.bid, cap, order_out, pos_out,
                                                 w.overflow, cap_pow2);
@@ -426,7 +497,7 @@ extern "C" int cb_permutation_static(int64_t n, uint64_t seed, uint64_t g, int32
   k_perm_scatter<<<grid, kPermThreads, 0, s>>>(n, ks, w.boff, w.cursor, w.bkey, w.bid);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_perm_scatter");
   const int cap = 2048;
-  const size_t ssm = static_cast<size_t>(cap) * (sizeof(uint64_t) + sizeof(int32_t));
+  const size_t ssm = bucket_smem_bytes(cap);
   const unsigned sgrid = static_cast<unsigned>(nb < num_sms * 8 ? nb : num_sms * 8);
   k_bucket_sort<<<sgrid, kPermThreads, ssm, s>>>(nb, w.boff, w.bkey, w.bid, cap, order_out, nullptr, w.overflow, cap);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "k_bucket_sort");
