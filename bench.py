@@ -165,7 +165,13 @@ def workload(name):
 # every launch of the unit in one super step) of the dominant unit of a
 # workload, and the sha256 of csrc/trade.cu the capture ran on; a unit whose
 # code changed since reports no traffic.  profiles/ holds the captures.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/rebuild_traffic_n2p25.md: mean of four super steps
+    ("rebuild phase (k_far_pack, k_chunk_rows, k_fixup passes)", "n2^25"): {
+        "bytes": 92507463040,
+        "trade_cu_sha256": "520f84d6e7f3b642fd77ef6bd40099d5bb9a66b709ef7f81e7dd394349543297",
+    },
+}
 
 
 def measured_traffic(unit, workload):
