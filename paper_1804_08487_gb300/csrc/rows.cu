@@ -334,86 +334,6 @@ __device__ void sort_above(Team& tm, const AboveArgs& a, int64_t x, int32_t* buf
   tm.sync();
 }
 
-// Rows of more than kRowWarpMax entries above the diagonal, in shared memory:
-// the values (distinct node ids) compacted into buf, then a counting sort on
-// the bins_lg bits below the highest bit where they differ (the values agree
-// above it, so the digit orders them) and a rank within each bin, written
-// straight to the value's pair.  Shared memory after buf (cap ints): bin
-// starts (bins + 1), bin cursors (bins), each bin slot's value index (cap
-// uint16).
-constexpr int kAboveMidBins = 11;   // rows up to 2048 values: about one per bin
-constexpr int kAboveBigBins = 13;   // rows up to kRowBlockSmem values
-size_t above_smem_bytes(int cap, int bins_lg) {
-  return static_cast<size_t>(cap) * (4 + 2) + ((size_t(2) << bins_lg) + 1) * 4;
-}
-template <int NT>
-__device__ void count_sort_above(BlockTeam<NT>& tm, const AboveArgs& a, int64_t x, int32_t* buf, int cap,
-                                 int bins_lg, unsigned* s_or, unsigned* s_and) {
-  const int bins = 1 << bins_lg;
-  int32_t* bstart = buf + cap;
-  int32_t* bcur = bstart + bins + 1;
-  uint16_t* slot = reinterpret_cast<uint16_t*>(bcur + bins);
-  const int64_t b = a.rp[x], len = a.rp[x + 1] - b;
-  const int c = a.cnt[x];
-  int64_t base = 0;
-  for (int64_t r0 = 0; r0 < len; r0 += NT) {
-    const int64_t i = r0 + tm.rank;
-    const int32_t v = i < len ? a.col[b + i] : -1;
-    const bool up = v > x;
-    const int64_t pos = tm.exscan(up ? 1 : 0);
-    if (up && base + pos < c) buf[base + pos] = v;
-    base += tm.sum(up ? 1 : 0);
-  }
-  if (base != c && tm.rank == 0) latch(a.err, kErrRowLength);
-  if (tm.rank == 0) {
-    *s_or = 0u;
-    *s_and = ~0u;
-  }
-  for (int i = tm.rank; i < bins; i += NT) bcur[i] = 0;
-  tm.sync();
-  unsigned lor = 0u, land = ~0u;
-  for (int i = tm.rank; i < c; i += NT) {
-    lor |= static_cast<unsigned>(buf[i]);
-    land &= static_cast<unsigned>(buf[i]);
-  }
-  atomicOr(s_or, lor);
-  atomicAnd(s_and, land);
-  tm.sync();
-  const unsigned diff = *s_or ^ *s_and;
-  const int top = diff ? 31 - __clz(static_cast<int>(diff)) : 0;
-  const int sh = top + 1 > bins_lg ? top + 1 - bins_lg : 0;
-  for (int i = tm.rank; i < c; i += NT) atomicAdd(&bcur[(buf[i] >> sh) & (bins - 1)], 1);
-  tm.sync();
-  // exclusive scan of the bin counts, bins / NT consecutive bins per thread
-  const int per = bins / NT;
-  int local = 0;
-  for (int q = 0; q < per; ++q) local += bcur[tm.rank * per + q];
-  int run = static_cast<int>(tm.exscan(local));
-  for (int q = 0; q < per; ++q) {
-    const int bi = tm.rank * per + q;
-    const int cnt = bcur[bi];
-    bstart[bi] = run;
-    bcur[bi] = run;
-    run += cnt;
-  }
-  if (tm.rank == 0) bstart[bins] = c;
-  tm.sync();
-  for (int i = tm.rank; i < c; i += NT)
-    slot[atomicAdd(&bcur[(buf[i] >> sh) & (bins - 1)], 1)] = static_cast<uint16_t>(i);
-  tm.sync();
-  const int32_t sb = a.seg_of ? static_cast<int32_t>(a.segs[a.seg_of[x]].off) : 0;
-  const int64_t o = a.off[x];
-  for (int i = tm.rank; i < c; i += NT) {
-    const int32_t v = buf[i];
-    const int d = (v >> sh) & (bins - 1);
-    int r = bstart[d];
-    for (int q = bstart[d]; q < bstart[d + 1]; ++q) r += buf[slot[q]] < v;
-    a.pairs[2 * (o + r)] = static_cast<int32_t>(x) - sb;
-    a.pairs[2 * (o + r) + 1] = v - sb;
-  }
-  tm.sync();
-}
-
 // rows with at most kRowWarpMax entries above the diagonal: one warp each
 __global__ void __launch_bounds__(256) k_above_warp(AboveArgs a) {
   __shared__ int32_t buf[8][kRowWarpMax];
@@ -424,20 +344,17 @@ __global__ void __launch_bounds__(256) k_above_warp(AboveArgs a) {
     if (a.cnt[x] <= kRowWarpMax) sort_above(tm, a, x, buf[w]);
 }
 
-// rows with lo < entries above the diagonal <= hi: one CTA each, counting
-// sort in shared memory up to `cap` values, above that a bitonic sort in a
-// global slice per CTA
-__global__ void __launch_bounds__(256) k_above_block(AboveArgs a, int lo, int64_t hi, int cap, int bins_lg,
-                                                     int32_t* gws, int64_t slice) {
+// rows with lo < entries above the diagonal <= hi: one CTA each, in `cap`
+// ints of shared memory or, above that, a global slice per CTA
+__global__ void __launch_bounds__(256) k_above_block(AboveArgs a, int lo, int64_t hi, int cap, int32_t* gws,
+                                                     int64_t slice) {
   extern __shared__ int32_t sbuf[];
   __shared__ int64_t red[BlockTeam<256>::kRedSlots];
-  __shared__ unsigned s_or, s_and;
   BlockTeam<256> tm(red);
   for (int64_t x = blockIdx.x; x < a.n; x += gridDim.x) {
     const int c = a.cnt[x];
     if (c <= lo || c > hi) continue;
-    if (c <= cap) count_sort_above(tm, a, x, sbuf, cap, bins_lg, &s_or, &s_and);
-    else sort_above(tm, a, x, gws + slice * blockIdx.x);
+    sort_above(tm, a, x, c <= cap ? sbuf : gws + slice * blockIdx.x);
   }
 }
 
@@ -590,10 +507,7 @@ int export_sorted_pairs(Graph* h, int32_t* pairs) {
   h->launches += 2;
   if (h->maxdeg > kRowWarpMax) {
     constexpr int kMid = 2048;
-    const size_t mid_smem = above_smem_bytes(kMid, kAboveMidBins);
-    CB_CUDA(h, cudaFuncSetAttribute(k_above_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(above_smem_bytes(kRowBlockSmem, kAboveBigBins))));
-    k_above_block<<<h->num_sms * 8, 256, mid_smem, s>>>(a, kRowWarpMax, kMid, kMid, kAboveMidBins, nullptr, 0);
+    k_above_block<<<h->num_sms * 8, 256, kMid * 4, s>>>(a, kRowWarpMax, kMid, kMid, nullptr, 0);
     CB_CUDA(h, cudaGetLastError());
     ++h->launches;
     if (h->maxdeg > kMid) {
@@ -607,8 +521,9 @@ int export_sorted_pairs(Graph* h, int32_t* pairs) {
         ctas = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ctas, budget / (slice * 4))));
         gws = static_cast<int32_t*>(h->ws_global);
       }
-      k_above_block<<<ctas, 256, above_smem_bytes(kRowBlockSmem, kAboveBigBins), s>>>(
-          a, kMid, INT64_MAX, kRowBlockSmem, kAboveBigBins, gws, slice);
+      CB_CUDA(h, cudaFuncSetAttribute(k_above_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kRowBlockSmem * 4));
+      k_above_block<<<ctas, 256, kRowBlockSmem * 4, s>>>(a, kMid, INT64_MAX, kRowBlockSmem, gws, slice);
       CB_CUDA(h, cudaGetLastError());
       ++h->launches;
     }
