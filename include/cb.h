@@ -217,12 +217,10 @@ int cb_timings(cb_handle h, double* ms, int count);
  *               graph launch per super step [0].  Not while "timing" is on.
  *               The handle's stream must support capture (not the legacy
  *               default stream).  Changing any other option re-records.
- *   "tile_max"  trades up to this size are "small" [128]; 0..128.
- *   "tile_paths" threshold phase of small trades: 2 one warp per trade
- *               with its entries in registers; 1 the flat tile kernel (one
- *               thread per entry, many trades per CTA); 0 the 256-thread
- *               kernel [2].  (The rebuild phase is one flat pass over all
- *               entries.)
+ *   "tile_max"  trades up to this size run on warps or parts of a warp
+ *               [128]; 0..128.
+ *   "tile_paths" 1: trades up to tile_max entries run on warps or parts of
+ *               a warp (see "lane_teams"); 0: on the larger teams [1].
  *   "block_max" trades up to this size run on a 256-thread CTA [1024];
  *               0..2048 (values below tile_max act as tile_max).
  *   "smem_max"  larger trades run on a 1024-thread CTA; with "cta_paths" 1
