@@ -168,8 +168,8 @@ def workload(name):
 MEASURED_TRAFFIC = {
     # profiles/rebuild_traffic_n2p25.md: mean of four super steps
     ("rebuild phase (k_far_pack, k_chunk_rows, k_fixup passes)", "n2^25"): {
-        "bytes": 92507463040,
-        "trade_cu_sha256": "520f84d6e7f3b642fd77ef6bd40099d5bb9a66b709ef7f81e7dd394349543297",
+        "bytes": 92497908608,
+        "trade_cu_sha256": "b26e86e52a3e925cb543617e951618e52e686e1993c7813d8156c38d44c58c1f",
     },
 }
 

@@ -34,6 +34,7 @@
 // 256-thread CTA, larger ones one per 1024-thread CTA with up to `smem_max`
 // entries in shared memory (a global-memory slice above that).
 #include <algorithm>
+#include <type_traits>
 
 #include "cb_internal.cuh"
 #include "philox.cuh"
@@ -84,6 +85,7 @@ struct StepCtx {
   int cand_max;                    // register paths: most candidates ranked directly (else more radix digits)
   uint64_t wait_ns;                // longest single wait on a dependency or a bulk copy
   int hold_publish;                // test hook: no trade publishes its done flag (waits run out)
+  uint32_t ks[20];                 // one graph (seg_of null): the Philox round keys of its seed
 };
 
 struct SelOut {
@@ -244,11 +246,18 @@ __device__ __forceinline__ KeyCtx key_ctx(const StepCtx& c, int64_t t) {
 }
 
 // Both trades' keys of the edge whose step-start positions are lo < hi.
+// kOneSeed: a handle of one graph, whose seed's round keys are c.ks.
 struct EdgeKeys {
   uint64_t lo_side, hi_side;
 };
-__device__ __forceinline__ EdgeKeys edge_keys(const KeyCtx& kc, uint32_t lo, uint32_t hi) {
-  const Philox4 r = philox4x32_10(lo - kc.off, hi - kc.off, kc.g, 1u, kc.seed);
+template <bool kOneSeed>
+__device__ __forceinline__ EdgeKeys edge_keys(const StepCtx& c, const KeyCtx& kc, uint32_t lo, uint32_t hi) {
+  Philox4 r;
+  if constexpr (kOneSeed) {
+    r = philox4x32_10_rk(lo - kc.off, hi - kc.off, kc.g, 1u, c.ks);
+  } else {
+    r = philox4x32_10(lo - kc.off, hi - kc.off, kc.g, 1u, kc.seed);
+  }
   return {(static_cast<uint64_t>(r.w0) << 32) | r.w1, (static_cast<uint64_t>(r.w2) << 32) | r.w3};
 }
 __device__ __forceinline__ uint64_t side_key(const KeyCtx& kc, uint32_t lo, uint32_t hi, bool lo_side) {
@@ -497,7 +506,7 @@ struct StageNext {
   uint64_t* mbar;
 };
 
-template <class Team>
+template <class Team, bool kOneSeed = false>
 __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, SelOut* sel,
                         const int32_t* ystage = nullptr, StageNext sn = StageNext{false, 0, 0, nullptr, nullptr}) {
   const TradeRows tr = trade_rows(c, t);
@@ -625,7 +634,7 @@ __device__ void phase_a(Team& tm, const StepCtx& c, int64_t t, const WsA& w, Sel
     // both trades' keys of this edge: own 16-bit prefix, far 6-bit prefix
     const uint32_t x = t2u + r, y = 2u * s + colb;
     const uint32_t lo = min(x, y), hi = max(x, y);
-    const EdgeKeys ek = edge_keys(kc, lo, hi);
+    const EdgeKeys ek = edge_keys<kOneSeed>(c, kc, lo, hi);
     const bool lo_mine = (lo >> 1) == t32;
     const uint32_t top = static_cast<uint32_t>((lo_mine ? ek.lo_side : ek.hi_side) >> 48);
     w.top[i] = static_cast<uint16_t>(top);
@@ -953,7 +962,7 @@ __device__ __forceinline__ void entry_lo_hi(uint32_t t2u, uint32_t m, uint32_t y
   *hi = max(x, y);
 }
 
-template <class Team, int J, int B, bool kKeepKey, class Ws>
+template <class Team, int J, int B, bool kKeepKey, bool kOneSeed = false, class Ws>
 __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) {
   static_assert(Team::N <= 2048 && Team::N * J < (1 << 20), "reduction fields: 20-bit count, 12-bit flags");
   constexpr int NB = 1 << B;
@@ -1092,7 +1101,7 @@ __device__ void phase_a_reg(Team& tm, const StepCtx& c, int64_t t, const Ws& w) 
     // both trades' keys of this edge (step-start positions)
     const uint32_t x = t2u + r, yb = y[j];
     const uint32_t lo = min(x, yb), hi = max(x, yb);
-    const EdgeKeys ek = edge_keys(kc, lo, hi);
+    const EdgeKeys ek = edge_keys<kOneSeed>(c, kc, lo, hi);
     const bool lo_mine = (lo >> 1) == t32;
     const uint64_t own = lo_mine ? ek.lo_side : ek.hi_side;
     const uint64_t far = lo_mine ? ek.hi_side : ek.lo_side;
@@ -1378,7 +1387,7 @@ struct TeamCfg {
   using Ws = RegWs<NT * kTeamJ, B>;
   static constexpr int kMax = NT * kTeamJ;
 };
-template <int CT, int NT>
+template <int CT, int NT, bool kOneSeed>
 __global__ void __launch_bounds__(CT, CT == 256 ? 4 : 1) k_phase_a_team(StepCtx c, const int32_t* __restrict__ lists,
                                                                       const int64_t* __restrict__ ctr, int cls) {
   constexpr int kTeams = CT / NT;
@@ -1391,7 +1400,7 @@ __global__ void __launch_bounds__(CT, CT == 256 ? 4 : 1) k_phase_a_team(StepCtx 
   const ClassList cl = class_list(lists, ctr, cls);
   const int64_t step = static_cast<int64_t>(gridDim.x) * kTeams;
   for (int64_t q = static_cast<int64_t>(blockIdx.x) * kTeams + id; q < cl.len; q += step)
-    phase_a_reg<SubTeam<NT>, kTeamJ, TeamCfg<NT>::B, false>(tm, c, cl.list[q], w);
+    phase_a_reg<SubTeam<NT>, kTeamJ, TeamCfg<NT>::B, false, kOneSeed>(tm, c, cl.list[q], w);
 }
 template <int CT, int NT>
 constexpr size_t team_smem() {
@@ -1771,7 +1780,7 @@ __global__ void __launch_bounds__(kFixThreads, 4) k_fixup(StepCtx c, int64_t nnz
 
 // ---------------------------------------------------------------- team paths
 
-template <int NT>
+template <int NT, bool kOneSeed>
 __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx c, const int32_t* __restrict__ lists,
                                                       const int64_t* __restrict__ ctr, int cls, int smem_max,
                                                       char* gws, size_t slice, int stage_cap) {
@@ -1836,7 +1845,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 4 : 1) k_phase_a_block(StepCtx
       }
       ys = stage + stage_off(tr.b0);
     }
-    phase_a(tm, c, t, carve_a(base, L), &sel, ys, sn);
+    phase_a<BlockTeam<NT>, kOneSeed>(tm, c, t, carve_a(base, L), &sel, ys, sn);
   }
   if (failed) {   // a copy did not complete in time: report, let it land, leave
     if (threadIdx.x == 0) latch(c.err, kErrStage);
@@ -2017,21 +2026,35 @@ int finish_step(Graph* h) {
 
 }  // namespace
 
+namespace {
+// Attributes of the kernels built in a one-graph and a general version.
+template <bool kOneSeed>
+int init_seed_kernels(Graph* h) {
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads, kOneSeed>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(block_smem_bytes(kBlockMaxCap))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads, kOneSeed>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(block_smem_bytes(kSmemMaxCap))));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, 512, kOneSeed>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(team_smem<kBigThreads, 512>())));
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, kBigThreads, kOneSeed>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(team_smem<kBigThreads, kBigThreads>())));
+  // shared memory, not L1, limits how many CTAs of this kernel an SM holds
+  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads, kOneSeed>,
+                                  cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+  return CB_OK;
+}
+}  // namespace
+
 int init_trade_kernels(Graph* h) {
   // the largest dynamic shared memory any handle may ask of each kernel
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(block_smem_bytes(kBlockMaxCap))));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(block_smem_bytes(kSmemMaxCap))));
+  int rc = init_seed_kernels<true>(h);
+  if (rc || (rc = init_seed_kernels<false>(h))) return rc;
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kBlockMaxCap))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_inorder<kBigThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(ws_a_bytes(kSmemMaxCap))));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(team_smem<kBigThreads, 512>())));
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_team<kBigThreads, kBigThreads>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(team_smem<kBigThreads, kBigThreads>())));
   CB_CUDA(h, cudaFuncSetAttribute(k_sort_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(kSortListMax * sizeof(int32_t))));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_list<kMedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2045,8 +2068,6 @@ int init_trade_kernels(Graph* h) {
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(LaneCfg<16>::kSmem)));
   // shared memory, not L1, limits how many CTAs of these kernels an SM holds
-  CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_block<kMedThreads>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  cudaSharedmemCarveoutMaxShared));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<8>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared));
   CB_CUDA(h, cudaFuncSetAttribute(k_phase_a_lanes<16>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -2100,6 +2121,7 @@ int super_step(Graph* h) {
   c.err = h->err;
   c.M = h->M;
   c.rp_next = h->rp[nxt];
+  philox_round_keys(h->hsegs[0].seed, c.ks);   // used only when the handle holds one graph
   // counters (kCtr* in cb_internal.cuh): class lists, the first pass's class
   // sizes, deferrals per pass, chunks claimed by the in-order pass,
   // global-workspace trades
@@ -2179,7 +2201,10 @@ int super_step(Graph* h) {
     return CB_OK;
   };
   const unsigned wgrid = static_cast<unsigned>(h->num_sms * 8);
-  auto run_classes = [&]() -> int {
+  // the team and shared-memory kernels come in a one-graph version (the
+  // seed's Philox round keys in the kernel parameters) and a general one
+  auto run_classes_as = [&](auto one_seed) -> int {
+    constexpr bool kOne = decltype(one_seed)::value;
     int r;
     if ((r = mark(0))) return r;
     if (h->lane_teams) {
@@ -2193,30 +2218,34 @@ int super_step(Graph* h) {
     k_phase_a_warp<<<wgrid, 32 * kWarpWarps, WarpWs::kBytes * kWarpWarps, s>>>(c, L, cnt, 2);
     if ((r = launched()) || (r = mark(3))) return r;
     if (h->cta_paths) {
-      k_phase_a_team<256, 64><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 3);
+      k_phase_a_team<256, 64, kOne><<<mgrid, 256, team_smem<256, 64>(), s>>>(c, L, cnt, 3);
       if ((r = launched()) || (r = mark(4))) return r;
-      k_phase_a_team<256, 128><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 4);
+      k_phase_a_team<256, 128, kOne><<<mgrid, 256, team_smem<256, 128>(), s>>>(c, L, cnt, 4);
       if ((r = launched()) || (r = mark(5))) return r;
-      k_phase_a_team<256, 256><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 5);
+      k_phase_a_team<256, 256, kOne><<<mgrid, 256, team_smem<256, 256>(), s>>>(c, L, cnt, 5);
       if ((r = launched()) || (r = mark(6))) return r;
-      k_phase_a_team<kBigThreads, 512><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt, 6);
+      k_phase_a_team<kBigThreads, 512, kOne><<<sgrid, kBigThreads, team_smem<kBigThreads, 512>(), s>>>(c, L, cnt,
+                                                                                                      6);
       if ((r = launched()) || (r = mark(7))) return r;
-      k_phase_a_team<kBigThreads, kBigThreads><<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(
-          c, L, cnt, 7);
+      k_phase_a_team<kBigThreads, kBigThreads, kOne>
+          <<<sgrid, kBigThreads, team_smem<kBigThreads, kBigThreads>(), s>>>(c, L, cnt, 7);
       if ((r = launched()) || (r = mark(8))) return r;
     } else {
-      k_phase_a_block<kMedThreads><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 5, block_max, gws, h->ws_slice,
-                                                                          block_max);
+      k_phase_a_block<kMedThreads, kOne><<<mgrid, kMedThreads, med_smem_st, s>>>(c, L, cnt, 5, block_max, gws,
+                                                                                h->ws_slice, block_max);
       if ((r = launched())) return r;
       for (int k = 4; k <= 8; ++k)
         if ((r = mark(k))) return r;
     }
     // the largest trades: 1024 threads, up to smem_max entries in shared
     // memory (staged by a bulk copy), a global-memory slice above
-    k_phase_a_block<kBigThreads><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 8, h->smem_max, gws, h->ws_slice,
-                                                                        h->smem_max);
+    k_phase_a_block<kBigThreads, kOne><<<bgrid, kBigThreads, big_smem_st, s>>>(c, L, cnt, 8, h->smem_max, gws,
+                                                                              h->ws_slice, h->smem_max);
     if ((r = launched())) return r;
     return mark(9);
+  };
+  auto run_classes = [&]() -> int {
+    return c.seg_of ? run_classes_as(std::false_type{}) : run_classes_as(std::true_type{});
   };
   // the first pass over every trade, then retry_passes parallel passes over
   // the deferred ones: each runs every deferred trade whose dependencies
