@@ -169,7 +169,7 @@ MEASURED_TRAFFIC = {
     # profiles/rebuild_traffic_n2p25.md: mean of four super steps
     ("rebuild phase (k_far_pack, k_chunk_rows, k_fixup passes)", "n2^25"): {
         "bytes": 92497908608,
-        "trade_cu_sha256": "b26e86e52a3e925cb543617e951618e52e686e1993c7813d8156c38d44c58c1f",
+        "trade_cu_sha256": "048fcb563ef234b9ff0c1de074ee5f6ff6650e8c2293f61419123590ebc5da4b",
     },
 }
 

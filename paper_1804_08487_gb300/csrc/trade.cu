@@ -14,25 +14,32 @@
 // (its endpoints' positions at the start of the step), not to a node.  So a
 // super step runs in two phases:
 //
-//  A. Every trade finds D = (A_u u A_v) \ (A_u n A_v) \ {u, v}
-//     (Def. "Simple Undirected Trade"), keys its elements and publishes the
-//     threshold (key, lo, hi) of its |A_{u-v}|-th smallest element: u keeps
-//     exactly the elements at or below it (Fig. 2: u receives the first
-//     |A_{u-v}| elements of sigma(D)).  A trade whose dependency has not
-//     published yet is marked deferred; one more pass runs the deferred
-//     trades in index order (see k_phase_a_inorder).  Per entry it stores one
-//     byte: whether its own trade moves the edge, whether the far trade will
-//     consider the edge, and the top six bits of the far trade's key for it.
-//  B. Every trade writes its two rows for step g+1: each entry goes to u or v
-//     by its own trade's bit; its far end is resolved against the far trade's
-//     threshold (six-bit prefix first, the full key only on a prefix tie), and
-//     positions are mapped to step g+1.  One flat pass over all entries.
+//  A. Threshold and placement.  Every trade finds
+//     D = (A_u u A_v) \ (A_u n A_v) \ {u, v} (Def. "Simple Undirected Trade"),
+//     keys its elements and publishes the threshold (key, lo, hi) of its
+//     |A_{u-v}|-th smallest element: u keeps exactly the elements at or below
+//     it (Fig. 2: u receives the first |A_{u-v}| elements of sigma(D)).  In
+//     the same pass it places every entry in the row of its node after the
+//     trade (step g+1 layout): the far end's step-g position as a placeholder,
+//     and a 16-bit side word (bit 0 the own trade's flip, bits 1..11 the top
+//     11 bits of the far trade's key for the edge, bit 12 set when the far
+//     trade decides the edge).  The first pass runs every trade by size
+//     class; a trade whose dependency has not published is deferred and
+//     listed, retry passes run the lists, and one in-order pass completes
+//     what is left, waiting (bounded) for its dependencies.
+//  B. Rebuild (fix-up).  Every placeholder becomes the step-(g+1) position
+//     of the far end: per far trade one packed record (the new positions of
+//     its two nodes, the top 8 bits of its threshold), read in slices small
+//     enough to stay in L2; the 8-bit prefix decides, then the 11-bit one,
+//     and only on a tie there the full key.
 //
-// Phase A by trade size: trades of at most `tile_max` entries run on the tile
-// path (a CTA takes a run of consecutive small trades, about 1024 entries,
-// one thread per entry); trades up to `block_max` entries run one per
-// 256-thread CTA, larger ones one per 1024-thread CTA with up to `smem_max`
-// entries in shared memory (a global-memory slice above that).
+// Phase A by trade size L = deg u + deg v (nine classes): lane teams of 8 or
+// 16 threads (several trades per warp) and whole warps up to `tile_max`
+// entries, teams of 64 to 1024 threads with the entries in registers up to
+// min(4096, `smem_max`), and a 1024-thread CTA with the entries in shared
+// memory (a global-memory slice above `smem_max`) for the largest.  The team
+// and shared-memory kernels come in a version for handles of one graph,
+// whose seed's Philox round keys are kernel parameters, and a general one.
 #include <algorithm>
 #include <type_traits>
 
@@ -51,10 +58,8 @@ constexpr uint8_t kR = 1;       // entry sits in v's row
 constexpr uint8_t kInD = 2;     // element of D_t
 constexpr uint8_t kFlip = 4;    // trade t moves the edge to its other node
 constexpr uint8_t kUV = 8;      // the edge {u_t, v_t}
-// bits 4..7: initial block matrix: u~2s, u~2s+1, v~2s, v~2s+1
+// (kCol and kPend below: the neighbour's column, not hashed yet)
 
-// hash slot: high word = position + 1 (0 = empty); low word flags: bit0 in u's
-// row, bit1 in v's row, bit2 the u-row entry flips, bit3 the v-row entry flips
 constexpr int kMedThreads = 256;
 constexpr int kBigThreads = 1024;
 
