@@ -2,8 +2,10 @@
 // gets the key philox64(seed; x, 0, g, 0) and the nodes are ordered by
 // (key, x).  Sorting is MSD-bucketed: a histogram of the top B key bits, a
 // scatter of (key, x) into buckets, then one CTA sorts each bucket (about 512
-// entries, keys are uniform) in shared memory.  A bucket above the shared
-// memory cap is ranked by a slow global-memory fallback.
+// entries, keys are uniform) in shared memory by a counting sort on the 10
+// key bits below the highest bit where the bucket's keys differ (about one
+// key per bin; keys sharing a bin are ranked against each other).  A bucket
+// above the shared memory cap is ranked by a slow global-memory fallback.
 #include "cb_internal.cuh"
 #include "philox.cuh"
 #include "team.cuh"

@@ -2,7 +2,7 @@
 // a trade performs as many neighbourhood swaps as edge ends that change node
 // (twice the pairs of neighbours it exchanges), out of deg(u) + deg(v)
 // possible.  With the "swap_stats" option on, every global super step adds
-// its counts: the entries whose side byte marks a move to the other node of
+// its counts: the entries whose side word marks a move to the other node of
 // their trade (the untraded node of an odd n never moves), and the degrees
 // of the traded positions.  Uniform trades add theirs in the executor
 // (uniform.cu).

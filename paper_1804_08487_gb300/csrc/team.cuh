@@ -1,4 +1,6 @@
-// Cooperative "teams": a warp or a whole CTA working on one trade or one row.
+// Cooperative "teams" working on one trade or one row: part of a warp (8 or
+// 16 lanes, LaneTeam), a warp (WarpTeam), part of a CTA (64 to 512 threads
+// with a named barrier, SubTeam) or a whole CTA (BlockTeam).
 // The trade and row algorithms are written once against this interface; all
 // members of a team must reach every team call (team-uniform control flow).
 #pragma once
